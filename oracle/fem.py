@@ -1,0 +1,226 @@
+"""P1 FEM assembly and the SPDE prior precision, written as element loops.
+
+Test infrastructure (see the package docstring): float64, slow, explicit.
+
+Readings of the paper used here (each is listed in the design notes):
+
+* n nodes per axis include the boundary; h = (hi - lo) / (n - 1).  Time
+  levels include t = 0, dt = T / (nt - 1).
+* 2D meshes split every cell (i, j) along the diagonal (i, j) -> (i+1, j+1).
+* Mass lumping everywhere (Sec. 2.2): Ml_ii = row sum of the consistent mass.
+* Homogeneous Dirichlet boundary (App. B, N_k = 0): rows and columns of the
+  constrained matrices are zeroed and the diagonal set to 1; the boundary
+  DOF is given variance eps2 (App. B "M_kk = eps_k^2"), independent of tau.
+* Space-time noise is white in space and lumped, w ~ N(0, tau^2 dt Ml)
+  (App. A with Sigma = M^-1), so the whole prior scales as tau^-2.  The
+  initial block is a Matern alpha = 2 precision with kappa0, normalised to
+  unit marginal variance (tau0).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def axis_nodes(lo: float, hi: float, n: int) -> np.ndarray:
+    return np.linspace(lo, hi, n)
+
+
+# ---------------------------------------------------------------------------
+# 1D P1 elements (segments)
+
+
+def p1_1d(x: np.ndarray, c: float = 0.0):
+    """Stiffness S_ij = int phi_i' phi_j', lumped mass ml_i = int phi_i and
+    advection Badv_ij = int phi_i c phi_j' on the segment mesh x (element
+    loop; Sec. 2.2, FEM discretisation of the SPDE)."""
+    n = len(x)
+    rows, cols, vs, va = [], [], [], []
+    ml = np.zeros(n)
+    for e in range(n - 1):
+        loc = (e, e + 1)
+        h = x[e + 1] - x[e]
+        grad = (-1.0 / h, 1.0 / h)          # derivatives of the two hats
+        for a in range(2):
+            ml[loc[a]] += 0.5 * h           # int phi_a over the segment
+            for b in range(2):
+                rows.append(loc[a])
+                cols.append(loc[b])
+                vs.append(h * grad[a] * grad[b])
+                va.append(0.5 * h * c * grad[b])   # int phi_a = h/2, phi_b' const
+    S = sp.csr_matrix((vs, (rows, cols)), shape=(n, n))
+    Badv = sp.csr_matrix((va, (rows, cols)), shape=(n, n))
+    return S, ml, Badv
+
+
+# ---------------------------------------------------------------------------
+# 2D P1 elements (triangles of a structured grid)
+
+
+def triangles(nx: int, ny: int):
+    """Vertex index triples; node (i, j) has index j * nx + i.  Each cell is
+    split along (i,j)->(i+1,j+1): lower (i,j),(i+1,j),(i+1,j+1) and upper
+    (i,j),(i+1,j+1),(i,j+1)."""
+    tris = []
+    for j in range(ny - 1):
+        for i in range(nx - 1):
+            a, b = j * nx + i, j * nx + i + 1
+            c, d = (j + 1) * nx + i + 1, (j + 1) * nx + i
+            tris.append((a, b, c))
+            tris.append((a, c, d))
+    return np.array(tris, dtype=np.int64)
+
+
+def p1_2d(xs: np.ndarray, ys: np.ndarray, vx: float = 0.0, vy: float = 0.0):
+    """Stiffness S_ab = int grad phi_a . grad phi_b, lumped mass ml_a =
+    int phi_a and advection Badv_ab = int phi_a (v . grad phi_b), assembled
+    triangle by triangle from barycentric gradients."""
+    nx, ny = len(xs), len(ys)
+    X = np.tile(xs, ny)
+    Y = np.repeat(ys, nx)
+    tris = triangles(nx, ny)
+    P = np.stack([X[tris], Y[tris]], axis=-1)          # [T, 3, 2]
+    x1, x2, x3 = P[:, 0, 0], P[:, 1, 0], P[:, 2, 0]
+    y1, y2, y3 = P[:, 0, 1], P[:, 1, 1], P[:, 2, 1]
+    det = (x2 - x1) * (y3 - y1) - (x3 - x1) * (y2 - y1)  # 2 * signed area
+    area = 0.5 * np.abs(det)
+    # gradient of barycentric coordinate lambda_a: (y_b - y_c, x_c - x_b) / det
+    gx = np.stack([y2 - y3, y3 - y1, y1 - y2], axis=1) / det[:, None]
+    gy = np.stack([x3 - x2, x1 - x3, x2 - x1], axis=1) / det[:, None]
+    rows, cols, vs, va = [], [], [], []
+    ml = np.zeros(nx * ny)
+    for a in range(3):
+        np.add.at(ml, tris[:, a], area / 3.0)
+        for b in range(3):
+            rows.append(tris[:, a])
+            cols.append(tris[:, b])
+            vs.append(area * (gx[:, a] * gx[:, b] + gy[:, a] * gy[:, b]))
+            va.append(area / 3.0 * (vx * gx[:, b] + vy * gy[:, b]))
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    N = nx * ny
+    S = sp.csr_matrix((np.concatenate(vs), (rows, cols)), shape=(N, N))
+    Badv = sp.csr_matrix((np.concatenate(va), (rows, cols)), shape=(N, N))
+    return S, ml, Badv
+
+
+# ---------------------------------------------------------------------------
+# Dirichlet constraint (App. B)
+
+
+def spatial_boundary(prior: dict) -> np.ndarray:
+    """Boolean mask over the spatial nodes of the Dirichlet boundary."""
+    nx, ny, _ = prior["n"]
+    i = np.tile(np.arange(nx), ny)
+    j = np.repeat(np.arange(ny), nx)
+    bnd = (i == 0) | (i == nx - 1)
+    if ny > 1:
+        bnd |= (j == 0) | (j == ny - 1)
+    return bnd
+
+
+def boundary_mask(prior: dict) -> np.ndarray:
+    """Dirichlet mask over all unknowns (the spatial boundary at every time
+    level)."""
+    _, _, nt = prior["n"]
+    return np.tile(spatial_boundary(prior), nt)
+
+
+def constrain(X: sp.spmatrix, bnd: np.ndarray) -> sp.csr_matrix:
+    """App. B with N_k = 0: zero column k, zero row k, set X_kk = 1."""
+    keep = sp.diags((~bnd).astype(float))
+    X = keep @ X @ keep
+    return (X + sp.diags(bnd.astype(float))).tocsr()
+
+
+# ---------------------------------------------------------------------------
+# spatial operators of each prior kind
+
+
+def spatial_mesh(prior: dict):
+    """Returns (S, ml, Badv, dim) on the spatial mesh of the prior, where
+    Badv already carries the velocity (cx, cy)."""
+    nx, ny, _ = prior["n"]
+    lo, hi = prior["lo"], prior["hi"]
+    xs = axis_nodes(lo[0], hi[0], nx)
+    if ny == 1:
+        S, ml, Badv = p1_1d(xs, prior["cx"])
+        return S, ml, Badv, 1
+    ys = axis_nodes(lo[1], hi[1], ny)
+    S, ml, Badv = p1_2d(xs, ys, prior["cx"], prior["cy"])
+    return S, ml, Badv, 2
+
+
+def matern_tau_unit(kappa: float, dim: int) -> float:
+    """tau giving unit marginal variance for the alpha = 2 Matern field,
+    sigma^2 = Gamma(nu)/(Gamma(nu + d/2) (4 pi)^(d/2) kappa^(2 nu) tau^2) with
+    nu = 2 - d/2 (Lindgren et al. 2011, the SPDE prior of Sec. 2.2):
+    1D: 1/(4 kappa^3 tau^2), 2D: 1/(4 pi kappa^2 tau^2)."""
+    if dim == 1:
+        return 1.0 / math.sqrt(4.0 * kappa ** 3)
+    return 1.0 / math.sqrt(4.0 * math.pi * kappa ** 2)
+
+
+def prior_root(prior: dict) -> sp.csr_matrix:
+    """Square sparse root B with Q = B^T B.
+
+    Spatial priors (Sec. 2.2): B = tau Ml^-1/2 Kc, Kc the constrained
+    K = kappa^2 Ml + nu S + Badv; boundary rows are e_k / eps.
+
+    Space-time (Sec. 2.4, App. A), block rows in time:
+      t = 0:  (tau0 / tau) Ml^-1/2 K0c, K0 = kappa0^2 Ml + S
+      t >= 1: (tau sqrt(dt))^-1 Ml^-1/2 (Gc u^k - Mlc u^(k-1)),
+              G = Ml + dt (nu S + Badv)
+    where Mlc is Ml with boundary rows removed; boundary rows e_k / eps.
+    """
+    kind = prior["kind"]
+    S, ml, Badv, dim = spatial_mesh(prior)
+    Ns = len(ml)
+    sbnd = spatial_boundary(prior)
+    inv_eps = 1.0 / math.sqrt(prior["eps2"])
+    if kind in ("matern2d", "steady_advdiff2d"):
+        K = prior["kappa"] ** 2 * sp.diags(ml) + prior["nu"] * S + Badv
+        Kc = constrain(K, sbnd)
+        d = np.where(sbnd, inv_eps, prior["tau"] / np.sqrt(ml))
+        return (sp.diags(d) @ Kc).tocsr()
+    assert kind in ("advdiff_st1d", "advdiff_st2d")
+    nt = prior["n"][2]
+    dt = (prior["hi"][2] - prior["lo"][2]) / (nt - 1)
+    tau = prior["tau"]
+    tau0 = matern_tau_unit(prior["kappa0"], dim)
+    K0c = constrain(prior["kappa0"] ** 2 * sp.diags(ml) + S, sbnd)
+    Gc = constrain(sp.diags(ml) + dt * (prior["nu"] * S + Badv), sbnd)
+    Mlc = sp.diags(np.where(sbnd, 0.0, ml))
+    d0 = np.where(sbnd, inv_eps, (tau0 / tau) / np.sqrt(ml))
+    dk = np.where(sbnd, inv_eps, 1.0 / (tau * math.sqrt(dt) * np.sqrt(ml)))
+    blocks = [[None] * nt for _ in range(nt)]
+    blocks[0][0] = sp.diags(d0) @ K0c
+    for k in range(1, nt):
+        blocks[k][k] = sp.diags(dk) @ Gc
+        blocks[k][k - 1] = -(sp.diags(dk) @ Mlc)
+    for k in range(nt):
+        for l in range(nt):
+            if blocks[k][l] is None and abs(k - l) > 1:
+                continue
+            if blocks[k][l] is None:
+                blocks[k][l] = sp.csr_matrix((Ns, Ns))
+    B = sp.bmat(blocks, format="csr")
+    return B
+
+
+def prior_precision(prior: dict) -> sp.csr_matrix:
+    """Q = B^T B (Sec. 2.2 eq. sparse-prec-matrix; App. A eq.
+    block-tridiag-prec)."""
+    B = prior_root(prior)
+    return (B.T @ B).tocsr()
+
+
+def grid_spacing(prior: dict):
+    nx, ny, nt = prior["n"]
+    lo, hi = prior["lo"], prior["hi"]
+    hx = (hi[0] - lo[0]) / (nx - 1)
+    hy = (hi[1] - lo[1]) / (ny - 1) if ny > 1 else 0.0
+    dt = (hi[2] - lo[2]) / (nt - 1) if nt > 1 else 0.0
+    return hx, hy, dt
