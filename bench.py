@@ -1,0 +1,269 @@
+"""Throughput benchmark of the GMRF posterior hot path on GB300.
+
+One step = one pass of the whole hot path over the 2D Matern workload
+(512 x 512 P1 grid, 262 144 unknowns, 10 000 point observations): build the
+data and 64 perturbation-sample right-hand sides, solve the 65 posterior
+systems by multigrid-preconditioned CG (FP32) inside FP64 refinement to a
+relative residual of 1e-8, and form the Rao-Blackwellised marginal variances.
+Metric: RHS x unknowns solved per second (whole job, all GPUs).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one process per GPU: each rank solves its own
+replica (the workload is one posterior; it has no data-parallel split), so
+per-GPU work is fixed ("weak").  --impl reference times the FP64 CPU oracle
+on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NS = 64                     # perturbation samples per step (plus the mean)
+N_SIDE, M_OBS = 512, 10000
+CPU_SAMPLES = 4             # oracle sample: condition + Cholesky + mean + 4 samples + variances
+
+
+def workload():
+    from paper_2503_08343_gb300 import workloads as W
+    pr, ob = W.c2_matern(n=N_SIDE, m=M_OBS)
+    return pr, ob, W.DRAW_SEED["c2"]
+
+
+CONFIG = {"workload": "matern2d_512x512_m10000_mean+64samples+rbmc_variance", "grid": [N_SIDE, N_SIDE],
+          "unknowns": N_SIDE * N_SIDE, "observations": M_OBS, "rhs_per_step": NS + 1, "rtol": 1e-8,
+          "l2": "inputs larger than L2 (~1.3 GB working set per step vs 129 MB L2)"}
+METRIC = "posterior solves/s (RHS*unknowns/s)"
+UNIT = "RHS*unknowns/s"
+
+
+def oracle_step(pr, ob, seed, ns):
+    """The oracle as it stands: assemble, banded Cholesky, mean, ns samples,
+    Rao-Blackwellised variances."""
+    from oracle import infer, linalg
+    post = infer.condition(pr, ob)
+    L = linalg.cholesky(post.Qpost)
+    infer.posterior_mean(post, L)
+    xs = infer.perturbation_samples(post, seed, range(ns), L)
+    infer.rbmc_variance(post.Qpost, xs)
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [v.strip() for v in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    pr, ob, seed = workload()
+    n = pr["n"][0] * pr["n"][1]
+    for _ in range(args.warmup):
+        oracle_step(pr, ob, seed, CPU_SAMPLES)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(pr, ob, seed, CPU_SAMPLES)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = (CPU_SAMPLES + 1) * n / dt
+    sample = (f"full 512x512 posterior per step: assembly, banded Cholesky, mean + {CPU_SAMPLES} "
+              f"perturbation samples, Rao-Blackwellised variances (FP64, numpy/scipy)")
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG, "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2503_08343_gb300 import gmrf
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    lib = gmrf.load()
+    pr, ob, seed = workload()
+    stream = torch.cuda.Stream()
+    prior = gmrf.Prior(pr, stream=stream)
+    post = gmrf.Posterior(prior, ob)
+    N = prior.N
+    mean = torch.empty(N, dtype=torch.float64, device="cuda")
+    var = torch.empty(N, dtype=torch.float64, device="cuda")
+    se = torch.empty(N, dtype=torch.float64, device="cuda")
+    opts = gmrf.default_opts()
+    C = __import__("ctypes")
+    info = gmrf.SolveInfo()
+
+    def step():
+        gmrf._check(lib.gmrf_marginal_var(post.h, NS, seed, gmrf._ptr(mean), gmrf._ptr(var), gmrf._ptr(se),
+                                          C.byref(opts), C.byref(info)))
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    l0 = lib.gmrf_launch_count()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    l1 = lib.gmrf_launch_count()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    units = (NS + 1) * N
+    value = world * units / (ms * 1e-3)
+    iters, refs = info.inner_iterations, info.refinements
+
+    # end to end through the C ABI with host buffers: data in, mean and variances out
+    y_host = torch.tensor(np.asarray(ob["y"]), dtype=torch.float64).pin_memory()
+    mean_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    var_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    ke2e = max(3, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke2e):
+        post.update_data(y_host)
+        gmrf._check(lib.gmrf_marginal_var(post.h, NS, seed, gmrf._ptr(mean_h), gmrf._ptr(var_h), None,
+                                          C.byref(opts), C.byref(info)))
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke2e
+    t = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * units / float(t.item())
+
+    # roofline of the dominant kernel: the fused FP32 posterior-precision
+    # stencil, timed with CUDA events on its stream over 50 launches
+    ms_k = post.time_apply(NS + 1, iters=50)
+    bytes_k = 8.0 * units                     # read p + write q, FP32, per RHS x unknown
+    achieved = bytes_k / (ms_k * 1e-3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 inner / f64 refinement", "data": "synthetic",
+        "config": dict(CONFIG, parallelism=f"replicas{world}", pcg_iterations=iters, fp64_residuals=refs),
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(ob["y"]),
+                "d2h_bytes_per_step": 16 * N},
+        "gpu_launches": int(l1 - l0),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_stencil<GEO_XY,float,M_APPLY> (fused Q_u|y apply)",
+                     "peak_kind": f"{peak_kind} burst copy bandwidth", "kernel_ms": ms_k,
+                     "algorithmic_bytes": bytes_k},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        oracle_step(pr, ob, seed, CPU_SAMPLES)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {
+            "value": (CPU_SAMPLES + 1) * N / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"one full 512x512 posterior: assembly, banded Cholesky, mean + {CPU_SAMPLES} samples, "
+                      f"RBMC variances ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * gmrf.h -- C ABI of the GB300 GMRF probabilistic PDE solver.
+ *
+ * Conditions an SPDE-discretised Gaussian Markov random field prior
+ * u ~ N(0, Q^-1) (P1 FEM in space, implicit Euler in time, lumped mass) on
+ * noisy point data and on linear or linearised PDE collocation, then
+ * computes posterior means, perturbation samples, marginal variances,
+ * Gauss-Newton steps and log-likelihood gradients.  The posterior precision
+ * Q_u|y = Q + A^T Q_eps A (Sec. 3.1, eq. posterior-mean) is applied
+ * matrix-free by fused stencil kernels and solved by multi-RHS conjugate
+ * gradients preconditioned by a geometric multigrid V-cycle, with FP32 inner
+ * iterations inside FP64 iterative refinement.
+ *
+ * Conventions for every entry point:
+ *  - Nothing aborts or prints.  A non-zero gmrf_status is returned and
+ *    gmrf_last_error() (thread-local) describes it.
+ *  - Work is ordered on the stream given to gmrf_build_prior; every call
+ *    returns after that stream has finished the call's work (scalars and
+ *    host outputs are valid on return).
+ *  - Array outputs are caller-owned.  A pointer may be host memory or device
+ *    memory (detected with cudaPointerGetAttributes); host buffers are
+ *    copied inside the call.  Device pointers must be on the handle's device.
+ *  - Vectors over the unknowns are ordered lexicographically,
+ *    index ((t * ny + y) * nx + x), FP64.  Batches of vectors are
+ *    [count][N], row-major.
+ *  - Handles own all device scratch.  Scratch for a batch of k right-hand
+ *    sides is allocated at the first call that needs k and reused after.
+ */
+#ifndef GMRF_H
+#define GMRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gmrf_status {
+    GMRF_OK = 0,
+    GMRF_E_INVALID = 1,        /* bad argument or descriptor */
+    GMRF_E_NOT_SPD = 2,        /* CG breakdown: p^T Q p <= 0 or non-finite */
+    GMRF_E_NO_CONVERGENCE = 3, /* iteration caps reached; info holds the residual */
+    GMRF_E_CUDA = 4,           /* a CUDA runtime call failed */
+    GMRF_E_OOM = 5,            /* device allocation failed */
+    GMRF_E_TIMEOUT = 6         /* wall-clock limit of gmrf_solve_opts reached */
+} gmrf_status;
+
+/* Prior families (Sec. 2.2, 2.3, 2.4 and App. A):
+ *  GMRF_MATERN2_2D        (kappa^2 - Lap) u = W / tau on [lo, hi]^2, alpha = 2:
+ *                         Q = tau^2 K Ml^-1 K, K = kappa^2 Ml + S.
+ *  GMRF_STEADY_ADVDIFF_2D Q = tau^2 K^T Ml^-1 K, K = kappa^2 Ml + nu S + cx Bx + cy By.
+ *  GMRF_ADVDIFF_ST_1D     u_t + c u_x - nu u_xx = tau W on [x0,x1] x [0,T]
+ *  GMRF_ADVDIFF_ST_2D     u_t + c . grad u - nu Lap u = tau W on [lo,hi]^2 x [0,T]:
+ *                         implicit Euler (App. A): G u^k = Ml u^(k-1) + w,
+ *                         G = Ml + dt (nu S + B_c), w ~ N(0, tau^2 dt Ml); the
+ *                         initial level is a unit-variance Matern (kappa0).
+ * Every prior is applied in the stacked form Q = B^T B with B a short stencil.
+ * Boundary nodes carry a homogeneous Dirichlet condition (App. B, N_k = 0):
+ * decoupled, variance eps2. */
+typedef enum gmrf_prior_kind {
+    GMRF_MATERN2_2D = 0,
+    GMRF_ADVDIFF_ST_1D = 1,
+    GMRF_ADVDIFF_ST_2D = 2,
+    GMRF_STEADY_ADVDIFF_2D = 3
+} gmrf_prior_kind;
+
+typedef struct gmrf_prior_desc {
+    int32_t kind;              /* gmrf_prior_kind */
+    int32_t nx, ny, nt;        /* nodes per axis incl. boundary; ny = 1 in 1D space, nt = 1 if spatial */
+    double lo[3], hi[3];       /* domain corners (x, y, t) */
+    double kappa;              /* Matern / steady: inverse range; space-time: unused */
+    double tau;                /* scale: Matern/steady Q ~ tau^2, space-time Q ~ tau^-2 */
+    double nu;                 /* diffusion (Matern: 1) */
+    double cx, cy;             /* advection velocity */
+    double kappa0;             /* space-time: Matern kappa of the initial level */
+    double eps2;               /* Dirichlet boundary variance (App. B "M_kk = eps^2") */
+} gmrf_prior_desc;
+
+/* Observations (Sec. 3.1).  All pointers are host memory, read during the call.
+ *  point data: y_k = phi(x_k) . u + e_k, e_k ~ N(0, sigma_k^2), with P1
+ *    barycentric weights in space times linear weights in time; coords are
+ *    [m][d], d = 2 (x, y) for spatial priors, 2 (x, t) for 1D space-time,
+ *    3 (x, y, t) for 2D space-time.
+ *  ic: the initial condition as data at every t = 0 node, values ic_values
+ *    [nx * ny] (NULL: -sin(pi x)), noise ic_sigma.
+ *  colloc: 1 = linear advection-diffusion residual with speed colloc_c and
+ *    right-hand side colloc_f (NULL: 0) at interior nodes of levels k >= 1;
+ *    2 = Burgers residual (Sec. 3.3), linearised at the point given to
+ *    gmrf_gauss_newton_step.  Diffusion colloc_nu, noise colloc_sigma.
+ *    Defined for GMRF_ADVDIFF_ST_1D only. */
+typedef struct gmrf_obs_desc {
+    int64_t m;
+    const double* coords;
+    const double* y;
+    const double* sigma;       /* [m], or NULL to use sigma_all */
+    double sigma_all;
+    int32_t ic;
+    double ic_sigma;
+    const double* ic_values;
+    int32_t colloc;
+    double colloc_sigma;
+    double colloc_c;
+    double colloc_nu;
+    const double* colloc_f;
+} gmrf_obs_desc;
+
+typedef struct gmrf_solve_opts {
+    double rtol;               /* per-RHS ||b - Q_u|y x|| / ||b|| target, FP64 (default 1e-8) */
+    int32_t max_refine;        /* FP64 refinement steps (default 12) */
+    int32_t max_inner;         /* inner PCG iterations per refinement step (default 40) */
+    double inner_rtol;         /* inner relative residual reduction (default 1e-3) */
+    int32_t precision;         /* 0: FP32 inner + FP64 refinement; 1: plain FP64 PCG */
+    int32_t batched;           /* 1: all right-hand sides in one batch; 0: one at a time */
+    double timeout_s;          /* wall-clock limit, 0 = none */
+} gmrf_solve_opts;
+
+typedef struct gmrf_solve_info {
+    int32_t nrhs;
+    int32_t refinements;       /* FP64 residual evaluations */
+    int32_t inner_iterations;  /* total PCG iterations (batched: per batch) */
+    int32_t converged;         /* 1 if every RHS reached rtol */
+    double max_rel_residual;   /* max over RHS of the final FP64 relative residual */
+    double seconds;
+} gmrf_solve_info;
+
+typedef struct gmrf_prior gmrf_prior;          /* opaque, library-owned */
+typedef struct gmrf_posterior gmrf_posterior;  /* opaque, library-owned */
+
+/* Fill opts with the defaults listed above. */
+void gmrf_default_opts(gmrf_solve_opts* opts);
+
+/* Builds the stencil description of Q = B^T B on every multigrid level
+ * (Sec. 2.2 eq. sparse-prec-matrix; App. A eq. block-tridiag-prec; App. B).
+ * stream: a cudaStream_t other than the legacy default stream, used for all
+ * work of this prior and its posteriors; NULL: the handle creates and owns a
+ * non-blocking stream.  *out receives the handle. */
+gmrf_status gmrf_build_prior(const gmrf_prior_desc* desc, void* stream, gmrf_prior** out);
+
+/* Conditions the prior on observations: builds the observation lists on every
+ * level and the right-hand side A^T Q_eps y (Sec. 3.1).  The prior must
+ * outlive the posterior. */
+gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_posterior** out);
+
+/* Replaces the point-data values y (length m of the descriptor; host or
+ * device memory) without rebuilding the observation operator. */
+gmrf_status gmrf_update_data(gmrf_posterior* post, const double* y);
+
+/* Posterior mean mu = Q_u|y^-1 A^T Q_eps y (eq. posterior-mean, prior mean 0).
+ * mu: [N]. */
+gmrf_status gmrf_solve_mean(gmrf_posterior* post, double* mu, const gmrf_solve_opts* opts,
+                            gmrf_solve_info* info);
+
+/* Perturbation samples x_s = Q_u|y^-1 L z_s ~ N(0, Q_u|y^-1) (Sec. 3.2) with
+ * the left root L = [B^T, A^T Q_eps^1/2] and z_s from Philox4x32-10 keyed by
+ * seed (sample s uses counter words (j, s, stream, 0)).  x: [ns][N]
+ * zero-mean perturbations.  mean: [N] or NULL; when given, the posterior mean
+ * is solved in the same batch. */
+gmrf_status gmrf_sample(gmrf_posterior* post, int32_t ns, uint64_t seed, double* mean, double* x,
+                        const gmrf_solve_opts* opts, gmrf_solve_info* info);
+
+/* Rao-Blackwellised Monte Carlo marginal variances (Sec. 3.2; Siden et al.
+ * 2018) from ns perturbation samples:
+ * var_i = 1/Q_ii + (1/ns) sum_s (sum_{j != i} Q_ij x_s,j / Q_ii)^2.
+ * var: [N]; stderr_: [N] or NULL (standard error of the Monte Carlo term);
+ * mean: [N] or NULL (posterior mean solved in the same batch). */
+gmrf_status gmrf_marginal_var(gmrf_posterior* post, int32_t ns, uint64_t seed, double* mean,
+                              double* var, double* stderr_, const gmrf_solve_opts* opts,
+                              gmrf_solve_info* info);
+
+/* One Gauss-Newton step on -log pi(u) (Sec. 3.3, eq. nonlinear-mode) for
+ * Burgers collocation: H = Q + J^T Q_eps J + A^T R^-1 A at mu_k, solve
+ * H d = -grad, warm-started from delta_prev, then Armijo backtracking
+ * (halving from 1, c1 = 1e-4, at most 20 halvings).  mu_k [N] (in/out, host
+ * or device), delta_prev [N] (in/out, may be all zero).  newton_decrement
+ * (host) receives d^T H d, alpha (host, may be NULL) the step length. */
+gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* delta_prev,
+                                   double* newton_decrement, double* alpha,
+                                   const gmrf_solve_opts* opts, gmrf_solve_info* info);
+
+/* Gradient of the log marginal likelihood of the point data with respect to
+ * (log kappa, log tau, log sigma, cx, nu), by one batched solve of the
+ * posterior system for the mean and nprobes Rademacher probes plus the same
+ * probes against the prior (Hutchinson trace estimates).  loglik (host, may
+ * be NULL) receives the data-fit part 1/2 b^T mu - 1/2 y^T R^-1 y (the
+ * log-determinants are not estimated).  grad[5], grad_stderr[5]: host. */
+gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t seed, double* loglik,
+                             double* grad, double* grad_stderr, const gmrf_solve_opts* opts,
+                             gmrf_solve_info* info);
+
+/* y = Q_u|y x in FP64 for a batch of k vectors x, y: [k][N].  Test hook for
+ * the fused stencil. */
+gmrf_status gmrf_apply_posterior(gmrf_posterior* post, int32_t k, const double* x, double* y);
+
+/* Normal draws of the sample stream: out[s][i] = z(seed, stream, sample0 + s, i)
+ * for s < count, i < n.  Test hook for the in-kernel generator. */
+gmrf_status gmrf_normals(uint64_t seed, int32_t stream, int32_t sample0, int32_t count, int64_t n,
+                         double* out);
+
+/* Average duration in milliseconds of the fused FP32 Q_u|y apply over `iters`
+ * launches on the handle's stream, for a batch of k right-hand sides
+ * (CUDA events around the launches). */
+gmrf_status gmrf_time_apply(gmrf_posterior* post, int32_t k, int32_t iters, double* ms);
+
+/* Number of kernels this library has launched in the process so far
+ * (kernels inside replayed CUDA graphs included). */
+uint64_t gmrf_launch_count(void);
+
+int64_t gmrf_num_unknowns(const gmrf_prior* prior);
+int32_t gmrf_num_levels(const gmrf_prior* prior);
+void gmrf_prior_destroy(gmrf_prior* prior);
+void gmrf_posterior_destroy(gmrf_posterior* post);
+const char* gmrf_status_string(gmrf_status s);
+const char* gmrf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMRF_H */

@@ -1,0 +1,511 @@
+// C ABI of the GMRF solver (declared in include/gmrf.h).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "host.h"
+
+using namespace gmrf;
+
+struct gmrf_prior {
+    Prior impl;
+    cudaStream_t user = 0;   // unused: work runs on impl.stream
+    bool own = false;        // impl.stream created by the library
+};
+
+struct gmrf_posterior {
+    Posterior impl;
+    gmrf_prior* prior = nullptr;
+};
+
+static thread_local std::string g_err;
+
+template <typename F> static gmrf_status guard(F&& f) {
+    try {
+        f();
+        return GMRF_OK;
+    } catch (const Error& e) {
+        g_err = e.what();
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        g_err = "host allocation failed";
+        return GMRF_E_OOM;
+    } catch (const std::exception& e) {
+        g_err = e.what();
+        return GMRF_E_INVALID;
+    }
+}
+
+static void require(bool ok, const std::string& msg) {
+    if (!ok) throw Error(GMRF_E_INVALID, msg);
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void copy_out(double* dst, const double* dev_src, size_t n, cudaStream_t s) {
+    GCK(cudaMemcpyAsync(dst, dev_src, n * sizeof(double),
+                        is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+static void copy_in(double* dev_dst, const double* src, size_t n, cudaStream_t s) {
+    GCK(cudaMemcpyAsync(dev_dst, src, n * sizeof(double),
+                        is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+static void enter(gmrf_prior* pr) {
+    if (pr->user) GCK(cudaStreamSynchronize(pr->user));
+}
+
+static gmrf_solve_opts resolve_opts(const gmrf_solve_opts* o) {
+    gmrf_solve_opts d;
+    gmrf_default_opts(&d);
+    if (!o) return d;
+    gmrf_solve_opts r = *o;
+    if (!(r.rtol > 0)) r.rtol = d.rtol;
+    if (r.max_refine <= 0) r.max_refine = d.max_refine;
+    if (r.max_inner <= 0) r.max_inner = d.max_inner;
+    if (!(r.inner_rtol > 0)) r.inner_rtol = d.inner_rtol;
+    return r;
+}
+
+static gmrf_status finish(const SolveStats& st, gmrf_solve_info* info, int nrhs, double seconds) {
+    if (info) {
+        info->nrhs = nrhs;
+        info->refinements = st.refinements;
+        info->inner_iterations = st.inner;
+        info->converged = st.converged ? 1 : 0;
+        info->max_rel_residual = st.max_rel;
+        info->seconds = seconds;
+    }
+    if (st.converged) return GMRF_OK;
+    if (st.breakdown) {
+        g_err = "conjugate gradients broke down (p^T Q p <= 0) before reaching rtol";
+        return GMRF_E_NOT_SPD;
+    }
+    g_err = "iteration caps reached before rtol; max relative residual " + std::to_string(st.max_rel);
+    return GMRF_E_NO_CONVERGENCE;
+}
+
+extern "C" {
+
+void gmrf_default_opts(gmrf_solve_opts* o) {
+    if (!o) return;
+    o->rtol = 1e-8;
+    o->max_refine = 12;
+    o->max_inner = 40;
+    o->inner_rtol = 1e-3;
+    o->precision = 0;
+    o->batched = 1;
+    o->timeout_s = 0.0;
+}
+
+const char* gmrf_status_string(gmrf_status s) {
+    switch (s) {
+        case GMRF_OK: return "ok";
+        case GMRF_E_INVALID: return "invalid argument";
+        case GMRF_E_NOT_SPD: return "operator not positive definite";
+        case GMRF_E_NO_CONVERGENCE: return "no convergence";
+        case GMRF_E_CUDA: return "CUDA error";
+        case GMRF_E_OOM: return "out of device memory";
+        case GMRF_E_TIMEOUT: return "timeout";
+    }
+    return "unknown status";
+}
+
+const char* gmrf_last_error(void) { return g_err.c_str(); }
+
+gmrf_status gmrf_build_prior(const gmrf_prior_desc* desc, void* stream, gmrf_prior** out) {
+    return guard([&] {
+        require(desc && out, "null argument");
+        const gmrf_prior_desc& d = *desc;
+        require(d.kind >= 0 && d.kind <= 3, "unknown prior kind");
+        const bool st = d.kind == GMRF_ADVDIFF_ST_1D || d.kind == GMRF_ADVDIFF_ST_2D;
+        require(d.nx >= 3, "nx must be >= 3");
+        if (d.kind == GMRF_ADVDIFF_ST_1D) require(d.ny == 1, "1D space-time needs ny = 1");
+        else require(d.ny >= 3, "2D priors need ny >= 3");
+        if (st) require(d.nt >= 2, "space-time priors need nt >= 2");
+        else require(d.nt == 1, "spatial priors need nt = 1");
+        require(d.eps2 > 0 && d.tau > 0, "eps2 and tau must be positive");
+        require(d.hi[0] > d.lo[0] && (d.ny == 1 || d.hi[1] > d.lo[1]) && (d.nt == 1 || d.hi[2] > d.lo[2]), "empty domain");
+        if (st) require(d.kappa0 > 0 && d.nu >= 0, "space-time priors need kappa0 > 0, nu >= 0");
+        else require(d.kappa > 0, "kappa must be positive");
+        require((long long)d.nx * d.ny * d.nt < (1LL << 31), "grid too large for 32-bit node indices");
+        gmrf_prior* p = new gmrf_prior();
+        p->impl.desc = d;
+        p->impl.geo = geometry_of(d);
+        // a caller stream is used as is; otherwise the handle owns a
+        // non-blocking stream (graph capture needs a stream other than 0)
+        p->user = nullptr;
+        p->own = stream == nullptr;
+        if (stream) {
+            p->impl.stream = (cudaStream_t)stream;
+        } else {
+            cudaError_t e = cudaStreamCreateWithFlags(&p->impl.stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                delete p;
+                cuda_check(e, "cudaStreamCreateWithFlags");
+            }
+        }
+        build_hierarchy(d, p->impl.levels);
+        *out = p;
+    });
+}
+
+int64_t gmrf_num_unknowns(const gmrf_prior* p) { return p ? (int64_t)p->impl.levels[0].N : 0; }
+int32_t gmrf_num_levels(const gmrf_prior* p) { return p ? (int32_t)p->impl.levels.size() : 0; }
+
+void gmrf_prior_destroy(gmrf_prior* p) {
+    if (!p) return;
+    if (p->own && p->impl.stream) cudaStreamDestroy(p->impl.stream);
+    delete p;
+}
+
+static void rebuild_bdata(Posterior& P, cudaStream_t s) {
+    const Level& L = P.levels[0];
+    GCK(cudaMemcpyAsync(P.d_bdata, P.d_bstatic, sizeof(double) * L.N, cudaMemcpyDeviceToDevice, s));
+    launch_obs_scatter(L.d_obs, (int)P.m, P.d_ypoint, P.d_bdata, s);
+}
+
+gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_posterior** out) {
+    gmrf_posterior* post = nullptr;
+    const gmrf_status st = guard([&] {
+        require(prior && obs && out, "null argument");
+        enter(prior);
+        const gmrf_prior_desc& d = prior->impl.desc;
+        const cudaStream_t s = prior->impl.stream;
+        require(obs->m >= 0, "negative observation count");
+        require(obs->m == 0 || (obs->coords && obs->y), "coords and y are required");
+        require(obs->m < (1LL << 30), "too many observations");
+        post = new gmrf_posterior();
+        post->prior = prior;
+        Posterior& P = post->impl;
+        P.prior = &prior->impl;
+        P.levels = prior->impl.levels;
+        for (Level& L : P.levels) {   // device members are per posterior
+            L.d_obs = nullptr; L.d_tile_ptr = nullptr; L.d_tile_idx = nullptr;
+        }
+        const int dimc = d.kind == GMRF_ADVDIFF_ST_2D ? 3 : 2;
+        P.m = obs->m;
+        std::vector<double> coords((size_t)P.m * dimc);
+        if (P.m) std::memcpy(coords.data(), obs->coords, coords.size() * sizeof(double));
+        for (int64_t k = 0; k < P.m; ++k)
+            for (int a = 0; a < dimc; ++a) require(std::isfinite(coords[(size_t)k * dimc + a]), "non-finite coordinate");
+        P.y_point.assign(obs->y, obs->y + P.m);
+        std::vector<double> rinv;
+        for (int64_t k = 0; k < P.m; ++k) {
+            const double sg = obs->sigma ? obs->sigma[k] : obs->sigma_all;
+            require(sg > 0 && std::isfinite(sg), "observation sigma must be positive");
+            require(std::isfinite(P.y_point[(size_t)k]), "non-finite observation value");
+            rinv.push_back(1.0 / (sg * sg));
+        }
+        const Level& F = P.levels[0];
+        std::vector<double> bstatic((size_t)F.N, 0.0);
+        P.nic = 0;
+        if (obs->ic) {
+            require(d.kind == GMRF_ADVDIFF_ST_1D || d.kind == GMRF_ADVDIFF_ST_2D, "initial-condition rows need a space-time prior");
+            require(obs->ic_sigma > 0, "ic_sigma must be positive");
+            P.nic = (int64_t)d.nx * d.ny;
+            P.ic_values.resize((size_t)P.nic);
+            for (int64_t k = 0; k < P.nic; ++k) {
+                const double x = d.lo[0] + (double)(k % d.nx) * F.hx;
+                P.ic_values[(size_t)k] = obs->ic_values ? obs->ic_values[k] : -std::sin(3.14159265358979323846 * x);
+                rinv.push_back(1.0 / (obs->ic_sigma * obs->ic_sigma));
+                bstatic[(size_t)k] += P.ic_values[(size_t)k] / (obs->ic_sigma * obs->ic_sigma);
+            }
+        }
+        P.colloc_kind = obs->colloc;
+        P.ncol = 0;
+        if (obs->colloc) {
+            require(d.kind == GMRF_ADVDIFF_ST_1D, "collocation rows need the 1D space-time prior");
+            require(obs->colloc == 1 || obs->colloc == 2, "colloc must be 0, 1 or 2");
+            require(obs->colloc_sigma > 0, "colloc_sigma must be positive");
+            P.ncol = (int64_t)(d.nx - 2) * (d.nt - 1);
+            P.colloc_qeps = 1.0 / (obs->colloc_sigma * obs->colloc_sigma);
+            P.colloc_nu = obs->colloc_nu;
+            P.colloc_c = obs->colloc_c;
+            for (Level& L : P.levels) {
+                const double ncl = (double)(L.nx - 2) * (L.nt - 1);
+                L.col.kind = obs->colloc == 1 ? 1 : 0;    // Burgers rows enter once linearised
+                L.col.qeps = P.colloc_qeps * (double)P.ncol / ncl;
+                L.col.inv_dt = 1.0 / L.dt;
+                L.col.inv_2h = 1.0 / (2.0 * L.hx);
+                L.col.nu_h2 = obs->colloc_nu / (L.hx * L.hx);
+                L.col.c = obs->colloc_c;
+                L.col.row0 = (int32_t)(P.m + P.nic);
+            }
+            if (obs->colloc == 1) {
+                // b += J^T Q_eps f on the fine level
+                const Level& L = P.levels[0];
+                for (int t = 1; t < L.nt; ++t)
+                    for (int x = 1; x < L.nx - 1; ++x) {
+                        const size_t r = (size_t)(t - 1) * (L.nx - 2) + (x - 1);
+                        const double f = obs->colloc_f ? obs->colloc_f[r] : 0.0;
+                        const double a = L.col.c;
+                        const double cC = L.col.inv_dt + 2.0 * L.col.nu_h2, cL = -a * L.col.inv_2h - L.col.nu_h2,
+                                     cR = a * L.col.inv_2h - L.col.nu_h2;
+                        const double v = L.col.qeps * f;
+                        bstatic[(size_t)t * L.nx + x] += cC * v;
+                        bstatic[(size_t)t * L.nx + x - 1] += cL * v;
+                        bstatic[(size_t)t * L.nx + x + 1] += cR * v;
+                        bstatic[(size_t)(t - 1) * L.nx + x] += -L.col.inv_dt * v;
+                    }
+            }
+        }
+        P.nrows = P.m + P.nic + P.ncol;
+        for (size_t l = 0; l < P.levels.size(); ++l) build_level_obs(d, P, coords, rinv, P.levels[l], l == 0);
+        if (obs->colloc == 2) {
+            for (Level& L : P.levels) {
+                L.d_mu32 = dev_alloc<float>((size_t)L.N);
+                L.d_mu64 = dev_alloc<double>((size_t)L.N);
+                GCK(cudaMemsetAsync(L.d_mu32, 0, sizeof(float) * L.N, s));
+                GCK(cudaMemsetAsync(L.d_mu64, 0, sizeof(double) * L.N, s));
+            }
+        }
+        posterior_setup_levels(P, s);
+        dev_upload(&P.d_bstatic, bstatic);
+        P.d_bdata = dev_alloc<double>((size_t)F.N);
+        P.d_ypoint = dev_alloc<double>((size_t)std::max<int64_t>(P.m, 1));
+        if (P.m) GCK(cudaMemcpyAsync(P.d_ypoint, P.y_point.data(), sizeof(double) * P.m, cudaMemcpyHostToDevice, s));
+        rebuild_bdata(P, s);
+        GCK(cudaStreamSynchronize(s));
+        *out = post;
+    });
+    if (st != GMRF_OK && post) gmrf_posterior_destroy(post);
+    return st;
+}
+
+void gmrf_posterior_destroy(gmrf_posterior* post) {
+    if (!post) return;
+    Posterior& P = post->impl;
+    cudaStreamSynchronize(P.prior->stream);
+    for (auto& kv : P.ws) workspace_free(kv.second);
+    P.ws.clear();
+    for (Level& L : P.levels) level_free(L);
+    dev_free(P.d_bdata);
+    dev_free(P.d_ypoint);
+    dev_free(P.d_bstatic);
+    delete post;
+}
+
+gmrf_status gmrf_update_data(gmrf_posterior* post, const double* y) {
+    return guard([&] {
+        require(post && (y || post->impl.m == 0), "null argument");
+        enter(post->prior);
+        Posterior& P = post->impl;
+        const cudaStream_t s = P.prior->stream;
+        if (P.m) copy_in(P.d_ypoint, y, (size_t)P.m, s);
+        rebuild_bdata(P, s);
+        GCK(cudaStreamSynchronize(s));
+    });
+}
+
+// Batch of right-hand sides: optional data slot (the mean) followed by
+// `ns` sample slots, padded to blocks of four.
+struct Batch {
+    int nrhs, nblk, off;
+    std::vector<int32_t> sample, mean_row, samp_row;
+};
+
+static Batch make_batch(int ns, bool with_mean) {
+    Batch b;
+    b.off = with_mean ? 1 : 0;
+    b.nrhs = ns + b.off;
+    b.nblk = (b.nrhs + 3) / 4;
+    const int P4 = b.nblk * 4;
+    b.sample.assign((size_t)P4, -2);
+    b.mean_row.assign((size_t)P4, -1);
+    b.samp_row.assign((size_t)P4, -1);
+    for (int i = 0; i < b.nrhs; ++i) {
+        if (with_mean && i == 0) {
+            b.sample[0] = -1;
+            b.mean_row[0] = 0;
+        } else {
+            b.sample[(size_t)i] = i - b.off;
+            b.samp_row[(size_t)i] = i - b.off;
+        }
+    }
+    return b;
+}
+
+static SolveStats run_batch(Posterior& P, const Batch& b, uint64_t seed, const gmrf_solve_opts& o, cudaStream_t s) {
+    Workspace& W = workspace(P, b.nblk);
+    GCK(cudaMemcpyAsync(W.slot_a, b.sample.data(), sizeof(int32_t) * b.sample.size(), cudaMemcpyHostToDevice, s));
+    launch_sample_rhs(P.levels[0].geo, P.levels[0].view<double>(), seed, W.slot_a, P.d_bdata, W.b64, b.nblk, 0, s);
+    GCK(cudaMemsetAsync(W.x64, 0, sizeof(double) * b.nblk * P.levels[0].N * 4, s));
+    if (o.batched || b.nblk == 1) return solve_blocked(P, b.nblk, W.b64, W.x64, o, s);
+    // one right-hand side per solve (the comparison path): the batch is
+    // spread to dense rows, each row solved alone, and the solutions packed back
+    SolveStats tot;
+    tot.converged = true;
+    Workspace& W1 = workspace(P, 1);
+    const long long N = P.levels[0].N;
+    std::vector<int32_t> rows((size_t)b.nblk * 4, -1);
+    for (int k = 0; k < b.nrhs; ++k) rows[(size_t)k] = k;
+    GCK(cudaMemcpyAsync(W.slot_b, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s));
+    launch_unpack(W.b64, W.t64, W.slot_b, N, b.nblk, s);
+    for (int i = 0; i < b.nrhs; ++i) {
+        std::vector<int32_t> one(4, -1);
+        one[0] = i;
+        GCK(cudaMemcpyAsync(W1.slot_b, one.data(), sizeof(int32_t) * 4, cudaMemcpyHostToDevice, s));
+        launch_pack(W.t64, W1.b64, W1.slot_b, N, 1, s);
+        GCK(cudaMemsetAsync(W1.x64, 0, sizeof(double) * N * 4, s));
+        SolveStats st = solve_blocked(P, 1, W1.b64, W1.x64, o, s);
+        tot.refinements += st.refinements;
+        tot.inner += st.inner;
+        tot.converged &= st.converged;
+        tot.breakdown |= st.breakdown;
+        tot.max_rel = std::max(tot.max_rel, st.max_rel);
+        launch_unpack(W1.x64, W.r64, W1.slot_b, N, 1, s);
+        GCK(cudaStreamSynchronize(s));
+    }
+    launch_pack(W.r64, W.x64, W.slot_b, N, b.nblk, s);
+    GCK(cudaStreamSynchronize(s));
+    return tot;
+}
+
+static void write_rows(Posterior& P, Workspace& W, const std::vector<int32_t>& rows, int count, double* dst,
+                       cudaStream_t s) {
+    if (!dst || count == 0) return;
+    const long long N = P.levels[0].N;
+    GCK(cudaMemcpyAsync(W.slot_b, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s));
+    if (is_device_ptr(dst)) {
+        launch_unpack(W.x64, dst, W.slot_b, N, W.nblk, s);
+    } else {
+        launch_unpack(W.x64, W.t64, W.slot_b, N, W.nblk, s);
+        GCK(cudaMemcpyAsync(dst, W.t64, sizeof(double) * N * count, cudaMemcpyDeviceToHost, s));
+    }
+    GCK(cudaStreamSynchronize(s));
+}
+
+gmrf_status gmrf_solve_mean(gmrf_posterior* post, double* mu, const gmrf_solve_opts* opts, gmrf_solve_info* info) {
+    gmrf_status rc = GMRF_OK;
+    const gmrf_status st = guard([&] {
+        require(post && mu, "null argument");
+        enter(post->prior);
+        Posterior& P = post->impl;
+        const cudaStream_t s = P.prior->stream;
+        const gmrf_solve_opts o = resolve_opts(opts);
+        const auto t0 = std::chrono::steady_clock::now();
+        const Batch b = make_batch(0, true);
+        const SolveStats ss = run_batch(P, b, 0, o, s);
+        write_rows(P, workspace(P, b.nblk), b.mean_row, 1, mu, s);
+        rc = finish(ss, info, 1, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+    });
+    return st != GMRF_OK ? st : rc;
+}
+
+gmrf_status gmrf_sample(gmrf_posterior* post, int32_t ns, uint64_t seed, double* mean, double* x,
+                        const gmrf_solve_opts* opts, gmrf_solve_info* info) {
+    gmrf_status rc = GMRF_OK;
+    const gmrf_status st = guard([&] {
+        require(post && ns >= 0 && (ns == 0 || x), "bad argument");
+        require(ns > 0 || mean, "nothing to compute");
+        enter(post->prior);
+        Posterior& P = post->impl;
+        const cudaStream_t s = P.prior->stream;
+        const gmrf_solve_opts o = resolve_opts(opts);
+        const auto t0 = std::chrono::steady_clock::now();
+        const Batch b = make_batch(ns, mean != nullptr);
+        const SolveStats ss = run_batch(P, b, seed, o, s);
+        Workspace& W = workspace(P, b.nblk);
+        write_rows(P, W, b.mean_row, 1, mean, s);
+        write_rows(P, W, b.samp_row, ns, x, s);
+        rc = finish(ss, info, b.nrhs, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+    });
+    return st != GMRF_OK ? st : rc;
+}
+
+gmrf_status gmrf_marginal_var(gmrf_posterior* post, int32_t ns, uint64_t seed, double* mean, double* var,
+                              double* stderr_, const gmrf_solve_opts* opts, gmrf_solve_info* info) {
+    gmrf_status rc = GMRF_OK;
+    const gmrf_status st = guard([&] {
+        require(post && ns >= 1 && var, "bad argument");
+        enter(post->prior);
+        Posterior& P = post->impl;
+        const cudaStream_t s = P.prior->stream;
+        const gmrf_solve_opts o = resolve_opts(opts);
+        const auto t0 = std::chrono::steady_clock::now();
+        const Batch b = make_batch(ns, mean != nullptr);
+        const SolveStats ss = run_batch(P, b, seed, o, s);
+        Workspace& W = workspace(P, b.nblk);
+        const long long N = P.levels[0].N;
+        write_rows(P, W, b.mean_row, 1, mean, s);
+        apply64(P, b.nblk, W.x64, W.r64, s);
+        GCK(cudaMemcpyAsync(W.slot_a, b.sample.data(), sizeof(int32_t) * b.sample.size(), cudaMemcpyHostToDevice, s));
+        launch_rbmc(W.r64, W.x64, P.levels[0].d_diag64, W.slot_a, N, b.nblk, ns, W.t64, W.t64 + N, s);
+        copy_out(var, W.t64, (size_t)N, s);
+        if (stderr_) copy_out(stderr_, W.t64 + N, (size_t)N, s);
+        GCK(cudaStreamSynchronize(s));
+        rc = finish(ss, info, b.nrhs, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+    });
+    return st != GMRF_OK ? st : rc;
+}
+
+gmrf_status gmrf_apply_posterior(gmrf_posterior* post, int32_t k, const double* x, double* y) {
+    return guard([&] {
+        require(post && k >= 1 && x && y, "bad argument");
+        enter(post->prior);
+        Posterior& P = post->impl;
+        const cudaStream_t s = P.prior->stream;
+        const int nblk = (k + 3) / 4;
+        Workspace& W = workspace(P, nblk);
+        const long long N = P.levels[0].N;
+        std::vector<int32_t> rows((size_t)nblk * 4, -1);
+        for (int i = 0; i < k; ++i) rows[(size_t)i] = i;
+        copy_in(W.t64, x, (size_t)N * k, s);
+        GCK(cudaMemcpyAsync(W.slot_b, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s));
+        launch_pack(W.t64, W.b64, W.slot_b, N, nblk, s);
+        apply64(P, nblk, W.b64, W.r64, s);
+        launch_unpack(W.r64, W.t64, W.slot_b, N, nblk, s);
+        copy_out(y, W.t64, (size_t)N * k, s);
+        GCK(cudaStreamSynchronize(s));
+    });
+}
+
+gmrf_status gmrf_normals(uint64_t seed, int32_t stream, int32_t sample0, int32_t count, int64_t n, double* out) {
+    return guard([&] {
+        require(out && count >= 0 && n >= 0 && stream >= 0 && sample0 >= 0, "bad argument");
+        if (count == 0 || n == 0) return;
+        double* d = dev_alloc<double>((size_t)count * n);
+        launch_normals(seed, stream, sample0, count, n, d, 0);
+        cudaError_t e = cudaMemcpy(out, d, sizeof(double) * count * n, cudaMemcpyDefault);
+        cudaFree(d);
+        cuda_check(e, "gmrf_normals copy");
+    });
+}
+
+gmrf_status gmrf_time_apply(gmrf_posterior* post, int32_t k, int32_t iters, double* ms) {
+    return guard([&] {
+        require(post && k >= 1 && iters >= 1 && ms, "bad argument");
+        enter(post->prior);
+        *ms = time_apply(post->impl, (k + 3) / 4, iters, post->prior->impl.stream);
+    });
+}
+
+uint64_t gmrf_launch_count(void) { return launch_count(); }
+
+gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* delta_prev, double* newton_decrement,
+                                   double* alpha, const gmrf_solve_opts* opts, gmrf_solve_info* info) {
+    (void)post; (void)mu_k; (void)delta_prev; (void)newton_decrement; (void)alpha; (void)opts; (void)info;
+    g_err = "gmrf_gauss_newton_step: not available in this build";
+    return GMRF_E_INVALID;
+}
+
+gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t seed, double* loglik, double* grad,
+                             double* grad_stderr, const gmrf_solve_opts* opts, gmrf_solve_info* info) {
+    (void)post; (void)nprobes; (void)seed; (void)loglik; (void)grad; (void)grad_stderr; (void)opts; (void)info;
+    g_err = "gmrf_loglik_grad: not available in this build";
+    return GMRF_E_INVALID;
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Device helpers shared by the GMRF kernels: the 4-wide right-hand-side
+// vector type, tile geometries, Philox4x32-10 normals and block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gmrf {
+
+// Right-hand sides are stored in blocks of four: element (rhs r, node n) of a
+// batch lives at ((r / 4) * N + n) * 4 + r % 4.  One thread owns one node of
+// one block and moves 16 B (FP32) or 32 B (FP64) per access.
+constexpr int RW = 4;
+
+template <typename T> struct alignas(sizeof(T) * 4) V4 { T a, b, c, d; };
+
+template <typename T> __device__ __forceinline__ V4<T> v4zero() { return V4<T>{T(0), T(0), T(0), T(0)}; }
+template <typename T> __device__ __forceinline__ V4<T> v4load(const T* p) { return *reinterpret_cast<const V4<T>*>(p); }
+template <typename T> __device__ __forceinline__ void v4store(T* p, V4<T> v) { *reinterpret_cast<V4<T>*>(p) = v; }
+template <typename T> __device__ __forceinline__ V4<T> operator+(V4<T> x, V4<T> y) { return {x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
+template <typename T> __device__ __forceinline__ V4<T> operator-(V4<T> x, V4<T> y) { return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; }
+template <typename T> __device__ __forceinline__ V4<T> operator*(T s, V4<T> x) { return {s * x.a, s * x.b, s * x.c, s * x.d}; }
+template <typename T> __device__ __forceinline__ V4<T> operator*(V4<T> x, V4<T> y) { return {x.a * y.a, x.b * y.b, x.c * y.c, x.d * y.d}; }
+template <typename T> __device__ __forceinline__ V4<T> fma4(T s, V4<T> x, V4<T> acc) {
+    return {fma(s, x.a, acc.a), fma(s, x.b, acc.b), fma(s, x.c, acc.c), fma(s, x.d, acc.d)};
+}
+template <typename T> __device__ __forceinline__ T comp(const V4<T>& v, int i) {
+    return i == 0 ? v.a : (i == 1 ? v.b : (i == 2 ? v.c : v.d));
+}
+
+// Tile geometries.  GEO_XY: 2D space; GEO_XT: 1D space x time (the y axis is
+// absent, ny = 1); GEO_XYT: 2D space x time.  A CTA of 256 threads owns one
+// TX x TY x TT tile of nodes for one block of four right-hand sides.  The
+// input vector is staged with a halo of 2 in x and y (the stacked stencil
+// B^T B reaches two nodes) and 1 in t.
+enum Geometry { GEO_XY = 0, GEO_XT = 1, GEO_XYT = 2 };
+
+template <int GEO> struct Geo;
+template <> struct Geo<GEO_XY>  { static constexpr int TX = 32, TY = 8, TT = 1, HY = 2, HT = 0; };
+template <> struct Geo<GEO_XT>  { static constexpr int TX = 32, TY = 1, TT = 8, HY = 0, HT = 1; };
+template <> struct Geo<GEO_XYT> { static constexpr int TX = 16, TY = 4, TT = 4, HY = 2, HT = 1; };
+
+inline int geo_tx(int g) { return g == GEO_XY ? 32 : (g == GEO_XT ? 32 : 16); }
+inline int geo_ty(int g) { return g == GEO_XY ? 8 : (g == GEO_XT ? 1 : 4); }
+inline int geo_tt(int g) { return g == GEO_XY ? 1 : (g == GEO_XT ? 8 : 4); }
+
+// Stencil taps of the root B (dx, dy, dt): 0 centre, 1 x-1, 2 x+1, 3 y-1,
+// 4 y+1, 5 (x-1, y-1), 6 (x+1, y+1), 7 t-1.
+constexpr int NTAP = 8;
+__host__ __device__ constexpr int tap_dx(int o) { return o == 1 || o == 5 ? -1 : (o == 2 || o == 6 ? 1 : 0); }
+__host__ __device__ constexpr int tap_dy(int o) { return o == 3 || o == 5 ? -1 : (o == 4 || o == 6 ? 1 : 0); }
+__host__ __device__ constexpr int tap_dt(int o) { return o == 7 ? -1 : 0; }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// with a Weyl-sequence key schedule.
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+    return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+// Standard normal number `idx` of (seed, stream, sample): pair j = idx / 2 of
+// counter (j, sample, stream, 0), Box-Muller on two 53-bit uniforms.
+__device__ __forceinline__ double philox_normal(uint64_t seed, uint32_t stream, uint32_t sample, uint64_t idx) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(idx >> 1), sample, stream, 0u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const double u1 = u53(w.x, w.y), u2 = u53(w.z, w.w);
+    const double r = sqrt(-2.0 * log(u1));
+    return (idx & 1) ? r * sinpi(2.0 * u2) : r * cospi(2.0 * u2);
+}
+
+__device__ __forceinline__ double philox_rademacher(uint64_t seed, uint32_t sample, uint64_t idx) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(idx >> 2), sample, 2u, 0u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const uint32_t word = (idx & 3) == 0 ? w.x : ((idx & 3) == 1 ? w.y : ((idx & 3) == 2 ? w.z : w.w));
+    return (word & 1u) ? -1.0 : 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of four FP64 partial sums (one per right-hand side of the
+// block) over a 256-thread CTA; thread 0 receives the totals.
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum4(double v[4], double* out /* 4 doubles, global */) {
+    __shared__ double red[NT / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = warp_sum(v[i]);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) red[warp][i] = v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+}  // namespace gmrf

@@ -1,0 +1,103 @@
+// Host-side helpers shared by the setup, solver and C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace gmrf {
+
+// Errors inside the library are thrown as Error and turned into a status at
+// the C boundary (nothing crosses extern "C" as an exception).
+struct Error : std::runtime_error {
+    gmrf_status status;
+    Error(gmrf_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+inline void cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) throw Error(GMRF_E_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    throw Error(GMRF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define GCK(call) ::gmrf::cuda_check((call), #call)
+
+template <typename T> T* dev_alloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    cuda_check(cudaMalloc(&p, n * sizeof(T)), "cudaMalloc");
+    return static_cast<T*>(p);
+}
+
+template <typename T> void dev_upload(T** dst, const std::vector<T>& v) {
+    if (*dst) cudaFree(*dst);
+    *dst = dev_alloc<T>(v.size());
+    if (!v.empty()) cuda_check(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+}
+
+inline void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+// setup.cu
+int geometry_of(const gmrf_prior_desc& d);
+void level_coefficients(const gmrf_prior_desc& d, Level& L);
+void build_hierarchy(const gmrf_prior_desc& d, std::vector<Level>& levels);
+void build_level_obs(const gmrf_prior_desc& d, const Posterior& P, const std::vector<double>& coords,
+                     const std::vector<double>& rinv, Level& L, bool fine);
+void build_transfer(Level& f, const Level& c);
+std::vector<double> dense_operator(const Level& L, const double* mu);
+bool spd_inverse(std::vector<double>& A, int n);
+
+// solver.cu
+struct SolveStats {
+    int refinements = 0;
+    int inner = 0;
+    bool converged = false;
+    double max_rel = 0.0;
+    bool breakdown = false;
+};
+
+void level_free(Level& L);
+void posterior_setup_levels(Posterior& P, cudaStream_t s);     // diag, Chebyshev bounds, transfers, dense inverse
+void posterior_refresh_operator(Posterior& P, cudaStream_t s); // after the linearisation point changed
+// Solve Q_u|y X = B for a blocked FP64 batch b64 (nblk blocks) into x64.
+SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
+                         cudaStream_t s);
+void apply64(Posterior& P, int nblk, const double* x64, double* y64, cudaStream_t s);
+Workspace& workspace(Posterior& P, int nblk);
+void workspace_free(Workspace* w);
+double time_apply(Posterior& P, int nblk, int iters, cudaStream_t s);
+
+// scratch of one batch size
+struct Workspace {
+    int nblk = 0;
+    // FP64 refinement vectors (blocked)
+    double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr;
+    // partial sums and per-RHS scalars
+    double* partial = nullptr;
+    size_t npartial = 0;
+    double* red = nullptr;
+    double* norms = nullptr;       // device, nblk * 4
+    double* sc32 = nullptr;        // PCG scalars of the FP32 inner solve
+    double* sc64 = nullptr;
+    double* h_red = nullptr;       // pinned host mirror of `red`
+    double* h_active = nullptr;    // pinned host mirror of the active flags
+    int32_t* slot_a = nullptr;     // per-slot ids (device)
+    int32_t* slot_b = nullptr;
+    // per-level vectors for each precision
+    struct Vecs {
+        bool ready = false;
+        void* pcg[5] = {};             // x, r, p, q, z (fine level)
+        std::vector<void*> xa, xb, d, res, b, t1, t2;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        double graph_tol = -1.0;   // inner tolerance baked into the captured graph
+        unsigned long long graph_kernels = 0;
+    } v32, v64;
+};
+
+}  // namespace gmrf

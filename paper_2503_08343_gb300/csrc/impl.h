@@ -1,0 +1,127 @@
+// Internal structures of the GMRF library (host and device views).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "gmrf.h"
+
+namespace gmrf {
+
+// One observation row on one grid level: up to 8 nodes with interpolation
+// weights (P1 barycentric in space x linear in time), its precision 1/sigma^2
+// and its global row index (for the Philox draws of perturbation samples).
+struct ObsRow {
+    int32_t node[8];
+    double wd[8];
+    float wf[8];
+    double rinv;
+    float rinvf;
+    int32_t nn;
+    int32_t row;
+    int32_t pad;
+};
+
+// Collocation rows J (Sec. 3.1 collocation; Sec. 3.3 Burgers): at interior
+// x and time levels >= 1, coefficients
+//   centre 1/dt + da + 2 nu/h^2, x-1: -a/(2h) - nu/h^2, x+1: a/(2h) - nu/h^2,
+//   t-1: -1/dt, with a = c (linear) or a = u_k(x) and da = (u_k(x+1) - u_k(x-1))/(2h)
+//   (Burgers, linearised at u_k).
+struct Colloc {
+    int kind;          // 0 none, 1 linear, 2 Burgers
+    double qeps;       // 1 / sigma^2, scaled on coarse levels by the row-count ratio
+    double inv_dt, inv_2h, nu_h2, c;
+    int32_t row0;      // global observation row of the first collocation row
+};
+
+// Everything a stencil kernel needs about one level, passed by value.
+template <typename T>
+struct LevelView {
+    int nx, ny, nt;
+    long long N;
+    int tiles_x, tiles_y, tiles_t;
+    T cf[2][NTAP];     // B taps: class 0 = interior (t >= 1 in space-time), class 1 = t = 0
+    T inv_eps2;        // Q_kk of a Dirichlet node
+    T inv_eps;         // B_kk of a Dirichlet node
+    Colloc col;
+    const T* mu;       // linearisation point (Burgers), [N] or null
+    const ObsRow* obs;
+    const int32_t* tile_ptr;
+    const int32_t* tile_idx;
+};
+
+struct Level {
+    int geo = 0;
+    int nx = 1, ny = 1, nt = 1;
+    long long N = 0;
+    double hx = 0, hy = 0, dt = 0;
+    double cd[2][NTAP] = {};
+    double inv_eps2 = 0, inv_eps = 0;
+    Colloc col = {};
+    int tiles_x = 1, tiles_y = 1, tiles_t = 1;
+    // observation rows of this level and their per-tile lists (device)
+    int nobs = 0;
+    ObsRow* d_obs = nullptr;
+    int32_t* d_tile_ptr = nullptr;
+    int32_t* d_tile_idx = nullptr;
+    std::vector<ObsRow> h_obs;
+    // linearisation point on this level (Burgers), device
+    float* d_mu32 = nullptr;
+    double* d_mu64 = nullptr;
+    // inverse Jacobi diagonal of Q_u|y, device
+    float* d_dinv32 = nullptr;
+    double* d_dinv64 = nullptr;
+    double* d_diag64 = nullptr;
+    // Chebyshev smoother on D^-1 Q: lambda_max estimate
+    double lmax = 0;
+    // grid transfer to the next coarser level, per axis (device):
+    // prolongation: fine i -> coarse j(i), weight w(i) of j(i)+1
+    int32_t* d_pj[3] = {nullptr, nullptr, nullptr};
+    float* d_pw[3] = {nullptr, nullptr, nullptr};
+    double* d_pwd[3] = {nullptr, nullptr, nullptr};
+    // restriction: coarse J -> fine range [rs(J), rs(J) + rc(J))
+    int32_t* d_rs[3] = {nullptr, nullptr, nullptr};
+    int32_t* d_rc[3] = {nullptr, nullptr, nullptr};
+    bool coarsen[3] = {false, false, false};
+    // coarsest level: dense inverse of Q_u|y (device, row-major)
+    float* d_dense32 = nullptr;
+    double* d_dense64 = nullptr;
+
+    template <typename T> LevelView<T> view() const;
+    long long ntiles() const { return (long long)tiles_x * tiles_y * tiles_t; }
+};
+
+struct Prior {
+    gmrf_prior_desc desc;
+    cudaStream_t stream = 0;
+    int geo = 0;
+    std::vector<Level> levels;   // rebuilt per posterior (observations differ); geometry here
+};
+
+struct Workspace;
+
+struct Posterior {
+    Prior* prior = nullptr;
+    std::vector<Level> levels;
+    int64_t m = 0;                 // point observations
+    int64_t nic = 0;               // initial-condition rows
+    int64_t ncol = 0;              // collocation rows on the fine level
+    int64_t nrows = 0;             // all observation rows
+    std::vector<double> y_point;   // point data values (host)
+    std::vector<double> ic_values;
+    std::vector<double> colloc_f;
+    double* d_bdata = nullptr;     // A^T Q_eps y on the fine level, [N]
+    double* d_ypoint = nullptr;
+    double* d_bstatic = nullptr;   // IC + linear collocation part of b, [N]
+    std::map<int, Workspace*> ws;  // scratch per batch size (blocks of four right-hand sides)
+    int colloc_kind = 0;           // requested collocation (2: Burgers, linearised on demand)
+    double colloc_qeps = 0.0, colloc_nu = 0.0, colloc_c = 0.0;
+    bool linearised = false;
+};
+
+}  // namespace gmrf

@@ -1,0 +1,83 @@
+// Host-callable launchers of the GMRF kernels (implemented in kernels.cu).
+#pragma once
+
+#include "impl.h"
+
+namespace gmrf {
+
+void note_launch();
+void capture_begin();
+unsigned long long capture_end();
+void note_graph_launch(unsigned long long kernels);
+unsigned long long launch_count();
+
+enum StencilMode { M_APPLY = 0, M_RESID = 1, M_CHEB = 2 };
+
+template <typename T>
+struct StencilArgs {
+    LevelView<T> L;
+    const T* x;        // input vector, staged with halo
+    const T* b;        // RESID / CHEB right-hand side
+    const T* d;        // CHEB previous direction (null on the first step)
+    const T* dinv;     // CHEB inverse diagonal [N]
+    T* out;            // APPLY: Q x; RESID: b - Q x; CHEB: x + d_new
+    T* out2;           // CHEB: d_new
+    T c1, c2;          // CHEB: d_new = c1 d + c2 D^-1 (b - Q x)
+    double* partial;   // per-CTA dot partials [nblk][ntiles][4] or null
+    int nblk;
+};
+
+// dot kinds written to `partial`: APPLY x.Qx, RESID |r|^2, CHEB b.x_new
+template <typename T> void launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s);
+
+// reduce [nblk][nparts][4] partials into out[nblk * 4]
+void launch_reduce(const double* partial, int nparts, int nblk, double* out, cudaStream_t s);
+
+// elementwise vector kernels over blocked batches ([nblk][N][4])
+template <typename T> void launch_cheb_first(const T* b, const T* dinv, T c2, T* x, T* d, long long N, int nblk, cudaStream_t s);
+template <typename T> void launch_restrict_axis(const T* in, T* out, int nx, int ny, int nt, int axis, int ncoarse,
+                                                const int32_t* rs, const int32_t* rc, const int32_t* pj, const T* pw,
+                                                int nblk, cudaStream_t s);
+template <typename T> void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, int nblk, cudaStream_t s);
+template <typename T> void launch_dense_solve(const T* Ainv, const T* b, T* x, int n, int nblk, cudaStream_t s);
+
+// PCG scalar and vector steps.  Per-RHS scalars live in `sc` (FP64):
+//   sc[0*P + r] = rz, sc[1*P + r] = pq, sc[2*P + r] = alpha, sc[3*P + r] = beta,
+//   sc[4*P + r] = rr, sc[5*P + r] = rr0, sc[6*P + r] = active (0/1), sc[7*P + r] = breakdown
+// with P = nblk * 4.
+template <typename T> void launch_pcg_update_xr(T* x, T* r, const T* p, const T* q, const double* sc, long long N,
+                                                int nblk, double* partial, int nparts, cudaStream_t s);
+template <typename T> void launch_pcg_update_p(T* p, const T* z, const double* sc, long long N, int nblk, cudaStream_t s);
+void launch_pcg_scalar(int kind, const double* red, double* sc, int nblk, double tol2, cudaStream_t s);
+int elem_parts(long long N);
+
+// mixed precision refinement
+void launch_scale_cast(const double* r64, const double* norms, float* r32, long long N, int nblk, cudaStream_t s);
+void launch_axpy_mixed(double* x64, const double* norms, const float* d32, long long N, int nblk, cudaStream_t s);
+void launch_axpy_scaled64(double* x64, const double* norms, const double* d64, long long N, int nblk, cudaStream_t s);
+void launch_scale64(const double* r64, const double* norms, double* out, long long N, int nblk, cudaStream_t s);
+
+// right-hand sides, layout conversion, variances
+void launch_sample_rhs(int geo, const LevelView<double>& L, uint64_t seed, const int32_t* slot_sample,
+                       const double* bdata, double* b64, int nblk, int use_probe, cudaStream_t s);
+void launch_obs_scatter(const ObsRow* obs, int nobs, const double* y, double* b, cudaStream_t s);
+void launch_pack(const double* src, double* dst, const int32_t* slot_src, long long N, int nblk, cudaStream_t s);
+void launch_unpack(const double* src, double* dst, const int32_t* slot_dst, long long N, int nblk, cudaStream_t s);
+void launch_rbmc(const double* Qx, const double* x, const double* diag, const int32_t* slot_sample, long long N,
+                 int nblk, int ns, double* var, double* se, cudaStream_t s);
+template <typename T> void launch_diag(int geo, const LevelView<T>& L, double* diag64, cudaStream_t s);
+void launch_obs_diag(const ObsRow* obs, int nobs, double* diag, cudaStream_t s);
+void launch_finish_diag(const double* diag, float* dinv32, double* dinv64, long long N, cudaStream_t s);
+void launch_normals(uint64_t seed, int stream, int sample0, int count, long long n, double* out, cudaStream_t s);
+template <typename T> void launch_cast(const double* in, T* out, long long n, cudaStream_t s);
+void launch_rademacher_fill(uint64_t seed, const int32_t* slot_sample, double* b64, long long N, int nblk, cudaStream_t s);
+void launch_dot_blocked(const double* a, const double* b, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
+
+}  // namespace gmrf
+
+namespace gmrf {
+template <typename T> void launch_norm2(const T* v, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
+void launch_power_scale(float* q, const float* dinv, long long N, double* partial, int nparts, cudaStream_t s);
+void launch_scale_comp(float* v, const float* w, const double* nrm2, long long N, cudaStream_t s);
+void launch_fill_random(float* v, long long N, uint64_t seed, cudaStream_t s);
+}  // namespace gmrf

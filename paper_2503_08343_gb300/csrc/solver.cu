@@ -1,0 +1,471 @@
+// Multi-RHS multigrid-preconditioned conjugate gradients inside FP64
+// iterative refinement (CG: Sec. 3.2 "Conjugate gradient method").
+//
+// Outer loop (FP64): r = b - Q_u|y x with the FP64 stencil, per-RHS norms,
+// stop at ||r|| <= rtol ||b||.  Inner solve (FP32): PCG on r / ||r|| to a
+// relative reduction inner_rtol, preconditioned by one V(2,2)-cycle with a
+// Chebyshev(2) smoother on D^-1 Q (D the diagonal of Q_u|y) over levels
+// rediscretised on coarser grids, and a dense inverse on the coarsest level.
+// One PCG iteration is captured into a CUDA graph and replayed.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "host.h"
+
+namespace gmrf {
+
+struct Cheb {
+    double c1[2], c2[2];
+};
+
+// Chebyshev iteration on [lmax/10, lmax]: x <- x + d_k, d_0 = r/theta,
+// d_k = rho_k rho_(k-1) d_(k-1) + (2 rho_k / delta) r, rho_k = 1/(2 sigma - rho_(k-1)).
+static Cheb cheb_coeffs(double lmax) {
+    const double lmin = lmax / 10.0;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+    const double sigma = theta / delta, rho0 = 1.0 / sigma;
+    const double rho1 = 1.0 / (2.0 * sigma - rho0);
+    Cheb c;
+    c.c1[0] = 0.0;
+    c.c2[0] = 1.0 / theta;
+    c.c1[1] = rho1 * rho0;
+    c.c2[1] = 2.0 * rho1 / delta;
+    return c;
+}
+
+template <typename T> static const T* dinv_of(const Level& L);
+template <> const float* dinv_of<float>(const Level& L) { return L.d_dinv32; }
+template <> const double* dinv_of<double>(const Level& L) { return L.d_dinv64; }
+template <typename T> static const T* dense_of(const Level& L);
+template <> const float* dense_of<float>(const Level& L) { return L.d_dense32; }
+template <> const double* dense_of<double>(const Level& L) { return L.d_dense64; }
+template <typename T> static const T* pw_of(const Level& L, int a);
+template <> const float* pw_of<float>(const Level& L, int a) { return L.d_pw[a]; }
+template <> const double* pw_of<double>(const Level& L, int a) { return L.d_pwd[a]; }
+
+void level_free(Level& L) {
+    dev_free(L.d_obs); dev_free(L.d_tile_ptr); dev_free(L.d_tile_idx);
+    dev_free(L.d_mu32); dev_free(L.d_mu64);
+    dev_free(L.d_dinv32); dev_free(L.d_dinv64); dev_free(L.d_diag64);
+    for (int a = 0; a < 3; ++a) {
+        dev_free(L.d_pj[a]); dev_free(L.d_pw[a]); dev_free(L.d_pwd[a]); dev_free(L.d_rs[a]); dev_free(L.d_rc[a]);
+    }
+    dev_free(L.d_dense32); dev_free(L.d_dense64);
+    L = Level();
+}
+
+static size_t partial_slots(const Posterior& P, int nblk) {
+    long long m = 1;
+    for (const Level& L : P.levels) m = std::max(m, std::max(L.ntiles(), (long long)elem_parts(L.N)));
+    return (size_t)m * nblk * 4;
+}
+
+// ---------------------------------------------------------------------------
+// operator-dependent setup: Jacobi diagonal, Chebyshev bound, dense inverse
+
+static double power_lmax(Posterior& P, Level& L, cudaStream_t s) {
+    const long long N = L.N;
+    float* v = dev_alloc<float>((size_t)N * 4);
+    float* q = dev_alloc<float>((size_t)N * 4);
+    const long long nt = L.ntiles();
+    const int np = elem_parts(N);
+    double* part = dev_alloc<double>((size_t)std::max<long long>(nt, np) * 4);
+    double* red = dev_alloc<double>(4);
+    launch_fill_random(v, N, 0x5eed, s);
+    StencilArgs<float> a{};
+    a.L = L.view<float>();
+    a.x = v;
+    a.out = q;
+    a.nblk = 1;
+    double lam = 0.0;
+    double h[4];
+    const int iters = 24;
+    for (int it = 0; it < iters; ++it) {
+        launch_stencil<float>(L.geo, M_APPLY, a, s);
+        launch_power_scale(q, L.d_dinv32, N, part, np, s);
+        launch_reduce(part, np, 1, red, s);
+        launch_scale_comp(v, q, red, N, s);
+        GCK(cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GCK(cudaStreamSynchronize(s));
+        if (it >= 2) {
+            double m = 0.0;
+            for (int c = 0; c < 4; ++c) m = std::max(m, std::sqrt(h[c]));
+            lam = std::max(lam, m);
+        }
+    }
+    dev_free(v); dev_free(q); dev_free(part); dev_free(red);
+    (void)P;
+    return lam;
+}
+
+static void setup_diag(Level& L, cudaStream_t s) {
+    if (!L.d_diag64) L.d_diag64 = dev_alloc<double>((size_t)L.N);
+    if (!L.d_dinv32) L.d_dinv32 = dev_alloc<float>((size_t)L.N);
+    if (!L.d_dinv64) L.d_dinv64 = dev_alloc<double>((size_t)L.N);
+    launch_diag<double>(L.geo, L.view<double>(), L.d_diag64, s);
+    launch_obs_diag(L.d_obs, L.nobs, L.d_diag64, s);
+    launch_finish_diag(L.d_diag64, L.d_dinv32, L.d_dinv64, L.N, s);
+}
+
+static void setup_dense(Level& L, cudaStream_t s) {
+    std::vector<double> mu;
+    if (L.col.kind == 2 && L.d_mu64) {
+        mu.resize((size_t)L.N);
+        GCK(cudaMemcpyAsync(mu.data(), L.d_mu64, mu.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GCK(cudaStreamSynchronize(s));
+    }
+    std::vector<double> A = dense_operator(L, mu.empty() ? nullptr : mu.data());
+    if (!spd_inverse(A, (int)L.N)) throw Error(GMRF_E_NOT_SPD, "coarsest-level operator is not positive definite");
+    std::vector<float> A32(A.size());
+    for (size_t i = 0; i < A.size(); ++i) A32[i] = (float)A[i];
+    dev_upload(&L.d_dense64, A);
+    dev_upload(&L.d_dense32, A32);
+}
+
+void posterior_refresh_operator(Posterior& P, cudaStream_t s) {
+    const int nl = (int)P.levels.size();
+    for (int l = 0; l < nl; ++l) setup_diag(P.levels[l], s);
+    for (int l = 0; l < nl - 1; ++l) P.levels[l].lmax = 1.1 * power_lmax(P, P.levels[l], s);
+    setup_dense(P.levels[nl - 1], s);
+    GCK(cudaStreamSynchronize(s));
+}
+
+void posterior_setup_levels(Posterior& P, cudaStream_t s) {
+    const int nl = (int)P.levels.size();
+    for (int l = 0; l + 1 < nl; ++l) build_transfer(P.levels[l], P.levels[l + 1]);
+    posterior_refresh_operator(P, s);
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+
+template <typename T> static void alloc_vecs(Posterior& P, Workspace& W, Workspace::Vecs& V) {
+    if (V.ready) return;
+    const int nblk = W.nblk;
+    const long long N0 = P.levels[0].N;
+    for (int i = 0; i < 5; ++i) V.pcg[i] = dev_alloc<T>((size_t)nblk * N0 * 4);
+    const size_t nl = P.levels.size();
+    V.xa.assign(nl, nullptr); V.xb.assign(nl, nullptr); V.d.assign(nl, nullptr); V.res.assign(nl, nullptr);
+    V.b.assign(nl, nullptr); V.t1.assign(nl, nullptr); V.t2.assign(nl, nullptr);
+    for (size_t l = 0; l < nl; ++l) {
+        const size_t n = (size_t)nblk * P.levels[l].N * 4;
+        V.xa[l] = dev_alloc<T>(n);
+        V.d[l] = dev_alloc<T>(n);
+        V.res[l] = dev_alloc<T>(n);
+        V.t1[l] = dev_alloc<T>(n);
+        V.t2[l] = dev_alloc<T>(n);
+        if (l > 0) {
+            V.b[l] = dev_alloc<T>(n);
+            V.xb[l] = dev_alloc<T>(n);
+        }
+    }
+    V.ready = true;
+}
+
+static void free_vecs(Workspace::Vecs& V) {
+    for (void* p : V.pcg) dev_free(p);
+    for (auto* vec : {&V.xa, &V.xb, &V.d, &V.res, &V.b, &V.t1, &V.t2})
+        for (void* p : *vec) dev_free(p);
+    if (V.exec) cudaGraphExecDestroy(V.exec);
+    if (V.graph) cudaGraphDestroy(V.graph);
+    V = Workspace::Vecs();
+}
+
+void workspace_free(Workspace* w) {
+    if (!w) return;
+    dev_free(w->b64); dev_free(w->x64); dev_free(w->r64); dev_free(w->t64);
+    dev_free(w->partial); dev_free(w->red); dev_free(w->norms); dev_free(w->sc32); dev_free(w->sc64);
+    dev_free(w->slot_a); dev_free(w->slot_b);
+    if (w->h_red) cudaFreeHost(w->h_red);
+    if (w->h_active) cudaFreeHost(w->h_active);
+    free_vecs(w->v32);
+    free_vecs(w->v64);
+    delete w;
+}
+
+Workspace& workspace(Posterior& P, int nblk) {
+    auto it = P.ws.find(nblk);
+    if (it != P.ws.end()) return *it->second;
+    Workspace* W = new Workspace();
+    W->nblk = nblk;
+    const size_t n = (size_t)nblk * P.levels[0].N * 4;
+    W->b64 = dev_alloc<double>(n);
+    W->x64 = dev_alloc<double>(n);
+    W->r64 = dev_alloc<double>(n);
+    W->t64 = dev_alloc<double>(n);
+    W->npartial = partial_slots(P, nblk);
+    W->partial = dev_alloc<double>(W->npartial);
+    W->red = dev_alloc<double>((size_t)nblk * 4);
+    W->norms = dev_alloc<double>((size_t)nblk * 4);
+    W->sc32 = dev_alloc<double>((size_t)nblk * 4 * 8);
+    W->sc64 = dev_alloc<double>((size_t)nblk * 4 * 8);
+    W->slot_a = dev_alloc<int32_t>((size_t)nblk * 4);
+    W->slot_b = dev_alloc<int32_t>((size_t)nblk * 4);
+    GCK(cudaMallocHost((void**)&W->h_red, sizeof(double) * nblk * 4));
+    GCK(cudaMallocHost((void**)&W->h_active, sizeof(double) * nblk * 4));
+    P.ws[nblk] = W;
+    return *W;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle
+
+template <typename T>
+static void vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T* b, T* x, double* rz_partial,
+                   cudaStream_t s) {
+    const int nl = (int)P.levels.size();
+    Level& L = P.levels[l];
+    const int nblk = W.nblk;
+    if (l == nl - 1) {
+        launch_dense_solve<T>(dense_of<T>(L), b, x, (int)L.N, nblk, s);
+        return;
+    }
+    const Cheb ch = cheb_coeffs(L.lmax);
+    T* X0 = (T*)V.xa[l];
+    T* D = (T*)V.d[l];
+    T* R = (T*)V.res[l];
+    const T* dinv = dinv_of<T>(L);
+    // pre-smoothing from x = 0
+    launch_cheb_first<T>(b, dinv, (T)ch.c2[0], X0, D, L.N, nblk, s);
+    StencilArgs<T> a{};
+    a.L = L.view<T>();
+    a.nblk = nblk;
+    a.x = X0; a.b = b; a.d = D; a.dinv = dinv; a.out = x; a.out2 = D;
+    a.c1 = (T)ch.c1[1]; a.c2 = (T)ch.c2[1];
+    launch_stencil<T>(L.geo, M_CHEB, a, s);
+    // residual and restriction (separable transpose of the interpolation)
+    StencilArgs<T> r = a;
+    r.x = x; r.b = b; r.d = nullptr; r.out = R; r.out2 = nullptr;
+    launch_stencil<T>(L.geo, M_RESID, r, s);
+    Level& C = P.levels[l + 1];
+    int dims[3] = {L.nx, L.ny, L.nt};
+    const int cdims[3] = {C.nx, C.ny, C.nt};
+    int last = -1;
+    for (int ax = 0; ax < 3; ++ax)
+        if (L.coarsen[ax]) last = ax;
+    const T* src = R;
+    bool use_t1 = true;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (!L.coarsen[ax]) continue;
+        T* dst = ax == last ? (T*)V.b[l + 1] : (use_t1 ? (T*)V.t1[l] : (T*)V.t2[l]);
+        use_t1 = !use_t1;
+        launch_restrict_axis<T>(src, dst, dims[0], dims[1], dims[2], ax, cdims[ax], L.d_rs[ax], L.d_rc[ax], L.d_pj[ax],
+                                pw_of<T>(L, ax), nblk, s);
+        dims[ax] = cdims[ax];
+        src = dst;
+    }
+    vcycle<T>(P, W, V, l + 1, (const T*)V.b[l + 1], (T*)V.xb[l + 1], nullptr, s);
+    launch_prolong_add<T>(x, (const T*)V.xb[l + 1], L, C, nblk, s);
+    // post-smoothing: a fresh Chebyshev(2) sweep
+    StencilArgs<T> p1 = a;
+    p1.x = x; p1.d = nullptr; p1.out = X0; p1.out2 = D; p1.c1 = T(0); p1.c2 = (T)ch.c2[0];
+    launch_stencil<T>(L.geo, M_CHEB, p1, s);
+    StencilArgs<T> p2 = a;
+    p2.x = X0; p2.d = D; p2.out = x; p2.out2 = D; p2.partial = rz_partial;
+    launch_stencil<T>(L.geo, M_CHEB, p2, s);
+}
+
+// ---------------------------------------------------------------------------
+// PCG
+
+template <typename T> static Workspace::Vecs& vecs(Workspace& W);
+template <> Workspace::Vecs& vecs<float>(Workspace& W) { return W.v32; }
+template <> Workspace::Vecs& vecs<double>(Workspace& W) { return W.v64; }
+template <typename T> static double* scal(Workspace& W);
+template <> double* scal<float>(Workspace& W) { return W.sc32; }
+template <> double* scal<double>(Workspace& W) { return W.sc64; }
+
+// one PCG iteration: q = Q p, alpha, x += alpha p, r -= alpha q, z = M r, beta, p = z + beta p
+template <typename T>
+static void pcg_iteration(Posterior& P, Workspace& W, Workspace::Vecs& V, double tol2, cudaStream_t s) {
+    Level& L = P.levels[0];
+    const int nblk = W.nblk;
+    T *x = (T*)V.pcg[0], *r = (T*)V.pcg[1], *p = (T*)V.pcg[2], *q = (T*)V.pcg[3], *z = (T*)V.pcg[4];
+    double* sc = scal<T>(W);
+    const int nt = (int)L.ntiles(), ne = elem_parts(L.N);
+    StencilArgs<T> a{};
+    a.L = L.view<T>();
+    a.nblk = nblk;
+    a.x = p; a.out = q; a.partial = W.partial;
+    launch_stencil<T>(L.geo, M_APPLY, a, s);
+    launch_reduce(W.partial, nt, nblk, W.red, s);
+    launch_pcg_scalar(0, W.red, sc, nblk, tol2, s);
+    launch_pcg_update_xr<T>(x, r, p, q, sc, L.N, nblk, W.partial, ne, s);
+    launch_reduce(W.partial, ne, nblk, W.red, s);
+    launch_pcg_scalar(1, W.red, sc, nblk, tol2, s);
+    vcycle<T>(P, W, V, 0, r, z, W.partial, s);
+    launch_reduce(W.partial, nt, nblk, W.red, s);
+    launch_pcg_scalar(2, W.red, sc, nblk, tol2, s);
+    launch_pcg_update_p<T>(p, z, sc, L.N, nblk, s);
+}
+
+static const int kItersPerGraph = 2;
+
+// Solves Q x = r (r already in V.pcg[1]) into V.pcg[0]; returns iterations.
+template <typename T>
+static int pcg(Posterior& P, Workspace& W, double tol, int maxit, cudaStream_t s, bool use_graph, bool* breakdown,
+               const std::chrono::steady_clock::time_point* deadline) {
+    Level& L = P.levels[0];
+    Workspace::Vecs& V = vecs<T>(W);
+    const int nblk = W.nblk;
+    T *x = (T*)V.pcg[0], *r = (T*)V.pcg[1], *p = (T*)V.pcg[2], *z = (T*)V.pcg[4];
+    double* sc = scal<T>(W);
+    const int nt = (int)L.ntiles(), ne = elem_parts(L.N);
+    const size_t bytes = (size_t)nblk * L.N * 4 * sizeof(T);
+    const double tol2 = tol * tol;
+    GCK(cudaMemsetAsync(x, 0, bytes, s));
+    launch_norm2<T>(r, L.N, nblk, W.partial, ne, s);
+    launch_reduce(W.partial, ne, nblk, W.red, s);
+    launch_pcg_scalar(4, W.red, sc, nblk, tol2, s);
+    vcycle<T>(P, W, V, 0, r, z, W.partial, s);
+    launch_reduce(W.partial, nt, nblk, W.red, s);
+    launch_pcg_scalar(3, W.red, sc, nblk, tol2, s);
+    GCK(cudaMemcpyAsync(p, z, bytes, cudaMemcpyDeviceToDevice, s));
+    const int P4 = nblk * 4;
+    if (use_graph && V.graph == nullptr) {
+        GCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        capture_begin();
+        for (int k = 0; k < kItersPerGraph; ++k) pcg_iteration<T>(P, W, V, tol2, s);
+        V.graph_kernels = capture_end();
+        cudaMemcpyAsync(W.h_active, sc + 6 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(W.h_red, sc + 7 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s);
+        GCK(cudaStreamEndCapture(s, &V.graph));
+        GCK(cudaGraphInstantiate(&V.exec, V.graph, 0));
+    }
+    int it = 0;
+    *breakdown = false;
+    while (it < maxit) {
+        if (use_graph) {
+            GCK(cudaGraphLaunch(V.exec, s));
+            note_graph_launch(V.graph_kernels);
+            it += kItersPerGraph;
+        } else {
+            pcg_iteration<T>(P, W, V, tol2, s);
+            GCK(cudaMemcpyAsync(W.h_active, sc + 6 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
+            GCK(cudaMemcpyAsync(W.h_red, sc + 7 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
+            it += 1;
+        }
+        GCK(cudaStreamSynchronize(s));
+        bool any = false;
+        for (int i = 0; i < P4; ++i) {
+            any |= W.h_active[i] != 0.0;
+            *breakdown |= W.h_red[i] != 0.0;
+        }
+        if (!any) break;
+        if (deadline && std::chrono::steady_clock::now() > *deadline) throw Error(GMRF_E_TIMEOUT, "solve exceeded timeout_s");
+    }
+    return it;
+}
+
+// The graph bakes in the tolerance; re-capture when it changes.
+template <typename T> static void invalidate_graph(Workspace::Vecs& V) {
+    if (V.exec) cudaGraphExecDestroy(V.exec);
+    if (V.graph) cudaGraphDestroy(V.graph);
+    V.exec = nullptr;
+    V.graph = nullptr;
+}
+
+
+// ---------------------------------------------------------------------------
+// FP64 iterative refinement
+
+void apply64(Posterior& P, int nblk, const double* x64, double* y64, cudaStream_t s) {
+    Level& L = P.levels[0];
+    StencilArgs<double> a{};
+    a.L = L.view<double>();
+    a.nblk = nblk;
+    a.x = x64;
+    a.out = y64;
+    launch_stencil<double>(L.geo, M_APPLY, a, s);
+}
+
+SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
+                         cudaStream_t s) {
+    Workspace& W = workspace(P, nblk);
+    Level& L = P.levels[0];
+    const int P4 = nblk * 4;
+    const bool fp64 = o.precision == 1;
+    const bool graph = o.batched != 0;
+    if (fp64) alloc_vecs<double>(P, W, W.v64);
+    else alloc_vecs<float>(P, W, W.v32);
+    std::chrono::steady_clock::time_point dl;
+    const bool has_dl = o.timeout_s > 0;
+    if (has_dl) dl = std::chrono::steady_clock::now() + std::chrono::microseconds((long long)(o.timeout_s * 1e6));
+    const double inner_tol = fp64 ? std::min(o.inner_rtol, 0.5 * o.rtol) : o.inner_rtol;
+    Workspace::Vecs& V = fp64 ? W.v64 : W.v32;
+    if (V.graph_tol != inner_tol) {
+        invalidate_graph<float>(V);
+        V.graph_tol = inner_tol;
+    }
+    std::vector<double> bn((size_t)P4, 0.0), rn((size_t)P4, 0.0), nrm((size_t)P4, 0.0);
+    SolveStats st;
+    const int nt = (int)L.ntiles();
+    for (int ref = 0; ref <= o.max_refine; ++ref) {
+        StencilArgs<double> a{};
+        a.L = L.view<double>();
+        a.nblk = nblk;
+        a.x = x64; a.b = b64; a.out = W.r64; a.partial = W.partial;
+        launch_stencil<double>(L.geo, M_RESID, a, s);
+        launch_reduce(W.partial, nt, nblk, W.red, s);
+        GCK(cudaMemcpyAsync(W.h_red, W.red, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
+        GCK(cudaStreamSynchronize(s));
+        st.refinements++;
+        bool conv = true;
+        st.max_rel = 0.0;
+        for (int i = 0; i < P4; ++i) {
+            rn[(size_t)i] = std::sqrt(std::max(W.h_red[i], 0.0));
+            if (!std::isfinite(W.h_red[i])) throw Error(GMRF_E_NOT_SPD, "non-finite residual in refinement");
+            if (ref == 0) bn[(size_t)i] = rn[(size_t)i];
+            const double rel = bn[(size_t)i] > 0 ? rn[(size_t)i] / bn[(size_t)i] : 0.0;
+            st.max_rel = std::max(st.max_rel, rel);
+            const bool done = rel <= o.rtol;
+            conv &= done;
+            nrm[(size_t)i] = done ? 0.0 : rn[(size_t)i];
+        }
+        if (conv) { st.converged = true; break; }
+        if (ref == o.max_refine) break;
+        GCK(cudaMemcpyAsync(W.norms, nrm.data(), sizeof(double) * P4, cudaMemcpyHostToDevice, s));
+        bool brk = false;
+        if (fp64) {
+            launch_scale64(W.r64, W.norms, (double*)W.v64.pcg[1], L.N, nblk, s);
+            st.inner += pcg<double>(P, W, inner_tol, o.max_inner, s, graph, &brk, has_dl ? &dl : nullptr);
+            launch_axpy_scaled64(x64, W.norms, (const double*)W.v64.pcg[0], L.N, nblk, s);
+        } else {
+            launch_scale_cast(W.r64, W.norms, (float*)W.v32.pcg[1], L.N, nblk, s);
+            st.inner += pcg<float>(P, W, inner_tol, o.max_inner, s, graph, &brk, has_dl ? &dl : nullptr);
+            launch_axpy_mixed(x64, W.norms, (const float*)W.v32.pcg[0], L.N, nblk, s);
+        }
+        st.breakdown |= brk;
+    }
+    return st;
+}
+
+double time_apply(Posterior& P, int nblk, int iters, cudaStream_t s) {
+    Workspace& W = workspace(P, nblk);
+    alloc_vecs<float>(P, W, W.v32);
+    Level& L = P.levels[0];
+    float* x = (float*)W.v32.pcg[2];
+    float* y = (float*)W.v32.pcg[3];
+    for (int b = 0; b < nblk; ++b) launch_fill_random(x + (size_t)b * L.N * 4, L.N, 99 + b, s);
+    StencilArgs<float> a{};
+    a.L = L.view<float>();
+    a.nblk = nblk;
+    a.x = x; a.out = y; a.partial = W.partial;
+    launch_stencil<float>(L.geo, M_APPLY, a, s);
+    cudaEvent_t e0, e1;
+    GCK(cudaEventCreate(&e0));
+    GCK(cudaEventCreate(&e1));
+    GCK(cudaEventRecord(e0, s));
+    for (int i = 0; i < iters; ++i) launch_stencil<float>(L.geo, M_APPLY, a, s);
+    GCK(cudaEventRecord(e1, s));
+    GCK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    GCK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / iters;
+}
+
+}  // namespace gmrf

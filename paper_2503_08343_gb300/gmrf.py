@@ -1,0 +1,271 @@
+"""Thin Python binding of the C ABI in include/gmrf.h (ctypes).
+
+Argument marshalling only: every step of the computation runs in libgmrf.so.
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory); float64, C-contiguous.  The library fails loudly when it is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+KIND = {"matern2d": 0, "advdiff_st1d": 1, "advdiff_st2d": 2, "steady_advdiff2d": 3}
+STATUS = {0: "ok", 1: "invalid argument", 2: "not positive definite", 3: "no convergence",
+          4: "CUDA error", 5: "out of device memory", 6: "timeout"}
+
+
+class PriorDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nt", C.c_int32),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("kappa", C.c_double), ("tau", C.c_double), ("nu", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("kappa0", C.c_double), ("eps2", C.c_double)]
+
+
+class ObsDesc(C.Structure):
+    _fields_ = [("m", C.c_int64), ("coords", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)),
+                ("sigma", C.POINTER(C.c_double)), ("sigma_all", C.c_double),
+                ("ic", C.c_int32), ("ic_sigma", C.c_double), ("ic_values", C.POINTER(C.c_double)),
+                ("colloc", C.c_int32), ("colloc_sigma", C.c_double), ("colloc_c", C.c_double),
+                ("colloc_nu", C.c_double), ("colloc_f", C.POINTER(C.c_double))]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_refine", C.c_int32), ("max_inner", C.c_int32),
+                ("inner_rtol", C.c_double), ("precision", C.c_int32), ("batched", C.c_int32),
+                ("timeout_s", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("nrhs", C.c_int32), ("refinements", C.c_int32), ("inner_iterations", C.c_int32),
+                ("converged", C.c_int32), ("max_rel_residual", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GmrfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libgmrf.so (built in-tree by paper_2503_08343_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libgmrf.so not built at {path}: run __graft_entry__.build() first")
+        _build.build()
+    lib = C.CDLL(path)
+    P, I32, I64, U64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    DP = C.POINTER(C.c_double)
+    sig = {
+        "gmrf_default_opts": (None, [C.POINTER(SolveOpts)]),
+        "gmrf_build_prior": (I32, [C.POINTER(PriorDesc), P, C.POINTER(P)]),
+        "gmrf_condition": (I32, [P, C.POINTER(ObsDesc), C.POINTER(P)]),
+        "gmrf_update_data": (I32, [P, P]),
+        "gmrf_solve_mean": (I32, [P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "gmrf_sample": (I32, [P, I32, U64, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "gmrf_marginal_var": (I32, [P, I32, U64, P, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "gmrf_gauss_newton_step": (I32, [P, P, P, DP, DP, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "gmrf_loglik_grad": (I32, [P, I32, U64, DP, DP, DP, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "gmrf_apply_posterior": (I32, [P, I32, P, P]),
+        "gmrf_normals": (I32, [U64, I32, I32, I32, I64, P]),
+        "gmrf_time_apply": (I32, [P, I32, I32, DP]),
+        "gmrf_num_unknowns": (I64, [P]),
+        "gmrf_num_levels": (I32, [P]),
+        "gmrf_prior_destroy": (None, [P]),
+        "gmrf_posterior_destroy": (None, [P]),
+        "gmrf_status_string": (C.c_char_p, [I32]),
+        "gmrf_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != 0:
+        raise GmrfError(st, load().gmrf_last_error().decode())
+
+
+def _ptr(a):
+    """Raw pointer of a float64 numpy array or CUDA tensor (or None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        assert a.dtype == torch.float64 and a.is_contiguous(), "tensors must be contiguous float64"
+        return C.c_void_p(a.data_ptr())
+    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return C.c_void_p(a.ctypes.data)
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def default_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    load().gmrf_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def prior_desc(prior: dict) -> PriorDesc:
+    d = PriorDesc()
+    d.kind = KIND[prior["kind"]]
+    d.nx, d.ny, d.nt = (int(v) for v in prior["n"])
+    for i in range(3):
+        d.lo[i] = float(prior["lo"][i])
+        d.hi[i] = float(prior["hi"][i])
+    for k in ("kappa", "tau", "nu", "cx", "cy", "kappa0", "eps2"):
+        setattr(d, k, float(prior[k]))
+    return d
+
+
+class Prior:
+    def __init__(self, prior: dict, stream=None):
+        lib = load()
+        self._desc = prior_desc(prior)
+        self.spec = prior
+        h = C.c_void_p()
+        s = C.c_void_p(stream.cuda_stream if stream is not None else 0)
+        _check(lib.gmrf_build_prior(C.byref(self._desc), s, C.byref(h)))
+        self.h = h
+
+    @property
+    def N(self) -> int:
+        return int(load().gmrf_num_unknowns(self.h))
+
+    @property
+    def levels(self) -> int:
+        return int(load().gmrf_num_levels(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gmrf_prior_destroy(self.h)
+            self.h = None
+
+
+class Posterior:
+    def __init__(self, prior: Prior, obs: dict):
+        lib = load()
+        self.prior = prior
+        self._keep = []
+        o = ObsDesc()
+        coords = np.ascontiguousarray(obs["coords"], dtype=np.float64)
+        y = np.ascontiguousarray(obs["y"], dtype=np.float64)
+        sigma = np.ascontiguousarray(obs["sigma"], dtype=np.float64)
+        o.m = len(y)
+        o.coords, o.y, o.sigma = _dptr(coords), _dptr(y), _dptr(sigma)
+        self._keep += [coords, y, sigma]
+        if obs.get("ic_sigma") is not None:
+            o.ic = 1
+            o.ic_sigma = float(obs["ic_sigma"])
+            if obs.get("ic_values") is not None:
+                icv = np.ascontiguousarray(obs["ic_values"], dtype=np.float64)
+                self._keep.append(icv)
+                o.ic_values = _dptr(icv)
+        if obs.get("colloc_sigma") is not None:
+            o.colloc = 1 if obs.get("colloc_c") is not None else 2
+            o.colloc_sigma = float(obs["colloc_sigma"])
+            o.colloc_c = float(obs.get("colloc_c") or 0.0)
+            o.colloc_nu = float(obs.get("burgers_nu", prior.spec["nu"]))
+            if obs.get("colloc_f") is not None:
+                f = np.ascontiguousarray(obs["colloc_f"], dtype=np.float64)
+                self._keep.append(f)
+                o.colloc_f = _dptr(f)
+        h = C.c_void_p()
+        _check(lib.gmrf_condition(prior.h, C.byref(o), C.byref(h)))
+        self.h = h
+        self.m = len(y)
+
+    @property
+    def N(self) -> int:
+        return self.prior.N
+
+    def update_data(self, y):
+        _check(load().gmrf_update_data(self.h, _ptr(y)))
+
+    def solve_mean(self, out=None, opts=None):
+        out = np.empty(self.N) if out is None else out
+        info = SolveInfo()
+        _check(load().gmrf_solve_mean(self.h, _ptr(out), C.byref(opts or default_opts()), C.byref(info)))
+        return out, info.as_dict()
+
+    def sample(self, ns, seed, mean=True, out=None, mean_out=None, opts=None):
+        x = np.empty((ns, self.N)) if out is None else out
+        mu = (np.empty(self.N) if mean_out is None else mean_out) if mean else None
+        info = SolveInfo()
+        _check(load().gmrf_sample(self.h, ns, seed, _ptr(mu), _ptr(x), C.byref(opts or default_opts()), C.byref(info)))
+        return mu, x, info.as_dict()
+
+    def marginal_var(self, ns, seed, mean=True, stderr=True, out=None, opts=None):
+        var = np.empty(self.N) if out is None else out
+        mu = np.empty(self.N) if mean else None
+        se = np.empty(self.N) if stderr else None
+        info = SolveInfo()
+        _check(load().gmrf_marginal_var(self.h, ns, seed, _ptr(mu), _ptr(var), _ptr(se),
+                                        C.byref(opts or default_opts()), C.byref(info)))
+        return mu, var, se, info.as_dict()
+
+    def gauss_newton_step(self, mu_k, delta_prev, opts=None):
+        dec = C.c_double()
+        alpha = C.c_double()
+        info = SolveInfo()
+        _check(load().gmrf_gauss_newton_step(self.h, _ptr(mu_k), _ptr(delta_prev), C.byref(dec), C.byref(alpha),
+                                             C.byref(opts or default_opts()), C.byref(info)))
+        return dec.value, alpha.value, info.as_dict()
+
+    def loglik_grad(self, nprobes, seed, opts=None):
+        ll = C.c_double()
+        g = np.zeros(5)
+        se = np.zeros(5)
+        info = SolveInfo()
+        _check(load().gmrf_loglik_grad(self.h, nprobes, seed, C.byref(ll), _dptr(g), _dptr(se),
+                                       C.byref(opts or default_opts()), C.byref(info)))
+        return ll.value, g, se, info.as_dict()
+
+    def apply(self, x):
+        x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+        y = np.empty_like(x)
+        _check(load().gmrf_apply_posterior(self.h, x.shape[0], _ptr(x), _ptr(y)))
+        return y
+
+    def time_apply(self, k, iters=20) -> float:
+        ms = C.c_double()
+        _check(load().gmrf_time_apply(self.h, k, iters, C.byref(ms)))
+        return ms.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gmrf_posterior_destroy(self.h)
+            self.h = None
+
+
+def normals(seed, stream, sample0, count, n):
+    out = np.empty((count, n))
+    _check(load().gmrf_normals(seed, stream, sample0, count, n, _ptr(out)))
+    return out
