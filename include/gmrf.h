@@ -23,6 +23,8 @@
  *  - Vectors over the unknowns are ordered lexicographically,
  *    index ((t * ny + y) * nx + x), FP64.  Batches of vectors are
  *    [count][N], row-major.
+ *  - Handles may be destroyed in any order: a prior stays alive until its
+ *    own handle and every posterior built on it are destroyed.
  *  - Handles own all device scratch.  Scratch for a batch of k right-hand
  *    sides is allocated at the first call that needs k and reused after.
  */
@@ -106,7 +108,7 @@ typedef struct gmrf_obs_desc {
 } gmrf_obs_desc;
 
 typedef struct gmrf_solve_opts {
-    double rtol;               /* per-RHS ||b - Q_u|y x|| / ||b|| target, FP64 (default 1e-8) */
+    double rtol;               /* per-RHS ||b - Q_u|y x|| / ||b|| target, FP64 (default 1e-10) */
     int32_t max_refine;        /* FP64 refinement steps (default 12) */
     int32_t max_inner;         /* inner PCG iterations per refinement step (default 40) */
     double inner_rtol;         /* inner relative residual reduction (default 1e-3) */
@@ -197,10 +199,13 @@ gmrf_status gmrf_apply_posterior(gmrf_posterior* post, int32_t k, const double* 
 gmrf_status gmrf_normals(uint64_t seed, int32_t stream, int32_t sample0, int32_t count, int64_t n,
                          double* out);
 
-/* Average duration in milliseconds of the fused FP32 Q_u|y apply over `iters`
- * launches on the handle's stream, for a batch of k right-hand sides
- * (CUDA events around the launches). */
-gmrf_status gmrf_time_apply(gmrf_posterior* post, int32_t k, int32_t iters, double* ms);
+/* Average duration in milliseconds of one launch of the fused FP32 stencil
+ * kernel on the finest level, over `iters` launches on the handle's stream
+ * (CUDA events around the launches), for a batch of k right-hand sides of
+ * random data.  kernel: 0 = apply (y = Q_u|y x), 1 = residual
+ * (r = b - Q_u|y x), 2 = Chebyshev smoothing step
+ * (d' = c1 d + c2 D^-1 (b - Q_u|y x), x' = x + d'). */
+gmrf_status gmrf_time_stencil(gmrf_posterior* post, int32_t kernel, int32_t k, int32_t iters, double* ms);
 
 /* Number of kernels this library has launched in the process so far
  * (kernels inside replayed CUDA graphs included). */

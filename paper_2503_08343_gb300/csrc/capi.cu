@@ -1,5 +1,6 @@
 // C ABI of the GMRF solver (declared in include/gmrf.h).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -10,11 +11,20 @@
 
 using namespace gmrf;
 
+// A prior lives while its handle or any posterior built on it is alive, so
+// the handles may be destroyed in any order.
 struct gmrf_prior {
     Prior impl;
     cudaStream_t user = 0;   // unused: work runs on impl.stream
     bool own = false;        // impl.stream created by the library
+    std::atomic<int> refs{1};
 };
+
+static void prior_release(gmrf_prior* p) {
+    if (p->refs.fetch_sub(1) != 1) return;
+    if (p->own && p->impl.stream) cudaStreamDestroy(p->impl.stream);
+    delete p;
+}
 
 struct gmrf_posterior {
     Posterior impl;
@@ -100,7 +110,7 @@ extern "C" {
 
 void gmrf_default_opts(gmrf_solve_opts* o) {
     if (!o) return;
-    o->rtol = 1e-8;
+    o->rtol = 1e-10;
     o->max_refine = 12;
     o->max_inner = 40;
     o->inner_rtol = 1e-3;
@@ -140,6 +150,7 @@ gmrf_status gmrf_build_prior(const gmrf_prior_desc* desc, void* stream, gmrf_pri
         if (st) require(d.kappa0 > 0 && d.nu >= 0, "space-time priors need kappa0 > 0, nu >= 0");
         else require(d.kappa > 0, "kappa must be positive");
         require((long long)d.nx * d.ny * d.nt < (1LL << 31), "grid too large for 32-bit node indices");
+        require(d.nx < 32768 && d.ny < 32768 && d.nt < 32768, "axes are limited to 32767 nodes");
         gmrf_prior* p = new gmrf_prior();
         p->impl.desc = d;
         p->impl.geo = geometry_of(d);
@@ -165,9 +176,7 @@ int64_t gmrf_num_unknowns(const gmrf_prior* p) { return p ? (int64_t)p->impl.lev
 int32_t gmrf_num_levels(const gmrf_prior* p) { return p ? (int32_t)p->impl.levels.size() : 0; }
 
 void gmrf_prior_destroy(gmrf_prior* p) {
-    if (!p) return;
-    if (p->own && p->impl.stream) cudaStreamDestroy(p->impl.stream);
-    delete p;
+    if (p) prior_release(p);
 }
 
 static void rebuild_bdata(Posterior& P, cudaStream_t s) {
@@ -188,11 +197,13 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
         require(obs->m < (1LL << 30), "too many observations");
         post = new gmrf_posterior();
         post->prior = prior;
+        prior->refs.fetch_add(1);
         Posterior& P = post->impl;
         P.prior = &prior->impl;
         P.levels = prior->impl.levels;
         for (Level& L : P.levels) {   // device members are per posterior
             L.d_obs = nullptr; L.d_tile_ptr = nullptr; L.d_tile_idx = nullptr;
+            L.d_omap = nullptr; L.d_oent32 = nullptr; L.d_oent64 = nullptr;
         }
         const int dimc = d.kind == GMRF_ADVDIFF_ST_2D ? 3 : 2;
         P.m = obs->m;
@@ -294,7 +305,9 @@ void gmrf_posterior_destroy(gmrf_posterior* post) {
     dev_free(P.d_bdata);
     dev_free(P.d_ypoint);
     dev_free(P.d_bstatic);
+    gmrf_prior* pr = post->prior;
     delete post;
+    if (pr) prior_release(pr);
 }
 
 gmrf_status gmrf_update_data(gmrf_posterior* post, const double* y) {
@@ -484,11 +497,11 @@ gmrf_status gmrf_normals(uint64_t seed, int32_t stream, int32_t sample0, int32_t
     });
 }
 
-gmrf_status gmrf_time_apply(gmrf_posterior* post, int32_t k, int32_t iters, double* ms) {
+gmrf_status gmrf_time_stencil(gmrf_posterior* post, int32_t kernel, int32_t k, int32_t iters, double* ms) {
     return guard([&] {
-        require(post && k >= 1 && iters >= 1 && ms, "bad argument");
+        require(post && k >= 1 && iters >= 1 && ms && kernel >= 0 && kernel <= 2, "bad argument");
         enter(post->prior);
-        *ms = time_apply(post->impl, (k + 3) / 4, iters, post->prior->impl.stream);
+        *ms = time_stencil(post->impl, kernel, (k + 3) / 4, iters, post->prior->impl.stream);
     });
 }
 

@@ -40,6 +40,17 @@ template <> struct Geo<GEO_XY>  { static constexpr int TX = 32, TY = 8, TT = 1, 
 template <> struct Geo<GEO_XT>  { static constexpr int TX = 32, TY = 1, TT = 8, HY = 0, HT = 1; };
 template <> struct Geo<GEO_XYT> { static constexpr int TX = 16, TY = 4, TT = 4, HY = 2, HT = 1; };
 
+// Offsets of the observation stencil A^T R^-1 A: all (dx, dy, dt) in
+// {-1, 0, 1} over the axes the geometry has (9 points in 2D, 27 in 3D).
+template <int GEO> struct ObsStencil;
+template <> struct ObsStencil<GEO_XY>  { static constexpr int OC = 9; };
+template <> struct ObsStencil<GEO_XT>  { static constexpr int OC = 9; };
+template <> struct ObsStencil<GEO_XYT> { static constexpr int OC = 27; };
+__host__ __device__ constexpr int obs_dx(int, int a) { return a % 3 - 1; }
+__host__ __device__ constexpr int obs_dy(int geo, int a) { return geo == GEO_XT ? 0 : (a / 3) % 3 - 1; }
+__host__ __device__ constexpr int obs_dt(int geo, int a) { return geo == GEO_XY ? 0 : (geo == GEO_XT ? a / 3 - 1 : a / 9 - 1); }
+inline int obs_oc(int g) { return g == GEO_XYT ? 27 : 9; }
+
 inline int geo_tx(int g) { return g == GEO_XY ? 32 : (g == GEO_XT ? 32 : 16); }
 inline int geo_ty(int g) { return g == GEO_XY ? 8 : (g == GEO_XT ? 1 : 4); }
 inline int geo_tt(int g) { return g == GEO_XY ? 1 : (g == GEO_XT ? 8 : 4); }
@@ -89,18 +100,21 @@ __device__ __forceinline__ double philox_rademacher(uint64_t seed, uint32_t samp
 }
 
 // ---------------------------------------------------------------------------
-// Block reduction of four FP64 partial sums (one per right-hand side of the
-// block) over a 256-thread CTA; thread 0 receives the totals.
+// Block reduction of four partial sums (one per right-hand side of the
+// block) over a 256-thread CTA; threads 0..3 write the totals as FP64.
+// Every thread of the CTA must call it.  FP32
+// kernels accumulate in FP32 inside the CTA (the FP64 pipe of GB300 is
+// narrow) and widen the CTA totals.
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename A> __device__ __forceinline__ A warp_sum(A v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-template <int NT>
-__device__ __forceinline__ void block_sum4(double v[4], double* out /* 4 doubles, global */) {
-    __shared__ double red[NT / 32][4];
+template <int NT, typename A>
+__device__ __forceinline__ void block_sum4(A v[4], double* out /* 4 doubles, global */) {
+    __shared__ A red[NT / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = warp_sum(v[i]);
@@ -112,9 +126,10 @@ __device__ __forceinline__ void block_sum4(double v[4], double* out /* 4 doubles
     if (threadIdx.x < 4) {
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < NT / 32; ++w) s += (double)red[w][threadIdx.x];
         out[threadIdx.x] = s;
     }
+    __syncthreads();   // the scratch may be reused by the next call
 }
 
 }  // namespace gmrf

@@ -49,6 +49,7 @@ void build_hierarchy(const gmrf_prior_desc& d, std::vector<Level>& levels);
 void build_level_obs(const gmrf_prior_desc& d, const Posterior& P, const std::vector<double>& coords,
                      const std::vector<double>& rinv, Level& L, bool fine);
 void build_transfer(Level& f, const Level& c);
+void build_obs_stencil(Level& L);
 std::vector<double> dense_operator(const Level& L, const double* mu);
 bool spd_inverse(std::vector<double>& A, int n);
 
@@ -70,7 +71,7 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
 void apply64(Posterior& P, int nblk, const double* x64, double* y64, cudaStream_t s);
 Workspace& workspace(Posterior& P, int nblk);
 void workspace_free(Workspace* w);
-double time_apply(Posterior& P, int nblk, int iters, cudaStream_t s);
+double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s);
 
 // scratch of one batch size
 struct Workspace {

@@ -18,6 +18,7 @@ namespace gmrf {
 // and its global row index (for the Philox draws of perturbation samples).
 struct ObsRow {
     int32_t node[8];
+    int16_t ox[8], oy[8], ot[8];   // grid coordinates of the nodes
     double wd[8];
     float wf[8];
     double rinv;
@@ -53,6 +54,12 @@ struct LevelView {
     const ObsRow* obs;
     const int32_t* tile_ptr;
     const int32_t* tile_idx;
+    // A^T R^-1 A as a per-node 3^k-point stencil in tile-local tables:
+    // omap[tile][node in tile] = entry index or -1, oent[tile][entry][OC]
+    const int16_t* omap;
+    const T* oent;
+    int ocap;          // entries per tile (0: no observation rows)
+    int ostride;       // bytes per tile of oent (multiple of 16)
 };
 
 struct Level {
@@ -70,6 +77,11 @@ struct Level {
     int32_t* d_tile_ptr = nullptr;
     int32_t* d_tile_idx = nullptr;
     std::vector<ObsRow> h_obs;
+    int16_t* d_omap = nullptr;
+    float* d_oent32 = nullptr;
+    double* d_oent64 = nullptr;
+    int ocap = 0;
+    int ostride32 = 0, ostride64 = 0;
     // linearisation point on this level (Burgers), device
     float* d_mu32 = nullptr;
     double* d_mu64 = nullptr;

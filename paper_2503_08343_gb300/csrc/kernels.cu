@@ -9,8 +9,12 @@
 // tile from a per-tile list, and finishes with a mode-specific epilogue.
 // All traffic is HBM-bound (about 3 flop per byte), so nothing here uses
 // tensor cores.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <map>
+#include <stdexcept>
+#include <string>
 
 #include "kernels.h"
 
@@ -30,6 +34,10 @@ unsigned long long capture_end() { g_capturing = false; return g_captured; }
 void note_graph_launch(unsigned long long kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(); }
 
+static void cuda_ok(cudaError_t e) {
+    if (e != cudaSuccess) throw std::runtime_error(std::string("kernel setup: ") + cudaGetErrorString(e));
+}
+
 
 template <typename T> LevelView<T> Level::view() const {
     LevelView<T> v;
@@ -45,6 +53,10 @@ template <typename T> LevelView<T> Level::view() const {
     v.obs = d_obs;
     v.tile_ptr = d_tile_ptr;
     v.tile_idx = d_tile_idx;
+    v.omap = d_omap;
+    if constexpr (sizeof(T) == 4) { v.oent = d_oent32; v.ostride = ostride32; }
+    else { v.oent = d_oent64; v.ostride = ostride64; }
+    v.ocap = d_omap ? ocap : 0;
     return v;
 }
 
@@ -76,219 +88,426 @@ __device__ __forceinline__ void jcoef(const Colloc& c, T mu_c, T mu_l, T mu_r, T
 
 // ---------------------------------------------------------------------------
 // fused posterior-precision stencil
+//
+// Persistent grid: CTA c walks the work units u = c, c + G, ... where a unit
+// is one (tile, block of four right-hand sides) pair, u = blk * ntiles + tile.
+// A cp.async pipeline of NS stages keeps the next units' input tiles (with
+// halo), right-hand sides, directions and inverse diagonals in flight while
+// the current unit runs its B / B^T / observation phases.
 
-template <int GEO, typename T, int MODE, int COL>
-__global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 8 : 0));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <typename T> __device__ __forceinline__ void cp_v4(V4<T>* smem, const T* gmem, bool pred) {
+    cp_async16(smem, gmem, pred);
+    if (sizeof(T) == 8) cp_async16(reinterpret_cast<char*>(smem) + 16, reinterpret_cast<const char*>(gmem) + 16, pred);
+}
+template <typename T> __device__ __forceinline__ void cp_scalar(T* smem, const T* gmem, bool pred) {
+    if (sizeof(T) == 8) cp_async8(smem, gmem, pred);
+    else cp_async4(smem, gmem, pred);
+}
+
+template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct StencilSmem {
     using G = Geo<GEO>;
-    constexpr int TX = G::TX, TY = G::TY, TT = G::TT, HY = G::HY, HT = G::HT;
-    constexpr int PX = TX + 4, PY = TY + 2 * HY, PT = TT + 2 * HT;
-    constexpr int SX = TX + 2, SY = TY + HY, ST = TT + HT;
+    static constexpr int TX = G::TX, TY = G::TY, TT = G::TT, HY = G::HY, HT = G::HT;
+    static constexpr int PX = TX + 4, PY = TY + 2 * HY, PT = TT + 2 * HT;
+    static constexpr int SX = TX + 2, SY = TY + HY, ST = TT + HT;
+    static constexpr int TN = TX * TY * TT, PN = PX * PY * PT, SN = SX * SY * ST;
+    static constexpr int NB = MODE == M_APPLY ? 1 : NS;
+    static constexpr int ND = MODE == M_CHEB ? NS : 1;
+    V4<T> p[NS][PN][KB];
+    V4<T> b[NB][TN][KB];
+    V4<T> d[ND][TN][KB];
+    V4<T> s[SN][KB];
+    V4<T> sj[COL ? SN : 1][KB];
+    T dinv[ND][TN];
+    T mu[COL == 2 ? NS : 1][COL == 2 ? PN : 1];
+};
+
+// Flat shared-memory offsets of the taps: in the staged input (row r reads
+// p at r + o) and in the s tile (node i gathers s at row i - o).
+template <int PX, int PY> __host__ __device__ constexpr int poff(int o) { return (tap_dt(o) * PY + tap_dy(o)) * PX + tap_dx(o); }
+template <int SX, int SY> __host__ __device__ constexpr int soff(int o) { return -((tap_dt(o) * SY + tap_dy(o)) * SX + tap_dx(o)); }
+
+// Position of a work unit: tile coordinates (tx, ty, tt) in tile units and
+// the block group.  Units advance by the grid size G with carry-adds only
+// (no integer division inside the unit loop).
+struct UnitPos {
+    int tx, ty, tt, grp;
+};
+__device__ __forceinline__ UnitPos unit_decompose(long long u, int tiles_x, int tiles_y, int tiles_t) {
+    UnitPos p;
+    const long long ntiles = (long long)tiles_x * tiles_y * tiles_t;
+    p.grp = (int)(u / ntiles);
+    const long long tile = u - (long long)p.grp * ntiles;
+    p.tx = (int)(tile % tiles_x);
+    const long long r = tile / tiles_x;
+    p.ty = (int)(r % tiles_y);
+    p.tt = (int)(r / tiles_y);
+    return p;
+}
+__device__ __forceinline__ void unit_advance(UnitPos& p, const UnitPos& d, int tiles_x, int tiles_y, int tiles_t) {
+    p.tx += d.tx;
+    if (p.tx >= tiles_x) { p.tx -= tiles_x; ++p.ty; }
+    p.ty += d.ty;
+    if (p.ty >= tiles_y) { p.ty -= tiles_y; ++p.tt; }
+    p.tt += d.tt;
+    if (p.tt >= tiles_t) { p.tt -= tiles_t; ++p.grp; }
+    p.grp += d.grp;
+}
+
+// One work unit is (tile, group of KB consecutive blocks of four right-hand
+// sides): all per-node index work, staging addresses and checks are shared
+// by the 4 KB right-hand sides of the group.
+template <int GEO, typename T, int MODE, int COL, int NS, int KB>
+__global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nunits) {
+    using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
+    constexpr int TX = SM::TX, TY = SM::TY, TT = SM::TT, HY = SM::HY, HT = SM::HT;
+    constexpr int PX = SM::PX, PY = SM::PY, PN = SM::PN, TN = SM::TN;
+    constexpr int SX = SM::SX, SY = SM::SY, SN = SM::SN;
     constexpr int HYS = HY / 2;
-    static_assert(SX * SY * ST >= TX * TY * TT, "q staging aliases the s tile");
-    __shared__ V4<T> sp[PT][PY][PX];
-    __shared__ V4<T> ss[ST][SY][SX];
-    __shared__ V4<T> sj[COL ? ST : 1][COL ? SY : 1][COL ? SX : 1];
-    __shared__ T smu[COL == 2 ? PT : 1][COL == 2 ? PY : 1][COL == 2 ? PX : 1];
+    constexpr int OC = ObsStencil<GEO>::OC;
+    constexpr int KP = (PN + 255) / 256, KS = (SN + 255) / 256;
+    static_assert(SN >= TN, "s tile covers the node tile");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SM& S = *reinterpret_cast<SM*>(smem_raw);
 
     const LevelView<T>& L = A.L;
     const int nx = L.nx, ny = L.ny, nt = L.nt;
-    const long long N = L.N;
-    const int tile = blockIdx.x, blk = blockIdx.y, tid = threadIdx.x;
-    const int tx0 = (tile % L.tiles_x) * TX;
-    const int rest = tile / L.tiles_x;
-    const int ty0 = (rest % L.tiles_y) * TY;
-    const int tt0 = (rest / L.tiles_y) * TT;
-    const T* xb = A.x + (size_t)blk * N * RW;
-
-    // 1. stage the input tile with halo
-    for (int e = tid; e < PX * PY * PT; e += 256) {
-        const int px = e % PX, py = (e / PX) % PY, pt = e / (PX * PY);
-        const int gx = tx0 - 2 + px, gy = ty0 - HY + py, gt = tt0 - HT + pt;
-        const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gt >= 0 && gt < nt;
-        const long long node = ((long long)gt * ny + gy) * nx + gx;
-        sp[pt][py][px] = in ? v4load(xb + node * RW) : v4zero<T>();
-        if (COL == 2) smu[COL == 2 ? pt : 0][COL == 2 ? py : 0][COL == 2 ? px : 0] = in ? L.mu[node] : T(0);
-    }
-    __syncthreads();
-
-    // 2. s = B p (Dirichlet columns masked) and sj = J p on the ring-extended tile
-    for (int e = tid; e < SX * SY * ST; e += 256) {
-        const int sx = e % SX, sy = (e / SX) % SY, st = e / (SX * SY);
-        const int rx = tx0 - 1 + sx, ry = ty0 - HYS + sy, rt = tt0 + st;
-        const bool inrow = rx >= 0 && rx < nx && ry >= 0 && ry < ny && rt < nt;
-        V4<T> s = v4zero<T>();
-        if (inrow && !is_dirichlet(rx, ry, nx, ny)) {
-            const int cls = (nt > 1 && rt == 0) ? 1 : 0;
-#pragma unroll
-            for (int o = 0; o < NTAP; ++o) {
-                if (HY == 0 && tap_dy(o) != 0) continue;
-                if (HT == 0 && tap_dt(o) != 0) continue;
-                const T c = L.cf[cls][o];
-                const int qx = rx + tap_dx(o), qy = ry + tap_dy(o), qt = rt + tap_dt(o);
-                if (c == T(0) || is_dirichlet(qx, qy, nx, ny)) continue;
-                s = fma4(c, sp[qt - tt0 + HT][qy - ty0 + HY][qx - tx0 + 2], s);
-            }
-        }
-        ss[st][sy][sx] = s;
-        if (COL) {
-            V4<T> sjv = v4zero<T>();
-            if (inrow && rx >= 1 && rx <= nx - 2 && rt >= 1) {
-                const int px = rx - tx0 + 2, pt = rt - tt0 + HT;
-                T cC, cL, cR;
-                if (COL == 2)
-                    jcoef<T, COL>(L.col, smu[COL == 2 ? pt : 0][0][COL == 2 ? px : 0],
-                                  smu[COL == 2 ? pt : 0][0][COL == 2 ? px - 1 : 0],
-                                  smu[COL == 2 ? pt : 0][0][COL == 2 ? px + 1 : 0], cC, cL, cR);
-                else
-                    jcoef<T, COL>(L.col, T(0), T(0), T(0), cC, cL, cR);
-                sjv = cC * sp[pt][0][px];
-                sjv = fma4(cL, sp[pt][0][px - 1], sjv);
-                sjv = fma4(cR, sp[pt][0][px + 1], sjv);
-                sjv = fma4((T)(-L.col.inv_dt), sp[pt - 1][0][px], sjv);
-            }
-            sj[COL ? st : 0][0][COL ? sx : 0] = sjv;
-        }
-    }
-    __syncthreads();
-
-    // 3. q = B^T s (+ J^T Q_eps sj) at the thread's own node
+    const int N = (int)L.N;
+    const int nblk = A.nblk;
+    const int ntiles = L.tiles_x * L.tiles_y * L.tiles_t;
+    const int tid = threadIdx.x;
     const int lx = tid % TX, ly = (tid / TX) % TY, lt = tid / (TX * TY);
-    const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
-    const bool own = gx < nx && gy < ny && gt < nt;
-    const V4<T> pown = sp[lt + HT][ly + HY][lx + 2];
-    V4<T> q = v4zero<T>();
-    if (own) {
-        if (is_dirichlet(gx, gy, nx, ny)) {
-            q = L.inv_eps2 * pown;
-        } else {
+    const int G = gridDim.x;
+    const bool has_obs = L.ocap > 0;
+    const int ostage = TN * 2 + L.ostride;     // bytes of one stage of observation tables
+    unsigned char* obs_smem = smem_raw + sizeof(SM);
+
+    T c0[NTAP], c1[NTAP];
 #pragma unroll
-            for (int o = 0; o < NTAP; ++o) {
-                if (HY == 0 && tap_dy(o) != 0) continue;
-                if (HT == 0 && tap_dt(o) != 0) continue;
-                const int rt = gt - tap_dt(o);
-                const int cls = (nt > 1 && rt == 0) ? 1 : 0;
-                const T c = L.cf[cls][o];
-                if (c == T(0)) continue;
-                q = fma4(c, ss[lt - tap_dt(o)][ly + HYS - tap_dy(o)][lx + 1 - tap_dx(o)], q);
+    for (int o = 0; o < NTAP; ++o) { c0[o] = L.cf[0][o]; c1[o] = L.cf[1][o]; }
+    auto tap_used = [](int o) { return !(HY == 0 && tap_dy(o) != 0) && !(HT == 0 && tap_dt(o) != 0); };
+
+    // per-thread geometry of the staged items and the s items (same every unit)
+    int p_dx[KP], p_dy[KP], p_dt[KP], p_rel[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+        const int e = tid + 256 * k;
+        const int px = e % PX, py = (e / PX) % PY, pt = e / (PX * PY);
+        p_dx[k] = px - 2; p_dy[k] = py - HY; p_dt[k] = pt - HT;
+        p_rel[k] = (p_dt[k] * ny + p_dy[k]) * nx + p_dx[k];
+    }
+    int s_dx[KS], s_dy[KS], s_dt[KS], s_base[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+        const int e = tid + 256 * k;
+        const int sx = e % SX, sy = (e / SX) % SY, stt = e / (SX * SY);
+        s_dx[k] = sx - 1; s_dy[k] = sy - HYS; s_dt[k] = stt;
+        s_base[k] = ((stt + HT) * PY + (sy + HY - HYS)) * PX + (sx + 1);
+    }
+    const int pbase = ((lt + HT) * PY + (ly + HY)) * PX + (lx + 2);
+    const int sbase = (lt * SY + (ly + HYS)) * SX + (lx + 1);
+
+    if (A.partial != nullptr)
+        for (int i = tid; i < nblk * 4; i += 256) A.partial[((size_t)(i >> 2) * G + blockIdx.x) * 4 + (i & 3)] = 0.0;
+
+    const int tiles_x = L.tiles_x, tiles_y = L.tiles_y, tiles_t = L.tiles_t;
+    const int ngroups = (nblk + KB - 1) / KB;
+    const UnitPos dG = unit_decompose(G, tiles_x, tiles_y, tiles_t);
+
+    auto issue = [&](const UnitPos& P, int st) {
+        if (P.grp < ngroups) {
+            const int grp = P.grp;
+            const int tile = (P.tt * tiles_y + P.ty) * tiles_x + P.tx;
+            const int tx0 = P.tx * TX, ty0 = P.ty * TY, tt0 = P.tt * TT;
+            const int tbase = (tt0 * ny + ty0) * nx + tx0;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const int e = tid + 256 * k;
+                if (KP * 256 > PN && e >= PN) break;
+                const int gx = tx0 + p_dx[k], gy = ty0 + p_dy[k], gt = tt0 + p_dt[k];
+                const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gt >= 0 && gt < nt;
+                const int node = in ? tbase + p_rel[k] : 0;
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    const int blk = grp * KB + j;
+                    const bool ok = in && blk < nblk;
+                    cp_v4<T>(&S.p[st][e][j], A.x + ((size_t)(ok ? blk : 0) * N + node) * RW, ok);
+                }
+                if (COL == 2) cp_scalar<T>(&S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0], L.mu + node, in);
+            }
+            const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
+            const bool own = gx < nx && gy < ny && gt < nt;
+            const int node = own ? (gt * ny + gy) * nx + gx : 0;
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                const int blk = grp * KB + j;
+                const bool ok = own && blk < nblk;
+                const size_t off = ((size_t)(ok ? blk : 0) * N + node) * RW;
+                if (MODE != M_APPLY) cp_v4<T>(&S.b[MODE != M_APPLY ? st : 0][tid][j], A.b + off, ok);
+                if (MODE == M_CHEB && A.d != nullptr) cp_v4<T>(&S.d[MODE == M_CHEB ? st : 0][tid][j], A.d + off, ok);
+            }
+            if (MODE == M_CHEB) cp_scalar<T>(&S.dinv[MODE == M_CHEB ? st : 0][tid], A.dinv + node, own);
+            if (has_obs) {
+                unsigned char* dst = obs_smem + (size_t)st * ostage;
+                const unsigned char* gmap = reinterpret_cast<const unsigned char*>(L.omap + (size_t)tile * TN);
+                const unsigned char* gent = reinterpret_cast<const unsigned char*>(L.oent) + (size_t)tile * L.ostride;
+                for (int c = tid; c < TN * 2 / 16; c += 256) cp_async16(dst + c * 16, gmap + c * 16, true);
+                for (int c = tid; c < L.ostride / 16; c += 256) cp_async16(dst + TN * 2 + c * 16, gent + c * 16, true);
             }
         }
-        if (COL) {
-            // rows touching this column: itself (centre), x-1 row (its x+1 tap),
-            // x+1 row (its x-1 tap), t+1 row (its t-1 tap)
-            const int px = lx + 2, pt = lt + HT;
-            T cC, cL, cR, tC, tL, tR;
-            V4<T> acc = v4zero<T>();
-            const T m0 = COL == 2 ? smu[COL == 2 ? pt : 0][0][COL == 2 ? px : 0] : T(0);
-            const T mm1 = COL == 2 ? smu[COL == 2 ? pt : 0][0][COL == 2 ? px - 1 : 0] : T(0);
-            const T mp1 = COL == 2 ? smu[COL == 2 ? pt : 0][0][COL == 2 ? px + 1 : 0] : T(0);
-            const T mm2 = COL == 2 ? smu[COL == 2 ? pt : 0][0][COL == 2 ? px - 2 : 0] : T(0);
-            const T mp2 = COL == 2 ? smu[COL == 2 ? pt : 0][0][COL == 2 ? px + 2 : 0] : T(0);
-            jcoef<T, COL>(L.col, m0, mm1, mp1, cC, cL, cR);
-            acc = cC * sj[COL ? lt : 0][0][COL ? lx + 1 : 0];
-            jcoef<T, COL>(L.col, mm1, mm2, m0, tC, tL, tR);     // row x-1
-            acc = fma4(tR, sj[COL ? lt : 0][0][COL ? lx : 0], acc);
-            jcoef<T, COL>(L.col, mp1, m0, mp2, tC, tL, tR);     // row x+1
-            acc = fma4(tL, sj[COL ? lt : 0][0][COL ? lx + 2 : 0], acc);
-            acc = fma4((T)(-L.col.inv_dt), sj[COL ? lt + 1 : 0][0][COL ? lx + 1 : 0], acc);
-            q = fma4((T)L.col.qeps, acc, q);
-        }
-    }
-    __syncthreads();
+        cp_commit();
+    };
 
-    // 4. observation rows of this tile: A^T R^-1 A p, scattered in shared memory
-    if (L.obs != nullptr) {
-        const int k0 = L.tile_ptr[tile], k1 = L.tile_ptr[tile + 1];
-        if (k1 > k0) {
-            V4<T>* sq = &ss[0][0][0];
-            sq[tid] = q;
-            __syncthreads();
-            for (int k = k0 + tid; k < k1; k += 256) {
-                const ObsRow& o = L.obs[L.tile_idx[k]];
-                int li[8];
-                V4<T> a = v4zero<T>();
-                for (int n = 0; n < o.nn; ++n) {
-                    const long long nd = o.node[n];
-                    const int ox = (int)(nd % nx);
-                    const long long r2 = nd / nx;
-                    const int oy = (int)(r2 % ny), ot = (int)(r2 / ny);
-                    a = fma4(obs_w<T>(o, n), sp[ot - tt0 + HT][oy - ty0 + HY][ox - tx0 + 2], a);
-                    const int ux = ox - tx0, uy = oy - ty0, ut = ot - tt0;
-                    li[n] = (ux >= 0 && ux < TX && uy >= 0 && uy < TY && ut >= 0 && ut < TT) ? (ut * TY + uy) * TX + ux : -1;
-                }
-                a = obs_rinv<T>(o) * a;
-                for (int n = 0; n < o.nn; ++n) {
-                    if (li[n] < 0) continue;
-                    const T w = obs_w<T>(o, n);
-                    T* dst = reinterpret_cast<T*>(&sq[li[n]]);
-                    atomicAdd(dst + 0, w * a.a);
-                    atomicAdd(dst + 1, w * a.b);
-                    atomicAdd(dst + 2, w * a.c);
-                    atomicAdd(dst + 3, w * a.d);
+    UnitPos cur = unit_decompose(blockIdx.x, tiles_x, tiles_y, tiles_t);
+    UnitPos ahead = cur;
+#pragma unroll 1
+    for (int k = 0; k < NS - 1; ++k) {
+        issue(ahead, k);
+        unit_advance(ahead, dG, tiles_x, tiles_y, tiles_t);
+    }
+
+    T dacc[KB][4];
+#pragma unroll
+    for (int j = 0; j < KB; ++j) dacc[j][0] = dacc[j][1] = dacc[j][2] = dacc[j][3] = T(0);
+    int st = 0;
+#pragma unroll 1
+    while (cur.grp < ngroups) {
+        issue(ahead, st == 0 ? NS - 1 : st - 1);
+        unit_advance(ahead, dG, tiles_x, tiles_y, tiles_t);
+        cp_wait<NS - 1>();
+        __syncthreads();
+        const int grp = cur.grp;
+        const int tx0 = cur.tx * TX, ty0 = cur.ty * TY, tt0 = cur.tt * TT;
+        const V4<T>(*sp)[KB] = S.p[st];
+        auto smu = [&](int e) -> T { return COL == 2 ? S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0] : T(0); };
+
+        // s = B p on the rows of the tile plus a one-node ring.  Dirichlet rows
+        // are zero; rows next to the boundary skip the Dirichlet columns
+        // (App. B column elimination), all other rows take every tap.
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int e = tid + 256 * k;
+            if (KS * 256 > SN && e >= SN) break;
+            const int rx = tx0 + s_dx[k], ry = ty0 + s_dy[k], rt = tt0 + s_dt[k];
+            const bool inrow = rx >= 0 && rx < nx && ry >= 0 && ry < ny && rt < nt;
+            const int base = s_base[k];
+            V4<T> sv[KB];
+#pragma unroll
+            for (int j = 0; j < KB; ++j) sv[j] = v4zero<T>();
+            if (inrow && !is_dirichlet(rx, ry, nx, ny)) {
+                const bool first = HT > 0 && nt > 1 && rt == 0;
+                const bool near = rx <= 1 || rx >= nx - 2 || (ny > 1 && (ry <= 1 || ry >= ny - 2));
+#pragma unroll
+                for (int o = 0; o < NTAP; ++o) {
+                    if (!tap_used(o)) continue;
+                    const T c = first ? c1[o] : c0[o];
+                    if (c == T(0)) continue;
+                    if (near && is_dirichlet(rx + tap_dx(o), ry + tap_dy(o), nx, ny)) continue;
+#pragma unroll
+                    for (int j = 0; j < KB; ++j) sv[j] = fma4(c, sp[base + poff<PX, PY>(o)][j], sv[j]);
                 }
             }
-            __syncthreads();
-            q = sq[tid];
+#pragma unroll
+            for (int j = 0; j < KB; ++j) S.s[e][j] = sv[j];
+            if (COL) {
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    V4<T> sjv = v4zero<T>();
+                    if (inrow && rx >= 1 && rx <= nx - 2 && rt >= 1) {
+                        T cC, cL, cR;
+                        jcoef<T, COL>(L.col, smu(base), smu(base - 1), smu(base + 1), cC, cL, cR);
+                        sjv = cC * sp[base][j];
+                        sjv = fma4(cL, sp[base - 1][j], sjv);
+                        sjv = fma4(cR, sp[base + 1][j], sjv);
+                        sjv = fma4((T)(-L.col.inv_dt), sp[base - PY * PX][j], sjv);
+                    }
+                    S.sj[COL ? e : 0][j] = sjv;
+                }
+            }
         }
-    }
+        __syncthreads();
 
-    // 5. epilogue
-    double dot[4] = {0.0, 0.0, 0.0, 0.0};
-    if (own) {
-        const long long node = ((long long)gt * ny + gy) * nx + gx;
-        const size_t off = ((size_t)blk * N + node) * RW;
-        if (MODE == M_APPLY) {
-            v4store(A.out + off, q);
-            dot[0] = (double)pown.a * q.a; dot[1] = (double)pown.b * q.b;
-            dot[2] = (double)pown.c * q.c; dot[3] = (double)pown.d * q.d;
-        } else if (MODE == M_RESID) {
-            const V4<T> r = v4load(A.b + off) - q;
-            v4store(A.out + off, r);
-            dot[0] = (double)r.a * r.a; dot[1] = (double)r.b * r.b;
-            dot[2] = (double)r.c * r.c; dot[3] = (double)r.d * r.d;
-        } else {
-            const V4<T> bb = v4load(A.b + off);
-            const V4<T> r = bb - q;
-            const T di = A.dinv[node];
-            V4<T> dn = (A.c2 * di) * r;
-            if (A.d != nullptr) dn = fma4(A.c1, v4load(A.d + off), dn);
-            const V4<T> xn = pown + dn;
-            v4store(A.out + off, xn);
-            v4store(A.out2 + off, dn);
-            dot[0] = (double)bb.a * xn.a; dot[1] = (double)bb.b * xn.b;
-            dot[2] = (double)bb.c * xn.c; dot[3] = (double)bb.d * xn.d;
+        // q = B^T s (+ J^T Q_eps sj + A^T R^-1 A p) at the thread's own node
+        const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
+        const bool own = gx < nx && gy < ny && gt < nt;
+        const int node = own ? (gt * ny + gy) * nx + gx : 0;
+        V4<T> q[KB], pown[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) { q[j] = v4zero<T>(); pown[j] = sp[pbase][j]; }
+        if (own) {
+            if (is_dirichlet(gx, gy, nx, ny)) {
+#pragma unroll
+                for (int j = 0; j < KB; ++j) q[j] = L.inv_eps2 * pown[j];
+            } else {
+#pragma unroll
+                for (int o = 0; o < NTAP; ++o) {
+                    if (!tap_used(o)) continue;
+                    const bool first = HT > 0 && nt > 1 && gt - tap_dt(o) == 0;
+                    const T c = first ? c1[o] : c0[o];
+                    if (c == T(0)) continue;
+#pragma unroll
+                    for (int j = 0; j < KB; ++j) q[j] = fma4(c, S.s[sbase + soff<SX, SY>(o)][j], q[j]);
+                }
+            }
+            if (COL) {
+                // rows touching this column: itself (centre), x-1 row (its x+1 tap),
+                // x+1 row (its x-1 tap), t+1 row (its t-1 tap)
+                const int sb = lt * SX + (lx + 1);
+                T cC, cL, cR, tC, tL, tR, uC, uL, uR;
+                const T m0 = smu(pbase), mm1 = smu(pbase - 1), mp1 = smu(pbase + 1);
+                const T mm2 = smu(pbase - 2), mp2 = smu(pbase + 2);
+                jcoef<T, COL>(L.col, m0, mm1, mp1, cC, cL, cR);
+                jcoef<T, COL>(L.col, mm1, mm2, m0, tC, tL, tR);
+                jcoef<T, COL>(L.col, mp1, m0, mp2, uC, uL, uR);
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    V4<T> acc = cC * S.sj[COL ? sb : 0][j];
+                    acc = fma4(tR, S.sj[COL ? sb - 1 : 0][j], acc);
+                    acc = fma4(uL, S.sj[COL ? sb + 1 : 0][j], acc);
+                    acc = fma4((T)(-L.col.inv_dt), S.sj[COL ? sb + SX : 0][j], acc);
+                    q[j] = fma4((T)L.col.qeps, acc, q[j]);
+                }
+            }
+            if (has_obs) {
+                const unsigned char* ob = obs_smem + (size_t)st * ostage;
+                const int ei = reinterpret_cast<const int16_t*>(ob)[tid];
+                if (ei >= 0) {
+                    const T* c = reinterpret_cast<const T*>(ob + TN * 2) + ei * OC;
+#pragma unroll
+                    for (int a = 0; a < OC; ++a) {
+                        const int po = pbase + (obs_dt(GEO, a) * PY + obs_dy(GEO, a)) * PX + obs_dx(GEO, a);
+#pragma unroll
+                        for (int j = 0; j < KB; ++j) q[j] = fma4(c[a], sp[po][j], q[j]);
+                    }
+                }
+            }
         }
+
+        // epilogue
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+            const int blk = grp * KB + j;
+            if (!own || blk >= nblk) continue;
+            const size_t off = ((size_t)blk * N + node) * RW;
+            if (MODE == M_APPLY) {
+                v4store(A.out + off, q[j]);
+                dacc[j][0] += pown[j].a * q[j].a; dacc[j][1] += pown[j].b * q[j].b;
+                dacc[j][2] += pown[j].c * q[j].c; dacc[j][3] += pown[j].d * q[j].d;
+            } else if (MODE == M_RESID) {
+                const V4<T> r = S.b[MODE != M_APPLY ? st : 0][tid][j] - q[j];
+                v4store(A.out + off, r);
+                dacc[j][0] += r.a * r.a; dacc[j][1] += r.b * r.b; dacc[j][2] += r.c * r.c; dacc[j][3] += r.d * r.d;
+            } else {
+                const V4<T> bb = S.b[MODE != M_APPLY ? st : 0][tid][j];
+                const V4<T> r = bb - q[j];
+                const T di = S.dinv[MODE == M_CHEB ? st : 0][tid];
+                V4<T> dn = (A.c2 * di) * r;
+                if (A.d != nullptr) dn = fma4(A.c1, S.d[MODE == M_CHEB ? st : 0][tid][j], dn);
+                const V4<T> xn = pown[j] + dn;
+                v4store(A.out + off, xn);
+                v4store(A.out2 + off, dn);
+                dacc[j][0] += bb.a * xn.a; dacc[j][1] += bb.b * xn.b; dacc[j][2] += bb.c * xn.c; dacc[j][3] += bb.d * xn.d;
+            }
+        }
+        // dot partials: one entry per (block, CTA), flushed when the group changes
+        UnitPos nxt = cur;
+        unit_advance(nxt, dG, tiles_x, tiles_y, tiles_t);
+        if (A.partial != nullptr) {
+            if (nxt.grp != grp) {
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    const int blk = grp * KB + j;
+                    if (blk < nblk) block_sum4<256, T>(dacc[j], A.partial + ((size_t)blk * G + blockIdx.x) * 4);
+                    dacc[j][0] = dacc[j][1] = dacc[j][2] = dacc[j][3] = T(0);
+                }
+            }
+        }
+        __syncthreads();
+        cur = nxt;
+        st = st + 1 == NS ? 0 : st + 1;
     }
-    if (A.partial != nullptr) {
-        const long long ntiles = (long long)L.tiles_x * L.tiles_y * L.tiles_t;
-        block_sum4<256>(dot, A.partial + ((size_t)blk * ntiles + tile) * 4);
+    cp_wait<0>();
+}
+
+// Largest persistent grid any stencil launch uses (sizes the partial buffers).
+constexpr int kMaxStencilGrid = 4096;
+
+#ifndef GMRF_STENCIL_STAGES
+#define GMRF_STENCIL_STAGES 2
+#endif
+#ifndef GMRF_STENCIL_KB
+#define GMRF_STENCIL_KB 1
+#endif
+
+template <int GEO, typename T, int MODE, int COL>
+static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
+    constexpr int NS = sizeof(T) == 8 ? 2 : GMRF_STENCIL_STAGES;
+    constexpr int KB = sizeof(T) == 8 ? 1 : GMRF_STENCIL_KB;
+    using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
+    auto kern = k_stencil<GEO, T, MODE, COL, NS, KB>;
+    static int attr_smem = 0;
+    static int sms = 0;
+    static std::map<size_t, int> per_sm;       // resident CTAs per SM by dynamic shared memory
+    const size_t smem = sizeof(SM) + (a.L.ocap > 0 ? (size_t)NS * (SM::TN * 2 + a.L.ostride) : 0);
+    if (sms == 0) {
+        int dev = 0;
+        cuda_ok(cudaGetDevice(&dev));
+        cuda_ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     }
+    if ((int)smem > attr_smem) {
+        cuda_ok(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_smem = (int)smem;
+    }
+    auto itp = per_sm.find(smem);
+    if (itp == per_sm.end()) {
+        int per = 0;
+        cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem));
+        if (per <= 0) throw std::runtime_error("stencil kernel does not fit on an SM (shared memory)");
+        itp = per_sm.emplace(smem, per).first;
+    }
+    const long long ntiles = (long long)a.L.tiles_x * a.L.tiles_y * a.L.tiles_t;
+    const long long nunits = ntiles * ((a.nblk + KB - 1) / KB);
+    const int grid = (int)std::min<long long>(std::min<long long>(nunits, (long long)sms * itp->second), kMaxStencilGrid);
+    { kern<<<(unsigned)grid, 256, smem, s>>>(a, (int)nunits); note_launch(); }
+    return grid;
 }
 
 template <int GEO, typename T, int MODE>
-static void launch_geo_mode(const StencilArgs<T>& a, cudaStream_t s) {
-    const dim3 grid((unsigned)((long long)a.L.tiles_x * a.L.tiles_y * a.L.tiles_t), (unsigned)a.nblk);
-    if (GEO == GEO_XT && a.L.col.kind == 1)
-        { k_stencil<GEO, T, MODE, (GEO == GEO_XT ? 1 : 0)><<<grid, 256, 0, s>>>(a); note_launch(); }
-    else if (GEO == GEO_XT && a.L.col.kind == 2)
-        { k_stencil<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0)><<<grid, 256, 0, s>>>(a); note_launch(); }
-    else
-        { k_stencil<GEO, T, MODE, 0><<<grid, 256, 0, s>>>(a); note_launch(); }
+static int launch_geo_mode(const StencilArgs<T>& a, cudaStream_t s) {
+    if (GEO == GEO_XT && a.L.col.kind == 1) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 1 : 0)>(a, s);
+    if (GEO == GEO_XT && a.L.col.kind == 2) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0)>(a, s);
+    return launch_one<GEO, T, MODE, 0>(a, s);
 }
 
 template <typename T, int GEO>
-static void launch_geo(int mode, const StencilArgs<T>& a, cudaStream_t s) {
-    if (mode == M_APPLY) launch_geo_mode<GEO, T, M_APPLY>(a, s);
-    else if (mode == M_RESID) launch_geo_mode<GEO, T, M_RESID>(a, s);
-    else launch_geo_mode<GEO, T, M_CHEB>(a, s);
+static int launch_geo(int mode, const StencilArgs<T>& a, cudaStream_t s) {
+    if (mode == M_APPLY) return launch_geo_mode<GEO, T, M_APPLY>(a, s);
+    if (mode == M_RESID) return launch_geo_mode<GEO, T, M_RESID>(a, s);
+    return launch_geo_mode<GEO, T, M_CHEB>(a, s);
 }
 
-template <typename T> void launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s) {
-    if (geo == GEO_XY) launch_geo<T, GEO_XY>(mode, a, s);
-    else if (geo == GEO_XT) launch_geo<T, GEO_XT>(mode, a, s);
-    else launch_geo<T, GEO_XYT>(mode, a, s);
+template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s) {
+    if (geo == GEO_XY) return launch_geo<T, GEO_XY>(mode, a, s);
+    if (geo == GEO_XT) return launch_geo<T, GEO_XT>(mode, a, s);
+    return launch_geo<T, GEO_XYT>(mode, a, s);
 }
-template void launch_stencil<float>(int, int, const StencilArgs<float>&, cudaStream_t);
-template void launch_stencil<double>(int, int, const StencilArgs<double>&, cudaStream_t);
+template int launch_stencil<float>(int, int, const StencilArgs<float>&, cudaStream_t);
+template int launch_stencil<double>(int, int, const StencilArgs<double>&, cudaStream_t);
+int stencil_max_grid() { return kMaxStencilGrid; }
 
 // ---------------------------------------------------------------------------
 // reductions and PCG scalars
@@ -300,7 +519,7 @@ __global__ void k_reduce(const double* __restrict__ partial, int nparts, double*
         const double* p = partial + ((size_t)blk * nparts + i) * 4;
         v[0] += p[0]; v[1] += p[1]; v[2] += p[2]; v[3] += p[3];
     }
-    block_sum4<256>(v, out + (size_t)blk * 4);
+    block_sum4<256, double>(v, out + (size_t)blk * 4);
 }
 
 void launch_reduce(const double* partial, int nparts, int nblk, double* out, cudaStream_t s) {
@@ -357,7 +576,7 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
     const int blk = blockIdx.y;
     const double* alpha = sc + 2 * (gridDim.y * RW) + blk * RW;
     const T a0 = (T)alpha[0], a1 = (T)alpha[1], a2 = (T)alpha[2], a3 = (T)alpha[3];
-    double dot[4] = {0, 0, 0, 0};
+    T dot[4] = {T(0), T(0), T(0), T(0)};
     for (int k = 0; k < EPT; ++k) {
         const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
         if (n >= N) break;
@@ -368,10 +587,10 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
         rv.a = fma(-a0, qv.a, rv.a); rv.b = fma(-a1, qv.b, rv.b); rv.c = fma(-a2, qv.c, rv.c); rv.d = fma(-a3, qv.d, rv.d);
         v4store(x + off, xv);
         v4store(r + off, rv);
-        dot[0] += (double)rv.a * rv.a; dot[1] += (double)rv.b * rv.b;
-        dot[2] += (double)rv.c * rv.c; dot[3] += (double)rv.d * rv.d;
+        dot[0] += rv.a * rv.a; dot[1] += rv.b * rv.b;
+        dot[2] += rv.c * rv.c; dot[3] += rv.d * rv.d;
     }
-    block_sum4<256>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
+    block_sum4<256, T>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
 }
 
 template <typename T>
@@ -930,7 +1149,7 @@ __global__ void k_dot_blocked(const double* __restrict__ a, const double* __rest
         const V4<double> av = v4load(a + off), bv = v4load(b + off);
         dot[0] += av.a * bv.a; dot[1] += av.b * bv.b; dot[2] += av.c * bv.c; dot[3] += av.d * bv.d;
     }
-    block_sum4<256>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
+    block_sum4<256, double>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
 }
 void launch_dot_blocked(const double* a, const double* b, long long N, int nblk, double* partial, int nparts, cudaStream_t s) {
     { k_dot_blocked<<<dim3(nparts, nblk), 256, 0, s>>>(a, b, N, partial, nparts); note_launch(); }
@@ -946,20 +1165,39 @@ namespace gmrf {
 template <typename T>
 __global__ void k_norm2(const T* __restrict__ v, long long N, double* __restrict__ partial, int nparts) {
     const int blk = blockIdx.y;
-    double dot[4] = {0, 0, 0, 0};
+    T dot[4] = {T(0), T(0), T(0), T(0)};
     for (int k = 0; k < EPT; ++k) {
         const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
         if (n >= N) break;
         const V4<T> a = v4load(v + ((size_t)blk * N + n) * RW);
-        dot[0] += (double)a.a * a.a; dot[1] += (double)a.b * a.b; dot[2] += (double)a.c * a.c; dot[3] += (double)a.d * a.d;
+        dot[0] += a.a * a.a; dot[1] += a.b * a.b; dot[2] += a.c * a.c; dot[3] += a.d * a.d;
     }
-    block_sum4<256>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
+    block_sum4<256, T>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
 }
 template <typename T> void launch_norm2(const T* v, long long N, int nblk, double* partial, int nparts, cudaStream_t s) {
     { k_norm2<T><<<dim3(nparts, nblk), 256, 0, s>>>(v, N, partial, nparts); note_launch(); }
 }
 template void launch_norm2<float>(const float*, long long, int, double*, int, cudaStream_t);
 template void launch_norm2<double>(const double*, long long, int, double*, int, cudaStream_t);
+
+template <typename T>
+__global__ void k_dot(const T* __restrict__ a, const T* __restrict__ b, long long N, double* __restrict__ partial, int nparts) {
+    const int blk = blockIdx.y;
+    T dot[4] = {T(0), T(0), T(0), T(0)};
+    for (int k = 0; k < EPT; ++k) {
+        const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
+        if (n >= N) break;
+        const size_t off = ((size_t)blk * N + n) * RW;
+        const V4<T> av = v4load(a + off), bv = v4load(b + off);
+        dot[0] += av.a * bv.a; dot[1] += av.b * bv.b; dot[2] += av.c * bv.c; dot[3] += av.d * bv.d;
+    }
+    block_sum4<256, T>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
+}
+template <typename T> void launch_dot(const T* a, const T* b, long long N, int nblk, double* partial, int nparts, cudaStream_t s) {
+    { k_dot<T><<<dim3(nparts, nblk), 256, 0, s>>>(a, b, N, partial, nparts); note_launch(); }
+}
+template void launch_dot<float>(const float*, const float*, long long, int, double*, int, cudaStream_t);
+template void launch_dot<double>(const double*, const double*, long long, int, double*, int, cudaStream_t);
 
 // power iteration on D^-1 Q in the D-norm: w = D^-1 q (in place), partial q.w
 __global__ void k_power_scale(float* __restrict__ q, const float* __restrict__ dinv, long long N, double* __restrict__ partial, int nparts) {
@@ -973,7 +1211,7 @@ __global__ void k_power_scale(float* __restrict__ q, const float* __restrict__ d
         v4store(q + n * RW, w);
         dot[0] += (double)a.a * w.a; dot[1] += (double)a.b * w.b; dot[2] += (double)a.c * w.c; dot[3] += (double)a.d * w.d;
     }
-    block_sum4<256>(dot, partial + (size_t)blockIdx.x * 4);
+    block_sum4<256, double>(dot, partial + (size_t)blockIdx.x * 4);
 }
 void launch_power_scale(float* q, const float* dinv, long long N, double* partial, int nparts, cudaStream_t s) {
     { k_power_scale<<<nparts, 256, 0, s>>>(q, dinv, N, partial, nparts); note_launch(); }

@@ -23,12 +23,14 @@ struct StencilArgs {
     T* out;            // APPLY: Q x; RESID: b - Q x; CHEB: x + d_new
     T* out2;           // CHEB: d_new
     T c1, c2;          // CHEB: d_new = c1 d + c2 D^-1 (b - Q x)
-    double* partial;   // per-CTA dot partials [nblk][ntiles][4] or null
+    double* partial;   // per-CTA dot partials [nblk][grid][4] or null
     int nblk;
 };
 
-// dot kinds written to `partial`: APPLY x.Qx, RESID |r|^2, CHEB b.x_new
-template <typename T> void launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s);
+// Dot partials written to `partial` as [nblk][grid][4] (APPLY x.Qx, RESID
+// |r|^2, CHEB b.x_new); returns the grid size, i.e. the partial count per block.
+template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s);
+int stencil_max_grid();
 
 // reduce [nblk][nparts][4] partials into out[nblk * 4]
 void launch_reduce(const double* partial, int nparts, int nblk, double* out, cudaStream_t s);
@@ -76,6 +78,7 @@ void launch_dot_blocked(const double* a, const double* b, long long N, int nblk,
 }  // namespace gmrf
 
 namespace gmrf {
+template <typename T> void launch_dot(const T* a, const T* b, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
 template <typename T> void launch_norm2(const T* v, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
 void launch_power_scale(float* q, const float* dinv, long long N, double* partial, int nparts, cudaStream_t s);
 void launch_scale_comp(float* v, const float* w, const double* nrm2, long long N, cudaStream_t s);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <stdexcept>
 
 #include "host.h"
@@ -234,6 +235,13 @@ void build_level_obs(const gmrf_prior_desc& d, const Posterior& P, const std::ve
             rows.push_back(o);
         }
     }
+    for (ObsRow& o : rows)
+        for (int n = 0; n < 8; ++n) {
+            const long long nd = o.node[n];
+            o.ox[n] = (int16_t)(nd % L.nx);
+            o.oy[n] = (int16_t)((nd / L.nx) % L.ny);
+            o.ot[n] = (int16_t)(nd / ((long long)L.nx * L.ny));
+        }
     L.nobs = (int)rows.size();
     // per-tile lists: an observation is listed in every tile holding one of its nodes
     const int TX = geo_tx(L.geo), TY = geo_ty(L.geo), TT = geo_tt(L.geo);
@@ -269,6 +277,64 @@ void build_level_obs(const gmrf_prior_desc& d, const Posterior& P, const std::ve
     dev_upload(&L.d_obs, rows);
     dev_upload(&L.d_tile_ptr, cnt);
     dev_upload(&L.d_tile_idx, idx);
+    build_obs_stencil(L);
+}
+
+// A^T R^-1 A = sum_k rinv_k w_k w_k^T as a per-node stencil: node i gets
+// C[i][off(j - i)] += rinv_k w_ki w_kj for every pair of nodes of row k
+// (FP64 sums), laid out per tile for the stencil kernel.
+void build_obs_stencil(Level& L) {
+    const int TX = geo_tx(L.geo), TY = geo_ty(L.geo), TT = geo_tt(L.geo), TN = TX * TY * TT;
+    const int OC = obs_oc(L.geo);
+    std::map<long long, std::vector<double>> C;
+    for (const ObsRow& o : L.h_obs)
+        for (int a = 0; a < o.nn; ++a) {
+            std::vector<double>& c = C[o.node[a]];
+            if (c.empty()) c.assign((size_t)OC, 0.0);
+            for (int b = 0; b < o.nn; ++b) {
+                const int dx = o.ox[b] - o.ox[a], dy = o.oy[b] - o.oy[a], dt = o.ot[b] - o.ot[a];
+                int idx;
+                if (L.geo == GEO_XY) idx = (dy + 1) * 3 + (dx + 1);
+                else if (L.geo == GEO_XT) idx = (dt + 1) * 3 + (dx + 1);
+                else idx = ((dt + 1) * 3 + (dy + 1)) * 3 + (dx + 1);
+                c[(size_t)idx] += o.rinv * o.wd[a] * o.wd[b];
+            }
+        }
+    const long long ntiles = L.ntiles();
+    std::vector<int> count((size_t)ntiles, 0);
+    auto tile_of = [&](long long nd, int& local) {
+        const int x = (int)(nd % L.nx);
+        const long long r = nd / L.nx;
+        const int y = (int)(r % L.ny), t = (int)(r / L.ny);
+        local = ((t % TT) * TY + (y % TY)) * TX + (x % TX);
+        return ((long long)(t / TT) * L.tiles_y + y / TY) * L.tiles_x + x / TX;
+    };
+    int cap = 0;
+    for (auto& kv : C) {
+        int local;
+        const long long t = tile_of(kv.first, local);
+        cap = std::max(cap, ++count[(size_t)t]);
+    }
+    L.ocap = cap;
+    L.ostride32 = ((cap * OC * 4 + 15) / 16) * 16;
+    L.ostride64 = ((cap * OC * 8 + 15) / 16) * 16;
+    std::vector<int16_t> map((size_t)ntiles * TN, (int16_t)-1);
+    std::vector<float> e32((size_t)ntiles * L.ostride32 / 4, 0.0f);
+    std::vector<double> e64((size_t)ntiles * L.ostride64 / 8, 0.0);
+    std::fill(count.begin(), count.end(), 0);
+    for (auto& kv : C) {
+        int local;
+        const long long t = tile_of(kv.first, local);
+        const int e = count[(size_t)t]++;
+        map[(size_t)t * TN + local] = (int16_t)e;
+        for (int a = 0; a < OC; ++a) {
+            e32[(size_t)t * (L.ostride32 / 4) + (size_t)e * OC + a] = (float)kv.second[(size_t)a];
+            e64[(size_t)t * (L.ostride64 / 8) + (size_t)e * OC + a] = kv.second[(size_t)a];
+        }
+    }
+    dev_upload(&L.d_omap, map);
+    dev_upload(&L.d_oent32, e32);
+    dev_upload(&L.d_oent64, e64);
 }
 
 // ---------------------------------------------------------------------------

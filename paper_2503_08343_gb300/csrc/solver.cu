@@ -47,6 +47,7 @@ template <> const double* pw_of<double>(const Level& L, int a) { return L.d_pwd[
 
 void level_free(Level& L) {
     dev_free(L.d_obs); dev_free(L.d_tile_ptr); dev_free(L.d_tile_idx);
+    dev_free(L.d_omap); dev_free(L.d_oent32); dev_free(L.d_oent64);
     dev_free(L.d_mu32); dev_free(L.d_mu64);
     dev_free(L.d_dinv32); dev_free(L.d_dinv64); dev_free(L.d_diag64);
     for (int a = 0; a < 3; ++a) {
@@ -59,6 +60,7 @@ void level_free(Level& L) {
 static size_t partial_slots(const Posterior& P, int nblk) {
     long long m = 1;
     for (const Level& L : P.levels) m = std::max(m, std::max(L.ntiles(), (long long)elem_parts(L.N)));
+    m = std::max<long long>(m, stencil_max_grid());
     return (size_t)m * nblk * 4;
 }
 
@@ -71,7 +73,7 @@ static double power_lmax(Posterior& P, Level& L, cudaStream_t s) {
     float* q = dev_alloc<float>((size_t)N * 4);
     const long long nt = L.ntiles();
     const int np = elem_parts(N);
-    double* part = dev_alloc<double>((size_t)std::max<long long>(nt, np) * 4);
+    double* part = dev_alloc<double>((size_t)std::max<long long>(std::max<long long>(nt, np), stencil_max_grid()) * 4);
     double* red = dev_alloc<double>(4);
     launch_fill_random(v, N, 0x5eed, s);
     StencilArgs<float> a{};
@@ -212,15 +214,21 @@ Workspace& workspace(Posterior& P, int nblk) {
 // ---------------------------------------------------------------------------
 // V-cycle
 
+// One V-cycle x = M b on level l.  With rz_partial, the partial sums of
+// b . x are written there; the return value is their count per block.
 template <typename T>
-static void vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T* b, T* x, double* rz_partial,
-                   cudaStream_t s) {
+static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T* b, T* x, double* rz_partial,
+                  cudaStream_t s) {
     const int nl = (int)P.levels.size();
     Level& L = P.levels[l];
     const int nblk = W.nblk;
     if (l == nl - 1) {
         launch_dense_solve<T>(dense_of<T>(L), b, x, (int)L.N, nblk, s);
-        return;
+        if (rz_partial) {
+            launch_dot<T>(b, x, L.N, nblk, rz_partial, elem_parts(L.N), s);
+            return elem_parts(L.N);
+        }
+        return 0;
     }
     const Cheb ch = cheb_coeffs(L.lmax);
     T* X0 = (T*)V.xa[l];
@@ -264,7 +272,7 @@ static void vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const 
     launch_stencil<T>(L.geo, M_CHEB, p1, s);
     StencilArgs<T> p2 = a;
     p2.x = X0; p2.d = D; p2.out = x; p2.out2 = D; p2.partial = rz_partial;
-    launch_stencil<T>(L.geo, M_CHEB, p2, s);
+    return launch_stencil<T>(L.geo, M_CHEB, p2, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -289,14 +297,14 @@ static void pcg_iteration(Posterior& P, Workspace& W, Workspace::Vecs& V, double
     a.L = L.view<T>();
     a.nblk = nblk;
     a.x = p; a.out = q; a.partial = W.partial;
-    launch_stencil<T>(L.geo, M_APPLY, a, s);
-    launch_reduce(W.partial, nt, nblk, W.red, s);
+    const int ng = launch_stencil<T>(L.geo, M_APPLY, a, s);
+    launch_reduce(W.partial, ng, nblk, W.red, s);
     launch_pcg_scalar(0, W.red, sc, nblk, tol2, s);
     launch_pcg_update_xr<T>(x, r, p, q, sc, L.N, nblk, W.partial, ne, s);
     launch_reduce(W.partial, ne, nblk, W.red, s);
     launch_pcg_scalar(1, W.red, sc, nblk, tol2, s);
-    vcycle<T>(P, W, V, 0, r, z, W.partial, s);
-    launch_reduce(W.partial, nt, nblk, W.red, s);
+    const int nz = vcycle<T>(P, W, V, 0, r, z, W.partial, s);
+    launch_reduce(W.partial, nz, nblk, W.red, s);
     launch_pcg_scalar(2, W.red, sc, nblk, tol2, s);
     launch_pcg_update_p<T>(p, z, sc, L.N, nblk, s);
 }
@@ -319,8 +327,8 @@ static int pcg(Posterior& P, Workspace& W, double tol, int maxit, cudaStream_t s
     launch_norm2<T>(r, L.N, nblk, W.partial, ne, s);
     launch_reduce(W.partial, ne, nblk, W.red, s);
     launch_pcg_scalar(4, W.red, sc, nblk, tol2, s);
-    vcycle<T>(P, W, V, 0, r, z, W.partial, s);
-    launch_reduce(W.partial, nt, nblk, W.red, s);
+    const int nz = vcycle<T>(P, W, V, 0, r, z, W.partial, s);
+    launch_reduce(W.partial, nz, nblk, W.red, s);
     launch_pcg_scalar(3, W.red, sc, nblk, tol2, s);
     GCK(cudaMemcpyAsync(p, z, bytes, cudaMemcpyDeviceToDevice, s));
     const int P4 = nblk * 4;
@@ -407,8 +415,8 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
         a.L = L.view<double>();
         a.nblk = nblk;
         a.x = x64; a.b = b64; a.out = W.r64; a.partial = W.partial;
-        launch_stencil<double>(L.geo, M_RESID, a, s);
-        launch_reduce(W.partial, nt, nblk, W.red, s);
+        const int ng = launch_stencil<double>(L.geo, M_RESID, a, s);
+        launch_reduce(W.partial, ng, nblk, W.red, s);
         GCK(cudaMemcpyAsync(W.h_red, W.red, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
         GCK(cudaStreamSynchronize(s));
         st.refinements++;
@@ -442,23 +450,32 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
     return st;
 }
 
-double time_apply(Posterior& P, int nblk, int iters, cudaStream_t s) {
+double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s) {
     Workspace& W = workspace(P, nblk);
     alloc_vecs<float>(P, W, W.v32);
     Level& L = P.levels[0];
     float* x = (float*)W.v32.pcg[2];
     float* y = (float*)W.v32.pcg[3];
-    for (int b = 0; b < nblk; ++b) launch_fill_random(x + (size_t)b * L.N * 4, L.N, 99 + b, s);
+    float* b = (float*)W.v32.pcg[1];
+    float* d = (float*)W.v32.d[0];
+    float* y2 = (float*)W.v32.xa[0];
+    for (int k = 0; k < nblk; ++k) {
+        launch_fill_random(x + (size_t)k * L.N * 4, L.N, 99 + k, s);
+        launch_fill_random(b + (size_t)k * L.N * 4, L.N, 199 + k, s);
+        launch_fill_random(d + (size_t)k * L.N * 4, L.N, 299 + k, s);
+    }
     StencilArgs<float> a{};
     a.L = L.view<float>();
     a.nblk = nblk;
     a.x = x; a.out = y; a.partial = W.partial;
-    launch_stencil<float>(L.geo, M_APPLY, a, s);
+    if (mode != M_APPLY) a.b = b;
+    if (mode == M_CHEB) { a.d = d; a.dinv = L.d_dinv32; a.out2 = y2; a.c1 = 0.5f; a.c2 = 0.25f; }
+    launch_stencil<float>(L.geo, mode, a, s);
     cudaEvent_t e0, e1;
     GCK(cudaEventCreate(&e0));
     GCK(cudaEventCreate(&e1));
     GCK(cudaEventRecord(e0, s));
-    for (int i = 0; i < iters; ++i) launch_stencil<float>(L.geo, M_APPLY, a, s);
+    for (int i = 0; i < iters; ++i) launch_stencil<float>(L.geo, mode, a, s);
     GCK(cudaEventRecord(e1, s));
     GCK(cudaEventSynchronize(e1));
     float ms = 0.f;

@@ -88,7 +88,7 @@ def load(build_if_missing: bool = False):
         "gmrf_loglik_grad": (I32, [P, I32, U64, DP, DP, DP, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "gmrf_apply_posterior": (I32, [P, I32, P, P]),
         "gmrf_normals": (I32, [U64, I32, I32, I32, I64, P]),
-        "gmrf_time_apply": (I32, [P, I32, I32, DP]),
+        "gmrf_time_stencil": (I32, [P, I32, I32, I32, DP]),
         "gmrf_num_unknowns": (I64, [P]),
         "gmrf_num_levels": (I32, [P]),
         "gmrf_prior_destroy": (None, [P]),
@@ -254,9 +254,10 @@ class Posterior:
         _check(load().gmrf_apply_posterior(self.h, x.shape[0], _ptr(x), _ptr(y)))
         return y
 
-    def time_apply(self, k, iters=20) -> float:
+    def time_stencil(self, kernel, k, iters=20) -> float:
+        """kernel: 0 apply, 1 residual, 2 Chebyshev step (finest level, FP32)."""
         ms = C.c_double()
-        _check(load().gmrf_time_apply(self.h, k, iters, C.byref(ms)))
+        _check(load().gmrf_time_stencil(self.h, kernel, k, iters, C.byref(ms)))
         return ms.value
 
     def __del__(self):

@@ -43,7 +43,7 @@ def test_status_strings_and_defaults_without_gpu(lib):
     from paper_2503_08343_gb300 import gmrf
     assert lib.gmrf_status_string(0) == b"ok"
     o = gmrf.default_opts()
-    assert o.rtol == 1e-8 and o.precision == 0 and o.batched == 1
+    assert o.rtol == 1e-10 and o.precision == 0 and o.batched == 1
 
 
 def test_product_path_does_not_import_the_oracle():
