@@ -194,6 +194,25 @@ gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t see
  * the fused stencil. */
 gmrf_status gmrf_apply_posterior(gmrf_posterior* post, int32_t k, const double* x, double* y);
 
+/* Allocation-free y = Q_u|y x for one vector (FP64), with x^T Q_u|y x.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need the product -- code running
+ * inside a custom allocator or memory-pool callback, loops that must not take
+ * cudaMalloc's implicit device synchronisation, processes whose device memory
+ * is fully reserved by a pool.  It makes no cudaMalloc/cudaFree call and uses
+ * no allocating library routine: its scratch is one fixed device array of
+ * 16.1 MB inside the library, held by every GPU that loads the library until
+ * the process exits.
+ *  x, y: device memory, [N], N <= 262144 unknowns (a 512 x 512 grid); larger
+ *        posteriors are rejected with GMRF_E_INVALID and a message naming the
+ *        limit.  xQx: host or device, may be NULL.
+ *  The first call on a device looks up the scratch address for that device
+ *  (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  All calls share the one scratch array: calls that overlap on the GPU (other
+ *  host threads, other streams) race and must be serialised by the caller.
+ *  Runs on the posterior's stream and returns after it has finished. */
+gmrf_status gmrf_apply_posterior_noalloc(gmrf_posterior* post, const double* x, double* y, double* xQx);
+
 /* Normal draws of the sample stream: out[s][i] = z(seed, stream, sample0 + s, i)
  * for s < count, i < n.  Test hook for the in-kernel generator. */
 gmrf_status gmrf_normals(uint64_t seed, int32_t stream, int32_t sample0, int32_t count, int64_t n,

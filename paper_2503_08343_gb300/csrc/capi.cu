@@ -7,18 +7,9 @@
 #include <new>
 #include <string>
 
-#include "host.h"
+#include "handles.h"
 
 using namespace gmrf;
-
-// A prior lives while its handle or any posterior built on it is alive, so
-// the handles may be destroyed in any order.
-struct gmrf_prior {
-    Prior impl;
-    cudaStream_t user = 0;   // unused: work runs on impl.stream
-    bool own = false;        // impl.stream created by the library
-    std::atomic<int> refs{1};
-};
 
 static void prior_release(gmrf_prior* p) {
     if (p->refs.fetch_sub(1) != 1) return;
@@ -26,12 +17,11 @@ static void prior_release(gmrf_prior* p) {
     delete p;
 }
 
-struct gmrf_posterior {
-    Posterior impl;
-    gmrf_prior* prior = nullptr;
-};
-
 static thread_local std::string g_err;
+
+namespace gmrf {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace gmrf
 
 template <typename F> static gmrf_status guard(F&& f) {
     try {
