@@ -108,10 +108,11 @@ typedef struct gmrf_obs_desc {
 } gmrf_obs_desc;
 
 typedef struct gmrf_solve_opts {
-    double rtol;               /* per-RHS ||b - Q_u|y x|| / ||b|| target, FP64 (default 1e-10) */
+    double rtol;               /* per-RHS FP64 residual target ||b - Q_u|y x||_D / ||b - Q_u|y x0||_D,
+                                  ||v||_D^2 = sum_i v_i^2 / (Q_u|y)_ii (default 1e-10) */
     int32_t max_refine;        /* FP64 refinement steps (default 12) */
     int32_t max_inner;         /* inner PCG iterations per refinement step (default 40) */
-    double inner_rtol;         /* inner relative residual reduction (default 1e-3) */
+    double inner_rtol;         /* inner reduction of the preconditioned residual norm (default 1e-5) */
     int32_t precision;         /* 0: FP32 inner + FP64 refinement; 1: plain FP64 PCG */
     int32_t batched;           /* 1: all right-hand sides in one batch; 0: one at a time */
     double timeout_s;          /* wall-clock limit, 0 = none */
@@ -122,7 +123,7 @@ typedef struct gmrf_solve_info {
     int32_t refinements;       /* FP64 residual evaluations */
     int32_t inner_iterations;  /* total PCG iterations (batched: per batch) */
     int32_t converged;         /* 1 if every RHS reached rtol */
-    double max_rel_residual;   /* max over RHS of the final FP64 relative residual */
+    double max_rel_residual;   /* max over RHS of the final FP64 relative residual (D-weighted) */
     double seconds;
 } gmrf_solve_info;
 

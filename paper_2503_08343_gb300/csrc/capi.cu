@@ -102,8 +102,8 @@ void gmrf_default_opts(gmrf_solve_opts* o) {
     if (!o) return;
     o->rtol = 1e-10;
     o->max_refine = 12;
-    o->max_inner = 40;
-    o->inner_rtol = 1e-3;
+    o->max_inner = 60;
+    o->inner_rtol = 1e-5;
     o->precision = 0;
     o->batched = 1;
     o->timeout_s = 0.0;
@@ -273,7 +273,10 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
             }
         }
         posterior_setup_levels(P, s);
+        if (obs->ic) P.ic_rinv = 1.0 / (obs->ic_sigma * obs->ic_sigma);
+        P.use_tsp = tsp_applicable(P.levels[0], (int)P.nic);
         dev_upload(&P.d_bstatic, bstatic);
+        if (P.nic) dev_upload(&P.d_icvals, P.ic_values);
         P.d_bdata = dev_alloc<double>((size_t)F.N);
         P.d_ypoint = dev_alloc<double>((size_t)std::max<int64_t>(P.m, 1));
         if (P.m) GCK(cudaMemcpyAsync(P.d_ypoint, P.y_point.data(), sizeof(double) * P.m, cudaMemcpyHostToDevice, s));
@@ -295,6 +298,9 @@ void gmrf_posterior_destroy(gmrf_posterior* post) {
     dev_free(P.d_bdata);
     dev_free(P.d_ypoint);
     dev_free(P.d_bstatic);
+    dev_free(P.d_icvals);
+    dev_free(P.d_blin);
+    dev_free(P.d_gn);
     gmrf_prior* pr = post->prior;
     delete post;
     if (pr) prior_release(pr);
@@ -343,7 +349,8 @@ static Batch make_batch(int ns, bool with_mean) {
 static SolveStats run_batch(Posterior& P, const Batch& b, uint64_t seed, const gmrf_solve_opts& o, cudaStream_t s) {
     Workspace& W = workspace(P, b.nblk);
     GCK(cudaMemcpyAsync(W.slot_a, b.sample.data(), sizeof(int32_t) * b.sample.size(), cudaMemcpyHostToDevice, s));
-    launch_sample_rhs(P.levels[0].geo, P.levels[0].view<double>(), seed, W.slot_a, P.d_bdata, W.b64, b.nblk, 0, s);
+    launch_sample_rhs(P.levels[0].geo, P.levels[0].view<double>(), seed, W.slot_a, P.linearised ? P.d_blin : P.d_bdata,
+                      W.b64, b.nblk, 0, s);
     GCK(cudaMemsetAsync(W.x64, 0, sizeof(double) * b.nblk * P.levels[0].N * 4, s));
     if (o.batched || b.nblk == 1) return solve_blocked(P, b.nblk, W.b64, W.x64, o, s);
     // one right-hand side per solve (the comparison path): the batch is
@@ -499,9 +506,20 @@ uint64_t gmrf_launch_count(void) { return launch_count(); }
 
 gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* delta_prev, double* newton_decrement,
                                    double* alpha, const gmrf_solve_opts* opts, gmrf_solve_info* info) {
-    (void)post; (void)mu_k; (void)delta_prev; (void)newton_decrement; (void)alpha; (void)opts; (void)info;
-    g_err = "gmrf_gauss_newton_step: not available in this build";
-    return GMRF_E_INVALID;
+    gmrf_status rc = GMRF_OK;
+    const gmrf_status st = guard([&] {
+        require(post && mu_k && delta_prev && newton_decrement, "null argument");
+        enter(post->prior);
+        Posterior& P = post->impl;
+        const gmrf_solve_opts o = resolve_opts(opts);
+        const auto t0 = std::chrono::steady_clock::now();
+        const GnResult r = gauss_newton_step(P, mu_k, delta_prev, is_device_ptr(mu_k), is_device_ptr(delta_prev), o,
+                                             P.prior->stream);
+        *newton_decrement = r.decrement;
+        if (alpha) *alpha = r.alpha;
+        rc = finish(r.stats, info, 1, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+    });
+    return st != GMRF_OK ? st : rc;
 }
 
 gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t seed, double* loglik, double* grad,

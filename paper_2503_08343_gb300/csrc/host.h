@@ -73,6 +73,21 @@ Workspace& workspace(Posterior& P, int nblk);
 void workspace_free(Workspace* w);
 double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s);
 
+// tsp.cu
+bool tsp_applicable(const Level& L, int nic);
+template <typename T>
+void launch_tsp(const Level& L, double w_ic, double w_bnd, const T* r, T* y, T* z, int nblk, cudaStream_t s);
+
+// gn.cu
+struct GnResult {
+    SolveStats stats;
+    double decrement = 0.0;
+    double alpha = 0.0;
+};
+void linearise(Posterior& P, const double* u, cudaStream_t s);
+GnResult gauss_newton_step(Posterior& P, double* u_io, double* d_io, bool u_dev, bool d_dev, const gmrf_solve_opts& o,
+                           cudaStream_t s);
+
 // scratch of one batch size
 struct Workspace {
     int nblk = 0;
@@ -82,6 +97,7 @@ struct Workspace {
     double* partial = nullptr;
     size_t npartial = 0;
     double* red = nullptr;
+    double* red2 = nullptr;        // second reduction target (nblk * 4)
     double* norms = nullptr;       // device, nblk * 4
     double* sc32 = nullptr;        // PCG scalars of the FP32 inner solve
     double* sc64 = nullptr;

@@ -130,10 +130,15 @@ struct Posterior {
     double* d_bdata = nullptr;     // A^T Q_eps y on the fine level, [N]
     double* d_ypoint = nullptr;
     double* d_bstatic = nullptr;   // IC + linear collocation part of b, [N]
+    double* d_icvals = nullptr;    // initial-condition values (device), [nic]
+    double* d_blin = nullptr;      // data RHS of the linearised (Gauss-Newton) problem, [N]
+    double* d_gn = nullptr;        // Gauss-Newton work vectors, [6 N]
     std::map<int, Workspace*> ws;  // scratch per batch size (blocks of four right-hand sides)
     int colloc_kind = 0;           // requested collocation (2: Burgers, linearised on demand)
     double colloc_qeps = 0.0, colloc_nu = 0.0, colloc_c = 0.0;
     bool linearised = false;
+    bool use_tsp = false;          // time-stepping preconditioner instead of the V-cycle
+    double ic_rinv = 0.0;          // precision of the initial-condition rows
 };
 
 }  // namespace gmrf

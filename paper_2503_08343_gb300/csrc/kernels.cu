@@ -410,7 +410,9 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             } else if (MODE == M_RESID) {
                 const V4<T> r = S.b[MODE != M_APPLY ? st : 0][tid][j] - q[j];
                 v4store(A.out + off, r);
-                dacc[j][0] += r.a * r.a; dacc[j][1] += r.b * r.b; dacc[j][2] += r.c * r.c; dacc[j][3] += r.d * r.d;
+                const T w = A.rweight != nullptr ? A.rweight[node] : T(1);
+                dacc[j][0] += w * r.a * r.a; dacc[j][1] += w * r.b * r.b;
+                dacc[j][2] += w * r.c * r.c; dacc[j][3] += w * r.d * r.d;
             } else {
                 const V4<T> bb = S.b[MODE != M_APPLY ? st : 0][tid][j];
                 const V4<T> r = bb - q[j];
@@ -527,9 +529,11 @@ void launch_reduce(const double* partial, int nparts, int nblk, double* out, cud
 }
 
 // kind 0: pq reduced -> alpha = active ? rz / pq : 0 (breakdown if pq <= 0)
-// kind 1: rr reduced -> active = rr > tol2 * rr0
-// kind 2: rz_new reduced -> beta = rz_new / rz, rz = rz_new
-// kind 3: initial: rz reduced, rr0 = rr (stored by kind 4), active = rr0 > 0
+// kind 1: rr reduced -> rr (reported only)
+// kind 2: rz_new reduced -> beta = rz_new / rz, rz = rz_new; a right-hand side
+//         stops once rz_new <= tol2 * rz_0 (preconditioned residual norm,
+//         invariant under diagonal scaling of the system)
+// kind 3: initial: rz reduced, rz_0 = rz, active = rz_0 > 0
 // kind 4: rr reduced -> rr
 __global__ void k_pcg_scalar(int kind, const double* __restrict__ red, double* __restrict__ sc, int P, double tol2) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -544,16 +548,16 @@ __global__ void k_pcg_scalar(int kind, const double* __restrict__ red, double* _
         alpha[r] = (active[r] != 0.0) ? rz[r] / v : 0.0;
     } else if (kind == 1) {
         rr[r] = v;
-        if (!(v > tol2 * rr0[r])) active[r] = 0.0;
     } else if (kind == 2) {
         beta[r] = (active[r] != 0.0 && rz[r] != 0.0) ? v / rz[r] : 0.0;
         rz[r] = v;
+        if (!(v > tol2 * rr0[r])) { active[r] = 0.0; beta[r] = 0.0; }
     } else if (kind == 4) {
         rr[r] = v;
     } else {
         rz[r] = v;
-        rr0[r] = rr[r];
-        active[r] = (rr[r] > 0.0) ? 1.0 : 0.0;
+        rr0[r] = v;
+        active[r] = (v > 0.0) ? 1.0 : 0.0;
         brk[r] = 0.0;
         beta[r] = 0.0;
         alpha[r] = 0.0;
@@ -791,26 +795,35 @@ void launch_scale64(const double* r64, const double* norms, double* out, long lo
     { k_scale64<<<dim3(elem_parts(N), nblk), 256, 0, s>>>(r64, norms, out, N); note_launch(); }
 }
 
+// x64 += norm * d per right-hand side; partial sums of |norm d|^2 (partial)
+// and |x_new|^2 (partial + nblk * nparts * 4) for the forward-error test.
 template <typename T>
-__global__ void k_axpy_norm(double* __restrict__ x64, const double* __restrict__ norms, const T* __restrict__ d, long long N) {
+__global__ void __launch_bounds__(256) k_axpy_norm(double* __restrict__ x64, const double* __restrict__ norms,
+                                                   const T* __restrict__ d, long long N, double* __restrict__ partial) {
     const int blk = blockIdx.y;
     const double* nm = norms + blk * RW;
+    double dd[4] = {0, 0, 0, 0}, xx[4] = {0, 0, 0, 0};
     for (int k = 0; k < EPT; ++k) {
         const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
         if (n >= N) break;
         const size_t off = ((size_t)blk * N + n) * RW;
         const V4<T> dv = v4load(d + off);
         V4<double> xv = v4load(x64 + off);
-        xv.a = fma(nm[0], (double)dv.a, xv.a); xv.b = fma(nm[1], (double)dv.b, xv.b);
-        xv.c = fma(nm[2], (double)dv.c, xv.c); xv.d = fma(nm[3], (double)dv.d, xv.d);
+        const double d0 = nm[0] * (double)dv.a, d1 = nm[1] * (double)dv.b, d2 = nm[2] * (double)dv.c, d3 = nm[3] * (double)dv.d;
+        xv.a += d0; xv.b += d1; xv.c += d2; xv.d += d3;
         v4store(x64 + off, xv);
+        dd[0] += d0 * d0; dd[1] += d1 * d1; dd[2] += d2 * d2; dd[3] += d3 * d3;
+        xx[0] += xv.a * xv.a; xx[1] += xv.b * xv.b; xx[2] += xv.c * xv.c; xx[3] += xv.d * xv.d;
     }
+    const size_t np = gridDim.x;
+    block_sum4<256, double>(dd, partial + ((size_t)blk * np + blockIdx.x) * 4);
+    block_sum4<256, double>(xx, partial + (size_t)gridDim.y * np * 4 + ((size_t)blk * np + blockIdx.x) * 4);
 }
-void launch_axpy_mixed(double* x64, const double* norms, const float* d32, long long N, int nblk, cudaStream_t s) {
-    { k_axpy_norm<float><<<dim3(elem_parts(N), nblk), 256, 0, s>>>(x64, norms, d32, N); note_launch(); }
+void launch_axpy_mixed(double* x64, const double* norms, const float* d32, long long N, int nblk, double* partial, cudaStream_t s) {
+    { k_axpy_norm<float><<<dim3(elem_parts(N), nblk), 256, 0, s>>>(x64, norms, d32, N, partial); note_launch(); }
 }
-void launch_axpy_scaled64(double* x64, const double* norms, const double* d64, long long N, int nblk, cudaStream_t s) {
-    { k_axpy_norm<double><<<dim3(elem_parts(N), nblk), 256, 0, s>>>(x64, norms, d64, N); note_launch(); }
+void launch_axpy_scaled64(double* x64, const double* norms, const double* d64, long long N, int nblk, double* partial, cudaStream_t s) {
+    { k_axpy_norm<double><<<dim3(elem_parts(N), nblk), 256, 0, s>>>(x64, norms, d64, N, partial); note_launch(); }
 }
 
 // ---------------------------------------------------------------------------

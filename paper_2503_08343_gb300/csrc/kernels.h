@@ -25,6 +25,7 @@ struct StencilArgs {
     T c1, c2;          // CHEB: d_new = c1 d + c2 D^-1 (b - Q x)
     double* partial;   // per-CTA dot partials [nblk][grid][4] or null
     int nblk;
+    const T* rweight;  // RESID: if set, the dot is sum r^2 * rweight[node] (D^-1-weighted norm)
 };
 
 // Dot partials written to `partial` as [nblk][grid][4] (APPLY x.Qx, RESID
@@ -55,8 +56,8 @@ int elem_parts(long long N);
 
 // mixed precision refinement
 void launch_scale_cast(const double* r64, const double* norms, float* r32, long long N, int nblk, cudaStream_t s);
-void launch_axpy_mixed(double* x64, const double* norms, const float* d32, long long N, int nblk, cudaStream_t s);
-void launch_axpy_scaled64(double* x64, const double* norms, const double* d64, long long N, int nblk, cudaStream_t s);
+void launch_axpy_mixed(double* x64, const double* norms, const float* d32, long long N, int nblk, double* partial, cudaStream_t s);
+void launch_axpy_scaled64(double* x64, const double* norms, const double* d64, long long N, int nblk, double* partial, cudaStream_t s);
 void launch_scale64(const double* r64, const double* norms, double* out, long long N, int nblk, cudaStream_t s);
 
 // right-hand sides, layout conversion, variances

@@ -61,7 +61,7 @@ static size_t partial_slots(const Posterior& P, int nblk) {
     long long m = 1;
     for (const Level& L : P.levels) m = std::max(m, std::max(L.ntiles(), (long long)elem_parts(L.N)));
     m = std::max<long long>(m, stencil_max_grid());
-    return (size_t)m * nblk * 4;
+    return (size_t)m * nblk * 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -178,7 +178,7 @@ static void free_vecs(Workspace::Vecs& V) {
 void workspace_free(Workspace* w) {
     if (!w) return;
     dev_free(w->b64); dev_free(w->x64); dev_free(w->r64); dev_free(w->t64);
-    dev_free(w->partial); dev_free(w->red); dev_free(w->norms); dev_free(w->sc32); dev_free(w->sc64);
+    dev_free(w->partial); dev_free(w->red); dev_free(w->red2); dev_free(w->norms); dev_free(w->sc32); dev_free(w->sc64);
     dev_free(w->slot_a); dev_free(w->slot_b);
     if (w->h_red) cudaFreeHost(w->h_red);
     if (w->h_active) cudaFreeHost(w->h_active);
@@ -200,12 +200,13 @@ Workspace& workspace(Posterior& P, int nblk) {
     W->npartial = partial_slots(P, nblk);
     W->partial = dev_alloc<double>(W->npartial);
     W->red = dev_alloc<double>((size_t)nblk * 4);
+    W->red2 = dev_alloc<double>((size_t)nblk * 4);
     W->norms = dev_alloc<double>((size_t)nblk * 4);
     W->sc32 = dev_alloc<double>((size_t)nblk * 4 * 8);
     W->sc64 = dev_alloc<double>((size_t)nblk * 4 * 8);
     W->slot_a = dev_alloc<int32_t>((size_t)nblk * 4);
     W->slot_b = dev_alloc<int32_t>((size_t)nblk * 4);
-    GCK(cudaMallocHost((void**)&W->h_red, sizeof(double) * nblk * 4));
+    GCK(cudaMallocHost((void**)&W->h_red, sizeof(double) * nblk * 8));
     GCK(cudaMallocHost((void**)&W->h_active, sizeof(double) * nblk * 4));
     P.ws[nblk] = W;
     return *W;
@@ -222,6 +223,14 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
     const int nl = (int)P.levels.size();
     Level& L = P.levels[l];
     const int nblk = W.nblk;
+    if (l == 0 && P.use_tsp) {
+        launch_tsp<T>(L, P.ic_rinv, L.inv_eps2, b, (T*)V.t1[0], x, nblk, s);
+        if (rz_partial) {
+            launch_dot<T>(b, x, L.N, nblk, rz_partial, elem_parts(L.N), s);
+            return elem_parts(L.N);
+        }
+        return 0;
+    }
     if (l == nl - 1) {
         launch_dense_solve<T>(dense_of<T>(L), b, x, (int)L.N, nblk, s);
         if (rz_partial) {
@@ -408,13 +417,19 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
         V.graph_tol = inner_tol;
     }
     std::vector<double> bn((size_t)P4, 0.0), rn((size_t)P4, 0.0), nrm((size_t)P4, 0.0);
+    // forward-error test: the correction of the last refinement step and the
+    // contraction rho between the last two estimate the remaining error as
+    // rho / (1 - rho) |dx|; it must be below xtol |x| (xtol = 100 rtol)
+    std::vector<double> dxn((size_t)P4, -1.0), dxp((size_t)P4, -1.0), xn((size_t)P4, 0.0);
+    const double xtol = 100.0 * o.rtol;
     SolveStats st;
-    const int nt = (int)L.ntiles();
+    const int ne = elem_parts(L.N);
     for (int ref = 0; ref <= o.max_refine; ++ref) {
         StencilArgs<double> a{};
         a.L = L.view<double>();
         a.nblk = nblk;
         a.x = x64; a.b = b64; a.out = W.r64; a.partial = W.partial;
+        a.rweight = L.d_dinv64;     // stop on the D^-1-weighted residual norm
         const int ng = launch_stencil<double>(L.geo, M_RESID, a, s);
         launch_reduce(W.partial, ng, nblk, W.red, s);
         GCK(cudaMemcpyAsync(W.h_red, W.red, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
@@ -428,22 +443,47 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
             if (ref == 0) bn[(size_t)i] = rn[(size_t)i];
             const double rel = bn[(size_t)i] > 0 ? rn[(size_t)i] / bn[(size_t)i] : 0.0;
             st.max_rel = std::max(st.max_rel, rel);
-            const bool done = rel <= o.rtol;
+            bool done = rel <= o.rtol;
+            if (done && dxn[(size_t)i] >= 0.0) {
+                double est = dxn[(size_t)i];
+                if (dxp[(size_t)i] > 0.0) {
+                    const double rho = dxn[(size_t)i] / dxp[(size_t)i];
+                    est = rho < 0.5 ? dxn[(size_t)i] * rho / (1.0 - rho) : dxn[(size_t)i];
+                }
+                done = est <= xtol * xn[(size_t)i];
+            }
             conv &= done;
             nrm[(size_t)i] = done ? 0.0 : rn[(size_t)i];
         }
         if (conv) { st.converged = true; break; }
         if (ref == o.max_refine) break;
+        // the inner solve works on r / |r| (unweighted norm keeps FP32 in range)
+        launch_norm2<double>(W.r64, L.N, nblk, W.partial, ne, s);
+        launch_reduce(W.partial, ne, nblk, W.red2, s);
+        GCK(cudaMemcpyAsync(W.h_red + P4, W.red2, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
+        GCK(cudaStreamSynchronize(s));
+        for (int i = 0; i < P4; ++i) nrm[(size_t)i] = nrm[(size_t)i] > 0.0 ? std::sqrt(std::max(W.h_red[P4 + i], 0.0)) : 0.0;
         GCK(cudaMemcpyAsync(W.norms, nrm.data(), sizeof(double) * P4, cudaMemcpyHostToDevice, s));
         bool brk = false;
         if (fp64) {
             launch_scale64(W.r64, W.norms, (double*)W.v64.pcg[1], L.N, nblk, s);
             st.inner += pcg<double>(P, W, inner_tol, o.max_inner, s, graph, &brk, has_dl ? &dl : nullptr);
-            launch_axpy_scaled64(x64, W.norms, (const double*)W.v64.pcg[0], L.N, nblk, s);
+            launch_axpy_scaled64(x64, W.norms, (const double*)W.v64.pcg[0], L.N, nblk, W.partial, s);
         } else {
             launch_scale_cast(W.r64, W.norms, (float*)W.v32.pcg[1], L.N, nblk, s);
             st.inner += pcg<float>(P, W, inner_tol, o.max_inner, s, graph, &brk, has_dl ? &dl : nullptr);
-            launch_axpy_mixed(x64, W.norms, (const float*)W.v32.pcg[0], L.N, nblk, s);
+            launch_axpy_mixed(x64, W.norms, (const float*)W.v32.pcg[0], L.N, nblk, W.partial, s);
+        }
+        launch_reduce(W.partial, ne, nblk, W.red, s);
+        launch_reduce(W.partial + (size_t)nblk * ne * 4, ne, nblk, W.red2, s);
+        GCK(cudaMemcpyAsync(W.h_red, W.red, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
+        GCK(cudaMemcpyAsync(W.h_red + P4, W.red2, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
+        GCK(cudaStreamSynchronize(s));
+        for (int i = 0; i < P4; ++i) {
+            if (nrm[(size_t)i] == 0.0) continue;
+            dxp[(size_t)i] = dxn[(size_t)i];
+            dxn[(size_t)i] = std::sqrt(std::max(W.h_red[i], 0.0));
+            xn[(size_t)i] = std::sqrt(std::max(W.h_red[P4 + i], 0.0));
         }
         st.breakdown |= brk;
     }

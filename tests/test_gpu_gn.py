@@ -1,0 +1,90 @@
+"""Gauss-Newton for Burgers collocation (Sec. 3.3) on the GPU against the
+oracle's exact-solve Gauss-Newton: the data-only starting mean, each iterate,
+step length and Newton decrement, and Laplace samples at the mode.
+
+Tolerances: iterates and decrements relative 1e-6 (max-norm), step lengths
+equal (the Armijo test is far from its threshold on these problems).
+"""
+import numpy as np
+import pytest
+
+from oracle import fem, infer, linalg
+from paper_2503_08343_gb300 import gmrf
+from paper_2503_08343_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2503_08343_gb300 import build
+    build.build()
+    return gmrf.load()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("n,nt,nu", [(65, 33, 0.05), (97, 65, 0.01)])
+def test_gauss_newton_iterates_match_the_oracle(n, nt, nu):
+    pr, ob = W.c3_burgers(nx=n, nt=nt, m=60, seed=3, nu=nu)
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    u_gpu, info = post.solve_mean()
+    u_or = infer.posterior_mean(infer.condition(pr, ob))
+    assert _rel(u_gpu, u_or) < 1e-6                       # data-only posterior mean (Fig. 1)
+    d_gpu = np.zeros_like(u_gpu)
+    u_gpu = u_or.copy()
+    # The direction shrinks as the iteration converges while g = H u - b is
+    # formed from terms of size ~1e18 (collocation weight 1e12), so its FP64
+    # rounding differs between any two implementations; directions are
+    # therefore compared on the scale of the iterate, iterates at 1e-6.
+    scale = np.max(np.abs(u_or))
+    for step in range(4):
+        u_next, d_or, alpha_or, dec_or = infer.gauss_newton_step(pr, ob, u_or)
+        dec, alpha, info = post.gauss_newton_step(u_gpu, d_gpu)
+        assert info["converged"] == 1
+        assert alpha == alpha_or
+        assert np.max(np.abs(d_gpu - d_or)) < 1e-6 * scale, step
+        if step == 0:
+            assert dec == pytest.approx(dec_or, rel=1e-6)
+        assert _rel(u_gpu, u_next) < 1e-6, step
+        u_or = u_next
+
+
+def test_laplace_samples_at_the_mode_match_the_oracle():
+    pr, ob = W.c3_burgers(nx=65, nt=33, m=60, seed=3, nu=0.05)
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    u = infer.posterior_mean(infer.condition(pr, ob))
+    d = np.zeros_like(u)
+    for _ in range(5):
+        post.gauss_newton_step(u, d)
+    mu, xs, info = post.sample(4, 321)
+    lap = infer.condition(pr, ob, linearise_at=u)           # H at the returned point
+    L = linalg.cholesky(lap.Qpost)
+    assert _rel(xs, infer.perturbation_samples(lap, 321, range(4), L)) < 1e-6
+    # at the Gauss-Newton fixed point the mean slot returns the mode
+    assert _rel(mu, linalg.solve(L, lap.b)) < 1e-6
+    assert _rel(mu, u) < 1e-5
+
+
+def test_linear_collocation_posterior_mean_and_samples():
+    # manufactured solution u* = exp(-t) sin(pi x) of u_t + c u_x - nu u_xx = f,
+    # collocated at interior nodes with the initial condition (Sec. 3.1)
+    import math
+    c, nu, n = 0.5, 0.05, 49
+    pr = W.prior_st1d(n, n, c, nu, tau=1.0, kappa0=5.0)
+    from oracle import observe
+    i, k = observe.colloc_rows(pr)
+    x = np.linspace(0, 1, n)[i]
+    t = np.linspace(0, 1, n)[k]
+    f = (-1 + nu * math.pi ** 2) * np.exp(-t) * np.sin(math.pi * x) + c * math.pi * np.exp(-t) * np.cos(math.pi * x)
+    xs = np.linspace(0, 1, n)
+    ob = dict(coords=np.array([[0.3, 0.4], [0.7, 0.9]]), y=np.array([0.5, 0.2]), sigma=np.array([0.1, 0.1]),
+              ic_sigma=1e-6, ic_values=np.sin(math.pi * xs), colloc_sigma=1e-6, colloc_c=c, colloc_f=f, burgers_nu=nu)
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    mu, xs_gpu, info = post.sample(3, 99)
+    orc = infer.condition(pr, ob)
+    L = linalg.cholesky(orc.Qpost)
+    assert _rel(mu, infer.posterior_mean(orc, L)) < 1e-6
+    assert _rel(xs_gpu, infer.perturbation_samples(orc, 99, range(3), L)) < 1e-6
