@@ -301,6 +301,8 @@ void gmrf_posterior_destroy(gmrf_posterior* post) {
     dev_free(P.d_icvals);
     dev_free(P.d_blin);
     dev_free(P.d_gn);
+    dev_free(P.d_grad_part);
+    if (P.prior_only) gmrf_posterior_destroy(static_cast<gmrf_posterior*>(P.prior_only));
     gmrf_prior* pr = post->prior;
     delete post;
     if (pr) prior_release(pr);
@@ -524,9 +526,32 @@ gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* d
 
 gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t seed, double* loglik, double* grad,
                              double* grad_stderr, const gmrf_solve_opts* opts, gmrf_solve_info* info) {
-    (void)post; (void)nprobes; (void)seed; (void)loglik; (void)grad; (void)grad_stderr; (void)opts; (void)info;
-    g_err = "gmrf_loglik_grad: not available in this build";
-    return GMRF_E_INVALID;
+    gmrf_status rc = GMRF_OK;
+    const gmrf_status st = guard([&] {
+        require(post && grad && nprobes >= 1, "bad argument");
+        Posterior& P = post->impl;
+        require(P.nic == 0 && P.colloc_kind == 0, "gmrf_loglik_grad is defined for point data only");
+        enter(post->prior);
+        const gmrf_solve_opts o = resolve_opts(opts);
+        const auto t0 = std::chrono::steady_clock::now();
+        if (!P.prior_only) {
+            gmrf_obs_desc none;
+            std::memset(&none, 0, sizeof(none));
+            gmrf_posterior* q = nullptr;
+            const gmrf_status s2 = gmrf_condition(post->prior, &none, &q);
+            if (s2 != GMRF_OK) throw Error(s2, std::string("prior-only operator: ") + g_err);
+            P.prior_only = q;
+        }
+        double g[5], se[5];
+        const SolveStats ss = loglik_grad(P, static_cast<gmrf_posterior*>(P.prior_only)->impl, nprobes, seed, o, loglik,
+                                          g, se, P.prior->stream);
+        for (int i = 0; i < 5; ++i) {
+            grad[i] = g[i];
+            if (grad_stderr) grad_stderr[i] = se[i];
+        }
+        rc = finish(ss, info, 2 * nprobes + 1, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+    });
+    return st != GMRF_OK ? st : rc;
 }
 
 }  // extern "C"

@@ -88,6 +88,10 @@ void linearise(Posterior& P, const double* u, cudaStream_t s);
 GnResult gauss_newton_step(Posterior& P, double* u_io, double* d_io, bool u_dev, bool d_dev, const gmrf_solve_opts& o,
                            cudaStream_t s);
 
+// grad.cu
+SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, const gmrf_solve_opts& o, double* loglik,
+                       double grad[5], double gse[5], cudaStream_t s);
+
 // scratch of one batch size
 struct Workspace {
     int nblk = 0;

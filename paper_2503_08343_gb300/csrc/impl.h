@@ -138,6 +138,9 @@ struct Posterior {
     double colloc_qeps = 0.0, colloc_nu = 0.0, colloc_c = 0.0;
     bool linearised = false;
     bool use_tsp = false;          // time-stepping preconditioner instead of the V-cycle
+    void* prior_only = nullptr;    // gmrf_posterior* of the same prior without observations (gradient traces)
+    double* d_grad_part = nullptr; // partial sums of the gradient contractions
+    size_t grad_part_n = 0;
     double ic_rinv = 0.0;          // precision of the initial-condition rows
 };
 
