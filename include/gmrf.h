@@ -171,6 +171,23 @@ gmrf_status gmrf_marginal_var(gmrf_posterior* post, int32_t ns, uint64_t seed, d
                               double* var, double* stderr_, const gmrf_solve_opts* opts,
                               gmrf_solve_info* info);
 
+/* Batched serving of independent posteriors (not in the paper, which solves
+ * one problem at a time; a serving workload of many uneven instances):
+ * gmrf_marginal_var for
+ * posts[0..count), instance i with seed + i, means[i] (NULL array or NULL
+ * entry: no mean) and vars[i] (non-NULL, [N_i]) outputs as in
+ * gmrf_marginal_var.  Instances whose posteriors share a prior handle run in
+ * list order on that prior's stream; instances of different priors run
+ * concurrently from min(nthreads, number of priors) host threads (<= 0: 16).
+ * Results equal those of calling gmrf_marginal_var on each instance alone.
+ * No posterior or prior in the list may be used elsewhere during the call.
+ * infos: [count] or NULL.  Returns GMRF_E_INVALID for a NULL entry before any
+ * work, else the status of the first instance in list order that failed
+ * (gmrf_last_error names it); the other instances still complete. */
+gmrf_status gmrf_marginal_var_batch(gmrf_posterior* const* posts, int32_t count, int32_t ns, uint64_t seed,
+                                    double* const* means, double* const* vars, const gmrf_solve_opts* opts,
+                                    gmrf_solve_info* infos, int32_t nthreads);
+
 /* One Gauss-Newton step on -log pi(u) (Sec. 3.3, eq. nonlinear-mode) for
  * Burgers collocation: H = Q + J^T Q_eps J + A^T R^-1 A at mu_k, solve
  * H d = -grad, warm-started from delta_prev, then Armijo backtracking
@@ -230,6 +247,18 @@ gmrf_status gmrf_time_stencil(gmrf_posterior* post, int32_t kernel, int32_t k, i
 /* Number of kernels this library has launched in the process so far
  * (kernels inside replayed CUDA graphs included). */
 uint64_t gmrf_launch_count(void);
+
+/* Multigrid hierarchy of a posterior: grid dimensions (nx, ny, nt) of level
+ * `level` (0 = finest) and the bound on the spectrum of D^-1 Q_u|y used by
+ * its Chebyshev smoother (0 on the coarsest level, which is solved directly). */
+gmrf_status gmrf_level_info(const gmrf_posterior* post, int32_t level, int32_t* dims, double* lmax);
+
+/* Grid transfer of the multigrid hierarchy in the space plane: *p1 = 1 for
+ * P1 interpolation on the triangulation (chosen when the observation rows
+ * contribute at least half of some fine-level diagonal entry of Q_u|y),
+ * 0 for bilinear; *data_share (may be NULL) receives that largest share.
+ * Both transfers reduce to linear interpolation along a single axis. */
+gmrf_status gmrf_transfer_info(const gmrf_posterior* post, int32_t* p1, double* data_share);
 
 int64_t gmrf_num_unknowns(const gmrf_prior* prior);
 int32_t gmrf_num_levels(const gmrf_prior* prior);

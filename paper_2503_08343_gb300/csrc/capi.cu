@@ -6,6 +6,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <map>
+#include <thread>
 
 #include "handles.h"
 
@@ -159,6 +161,25 @@ gmrf_status gmrf_build_prior(const gmrf_prior_desc* desc, void* stream, gmrf_pri
         }
         build_hierarchy(d, p->impl.levels);
         *out = p;
+    });
+}
+
+gmrf_status gmrf_level_info(const gmrf_posterior* post, int32_t level, int32_t* dims, double* lmax) {
+    return guard([&] {
+        require(post && dims && level >= 0 && level < (int32_t)post->impl.levels.size(), "bad argument");
+        const Level& L = post->impl.levels[(size_t)level];
+        dims[0] = L.nx;
+        dims[1] = L.ny;
+        dims[2] = L.nt;
+        if (lmax) *lmax = L.lmax;
+    });
+}
+
+gmrf_status gmrf_transfer_info(const gmrf_posterior* post, int32_t* p1, double* data_share) {
+    return guard([&] {
+        require(post && p1, "bad argument");
+        *p1 = post->impl.transfer_p1 ? 1 : 0;
+        if (data_share) *data_share = post->impl.data_share;
     });
 }
 
@@ -461,6 +482,71 @@ gmrf_status gmrf_marginal_var(gmrf_posterior* post, int32_t ns, uint64_t seed, d
         rc = finish(ss, info, b.nrhs, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     });
     return st != GMRF_OK ? st : rc;
+}
+
+gmrf_status gmrf_marginal_var_batch(gmrf_posterior* const* posts, int32_t count, int32_t ns, uint64_t seed,
+                                    double* const* means, double* const* vars, const gmrf_solve_opts* opts,
+                                    gmrf_solve_info* infos, int32_t nthreads) {
+    if (!posts || count < 0 || !vars) {
+        g_err = "gmrf_marginal_var_batch: bad argument";
+        return GMRF_E_INVALID;
+    }
+    for (int i = 0; i < count; ++i) {
+        if (!posts[i] || !vars[i]) {
+            g_err = "gmrf_marginal_var_batch: null posterior or output at instance " + std::to_string(i);
+            return GMRF_E_INVALID;
+        }
+    }
+    // Posteriors of one prior share its stream (and a posterior listed twice
+    // shares its workspace), so each group of instances with the same prior
+    // goes to one worker, in list order; groups run concurrently.
+    std::vector<std::vector<int>> groups;
+    {
+        std::map<const gmrf_prior*, size_t> at;
+        for (int i = 0; i < count; ++i) {
+            auto it = at.find(posts[i]->prior);
+            if (it == at.end()) {
+                at.emplace(posts[i]->prior, groups.size());
+                groups.push_back({i});
+            } else {
+                groups[it->second].push_back(i);
+            }
+        }
+    }
+    const int ngroups = (int)groups.size();
+    const int nt = std::max(1, std::min<int>(nthreads > 0 ? nthreads : 16, std::max(ngroups, 1)));
+    std::atomic<int> next{0};
+    std::vector<gmrf_status> sts((size_t)std::max(count, 1), GMRF_OK);
+    std::vector<std::string> errs((size_t)std::max(count, 1));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        for (;;) {
+            const int g = next.fetch_add(1);
+            if (g >= ngroups) break;
+            for (const int i : groups[(size_t)g]) {
+                gmrf_solve_info inf;
+                std::memset(&inf, 0, sizeof(inf));
+                const gmrf_status st = gmrf_marginal_var(posts[i], ns, seed + (uint64_t)i, means ? means[i] : nullptr,
+                                                         vars[i], nullptr, opts, &inf);
+                if (infos) infos[i] = inf;
+                sts[(size_t)i] = st;
+                if (st != GMRF_OK) errs[(size_t)i] = g_err;
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    for (int i = 0; i < count; ++i) {       // report the first failing instance in list order
+        if (sts[(size_t)i] != GMRF_OK) {
+            g_err = "instance " + std::to_string(i) + ": " + errs[(size_t)i];
+            return sts[(size_t)i];
+        }
+    }
+    return GMRF_OK;
 }
 
 gmrf_status gmrf_apply_posterior(gmrf_posterior* post, int32_t k, const double* x, double* y) {

@@ -138,9 +138,6 @@ DerivTaps derivative_taps(const gmrf_prior_desc& d, const Level& L) {
     std::memset(&D, 0, sizeof(D));
     const bool st = d.kind == GMRF_ADVDIFF_ST_1D || d.kind == GMRF_ADVDIFF_ST_2D;
     const int dim = d.kind == GMRF_ADVDIFF_ST_1D ? 1 : 2;
-    // unit-coefficient operators on this level
-    gmrf_prior_desc one = d;
-    Level tmp = L;
     auto coeffs = [&](const gmrf_prior_desc& dd, double out[2][NTAP]) {
         Level t2 = L;
         level_coefficients(dd, t2);
@@ -180,8 +177,6 @@ DerivTaps derivative_taps(const gmrf_prior_desc& d, const Level& L) {
         for (int o = 0; o < NTAP; ++o) D.d[0][1][o] = dlog * base[1][o];
         D.d[0][1][0] += d0 * 2.0 * d.kappa0 * d.kappa0 * M;
     }
-    (void)one;
-    (void)tmp;
     return D;
 }
 

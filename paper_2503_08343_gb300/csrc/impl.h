@@ -117,6 +117,8 @@ struct Prior {
 
 struct Workspace;
 
+constexpr double kP1DataShare = 0.5;
+
 struct Posterior {
     Prior* prior = nullptr;
     std::vector<Level> levels;
@@ -138,6 +140,16 @@ struct Posterior {
     double colloc_qeps = 0.0, colloc_nu = 0.0, colloc_c = 0.0;
     bool linearised = false;
     bool use_tsp = false;          // time-stepping preconditioner instead of the V-cycle
+    // Grid transfers in the space plane: P1 interpolation on the triangulation
+    // when observation rows dominate the diagonal of some fine-level node,
+    // else bilinear.  With P1 transfers on nested grids the coarse space is a
+    // subspace of the fine one, so point data rediscretised on a coarse level
+    // equals its Galerkin projection; bilinear transfers break that
+    // consistency and strongly observed problems then stall, while weakly
+    // observed ones converge a little faster with the symmetric bilinear
+    // transfer.
+    double data_share = 0.0;       // max_n (obs part of diag_n) / diag_n, fine level
+    bool transfer_p1 = false;
     void* prior_only = nullptr;    // gmrf_posterior* of the same prior without observations (gradient traces)
     double* d_grad_part = nullptr; // partial sums of the gradient contractions
     size_t grad_part_n = 0;

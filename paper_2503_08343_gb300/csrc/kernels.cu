@@ -13,6 +13,7 @@
 #include <atomic>
 #include <cstdio>
 #include <map>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 
@@ -464,26 +465,32 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
     static int attr_smem = 0;
     static int sms = 0;
     static std::map<size_t, int> per_sm;       // resident CTAs per SM by dynamic shared memory
+    static std::mutex mu;                      // solves of independent posteriors may run on several host threads
     const size_t smem = sizeof(SM) + (a.L.ocap > 0 ? (size_t)NS * (SM::TN * 2 + a.L.ostride) : 0);
-    if (sms == 0) {
-        int dev = 0;
-        cuda_ok(cudaGetDevice(&dev));
-        cuda_ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    }
-    if ((int)smem > attr_smem) {
-        cuda_ok(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_smem = (int)smem;
-    }
-    auto itp = per_sm.find(smem);
-    if (itp == per_sm.end()) {
-        int per = 0;
-        cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem));
-        if (per <= 0) throw std::runtime_error("stencil kernel does not fit on an SM (shared memory)");
-        itp = per_sm.emplace(smem, per).first;
+    int resident = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (sms == 0) {
+            int dev = 0;
+            cuda_ok(cudaGetDevice(&dev));
+            cuda_ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        if ((int)smem > attr_smem) {
+            cuda_ok(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_smem = (int)smem;
+        }
+        auto itp = per_sm.find(smem);
+        if (itp == per_sm.end()) {
+            int per = 0;
+            cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem));
+            if (per <= 0) throw std::runtime_error("stencil kernel does not fit on an SM (shared memory)");
+            itp = per_sm.emplace(smem, per).first;
+        }
+        resident = sms * itp->second;
     }
     const long long ntiles = (long long)a.L.tiles_x * a.L.tiles_y * a.L.tiles_t;
     const long long nunits = ntiles * ((a.nblk + KB - 1) / KB);
-    const int grid = (int)std::min<long long>(std::min<long long>(nunits, (long long)sms * itp->second), kMaxStencilGrid);
+    const int grid = (int)std::min<long long>(std::min<long long>(nunits, (long long)resident), kMaxStencilGrid);
     { kern<<<(unsigned)grid, 256, smem, s>>>(a, (int)nunits); note_launch(); }
     return grid;
 }
@@ -691,11 +698,66 @@ void launch_restrict_axis(const T* in, T* out, int nx, int ny, int nt, int axis,
 template void launch_restrict_axis<float>(const float*, float*, int, int, int, int, int, const int32_t*, const int32_t*, const int32_t*, const float*, int, cudaStream_t);
 template void launch_restrict_axis<double>(const double*, double*, int, int, int, int, int, const int32_t*, const int32_t*, const int32_t*, const double*, int, cudaStream_t);
 
+// Weight of the coarse corner (dx, dy) of a cell for a fine node at cell
+// offsets (wx, wy) in [0, 1]^2 under P1 interpolation on the triangulation
+// with diagonals (i, j)-(i+1, j+1): the coarse finite-element function
+// evaluated at the fine node.  On nested grids the coarse space is then a
+// subspace of the fine one, so point data rediscretised on a coarse level
+// equals its Galerkin projection.
+template <typename T>
+__device__ __forceinline__ T p1_weight(int dx, int dy, T wx, T wy) {
+    if (dx == 0 && dy == 0) return T(1) - (wx > wy ? wx : wy);
+    if (dx == 1 && dy == 0) return wx > wy ? wx - wy : T(0);
+    if (dx == 0 && dy == 1) return wy > wx ? wy - wx : T(0);
+    if (dx == 1 && dy == 1) return wx < wy ? wx : wy;
+    return T(0);
+}
+
+// Restriction in the (x, y) plane (transpose of the P1 interpolation) when
+// both space axes coarsen: out[.., Jy, Jx] = sum P(x, y; Jx, Jy) in[.., y, x]
+// over the fine ranges of Jx and Jy.
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_xy(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nt,
+                                                     int cx, int cy, const int32_t* __restrict__ rsx,
+                                                     const int32_t* __restrict__ rcx, const int32_t* __restrict__ pjx,
+                                                     const T* __restrict__ pwx, const int32_t* __restrict__ rsy,
+                                                     const int32_t* __restrict__ rcy, const int32_t* __restrict__ pjy,
+                                                     const T* __restrict__ pwy) {
+    const long long Nout = (long long)cx * cy * nt, Nin = (long long)nx * ny * nt;
+    const int blk = blockIdx.y;
+    const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (n >= Nout) return;
+    const int Jx = (int)(n % cx);
+    const long long r = n / cx;
+    const int Jy = (int)(r % cy), t = (int)(r / cy);
+    const T* src = in + ((size_t)blk * Nin + (size_t)t * nx * ny) * RW;
+    V4<T> acc = v4zero<T>();
+    const int x0 = rsx[Jx], x1 = x0 + rcx[Jx], y0 = rsy[Jy], y1 = y0 + rcy[Jy];
+    for (int y = y0; y < y1; ++y) {
+        const int dy = Jy - pjy[y];
+        const T wy = pwy[y];
+        for (int x = x0; x < x1; ++x) {
+            const T w = p1_weight<T>(Jx - pjx[x], dy, pwx[x], wy);
+            if (w != T(0)) acc = fma4(w, v4load(src + ((size_t)y * nx + x) * RW), acc);
+        }
+    }
+    v4store(out + ((size_t)blk * Nout + n) * RW, acc);
+}
+
+template <typename T>
+void launch_restrict_xy(const T* in, T* out, int nx, int ny, int nt, int cx, int cy, const int32_t* const rs[2],
+                        const int32_t* const rc[2], const int32_t* const pj[2], const T* const pw[2], int nblk, cudaStream_t s) {
+    const long long Nout = (long long)cx * cy * nt;
+    { k_restrict_xy<T><<<dim3((unsigned)((Nout + 255) / 256), nblk), 256, 0, s>>>(in, out, nx, ny, nt, cx, cy, rs[0], rc[0], pj[0], pw[0], rs[1], rc[1], pj[1], pw[1]); note_launch(); }
+}
+template void launch_restrict_xy<float>(const float*, float*, int, int, int, int, int, const int32_t* const[2], const int32_t* const[2], const int32_t* const[2], const float* const[2], int, cudaStream_t);
+template void launch_restrict_xy<double>(const double*, double*, int, int, int, int, int, const int32_t* const[2], const int32_t* const[2], const int32_t* const[2], const double* const[2], int, cudaStream_t);
+
 struct AxisMap { const int32_t* j; const void* w; bool on; };
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(T* __restrict__ xf, const T* __restrict__ xc, int nx, int ny, int nt,
-                                                     int cx, int cy, int ct, AxisMap ax, AxisMap ay, AxisMap at) {
+                                                     int cx, int cy, int ct, AxisMap ax, AxisMap ay, AxisMap at, bool p1) {
     const long long Nf = (long long)nx * ny * nt, Nc = (long long)cx * cy * ct;
     const int blk = blockIdx.y;
     const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
@@ -710,14 +772,17 @@ __global__ void __launch_bounds__(256) k_prolong_add(T* __restrict__ xf, const T
     if (at.on) { jt = at.j[t]; wt = ((const T*)at.w)[t]; }
     const T* xb = xc + (size_t)blk * Nc * RW;
     V4<T> acc = v4zero<T>();
+    // space: P1 on the triangulation (p1) or bilinear; both reduce to linear
+    // along a single coarsened axis, where the other offset is 0.  Time: linear.
     for (int dt = 0; dt < (at.on ? 2 : 1); ++dt) {
         const T ft = at.on ? (dt ? wt : T(1) - wt) : T(1);
         for (int dy = 0; dy < (ay.on ? 2 : 1); ++dy) {
-            const T fy = ay.on ? (dy ? wy : T(1) - wy) : T(1);
             for (int dx = 0; dx < (ax.on ? 2 : 1); ++dx) {
-                const T fx = ax.on ? (dx ? wx : T(1) - wx) : T(1);
+                const T fs = p1 ? p1_weight<T>(dx, dy, wx, wy) : (dx ? wx : T(1) - wx) * (dy ? wy : T(1) - wy);
+                const T f = ft * fs;
+                if (f == T(0)) continue;
                 const long long c = ((long long)(jt + dt) * cy + (jy + dy)) * cx + (jx + dx);
-                acc = fma4(ft * fy * fx, v4load(xb + c * RW), acc);
+                acc = fma4(f, v4load(xb + c * RW), acc);
             }
         }
     }
@@ -726,15 +791,15 @@ __global__ void __launch_bounds__(256) k_prolong_add(T* __restrict__ xf, const T
 }
 
 template <typename T>
-void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, int nblk, cudaStream_t s) {
+void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, bool p1, int nblk, cudaStream_t s) {
     const bool dbl = sizeof(T) == 8;
     AxisMap ax{f.d_pj[0], dbl ? (const void*)f.d_pwd[0] : (const void*)f.d_pw[0], f.coarsen[0]};
     AxisMap ay{f.d_pj[1], dbl ? (const void*)f.d_pwd[1] : (const void*)f.d_pw[1], f.coarsen[1]};
     AxisMap at{f.d_pj[2], dbl ? (const void*)f.d_pwd[2] : (const void*)f.d_pw[2], f.coarsen[2]};
-    { k_prolong_add<T><<<dim3((unsigned)((f.N + 255) / 256), nblk), 256, 0, s>>>(xf, xc, f.nx, f.ny, f.nt, c.nx, c.ny, c.nt, ax, ay, at); note_launch(); }
+    { k_prolong_add<T><<<dim3((unsigned)((f.N + 255) / 256), nblk), 256, 0, s>>>(xf, xc, f.nx, f.ny, f.nt, c.nx, c.ny, c.nt, ax, ay, at, p1); note_launch(); }
 }
-template void launch_prolong_add<float>(float*, const float*, const Level&, const Level&, int, cudaStream_t);
-template void launch_prolong_add<double>(double*, const double*, const Level&, const Level&, int, cudaStream_t);
+template void launch_prolong_add<float>(float*, const float*, const Level&, const Level&, bool, int, cudaStream_t);
+template void launch_prolong_add<double>(double*, const double*, const Level&, const Level&, bool, int, cudaStream_t);
 
 // coarsest level: x = Q_c^-1 b with the stored dense inverse
 template <typename T>
@@ -1120,6 +1185,31 @@ void launch_obs_diag(const ObsRow* obs, int nobs, double* diag, cudaStream_t s) 
     if (nobs > 0) { k_obs_diag<<<(nobs + 255) / 256, 256, 0, s>>>(obs, nobs, diag); note_launch(); }
 }
 
+// max_n (total_n - prior_n) / total_n: the largest share of a node's diagonal
+// contributed by the observation rows.  Non-negative doubles order like their
+// bit patterns, so the block maxima combine with an integer atomicMax.
+__global__ void k_max_share(const double* __restrict__ prior, const double* __restrict__ total, long long N,
+                            unsigned long long* __restrict__ out) {
+    __shared__ double red[256];
+    double m = 0.0;
+    for (long long n = (long long)blockIdx.x * 256 + threadIdx.x; n < N; n += (long long)gridDim.x * 256) {
+        const double t = total[n];
+        if (t > 0.0) m = fmax(m, fmax(0.0, (t - prior[n]) / t));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(red[0]));
+}
+void launch_max_share(const double* prior, const double* total, long long N, unsigned long long* out, cudaStream_t s) {
+    const long long want = (N + 255) / 256;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(want, 4 * 152));
+    { k_max_share<<<grid, 256, 0, s>>>(prior, total, N, out); note_launch(); }
+}
+
 __global__ void k_finish_diag(const double* __restrict__ diag, float* __restrict__ dinv32, double* __restrict__ dinv64, long long N) {
     const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
     if (n >= N) return;
@@ -1242,15 +1332,17 @@ void launch_scale_comp(float* v, const float* w, const double* nrm2, long long N
     { k_scale_comp<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(v, w, nrm2, N); note_launch(); }
 }
 
-__global__ void k_fill_random(float* __restrict__ v, long long N, uint64_t seed) {
+// Standard normals, each node scaled by sqrt(dinv[n]) when dinv is given.
+__global__ void k_fill_random(float* __restrict__ v, long long N, uint64_t seed, const float* __restrict__ dinv) {
     const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
     if (n >= N) return;
+    const float sc = dinv ? sqrtf(dinv[n]) : 1.f;
     float r[4];
-    for (int c = 0; c < 4; ++c) r[c] = (float)philox_normal(seed, 7u, (uint32_t)c, (uint64_t)n);
+    for (int c = 0; c < 4; ++c) r[c] = sc * (float)philox_normal(seed, 7u, (uint32_t)c, (uint64_t)n);
     v4store(v + n * RW, V4<float>{r[0], r[1], r[2], r[3]});
 }
-void launch_fill_random(float* v, long long N, uint64_t seed, cudaStream_t s) {
-    { k_fill_random<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(v, N, seed); note_launch(); }
+void launch_fill_random(float* v, long long N, uint64_t seed, cudaStream_t s, const float* dinv) {
+    { k_fill_random<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(v, N, seed, dinv); note_launch(); }
 }
 
 }  // namespace gmrf

@@ -41,7 +41,10 @@ template <typename T> void launch_cheb_first(const T* b, const T* dinv, T c2, T*
 template <typename T> void launch_restrict_axis(const T* in, T* out, int nx, int ny, int nt, int axis, int ncoarse,
                                                 const int32_t* rs, const int32_t* rc, const int32_t* pj, const T* pw,
                                                 int nblk, cudaStream_t s);
-template <typename T> void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, int nblk, cudaStream_t s);
+template <typename T> void launch_restrict_xy(const T* in, T* out, int nx, int ny, int nt, int cx, int cy,
+                                              const int32_t* const rs[2], const int32_t* const rc[2],
+                                              const int32_t* const pj[2], const T* const pw[2], int nblk, cudaStream_t s);
+template <typename T> void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, bool p1, int nblk, cudaStream_t s);
 template <typename T> void launch_dense_solve(const T* Ainv, const T* b, T* x, int n, int nblk, cudaStream_t s);
 
 // PCG scalar and vector steps.  Per-RHS scalars live in `sc` (FP64):
@@ -70,6 +73,7 @@ void launch_rbmc(const double* Qx, const double* x, const double* diag, const in
                  int nblk, int ns, double* var, double* se, cudaStream_t s);
 template <typename T> void launch_diag(int geo, const LevelView<T>& L, double* diag64, cudaStream_t s);
 void launch_obs_diag(const ObsRow* obs, int nobs, double* diag, cudaStream_t s);
+void launch_max_share(const double* prior, const double* total, long long N, unsigned long long* out, cudaStream_t s);
 void launch_finish_diag(const double* diag, float* dinv32, double* dinv64, long long N, cudaStream_t s);
 void launch_normals(uint64_t seed, int stream, int sample0, int count, long long n, double* out, cudaStream_t s);
 template <typename T> void launch_cast(const double* in, T* out, long long n, cudaStream_t s);
@@ -83,5 +87,5 @@ template <typename T> void launch_dot(const T* a, const T* b, long long N, int n
 template <typename T> void launch_norm2(const T* v, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
 void launch_power_scale(float* q, const float* dinv, long long N, double* partial, int nparts, cudaStream_t s);
 void launch_scale_comp(float* v, const float* w, const double* nrm2, long long N, cudaStream_t s);
-void launch_fill_random(float* v, long long N, uint64_t seed, cudaStream_t s);
+void launch_fill_random(float* v, long long N, uint64_t seed, cudaStream_t s, const float* dinv = nullptr);
 }  // namespace gmrf

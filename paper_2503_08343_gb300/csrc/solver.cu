@@ -75,7 +75,12 @@ static double power_lmax(Posterior& P, Level& L, cudaStream_t s) {
     const int np = elem_parts(N);
     double* part = dev_alloc<double>((size_t)std::max<long long>(std::max<long long>(nt, np), stencil_max_grid()) * 4);
     double* red = dev_alloc<double>(4);
-    launch_fill_random(v, N, 0x5eed, s);
+    // Start from D^-1/2 g: every node then carries the same weight in the
+    // D-norm.  A plain normal start would be dominated by the Dirichlet rows
+    // (D = 1/eps^2, eigenvalue exactly 1) and, when lambda_max is close to 1
+    // (mass-dominated operators, kappa^2 h^2 >> nu), 24 steps could not lift
+    // the interior modes above them.
+    launch_fill_random(v, N, 0x5eed, s, L.d_dinv32);
     StencilArgs<float> a{};
     a.L = L.view<float>();
     a.x = v;
@@ -102,12 +107,29 @@ static double power_lmax(Posterior& P, Level& L, cudaStream_t s) {
     return lam;
 }
 
-static void setup_diag(Level& L, cudaStream_t s) {
+// Jacobi diagonal of level L; with share != nullptr also the largest share of
+// a node's diagonal that the observation rows contribute (dinv64 holds the
+// prior diagonal until the final step overwrites it).
+static void setup_diag(Level& L, cudaStream_t s, double* share = nullptr) {
     if (!L.d_diag64) L.d_diag64 = dev_alloc<double>((size_t)L.N);
     if (!L.d_dinv32) L.d_dinv32 = dev_alloc<float>((size_t)L.N);
     if (!L.d_dinv64) L.d_dinv64 = dev_alloc<double>((size_t)L.N);
     launch_diag<double>(L.geo, L.view<double>(), L.d_diag64, s);
+    unsigned long long* d_share = nullptr;
+    if (share) {
+        d_share = dev_alloc<unsigned long long>(1);
+        GCK(cudaMemsetAsync(d_share, 0, sizeof(unsigned long long), s));
+        GCK(cudaMemcpyAsync(L.d_dinv64, L.d_diag64, (size_t)L.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     launch_obs_diag(L.d_obs, L.nobs, L.d_diag64, s);
+    if (share) {
+        launch_max_share(L.d_dinv64, L.d_diag64, L.N, d_share, s);
+        unsigned long long bits = 0;
+        GCK(cudaMemcpyAsync(&bits, d_share, sizeof(bits), cudaMemcpyDeviceToHost, s));
+        GCK(cudaStreamSynchronize(s));
+        std::memcpy(share, &bits, sizeof(double));
+        dev_free(d_share);
+    }
     launch_finish_diag(L.d_diag64, L.d_dinv32, L.d_dinv64, L.N, s);
 }
 
@@ -128,7 +150,10 @@ static void setup_dense(Level& L, cudaStream_t s) {
 
 void posterior_refresh_operator(Posterior& P, cudaStream_t s) {
     const int nl = (int)P.levels.size();
-    for (int l = 0; l < nl; ++l) setup_diag(P.levels[l], s);
+    double share = 0.0;
+    for (int l = 0; l < nl; ++l) setup_diag(P.levels[l], s, l == 0 ? &share : nullptr);
+    P.data_share = share;
+    P.transfer_p1 = share >= kP1DataShare;
     for (int l = 0; l < nl - 1; ++l) P.levels[l].lmax = 1.1 * power_lmax(P, P.levels[l], s);
     setup_dense(P.levels[nl - 1], s);
     GCK(cudaStreamSynchronize(s));
@@ -252,7 +277,8 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
     a.x = X0; a.b = b; a.d = D; a.dinv = dinv; a.out = x; a.out2 = D;
     a.c1 = (T)ch.c1[1]; a.c2 = (T)ch.c2[1];
     launch_stencil<T>(L.geo, M_CHEB, a, s);
-    // residual and restriction (separable transpose of the interpolation)
+    // residual and restriction (transpose of the interpolation: P1 in the
+    // space plane when both space axes coarsen, then linear per axis)
     StencilArgs<T> r = a;
     r.x = x; r.b = b; r.d = nullptr; r.out = R; r.out2 = nullptr;
     launch_stencil<T>(L.geo, M_RESID, r, s);
@@ -264,7 +290,20 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
         if (L.coarsen[ax]) last = ax;
     const T* src = R;
     bool use_t1 = true;
-    for (int ax = 0; ax < 3; ++ax) {
+    const bool plane = P.transfer_p1 && L.coarsen[0] && L.coarsen[1];
+    if (plane) {
+        T* dst = last == 1 ? (T*)V.b[l + 1] : (T*)V.t1[l];
+        use_t1 = false;
+        const int32_t* const rs[2] = {L.d_rs[0], L.d_rs[1]};
+        const int32_t* const rc[2] = {L.d_rc[0], L.d_rc[1]};
+        const int32_t* const pj[2] = {L.d_pj[0], L.d_pj[1]};
+        const T* const pw[2] = {pw_of<T>(L, 0), pw_of<T>(L, 1)};
+        launch_restrict_xy<T>(src, dst, dims[0], dims[1], dims[2], cdims[0], cdims[1], rs, rc, pj, pw, nblk, s);
+        dims[0] = cdims[0];
+        dims[1] = cdims[1];
+        src = dst;
+    }
+    for (int ax = plane ? 2 : 0; ax < 3; ++ax) {
         if (!L.coarsen[ax]) continue;
         T* dst = ax == last ? (T*)V.b[l + 1] : (use_t1 ? (T*)V.t1[l] : (T*)V.t2[l]);
         use_t1 = !use_t1;
@@ -274,7 +313,7 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
         src = dst;
     }
     vcycle<T>(P, W, V, l + 1, (const T*)V.b[l + 1], (T*)V.xb[l + 1], nullptr, s);
-    launch_prolong_add<T>(x, (const T*)V.xb[l + 1], L, C, nblk, s);
+    launch_prolong_add<T>(x, (const T*)V.xb[l + 1], L, C, P.transfer_p1, nblk, s);
     // post-smoothing: a fresh Chebyshev(2) sweep
     StencilArgs<T> p1 = a;
     p1.x = x; p1.d = nullptr; p1.out = X0; p1.out2 = D; p1.c1 = T(0); p1.c2 = (T)ch.c2[0];

@@ -87,8 +87,12 @@ def load(build_if_missing: bool = False):
         "gmrf_gauss_newton_step": (I32, [P, P, P, DP, DP, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "gmrf_loglik_grad": (I32, [P, I32, U64, DP, DP, DP, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "gmrf_apply_posterior": (I32, [P, I32, P, P]),
+        "gmrf_marginal_var_batch": (I32, [C.POINTER(P), I32, I32, U64, C.POINTER(P), C.POINTER(P),
+                                          C.POINTER(SolveOpts), C.POINTER(SolveInfo), I32]),
         "gmrf_normals": (I32, [U64, I32, I32, I32, I64, P]),
         "gmrf_time_stencil": (I32, [P, I32, I32, I32, DP]),
+        "gmrf_level_info": (I32, [P, I32, C.POINTER(C.c_int32), DP]),
+        "gmrf_transfer_info": (I32, [P, C.POINTER(C.c_int32), DP]),
         "gmrf_num_unknowns": (I64, [P]),
         "gmrf_num_levels": (I32, [P]),
         "gmrf_prior_destroy": (None, [P]),
@@ -254,6 +258,24 @@ class Posterior:
         _check(load().gmrf_apply_posterior(self.h, x.shape[0], _ptr(x), _ptr(y)))
         return y
 
+    def level_info(self):
+        """[(nx, ny, nt, chebyshev lambda_max bound)] from finest to coarsest."""
+        out = []
+        for l in range(self.prior.levels):
+            dims = (C.c_int32 * 3)()
+            lm = C.c_double()
+            _check(load().gmrf_level_info(self.h, l, dims, C.byref(lm)))
+            out.append((dims[0], dims[1], dims[2], lm.value))
+        return out
+
+    def transfer_info(self):
+        """(True for P1 space-plane grid transfers / False for bilinear,
+        largest observation share of a fine-level diagonal entry)."""
+        p1 = C.c_int32()
+        share = C.c_double()
+        _check(load().gmrf_transfer_info(self.h, C.byref(p1), C.byref(share)))
+        return bool(p1.value), share.value
+
     def time_stencil(self, kernel, k, iters=20) -> float:
         """kernel: 0 apply, 1 residual, 2 Chebyshev step (finest level, FP32)."""
         ms = C.c_double()
@@ -264,6 +286,21 @@ class Posterior:
         if getattr(self, "h", None) and _lib is not None:
             _lib.gmrf_posterior_destroy(self.h)
             self.h = None
+
+
+def marginal_var_batch(posts, ns, seed, means=True, opts=None, nthreads=16):
+    """gmrf_marginal_var over independent posteriors, concurrently across
+    priors (posteriors of one prior run in list order); instance i uses
+    seed + i.  Returns (means, vars, infos)."""
+    k = len(posts)
+    vs = [np.empty(p.N) for p in posts]
+    ms = [np.empty(p.N) for p in posts] if means else None
+    hp = (C.c_void_p * k)(*[p.h.value for p in posts])
+    vp = (C.c_void_p * k)(*[v.ctypes.data for v in vs])
+    mp = (C.c_void_p * k)(*[m.ctypes.data for m in ms]) if means else None
+    infos = (SolveInfo * k)()
+    _check(load().gmrf_marginal_var_batch(hp, k, ns, seed, mp, vp, C.byref(opts or default_opts()), infos, nthreads))
+    return ms, vs, [i.as_dict() for i in infos]
 
 
 def normals(seed, stream, sample0, count, n):

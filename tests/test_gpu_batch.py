@@ -1,0 +1,108 @@
+"""Batched serving of independent posteriors (uneven 2D instances, Matern
+and steady advection-diffusion mixed): the concurrent batch entry point
+gives the same results as solving each instance alone, and the means match
+the oracle.  Mass-dominated steady instances (kappa^2 h^2 / nu >> 1) put
+lambda_max(D^-1 Q) close to 1, which the Chebyshev bound must still cover."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import infer
+from paper_2503_08343_gb300 import gmrf
+from paper_2503_08343_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+INSTANCES = dict(count=12, seed=4, smin=20, smax=72)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2503_08343_gb300 import build
+    build.build()
+    return gmrf.load()
+
+
+def _jacobi_spectrum(Q):
+    d = Q.diagonal()
+    s = sp.diags(1.0 / np.sqrt(d))
+    ev = np.linalg.eigvalsh((s @ Q @ s).toarray())
+    return ev.min(), ev.max()
+
+
+@pytest.mark.parametrize("index", [1, 5, 7])
+def test_chebyshev_bound_covers_the_fine_level_spectrum(index):
+    # instances 1 and 5 are mass-dominated (lambda_max about 1.3), 7 is not
+    pr, ob = W.c4_instances(**INSTANCES)[index]
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    lo, hi = _jacobi_spectrum(infer.condition(pr, ob).Qpost)
+    bound = post.level_info()[0][3]
+    assert hi <= bound <= 1.1 * hi * 1.0001, (lo, hi, bound)
+    mu, info = post.solve_mean()
+    assert info["converged"] == 1
+    want = infer.posterior_mean(infer.condition(pr, ob))
+    assert np.max(np.abs(mu - want)) < 1e-6 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("index", [186, 29])
+def test_strong_point_data_converges_quickly(index):
+    # 186: steady, 257^2 (nested coarse grids), 2698 observations at sigma 0.002;
+    # 29: Matern, 262^2 (non-nested coarse grids), 3248 at sigma 0.003.  Coarse
+    # levels carry more observations than nodes; with P1 grid transfers the
+    # rediscretised data term stays consistent and PCG converges in tens of
+    # iterations (bilinear transfers stalled here).
+    pr, ob = W.c4_instances(count=256)[index]
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    orc = infer.condition(pr, ob)
+    p1, share = post.transfer_info()
+    assert share == pytest.approx(np.max(1.0 - orc.Q.diagonal() / orc.Qpost.diagonal()), rel=1e-9)
+    assert p1 and share > 0.99
+    mu, info = post.solve_mean()
+    assert info["converged"] == 1
+    assert info["inner_iterations"] <= 200, info
+    want = infer.posterior_mean(orc)
+    assert np.max(np.abs(mu - want)) < 1e-6 * np.max(np.abs(want))
+
+
+def test_weak_point_data_keeps_bilinear_transfers():
+    # 128^2 Matern, 2000 observations at sigma 0.5: largest data share about 0.1
+    pr = W.prior_matern2d(128, 20.0)
+    ob = W.point_obs(pr, 2000, 0.5, lambda z: np.sin(3 * z[:, 0]) * np.cos(2 * z[:, 1]), seed=3)
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    orc = infer.condition(pr, ob)
+    p1, share = post.transfer_info()
+    assert share == pytest.approx(np.max(1.0 - orc.Q.diagonal() / orc.Qpost.diagonal()), rel=1e-9)
+    assert not p1 and share < 0.5
+    mu, info = post.solve_mean()
+    assert info["converged"] == 1
+    want = infer.posterior_mean(orc)
+    assert np.max(np.abs(mu - want)) < 1e-6 * np.max(np.abs(want))
+
+
+def test_batch_equals_individual_solves_and_oracle_means():
+    insts = W.c4_instances(**INSTANCES)
+    posts = [gmrf.Posterior(gmrf.Prior(pr), ob) for pr, ob in insts]
+    ms, vs, infos = gmrf.marginal_var_batch(posts, 16, 1004, nthreads=6)
+    assert all(i["converged"] == 1 for i in infos)
+    for i, (post, (pr, ob)) in enumerate(zip(posts, insts)):
+        mu, var, se, info = post.marginal_var(16, 1004 + i)
+        assert np.array_equal(ms[i], mu) and np.array_equal(vs[i], var)
+        want = infer.posterior_mean(infer.condition(pr, ob))
+        assert np.max(np.abs(mu - want)) < 1e-6 * np.max(np.abs(want)), i
+
+
+def test_batch_with_shared_prior_and_repeated_posterior():
+    # two posteriors of one prior (one stream) and one posterior listed twice:
+    # grouped onto one worker in list order, results as solo calls
+    insts = W.c4_instances(count=3, seed=9, smin=20, smax=40)
+    pr, ob = insts[0]
+    prior = gmrf.Prior(pr)
+    ob2 = dict(ob, y=np.asarray(ob["y"]) * 0.5)
+    a, b = gmrf.Posterior(prior, ob), gmrf.Posterior(prior, ob2)
+    c = gmrf.Posterior(gmrf.Prior(insts[1][0]), insts[1][1])
+    posts = [a, c, b, a]
+    ms, vs, infos = gmrf.marginal_var_batch(posts, 8, 55, nthreads=4)
+    assert all(i["converged"] == 1 for i in infos)
+    for i, post in enumerate(posts):
+        mu, var, se, info = post.marginal_var(8, 55 + i)
+        assert np.array_equal(ms[i], mu) and np.array_equal(vs[i], var), i
