@@ -24,6 +24,56 @@ template <typename T> __device__ __forceinline__ V4<T> operator*(V4<T> x, V4<T> 
 template <typename T> __device__ __forceinline__ V4<T> fma4(T s, V4<T> x, V4<T> acc) {
     return {fma(s, x.a, acc.a), fma(s, x.b, acc.b), fma(s, x.c, acc.c), fma(s, x.d, acc.d)};
 }
+// FP32: two packed f32x2 instructions per 4-wide operation (sm_100 and
+// later); each lane rounds exactly like the scalar fma.rn / add.rn / mul.rn,
+// so results are bit-identical to the generic form above while the FP32
+// pipe issues half the instructions.
+template <> __device__ __forceinline__ V4<float> fma4<float>(float s, V4<float> x, V4<float> acc) {
+    V4<float> r;
+    asm("{\n\t.reg .b64 s2, x0, x1, a0, a1, r0, r1;\n\t"
+        "mov.b64 s2, {%8, %8};\n\t"
+        "mov.b64 x0, {%9, %10};\n\tmov.b64 x1, {%11, %12};\n\t"
+        "mov.b64 a0, {%4, %5};\n\tmov.b64 a1, {%6, %7};\n\t"
+        "fma.rn.f32x2 r0, s2, x0, a0;\n\tfma.rn.f32x2 r1, s2, x1, a1;\n\t"
+        "mov.b64 {%0, %1}, r0;\n\tmov.b64 {%2, %3}, r1;\n\t}"
+        : "=f"(r.a), "=f"(r.b), "=f"(r.c), "=f"(r.d)
+        : "f"(acc.a), "f"(acc.b), "f"(acc.c), "f"(acc.d), "f"(s), "f"(x.a), "f"(x.b), "f"(x.c), "f"(x.d));
+    return r;
+}
+template <> __device__ __forceinline__ V4<float> operator*<float>(float s, V4<float> x) {
+    V4<float> r;
+    asm("{\n\t.reg .b64 s2, x0, x1, r0, r1;\n\t"
+        "mov.b64 s2, {%4, %4};\n\t"
+        "mov.b64 x0, {%5, %6};\n\tmov.b64 x1, {%7, %8};\n\t"
+        "mul.rn.f32x2 r0, s2, x0;\n\tmul.rn.f32x2 r1, s2, x1;\n\t"
+        "mov.b64 {%0, %1}, r0;\n\tmov.b64 {%2, %3}, r1;\n\t}"
+        : "=f"(r.a), "=f"(r.b), "=f"(r.c), "=f"(r.d)
+        : "f"(s), "f"(x.a), "f"(x.b), "f"(x.c), "f"(x.d));
+    return r;
+}
+template <> __device__ __forceinline__ V4<float> operator+<float>(V4<float> x, V4<float> y) {
+    V4<float> r;
+    asm("{\n\t.reg .b64 x0, x1, y0, y1, r0, r1;\n\t"
+        "mov.b64 x0, {%4, %5};\n\tmov.b64 x1, {%6, %7};\n\t"
+        "mov.b64 y0, {%8, %9};\n\tmov.b64 y1, {%10, %11};\n\t"
+        "add.rn.f32x2 r0, x0, y0;\n\tadd.rn.f32x2 r1, x1, y1;\n\t"
+        "mov.b64 {%0, %1}, r0;\n\tmov.b64 {%2, %3}, r1;\n\t}"
+        : "=f"(r.a), "=f"(r.b), "=f"(r.c), "=f"(r.d)
+        : "f"(x.a), "f"(x.b), "f"(x.c), "f"(x.d), "f"(y.a), "f"(y.b), "f"(y.c), "f"(y.d));
+    return r;
+}
+template <> __device__ __forceinline__ V4<float> operator-<float>(V4<float> x, V4<float> y) {
+    V4<float> r;
+    asm("{\n\t.reg .b64 x0, x1, y0, y1, r0, r1;\n\t"
+        "mov.b64 x0, {%4, %5};\n\tmov.b64 x1, {%6, %7};\n\t"
+        "mov.b64 y0, {%8, %9};\n\tmov.b64 y1, {%10, %11};\n\t"
+        "sub.rn.f32x2 r0, x0, y0;\n\tsub.rn.f32x2 r1, x1, y1;\n\t"
+        "mov.b64 {%0, %1}, r0;\n\tmov.b64 {%2, %3}, r1;\n\t}"
+        : "=f"(r.a), "=f"(r.b), "=f"(r.c), "=f"(r.d)
+        : "f"(x.a), "f"(x.b), "f"(x.c), "f"(x.d), "f"(y.a), "f"(y.b), "f"(y.c), "f"(y.d));
+    return r;
+}
+
 template <typename T> __device__ __forceinline__ T comp(const V4<T>& v, int i) {
     return i == 0 ? v.a : (i == 1 ? v.b : (i == 2 ? v.c : v.d));
 }

@@ -143,8 +143,10 @@ template <int PX, int PY> __host__ __device__ constexpr int poff(int o) { return
 template <int SX, int SY> __host__ __device__ constexpr int soff(int o) { return -((tap_dt(o) * SY + tap_dy(o)) * SX + tap_dx(o)); }
 
 // Position of a work unit: tile coordinates (tx, ty, tt) in tile units and
-// the block group.  Units advance by the grid size G with carry-adds only
-// (no integer division inside the unit loop).
+// the block group.  Units are numbered group-major (u = grp * ntiles + tile);
+// each CTA takes one contiguous chunk of units, so it crosses few group
+// boundaries (where the dot partials are flushed), and steps through its
+// chunk with carry-adds (no integer division inside the unit loop).
 struct UnitPos {
     int tx, ty, tt, grp;
 };
@@ -159,14 +161,14 @@ __device__ __forceinline__ UnitPos unit_decompose(long long u, int tiles_x, int 
     p.tt = (int)(r / tiles_y);
     return p;
 }
-__device__ __forceinline__ void unit_advance(UnitPos& p, const UnitPos& d, int tiles_x, int tiles_y, int tiles_t) {
-    p.tx += d.tx;
-    if (p.tx >= tiles_x) { p.tx -= tiles_x; ++p.ty; }
-    p.ty += d.ty;
-    if (p.ty >= tiles_y) { p.ty -= tiles_y; ++p.tt; }
-    p.tt += d.tt;
-    if (p.tt >= tiles_t) { p.tt -= tiles_t; ++p.grp; }
-    p.grp += d.grp;
+__device__ __forceinline__ void unit_next(UnitPos& p, int tiles_x, int tiles_y, int tiles_t) {
+    if (++p.tx == tiles_x) {
+        p.tx = 0;
+        if (++p.ty == tiles_y) {
+            p.ty = 0;
+            if (++p.tt == tiles_t) { p.tt = 0; ++p.grp; }
+        }
+    }
 }
 
 // One work unit is (tile, group of KB consecutive blocks of four right-hand
@@ -226,15 +228,24 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         for (int i = tid; i < nblk * 4; i += 256) A.partial[((size_t)(i >> 2) * G + blockIdx.x) * 4 + (i & 3)] = 0.0;
 
     const int tiles_x = L.tiles_x, tiles_y = L.tiles_y, tiles_t = L.tiles_t;
-    const int ngroups = (nblk + KB - 1) / KB;
-    const UnitPos dG = unit_decompose(G, tiles_x, tiles_y, tiles_t);
+    const long long chunk = ((long long)nunits + G - 1) / G;
+    const long long u0 = (long long)blockIdx.x * chunk;
+    const int count = (int)std::max<long long>(0, std::min<long long>(chunk, (long long)nunits - u0));
 
-    auto issue = [&](const UnitPos& P, int st) {
-        if (P.grp < ngroups) {
+    auto issue = [&](const UnitPos& P, int st, bool valid) {
+        if (valid) {
             const int grp = P.grp;
             const int tile = (P.tt * tiles_y + P.ty) * tiles_x + P.tx;
             const int tx0 = P.tx * TX, ty0 = P.ty * TY, tt0 = P.tt * TT;
             const int tbase = (tt0 * ny + ty0) * nx + tx0;
+            const T* xb[KB];
+            bool bok[KB];
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                const int blk = grp * KB + j;
+                bok[j] = blk < nblk;
+                xb[j] = A.x + (size_t)(bok[j] ? blk : 0) * N * RW;
+            }
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
                 const int e = tid + 256 * k;
@@ -243,11 +254,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gt >= 0 && gt < nt;
                 const int node = in ? tbase + p_rel[k] : 0;
 #pragma unroll
-                for (int j = 0; j < KB; ++j) {
-                    const int blk = grp * KB + j;
-                    const bool ok = in && blk < nblk;
-                    cp_v4<T>(&S.p[st][e][j], A.x + ((size_t)(ok ? blk : 0) * N + node) * RW, ok);
-                }
+                for (int j = 0; j < KB; ++j) cp_v4<T>(&S.p[st][e][j], xb[j] + node * RW, in && bok[j]);
                 if (COL == 2) cp_scalar<T>(&S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0], L.mu + node, in);
             }
             const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
@@ -255,11 +262,11 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             const int node = own ? (gt * ny + gy) * nx + gx : 0;
 #pragma unroll
             for (int j = 0; j < KB; ++j) {
-                const int blk = grp * KB + j;
-                const bool ok = own && blk < nblk;
-                const size_t off = ((size_t)(ok ? blk : 0) * N + node) * RW;
-                if (MODE != M_APPLY) cp_v4<T>(&S.b[MODE != M_APPLY ? st : 0][tid][j], A.b + off, ok);
-                if (MODE == M_CHEB && A.d != nullptr) cp_v4<T>(&S.d[MODE == M_CHEB ? st : 0][tid][j], A.d + off, ok);
+                const bool ok = own && bok[j];
+                const size_t boff = (size_t)(xb[j] - A.x);
+                if (MODE != M_APPLY) cp_v4<T>(&S.b[MODE != M_APPLY ? st : 0][tid][j], A.b + boff + node * RW, ok);
+                if (MODE == M_CHEB && A.d != nullptr)
+                    cp_v4<T>(&S.d[MODE == M_CHEB ? st : 0][tid][j], A.d + boff + node * RW, ok);
             }
             if (MODE == M_CHEB) cp_scalar<T>(&S.dinv[MODE == M_CHEB ? st : 0][tid], A.dinv + node, own);
             if (has_obs) {
@@ -273,12 +280,12 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         cp_commit();
     };
 
-    UnitPos cur = unit_decompose(blockIdx.x, tiles_x, tiles_y, tiles_t);
+    UnitPos cur = unit_decompose(u0 < nunits ? u0 : 0, tiles_x, tiles_y, tiles_t);
     UnitPos ahead = cur;
 #pragma unroll 1
     for (int k = 0; k < NS - 1; ++k) {
-        issue(ahead, k);
-        unit_advance(ahead, dG, tiles_x, tiles_y, tiles_t);
+        issue(ahead, k, k < count);
+        unit_next(ahead, tiles_x, tiles_y, tiles_t);
     }
 
     T dacc[KB][4];
@@ -286,9 +293,9 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     for (int j = 0; j < KB; ++j) dacc[j][0] = dacc[j][1] = dacc[j][2] = dacc[j][3] = T(0);
     int st = 0;
 #pragma unroll 1
-    while (cur.grp < ngroups) {
-        issue(ahead, st == 0 ? NS - 1 : st - 1);
-        unit_advance(ahead, dG, tiles_x, tiles_y, tiles_t);
+    for (int done = 0; done < count; ++done) {
+        issue(ahead, st == 0 ? NS - 1 : st - 1, done + NS - 1 < count);
+        unit_next(ahead, tiles_x, tiles_y, tiles_t);
         cp_wait<NS - 1>();
         __syncthreads();
         const int grp = cur.grp;
@@ -311,13 +318,18 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             for (int j = 0; j < KB; ++j) sv[j] = v4zero<T>();
             if (inrow && !is_dirichlet(rx, ry, nx, ny)) {
                 const bool first = HT > 0 && nt > 1 && rt == 0;
-                const bool near = rx <= 1 || rx >= nx - 2 || (ny > 1 && (ry <= 1 || ry >= ny - 2));
+                // a tap of a non-Dirichlet row reaches a Dirichlet column only
+                // from the second or second-last node of an axis
+                const bool xl = rx == 1, xr = rx == nx - 2;
+                const bool yl = HY > 0 && ry == 1, yr = HY > 0 && ry == ny - 2;
 #pragma unroll
                 for (int o = 0; o < NTAP; ++o) {
                     if (!tap_used(o)) continue;
                     const T c = first ? c1[o] : c0[o];
                     if (c == T(0)) continue;
-                    if (near && is_dirichlet(rx + tap_dx(o), ry + tap_dy(o), nx, ny)) continue;
+                    const bool hit = (tap_dx(o) < 0 && xl) || (tap_dx(o) > 0 && xr) || (tap_dy(o) < 0 && yl) ||
+                                     (tap_dy(o) > 0 && yr);
+                    if (hit) continue;
 #pragma unroll
                     for (int j = 0; j < KB; ++j) sv[j] = fma4(c, sp[base + poff<PX, PY>(o)][j], sv[j]);
                 }
@@ -428,9 +440,9 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         }
         // dot partials: one entry per (block, CTA), flushed when the group changes
         UnitPos nxt = cur;
-        unit_advance(nxt, dG, tiles_x, tiles_y, tiles_t);
+        unit_next(nxt, tiles_x, tiles_y, tiles_t);
         if (A.partial != nullptr) {
-            if (nxt.grp != grp) {
+            if (nxt.grp != grp || done + 1 == count) {
 #pragma unroll
                 for (int j = 0; j < KB; ++j) {
                     const int blk = grp * KB + j;
