@@ -55,7 +55,8 @@ struct LevelView {
     const int32_t* tile_ptr;
     const int32_t* tile_idx;
     // A^T R^-1 A as a per-node 3^k-point stencil in tile-local tables:
-    // omap[tile][node in tile] = entry index or -1, oent[tile][entry][OC]
+    // omap[tile][node in tile] = entry index or -1; the tile's block of oent
+    // holds [entry][OC] coefficients, then int16 node[entry] (-1: unused)
     const int16_t* omap;
     const T* oent;
     int ocap;          // entries per tile (0: no observation rows)

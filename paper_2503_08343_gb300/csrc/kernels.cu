@@ -133,6 +133,7 @@ template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct Stencil
     V4<T> d[ND][TN][KB];
     V4<T> s[SN][KB];
     V4<T> sj[COL ? SN : 1][KB];
+    V4<T> qobs[TN][KB];        // A^T R^-1 A p at the tile's observed nodes
     T dinv[ND][TN];
     T mu[COL == 2 ? NS : 1][COL == 2 ? PN : 1];
 };
@@ -352,6 +353,29 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 }
             }
         }
+        // A^T R^-1 A p at the observed nodes of the tile: entry e (one node's
+        // 3^k-point stencil) is evaluated by thread e, so only the first
+        // ceil(entries / 32) warps run the loop
+        if (has_obs && tid < L.ocap) {
+            const unsigned char* ob = obs_smem + (size_t)st * ostage;
+            const int nd = reinterpret_cast<const int16_t*>(ob + TN * 2 + (size_t)L.ocap * OC * sizeof(T))[tid];
+            if (nd >= 0) {
+                const int ex = nd % TX, ey = (nd / TX) % TY, et = nd / (TX * TY);
+                const int pb = ((et + HT) * PY + (ey + HY)) * PX + (ex + 2);
+                const T* c = reinterpret_cast<const T*>(ob + TN * 2) + tid * OC;
+                V4<T> v[KB];
+#pragma unroll
+                for (int j = 0; j < KB; ++j) v[j] = v4zero<T>();
+#pragma unroll
+                for (int a = 0; a < OC; ++a) {
+                    const int po = pb + (obs_dt(GEO, a) * PY + obs_dy(GEO, a)) * PX + obs_dx(GEO, a);
+#pragma unroll
+                    for (int j = 0; j < KB; ++j) v[j] = fma4(c[a], sp[po][j], v[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < KB; ++j) S.qobs[nd][j] = v[j];
+            }
+        }
         __syncthreads();
 
         // q = B^T s (+ J^T Q_eps sj + A^T R^-1 A p) at the thread's own node
@@ -397,15 +421,9 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             }
             if (has_obs) {
                 const unsigned char* ob = obs_smem + (size_t)st * ostage;
-                const int ei = reinterpret_cast<const int16_t*>(ob)[tid];
-                if (ei >= 0) {
-                    const T* c = reinterpret_cast<const T*>(ob + TN * 2) + ei * OC;
+                if (reinterpret_cast<const int16_t*>(ob)[tid] >= 0) {
 #pragma unroll
-                    for (int a = 0; a < OC; ++a) {
-                        const int po = pbase + (obs_dt(GEO, a) * PY + obs_dy(GEO, a)) * PX + obs_dx(GEO, a);
-#pragma unroll
-                        for (int j = 0; j < KB; ++j) q[j] = fma4(c[a], sp[po][j], q[j]);
-                    }
+                    for (int j = 0; j < KB; ++j) q[j] = q[j] + S.qobs[tid][j];
                 }
             }
         }

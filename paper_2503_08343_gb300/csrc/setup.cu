@@ -315,12 +315,20 @@ void build_obs_stencil(Level& L) {
         const long long t = tile_of(kv.first, local);
         cap = std::max(cap, ++count[(size_t)t]);
     }
+    // per tile: cap entries of OC coefficients, then the tile-local node of
+    // each entry as int16 (-1 for unused entries)
     L.ocap = cap;
-    L.ostride32 = ((cap * OC * 4 + 15) / 16) * 16;
-    L.ostride64 = ((cap * OC * 8 + 15) / 16) * 16;
+    L.ostride32 = ((cap * OC * 4 + cap * 2 + 15) / 16) * 16;
+    L.ostride64 = ((cap * OC * 8 + cap * 2 + 15) / 16) * 16;
     std::vector<int16_t> map((size_t)ntiles * TN, (int16_t)-1);
     std::vector<float> e32((size_t)ntiles * L.ostride32 / 4, 0.0f);
     std::vector<double> e64((size_t)ntiles * L.ostride64 / 8, 0.0);
+    const int16_t none = -1;
+    for (long long t = 0; t < ntiles; ++t)
+        for (int e = 0; e < cap; ++e) {
+            std::memcpy(reinterpret_cast<char*>(e32.data()) + (size_t)t * L.ostride32 + (size_t)cap * OC * 4 + (size_t)e * 2, &none, 2);
+            std::memcpy(reinterpret_cast<char*>(e64.data()) + (size_t)t * L.ostride64 + (size_t)cap * OC * 8 + (size_t)e * 2, &none, 2);
+        }
     std::fill(count.begin(), count.end(), 0);
     for (auto& kv : C) {
         int local;
@@ -331,6 +339,9 @@ void build_obs_stencil(Level& L) {
             e32[(size_t)t * (L.ostride32 / 4) + (size_t)e * OC + a] = (float)kv.second[(size_t)a];
             e64[(size_t)t * (L.ostride64 / 8) + (size_t)e * OC + a] = kv.second[(size_t)a];
         }
+        const int16_t nd = (int16_t)local;
+        std::memcpy(reinterpret_cast<char*>(e32.data()) + (size_t)t * L.ostride32 + (size_t)cap * OC * 4 + (size_t)e * 2, &nd, 2);
+        std::memcpy(reinterpret_cast<char*>(e64.data()) + (size_t)t * L.ostride64 + (size_t)cap * OC * 8 + (size_t)e * 2, &nd, 2);
     }
     dev_upload(&L.d_omap, map);
     dev_upload(&L.d_oent32, e32);
