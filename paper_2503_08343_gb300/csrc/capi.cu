@@ -372,10 +372,11 @@ static Batch make_batch(int ns, bool with_mean) {
 static SolveStats run_batch(Posterior& P, const Batch& b, uint64_t seed, const gmrf_solve_opts& o, cudaStream_t s) {
     Workspace& W = workspace(P, b.nblk);
     GCK(cudaMemcpyAsync(W.slot_a, b.sample.data(), sizeof(int32_t) * b.sample.size(), cudaMemcpyHostToDevice, s));
+    const bool draws = b.nrhs > b.off;     // any sample slot (t64 is free until the solve ends)
     launch_sample_rhs(P.levels[0].geo, P.levels[0].view<double>(), seed, W.slot_a, P.linearised ? P.d_blin : P.d_bdata,
-                      W.b64, b.nblk, 0, s);
+                      W.b64, draws ? W.t64 : nullptr, b.nblk, s);
     GCK(cudaMemsetAsync(W.x64, 0, sizeof(double) * b.nblk * P.levels[0].N * 4, s));
-    if (o.batched || b.nblk == 1) return solve_blocked(P, b.nblk, W.b64, W.x64, o, s);
+    if (o.batched || b.nblk == 1) return solve_blocked(P, b.nblk, W.b64, W.x64, o, s, true);
     // one right-hand side per solve (the comparison path): the batch is
     // spread to dense rows, each row solved alone, and the solutions packed back
     SolveStats tot;
@@ -392,7 +393,7 @@ static SolveStats run_batch(Posterior& P, const Batch& b, uint64_t seed, const g
         GCK(cudaMemcpyAsync(W1.slot_b, one.data(), sizeof(int32_t) * 4, cudaMemcpyHostToDevice, s));
         launch_pack(W.t64, W1.b64, W1.slot_b, N, 1, s);
         GCK(cudaMemsetAsync(W1.x64, 0, sizeof(double) * N * 4, s));
-        SolveStats st = solve_blocked(P, 1, W1.b64, W1.x64, o, s);
+        SolveStats st = solve_blocked(P, 1, W1.b64, W1.x64, o, s, true);
         tot.refinements += st.refinements;
         tot.inner += st.inner;
         tot.converged &= st.converged;
@@ -473,9 +474,26 @@ gmrf_status gmrf_marginal_var(gmrf_posterior* post, int32_t ns, uint64_t seed, d
         Workspace& W = workspace(P, b.nblk);
         const long long N = P.levels[0].N;
         write_rows(P, W, b.mean_row, 1, mean, s);
-        apply64(P, b.nblk, W.x64, W.r64, s);
         GCK(cudaMemcpyAsync(W.slot_a, b.sample.data(), sizeof(int32_t) * b.sample.size(), cudaMemcpyHostToDevice, s));
-        launch_rbmc(W.r64, W.x64, P.levels[0].d_diag64, W.slot_a, N, b.nblk, ns, W.t64, W.t64 + N, s);
+        if (W.v32.ready) {
+            // Q x of the FP64 samples by the FP32 apply: each term carries a
+            // relative error of about 1e-7, and the off-diagonal sum e_i is of
+            // the size of x_i (no cancellation), far inside the Monte Carlo
+            // error of the estimator
+            float* x32 = static_cast<float*>(W.v32.pcg[0]);
+            float* q32 = static_cast<float*>(W.v32.pcg[3]);
+            launch_cast<float>(W.x64, x32, (long long)b.nblk * N * 4, s);
+            StencilArgs<float> a{};
+            a.L = P.levels[0].view<float>();
+            a.nblk = b.nblk;
+            a.x = x32;
+            a.out = q32;
+            launch_stencil<float>(P.levels[0].geo, M_APPLY, a, s);
+            launch_rbmc<float>(q32, W.x64, P.levels[0].d_diag64, W.slot_a, N, b.nblk, ns, W.t64, W.t64 + N, s);
+        } else {
+            apply64(P, b.nblk, W.x64, W.r64, s);
+            launch_rbmc<double>(W.r64, W.x64, P.levels[0].d_diag64, W.slot_a, N, b.nblk, ns, W.t64, W.t64 + N, s);
+        }
         copy_out(var, W.t64, (size_t)N, s);
         if (stderr_) copy_out(stderr_, W.t64 + N, (size_t)N, s);
         GCK(cudaStreamSynchronize(s));

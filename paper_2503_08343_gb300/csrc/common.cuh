@@ -142,6 +142,18 @@ __device__ __forceinline__ double philox_normal(uint64_t seed, uint32_t stream, 
     return (idx & 1) ? r * sinpi(2.0 * u2) : r * cospi(2.0 * u2);
 }
 
+// Both numbers of pair j: z0 = number 2j (cosine branch), z1 = number 2j + 1
+// (sine branch), bit-identical to philox_normal for those indices.
+__device__ __forceinline__ void philox_normal_pair(uint64_t seed, uint32_t stream, uint32_t sample, uint64_t j,
+                                                   double& z0, double& z1) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, sample, stream, 0u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const double u1 = u53(w.x, w.y), u2 = u53(w.z, w.w);
+    const double r = sqrt(-2.0 * log(u1));
+    z0 = r * cospi(2.0 * u2);
+    z1 = r * sinpi(2.0 * u2);
+}
+
 __device__ __forceinline__ double philox_rademacher(uint64_t seed, uint32_t sample, uint64_t idx) {
     const uint4 w = philox4x32_10(make_uint4((uint32_t)(idx >> 2), sample, 2u, 0u),
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));

@@ -196,12 +196,12 @@ SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, co
     pid[0] = -1;
     for (int i = 1; i < nrhs; ++i) pid[(size_t)i] = i - 1;
     GCK(cudaMemcpyAsync(W.slot_a, sid.data(), sizeof(int32_t) * sid.size(), cudaMemcpyHostToDevice, s));
-    launch_sample_rhs(F.geo, F.view<double>(), seed, W.slot_a, P.d_bdata, W.b64, nblk, 0, s);
+    launch_sample_rhs(F.geo, F.view<double>(), seed, W.slot_a, P.d_bdata, W.b64, nullptr, nblk, s);
     GCK(cudaMemcpyAsync(W.slot_b, pid.data(), sizeof(int32_t) * pid.size(), cudaMemcpyHostToDevice, s));
     k_rademacher_slots<<<dim3(nb256(N), nblk), 256, 0, s>>>(seed, W.slot_b, W.b64, N);
     note_launch();
     GCK(cudaMemsetAsync(W.x64, 0, sizeof(double) * nblk * N * 4, s));
-    SolveStats st = solve_blocked(P, nblk, W.b64, W.x64, o, s);
+    SolveStats st = solve_blocked(P, nblk, W.b64, W.x64, o, s, true);
     // 2. prior batch on the same slots (slot 0 holds probe 0 twice: harmless, ignored)
     Workspace& Wp = workspace(Pprior, nblk);
     std::vector<int32_t> pidp = pid;
@@ -211,7 +211,7 @@ SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, co
     k_rademacher_slots<<<dim3(nb256(N), nblk), 256, 0, s>>>(seed, Wp.slot_b, Wp.b64, N);
     note_launch();
     GCK(cudaMemsetAsync(Wp.x64, 0, sizeof(double) * nblk * N * 4, s));
-    const SolveStats sp = solve_blocked(Pprior, nblk, Wp.b64, Wp.x64, o, s);
+    const SolveStats sp = solve_blocked(Pprior, nblk, Wp.b64, Wp.x64, o, s, true);
     st.refinements += sp.refinements;
     st.inner += sp.inner;
     st.converged = st.converged && sp.converged;

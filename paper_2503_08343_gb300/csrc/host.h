@@ -65,9 +65,10 @@ struct SolveStats {
 void level_free(Level& L);
 void posterior_setup_levels(Posterior& P, cudaStream_t s);     // diag, Chebyshev bounds, transfers, dense inverse
 void posterior_refresh_operator(Posterior& P, cudaStream_t s); // after the linearisation point changed
-// Solve Q_u|y X = B for a blocked FP64 batch b64 (nblk blocks) into x64.
+// Solve Q_u|y X = B for a blocked FP64 batch b64 (nblk blocks) into x64;
+// x64 holds the starting guess (x_zero: it is zero, so r = b needs no apply).
 SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
-                         cudaStream_t s);
+                         cudaStream_t s, bool x_zero = false);
 void apply64(Posterior& P, int nblk, const double* x64, double* y64, cudaStream_t s);
 Workspace& workspace(Posterior& P, int nblk);
 void workspace_free(Workspace* w);

@@ -101,6 +101,9 @@ struct Level {
     int32_t* d_rs[3] = {nullptr, nullptr, nullptr};
     int32_t* d_rc[3] = {nullptr, nullptr, nullptr};
     bool coarsen[3] = {false, false, false};
+    // largest fine span (x, y) under one restriction tile of kRestrictTX x
+    // kRestrictTY coarse nodes (sizes the shared-memory tile)
+    int rspan[2] = {0, 0};
     // coarsest level: dense inverse of Q_u|y (device, row-major)
     float* d_dense32 = nullptr;
     double* d_dense64 = nullptr;
@@ -119,6 +122,7 @@ struct Prior {
 struct Workspace;
 
 constexpr double kP1DataShare = 0.5;
+constexpr int kRestrictTX = 32, kRestrictTY = 8;
 
 struct Posterior {
     Prior* prior = nullptr;

@@ -128,6 +128,7 @@ template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct Stencil
     static constexpr int TN = TX * TY * TT, PN = PX * PY * PT, SN = SX * SY * ST;
     static constexpr int NB = MODE == M_APPLY ? 1 : NS;
     static constexpr int ND = MODE == M_CHEB ? NS : 1;
+    static constexpr int NH = MODE == M_CHEB0 ? NS : 1, PH = MODE == M_CHEB0 ? PN : 1;
     V4<T> p[NS][PN][KB];
     V4<T> b[NB][TN][KB];
     V4<T> d[ND][TN][KB];
@@ -135,6 +136,7 @@ template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct Stencil
     V4<T> sj[COL ? SN : 1][KB];
     V4<T> qobs[TN][KB];        // A^T R^-1 A p at the tile's observed nodes
     T dinv[ND][TN];
+    T dinvh[NH][PH];           // CHEB0: D^-1 on the staged nodes
     T mu[COL == 2 ? NS : 1][COL == 2 ? PN : 1];
 };
 
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             for (int j = 0; j < KB; ++j) {
                 const int blk = grp * KB + j;
                 bok[j] = blk < nblk;
-                xb[j] = A.x + (size_t)(bok[j] ? blk : 0) * N * RW;
+                xb[j] = (MODE == M_CHEB0 ? A.b : A.x) + (size_t)(bok[j] ? blk : 0) * N * RW;
             }
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
 #pragma unroll
                 for (int j = 0; j < KB; ++j) cp_v4<T>(&S.p[st][e][j], xb[j] + node * RW, in && bok[j]);
                 if (COL == 2) cp_scalar<T>(&S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0], L.mu + node, in);
+                if (MODE == M_CHEB0) cp_scalar<T>(&S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? e : 0], A.dinv + node, in);
             }
             const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
             const bool own = gx < nx && gy < ny && gt < nt;
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
 #pragma unroll
             for (int j = 0; j < KB; ++j) {
                 const bool ok = own && bok[j];
-                const size_t boff = (size_t)(xb[j] - A.x);
+                const size_t boff = (size_t)(xb[j] - (MODE == M_CHEB0 ? A.b : A.x));
                 if (MODE != M_APPLY) cp_v4<T>(&S.b[MODE != M_APPLY ? st : 0][tid][j], A.b + boff + node * RW, ok);
                 if (MODE == M_CHEB && A.d != nullptr)
                     cp_v4<T>(&S.d[MODE == M_CHEB ? st : 0][tid][j], A.d + boff + node * RW, ok);
@@ -299,6 +302,17 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         unit_next(ahead, tiles_x, tiles_y, tiles_t);
         cp_wait<NS - 1>();
         __syncthreads();
+        if (MODE == M_CHEB0) {      // staged b -> x1 = c0 D^-1 b in place
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const int e = tid + 256 * k;
+                if (KP * 256 > PN && e >= PN) break;
+                const T f = A.c0 * S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? e : 0];
+#pragma unroll
+                for (int j = 0; j < KB; ++j) S.p[st][e][j] = f * S.p[st][e][j];
+            }
+            __syncthreads();
+        }
         const int grp = cur.grp;
         const int tx0 = cur.tx * TX, ty0 = cur.ty * TY, tt0 = cur.tt * TT;
         const V4<T>(*sp)[KB] = S.p[st];
@@ -447,9 +461,11 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             } else {
                 const V4<T> bb = S.b[MODE != M_APPLY ? st : 0][tid][j];
                 const V4<T> r = bb - q[j];
-                const T di = S.dinv[MODE == M_CHEB ? st : 0][tid];
+                const T di = MODE == M_CHEB0 ? S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? pbase : 0]
+                                             : S.dinv[MODE == M_CHEB ? st : 0][tid];
                 V4<T> dn = (A.c2 * di) * r;
-                if (A.d != nullptr) dn = fma4(A.c1, S.d[MODE == M_CHEB ? st : 0][tid][j], dn);
+                if (MODE == M_CHEB0) dn = fma4(A.c1, pown[j], dn);          // d = x1
+                else if (A.d != nullptr) dn = fma4(A.c1, S.d[MODE == M_CHEB ? st : 0][tid][j], dn);
                 const V4<T> xn = pown[j] + dn;
                 v4store(A.out + off, xn);
                 v4store(A.out2 + off, dn);
@@ -536,6 +552,7 @@ template <typename T, int GEO>
 static int launch_geo(int mode, const StencilArgs<T>& a, cudaStream_t s) {
     if (mode == M_APPLY) return launch_geo_mode<GEO, T, M_APPLY>(a, s);
     if (mode == M_RESID) return launch_geo_mode<GEO, T, M_RESID>(a, s);
+    if (mode == M_CHEB0) return launch_geo_mode<GEO, T, M_CHEB0>(a, s);
     return launch_geo_mode<GEO, T, M_CHEB>(a, s);
 }
 
@@ -743,45 +760,70 @@ __device__ __forceinline__ T p1_weight(int dx, int dy, T wx, T wy) {
     return T(0);
 }
 
-// Restriction in the (x, y) plane (transpose of the P1 interpolation) when
-// both space axes coarsen: out[.., Jy, Jx] = sum P(x, y; Jx, Jy) in[.., y, x]
-// over the fine ranges of Jx and Jy.
+// Restriction in the (x, y) plane when both space axes coarsen (transpose of
+// the P1 interpolation when p1, else of the bilinear one):
+// out[.., Jy, Jx] = sum P(x, y; Jx, Jy) in[.., y, x] over the fine ranges of
+// Jx and Jy.  A CTA owns kRestrictTX x kRestrictTY coarse nodes of one time
+// level and block: it stages the fine region under them (span W x H, rows
+// read contiguously) in shared memory, then each thread sums its node.
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_xy(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nt,
                                                      int cx, int cy, const int32_t* __restrict__ rsx,
                                                      const int32_t* __restrict__ rcx, const int32_t* __restrict__ pjx,
                                                      const T* __restrict__ pwx, const int32_t* __restrict__ rsy,
                                                      const int32_t* __restrict__ rcy, const int32_t* __restrict__ pjy,
-                                                     const T* __restrict__ pwy) {
-    const long long Nout = (long long)cx * cy * nt, Nin = (long long)nx * ny * nt;
-    const int blk = blockIdx.y;
-    const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
-    if (n >= Nout) return;
-    const int Jx = (int)(n % cx);
-    const long long r = n / cx;
-    const int Jy = (int)(r % cy), t = (int)(r / cy);
+                                                     const T* __restrict__ pwy, bool p1, int W, int tiles_cy) {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    V4<T>* tile = reinterpret_cast<V4<T>*>(rsm);
+    const int blk = blockIdx.z;
+    const int t = blockIdx.y / tiles_cy;
+    const int Jx0 = blockIdx.x * kRestrictTX, Jy0 = (blockIdx.y - t * tiles_cy) * kRestrictTY;
+    const int Jx1 = min(Jx0 + kRestrictTX, cx), Jy1 = min(Jy0 + kRestrictTY, cy);
+    const int fx0 = rsx[Jx0], fx1 = rsx[Jx1 - 1] + rcx[Jx1 - 1];
+    const int fy0 = rsy[Jy0], fy1 = rsy[Jy1 - 1] + rcy[Jy1 - 1];
+    const long long Nin = (long long)nx * ny * nt;
     const T* src = in + ((size_t)blk * Nin + (size_t)t * nx * ny) * RW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int y = fy0 + warp; y < fy1; y += 8)
+        for (int x = fx0 + lane; x < fx1; x += 32)
+            tile[(y - fy0) * W + (x - fx0)] = v4load(src + ((size_t)y * nx + x) * RW);
+    __syncthreads();
+    const int Jx = Jx0 + (threadIdx.x % kRestrictTX), Jy = Jy0 + (threadIdx.x / kRestrictTX);
+    if (Jx >= Jx1 || Jy >= Jy1) return;
     V4<T> acc = v4zero<T>();
     const int x0 = rsx[Jx], x1 = x0 + rcx[Jx], y0 = rsy[Jy], y1 = y0 + rcy[Jy];
     for (int y = y0; y < y1; ++y) {
         const int dy = Jy - pjy[y];
         const T wy = pwy[y];
         for (int x = x0; x < x1; ++x) {
-            const T w = p1_weight<T>(Jx - pjx[x], dy, pwx[x], wy);
-            if (w != T(0)) acc = fma4(w, v4load(src + ((size_t)y * nx + x) * RW), acc);
+            const int dx = Jx - pjx[x];
+            const T wx = pwx[x];
+            const T w = p1 ? p1_weight<T>(dx, dy, wx, wy)
+                           : (dx == 0 ? T(1) - wx : (dx == 1 ? wx : T(0))) * (dy == 0 ? T(1) - wy : (dy == 1 ? wy : T(0)));
+            if (w != T(0)) acc = fma4(w, tile[(y - fy0) * W + (x - fx0)], acc);
         }
     }
-    v4store(out + ((size_t)blk * Nout + n) * RW, acc);
+    const long long Nout = (long long)cx * cy * nt;
+    v4store(out + ((size_t)blk * Nout + ((size_t)t * cy + Jy) * cx + Jx) * RW, acc);
 }
 
 template <typename T>
 void launch_restrict_xy(const T* in, T* out, int nx, int ny, int nt, int cx, int cy, const int32_t* const rs[2],
-                        const int32_t* const rc[2], const int32_t* const pj[2], const T* const pw[2], int nblk, cudaStream_t s) {
-    const long long Nout = (long long)cx * cy * nt;
-    { k_restrict_xy<T><<<dim3((unsigned)((Nout + 255) / 256), nblk), 256, 0, s>>>(in, out, nx, ny, nt, cx, cy, rs[0], rc[0], pj[0], pw[0], rs[1], rc[1], pj[1], pw[1]); note_launch(); }
+                        const int32_t* const rc[2], const int32_t* const pj[2], const T* const pw[2], bool p1,
+                        const int span[2], int nblk, cudaStream_t s) {
+    static_assert(kRestrictTX * kRestrictTY == 256, "one thread per coarse node of the tile");
+    const int tiles_cx = (cx + kRestrictTX - 1) / kRestrictTX, tiles_cy = (cy + kRestrictTY - 1) / kRestrictTY;
+    const size_t smem = (size_t)span[0] * span[1] * sizeof(V4<T>);
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cuda_ok(cudaFuncSetAttribute(k_restrict_xy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    });
+    if (smem > 200 * 1024) throw std::runtime_error("restriction tile exceeds shared memory");
+    const dim3 grid((unsigned)tiles_cx, (unsigned)(tiles_cy * nt), (unsigned)nblk);
+    { k_restrict_xy<T><<<grid, 256, smem, s>>>(in, out, nx, ny, nt, cx, cy, rs[0], rc[0], pj[0], pw[0], rs[1], rc[1], pj[1], pw[1], p1, span[0], tiles_cy); note_launch(); }
 }
-template void launch_restrict_xy<float>(const float*, float*, int, int, int, int, int, const int32_t* const[2], const int32_t* const[2], const int32_t* const[2], const float* const[2], int, cudaStream_t);
-template void launch_restrict_xy<double>(const double*, double*, int, int, int, int, int, const int32_t* const[2], const int32_t* const[2], const int32_t* const[2], const double* const[2], int, cudaStream_t);
+template void launch_restrict_xy<float>(const float*, float*, int, int, int, int, int, const int32_t* const[2], const int32_t* const[2], const int32_t* const[2], const float* const[2], bool, const int[2], int, cudaStream_t);
+template void launch_restrict_xy<double>(const double*, double*, int, int, int, int, int, const int32_t* const[2], const int32_t* const[2], const int32_t* const[2], const double* const[2], bool, const int[2], int, cudaStream_t);
 
 struct AxisMap { const int32_t* j; const void* w; bool on; };
 
@@ -831,7 +873,9 @@ void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, bool
 template void launch_prolong_add<float>(float*, const float*, const Level&, const Level&, bool, int, cudaStream_t);
 template void launch_prolong_add<double>(double*, const double*, const Level&, const Level&, bool, int, cudaStream_t);
 
-// coarsest level: x = Q_c^-1 b with the stored dense inverse
+// coarsest level: x = Q_c^-1 b with the stored dense inverse.  The inverse is
+// stored exactly symmetric, so thread i walks column i (A[j][i] = A[i][j]) and
+// a warp's loads of one j are contiguous.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_solve(const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x, int n) {
     extern __shared__ unsigned char dsm[];
@@ -841,8 +885,15 @@ __global__ void __launch_bounds__(256) k_dense_solve(const T* __restrict__ Ainv,
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += 256) {
         V4<T> acc = v4zero<T>();
-        const T* row = Ainv + (size_t)i * n;
-        for (int j = 0; j < n; ++j) acc = fma4(row[j], sb[j], acc);
+        int j = 0;
+        for (; j + 8 <= n; j += 8) {         // eight independent loads in flight
+            T a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = Ainv[(size_t)(j + u) * n + i];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc = fma4(a[u], sb[j + u], acc);
+        }
+        for (; j < n; ++j) acc = fma4(Ainv[(size_t)j * n + i], sb[j], acc);
         v4store(x + ((size_t)blk * n + i) * RW, acc);
     }
 }
@@ -927,10 +978,32 @@ void launch_axpy_scaled64(double* x64, const double* norms, const double* d64, l
 // A slot with sample id -1 copies the data right-hand side, -2 is padding,
 // >= 0 draws sample `id`.  With use_probe the slot holds a Rademacher probe.
 
+// z1[blk][n][c]: the prior-row normals (stream 0) of the sample in slot
+// (blk, c), zero for slots without a sample.  One thread per Box-Muller
+// pair of rows (2j, 2j + 1), so each pair's transcendentals run once.
+__global__ void __launch_bounds__(256) k_sample_normals(uint64_t seed, const int32_t* __restrict__ slot_sample,
+                                                        long long N, double* __restrict__ z1) {
+    const int blk = blockIdx.y;
+    const long long j = (long long)blockIdx.x * 256 + threadIdx.x;
+    const long long n0 = 2 * j;
+    if (n0 >= N) return;
+    double a[4], b[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int sid = slot_sample[blk * RW + c];
+        a[c] = b[c] = 0.0;
+        if (sid >= 0) philox_normal_pair(seed, 0u, (uint32_t)sid, (uint64_t)j, a[c], b[c]);
+    }
+    double* p = z1 + ((size_t)blk * N + n0) * RW;
+    v4store(p, V4<double>{a[0], a[1], a[2], a[3]});
+    if (n0 + 1 < N) v4store(p + RW, V4<double>{b[0], b[1], b[2], b[3]});
+}
+
 template <int GEO>
 __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, uint64_t seed,
                                                     const int32_t* __restrict__ slot_sample,
-                                                    const double* __restrict__ bdata, double* __restrict__ b64) {
+                                                    const double* __restrict__ bdata, const double* __restrict__ z1,
+                                                    double* __restrict__ b64) {
     using G = Geo<GEO>;
     constexpr int TX = G::TX, TY = G::TY, TT = G::TT, HY = G::HY, HT = G::HT;
     constexpr int HYS = HY / 2;
@@ -952,12 +1025,9 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
         const int sx = e % SX, sy = (e / SX) % SY, st = e / (SX * SY);
         const int rx = tx0 - 1 + sx, ry = ty0 - HYS + sy, rt = tt0 + st;
         V4<double> z = v4zero<double>();
-        if (rx >= 0 && rx < nx && ry >= 0 && ry < ny && rt < nt) {
+        if (z1 != nullptr && rx >= 0 && rx < nx && ry >= 0 && ry < ny && rt < nt) {
             const long long row = ((long long)rt * ny + ry) * nx + rx;
-            double v[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = sid[c] >= 0 ? philox_normal(seed, 0u, (uint32_t)sid[c], (uint64_t)row) : 0.0;
-            z = V4<double>{v[0], v[1], v[2], v[3]};
+            z = v4load(z1 + ((size_t)blk * N + row) * RW);
         }
         sz[st][sy][sx] = z;
     }
@@ -1053,12 +1123,16 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
 }
 
 void launch_sample_rhs(int geo, const LevelView<double>& L, uint64_t seed, const int32_t* slot_sample,
-                       const double* bdata, double* b64, int nblk, int use_probe, cudaStream_t s) {
-    (void)use_probe;
+                       const double* bdata, double* b64, double* z1, int nblk, cudaStream_t s) {
+    if (z1 != nullptr) {
+        const long long pairs = (L.N + 1) / 2;
+        k_sample_normals<<<dim3((unsigned)((pairs + 255) / 256), (unsigned)nblk), 256, 0, s>>>(seed, slot_sample, L.N, z1);
+        note_launch();
+    }
     const dim3 grid((unsigned)((long long)L.tiles_x * L.tiles_y * L.tiles_t), (unsigned)nblk);
-    if (geo == GEO_XY) { k_sample_rhs<GEO_XY><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, b64); note_launch(); }
-    else if (geo == GEO_XT) { k_sample_rhs<GEO_XT><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, b64); note_launch(); }
-    else { k_sample_rhs<GEO_XYT><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, b64); note_launch(); }
+    if (geo == GEO_XY) { k_sample_rhs<GEO_XY><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, z1, b64); note_launch(); }
+    else if (geo == GEO_XT) { k_sample_rhs<GEO_XT><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, z1, b64); note_launch(); }
+    else { k_sample_rhs<GEO_XYT><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, z1, b64); note_launch(); }
 }
 
 // Rademacher probes: slot id >= 0 holds probe `id` (stream 2), -1 the data rhs.
@@ -1123,7 +1197,8 @@ void launch_unpack(const double* src, double* dst, const int32_t* slot_dst, long
 
 // Rao-Blackwellised variance: e = (Q x - Q_ii x_i) / Q_ii per sample slot,
 // var = 1/Q_ii + mean(e^2), se = std(e^2) / sqrt(ns)
-__global__ void k_rbmc(const double* __restrict__ Qx, const double* __restrict__ x, const double* __restrict__ diag,
+template <typename QT>
+__global__ void k_rbmc(const QT* __restrict__ Qx, const double* __restrict__ x, const double* __restrict__ diag,
                        const int32_t* __restrict__ slot_sample, long long N, int nblk, int ns, double* __restrict__ var,
                        double* __restrict__ se) {
     const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
@@ -1132,7 +1207,8 @@ __global__ void k_rbmc(const double* __restrict__ Qx, const double* __restrict__
     double s1 = 0.0, s2 = 0.0;
     for (int blk = 0; blk < nblk; ++blk) {
         const size_t off = ((size_t)blk * N + n) * RW;
-        const V4<double> qx = v4load(Qx + off), xv = v4load(x + off);
+        const V4<QT> qx = v4load(Qx + off);
+        const V4<double> xv = v4load(x + off);
         const double a[4] = {qx.a, qx.b, qx.c, qx.d}, b[4] = {xv.a, xv.b, xv.c, xv.d};
         for (int c = 0; c < 4; ++c) {
             if (slot_sample[blk * RW + c] < 0) continue;
@@ -1148,10 +1224,15 @@ __global__ void k_rbmc(const double* __restrict__ Qx, const double* __restrict__
         se[n] = sqrt(fmax(v, 0.0) / ns);
     }
 }
-void launch_rbmc(const double* Qx, const double* x, const double* diag, const int32_t* slot_sample, long long N,
+template <typename QT>
+void launch_rbmc(const QT* Qx, const double* x, const double* diag, const int32_t* slot_sample, long long N,
                  int nblk, int ns, double* var, double* se, cudaStream_t s) {
-    { k_rbmc<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Qx, x, diag, slot_sample, N, nblk, ns, var, se); note_launch(); }
+    { k_rbmc<QT><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Qx, x, diag, slot_sample, N, nblk, ns, var, se); note_launch(); }
 }
+template void launch_rbmc<float>(const float*, const double*, const double*, const int32_t*, long long, int, int, double*,
+                                 double*, cudaStream_t);
+template void launch_rbmc<double>(const double*, const double*, const double*, const int32_t*, long long, int, int,
+                                  double*, double*, cudaStream_t);
 
 // diagonal of B^T B + J^T Q_eps J at every node (observation part added by k_obs_diag)
 template <typename T>
@@ -1307,6 +1388,24 @@ __global__ void k_norm2(const T* __restrict__ v, long long N, double* __restrict
     }
     block_sum4<256, T>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
 }
+// sum_n w[n] v_n^2 per right-hand side (the D^-1-weighted residual norm)
+__global__ void k_norm2w(const double* __restrict__ v, const double* __restrict__ w, long long N, double* __restrict__ partial,
+                         int nparts) {
+    const int blk = blockIdx.y;
+    double dot[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < EPT; ++k) {
+        const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
+        if (n >= N) break;
+        const V4<double> a = v4load(v + ((size_t)blk * N + n) * RW);
+        const double wn = w[n];
+        dot[0] += wn * a.a * a.a; dot[1] += wn * a.b * a.b; dot[2] += wn * a.c * a.c; dot[3] += wn * a.d * a.d;
+    }
+    block_sum4<256, double>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
+}
+void launch_norm2w(const double* v, const double* w, long long N, int nblk, double* partial, int nparts, cudaStream_t s) {
+    { k_norm2w<<<dim3(nparts, nblk), 256, 0, s>>>(v, w, N, partial, nparts); note_launch(); }
+}
+
 template <typename T> void launch_norm2(const T* v, long long N, int nblk, double* partial, int nparts, cudaStream_t s) {
     { k_norm2<T><<<dim3(nparts, nblk), 256, 0, s>>>(v, N, partial, nparts); note_launch(); }
 }

@@ -11,7 +11,9 @@ unsigned long long capture_end();
 void note_graph_launch(unsigned long long kernels);
 unsigned long long launch_count();
 
-enum StencilMode { M_APPLY = 0, M_RESID = 1, M_CHEB = 2 };
+// CHEB0: the first two Chebyshev steps from x = 0 in one pass; x1 = c0 D^-1 b
+// is formed in shared memory from the staged b, then one CHEB step with d = x1
+enum StencilMode { M_APPLY = 0, M_RESID = 1, M_CHEB = 2, M_CHEB0 = 3 };
 
 template <typename T>
 struct StencilArgs {
@@ -23,6 +25,7 @@ struct StencilArgs {
     T* out;            // APPLY: Q x; RESID: b - Q x; CHEB: x + d_new
     T* out2;           // CHEB: d_new
     T c1, c2;          // CHEB: d_new = c1 d + c2 D^-1 (b - Q x)
+    T c0;              // CHEB0: x = c0 D^-1 b before the step (x is not read)
     double* partial;   // per-CTA dot partials [nblk][grid][4] or null
     int nblk;
     const T* rweight;  // RESID: if set, the dot is sum r^2 * rweight[node] (D^-1-weighted norm)
@@ -43,7 +46,8 @@ template <typename T> void launch_restrict_axis(const T* in, T* out, int nx, int
                                                 int nblk, cudaStream_t s);
 template <typename T> void launch_restrict_xy(const T* in, T* out, int nx, int ny, int nt, int cx, int cy,
                                               const int32_t* const rs[2], const int32_t* const rc[2],
-                                              const int32_t* const pj[2], const T* const pw[2], int nblk, cudaStream_t s);
+                                              const int32_t* const pj[2], const T* const pw[2], bool p1,
+                                              const int span[2], int nblk, cudaStream_t s);
 template <typename T> void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, bool p1, int nblk, cudaStream_t s);
 template <typename T> void launch_dense_solve(const T* Ainv, const T* b, T* x, int n, int nblk, cudaStream_t s);
 
@@ -64,12 +68,15 @@ void launch_axpy_scaled64(double* x64, const double* norms, const double* d64, l
 void launch_scale64(const double* r64, const double* norms, double* out, long long N, int nblk, cudaStream_t s);
 
 // right-hand sides, layout conversion, variances
+// b64 slots: sample RHS, data RHS or zero by slot id; z1 ([nblk][N][4] FP64
+// scratch) receives the prior-row normals, NULL when no slot draws a sample
 void launch_sample_rhs(int geo, const LevelView<double>& L, uint64_t seed, const int32_t* slot_sample,
-                       const double* bdata, double* b64, int nblk, int use_probe, cudaStream_t s);
+                       const double* bdata, double* b64, double* z1, int nblk, cudaStream_t s);
 void launch_obs_scatter(const ObsRow* obs, int nobs, const double* y, double* b, cudaStream_t s);
 void launch_pack(const double* src, double* dst, const int32_t* slot_src, long long N, int nblk, cudaStream_t s);
 void launch_unpack(const double* src, double* dst, const int32_t* slot_dst, long long N, int nblk, cudaStream_t s);
-void launch_rbmc(const double* Qx, const double* x, const double* diag, const int32_t* slot_sample, long long N,
+template <typename QT>
+void launch_rbmc(const QT* Qx, const double* x, const double* diag, const int32_t* slot_sample, long long N,
                  int nblk, int ns, double* var, double* se, cudaStream_t s);
 template <typename T> void launch_diag(int geo, const LevelView<T>& L, double* diag64, cudaStream_t s);
 void launch_obs_diag(const ObsRow* obs, int nobs, double* diag, cudaStream_t s);
@@ -84,6 +91,7 @@ void launch_dot_blocked(const double* a, const double* b, long long N, int nblk,
 
 namespace gmrf {
 template <typename T> void launch_dot(const T* a, const T* b, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
+void launch_norm2w(const double* v, const double* w, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
 template <typename T> void launch_norm2(const T* v, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
 void launch_power_scale(float* q, const float* dinv, long long N, double* partial, int nparts, cudaStream_t s);
 void launch_scale_comp(float* v, const float* w, const double* nrm2, long long N, cudaStream_t s);

@@ -379,6 +379,15 @@ void build_transfer(Level& f, const Level& c) {
             if (re[(size_t)J] < rs[(size_t)J]) { rs[(size_t)J] = 0; rc[(size_t)J] = 0; }
             else rc[(size_t)J] = re[(size_t)J] - rs[(size_t)J] + 1;
         }
+        if (a < 2) {
+            const int T = a == 0 ? kRestrictTX : kRestrictTY;
+            int span = 0;
+            for (int J0 = 0; J0 < m; J0 += T) {
+                const int J1 = std::min(J0 + T, m) - 1;
+                span = std::max(span, rs[(size_t)J1] + rc[(size_t)J1] - rs[(size_t)J0]);
+            }
+            f.rspan[a] = span;
+        }
         dev_upload(&f.d_pj[a], pj);
         dev_upload(&f.d_pw[a], pw);
         dev_upload(&f.d_pwd[a], pwd);

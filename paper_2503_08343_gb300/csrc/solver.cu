@@ -142,6 +142,13 @@ static void setup_dense(Level& L, cudaStream_t s) {
     }
     std::vector<double> A = dense_operator(L, mu.empty() ? nullptr : mu.data());
     if (!spd_inverse(A, (int)L.N)) throw Error(GMRF_E_NOT_SPD, "coarsest-level operator is not positive definite");
+    const int n = (int)L.N;            // store the inverse exactly symmetric (the solve kernel reads columns)
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            const double v = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+            A[(size_t)i * n + j] = v;
+            A[(size_t)j * n + i] = v;
+        }
     std::vector<float> A32(A.size());
     for (size_t i = 0; i < A.size(); ++i) A32[i] = (float)A[i];
     dev_upload(&L.d_dense64, A);
@@ -269,16 +276,17 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
     T* D = (T*)V.d[l];
     T* R = (T*)V.res[l];
     const T* dinv = dinv_of<T>(L);
-    // pre-smoothing from x = 0
-    launch_cheb_first<T>(b, dinv, (T)ch.c2[0], X0, D, L.N, nblk, s);
+    // pre-smoothing from x = 0: both Chebyshev steps in one pass (the first,
+    // x1 = c2[0] D^-1 b, is pointwise and formed in shared memory)
     StencilArgs<T> a{};
     a.L = L.view<T>();
     a.nblk = nblk;
-    a.x = X0; a.b = b; a.d = D; a.dinv = dinv; a.out = x; a.out2 = D;
-    a.c1 = (T)ch.c1[1]; a.c2 = (T)ch.c2[1];
-    launch_stencil<T>(L.geo, M_CHEB, a, s);
-    // residual and restriction (transpose of the interpolation: P1 in the
-    // space plane when both space axes coarsen, then linear per axis)
+    a.x = nullptr; a.b = b; a.d = nullptr; a.dinv = dinv; a.out = x; a.out2 = D;
+    a.c0 = (T)ch.c2[0]; a.c1 = (T)ch.c1[1]; a.c2 = (T)ch.c2[1];
+    launch_stencil<T>(L.geo, M_CHEB0, a, s);
+    // residual and restriction (transpose of the interpolation): one pass
+    // over the space plane when both space axes coarsen (P1 or bilinear),
+    // then linear per remaining axis
     StencilArgs<T> r = a;
     r.x = x; r.b = b; r.d = nullptr; r.out = R; r.out2 = nullptr;
     launch_stencil<T>(L.geo, M_RESID, r, s);
@@ -290,7 +298,7 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
         if (L.coarsen[ax]) last = ax;
     const T* src = R;
     bool use_t1 = true;
-    const bool plane = P.transfer_p1 && L.coarsen[0] && L.coarsen[1];
+    const bool plane = L.coarsen[0] && L.coarsen[1];
     if (plane) {
         T* dst = last == 1 ? (T*)V.b[l + 1] : (T*)V.t1[l];
         use_t1 = false;
@@ -298,7 +306,8 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
         const int32_t* const rc[2] = {L.d_rc[0], L.d_rc[1]};
         const int32_t* const pj[2] = {L.d_pj[0], L.d_pj[1]};
         const T* const pw[2] = {pw_of<T>(L, 0), pw_of<T>(L, 1)};
-        launch_restrict_xy<T>(src, dst, dims[0], dims[1], dims[2], cdims[0], cdims[1], rs, rc, pj, pw, nblk, s);
+        launch_restrict_xy<T>(src, dst, dims[0], dims[1], dims[2], cdims[0], cdims[1], rs, rc, pj, pw, P.transfer_p1,
+                              L.rspan, nblk, s);
         dims[0] = cdims[0];
         dims[1] = cdims[1];
         src = dst;
@@ -438,7 +447,7 @@ void apply64(Posterior& P, int nblk, const double* x64, double* y64, cudaStream_
 }
 
 SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool x_zero) {
     Workspace& W = workspace(P, nblk);
     Level& L = P.levels[0];
     const int P4 = nblk * 4;
@@ -464,13 +473,19 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
     SolveStats st;
     const int ne = elem_parts(L.N);
     for (int ref = 0; ref <= o.max_refine; ++ref) {
-        StencilArgs<double> a{};
-        a.L = L.view<double>();
-        a.nblk = nblk;
-        a.x = x64; a.b = b64; a.out = W.r64; a.partial = W.partial;
-        a.rweight = L.d_dinv64;     // stop on the D^-1-weighted residual norm
-        const int ng = launch_stencil<double>(L.geo, M_RESID, a, s);
-        launch_reduce(W.partial, ng, nblk, W.red, s);
+        if (ref == 0 && x_zero) {   // r = b
+            GCK(cudaMemcpyAsync(W.r64, b64, sizeof(double) * (size_t)nblk * L.N * 4, cudaMemcpyDeviceToDevice, s));
+            launch_norm2w(W.r64, L.d_dinv64, L.N, nblk, W.partial, ne, s);
+            launch_reduce(W.partial, ne, nblk, W.red, s);
+        } else {
+            StencilArgs<double> a{};
+            a.L = L.view<double>();
+            a.nblk = nblk;
+            a.x = x64; a.b = b64; a.out = W.r64; a.partial = W.partial;
+            a.rweight = L.d_dinv64;     // stop on the D^-1-weighted residual norm
+            const int ng = launch_stencil<double>(L.geo, M_RESID, a, s);
+            launch_reduce(W.partial, ng, nblk, W.red, s);
+        }
         GCK(cudaMemcpyAsync(W.h_red, W.red, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
         GCK(cudaStreamSynchronize(s));
         st.refinements++;
