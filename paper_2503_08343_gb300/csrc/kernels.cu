@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     constexpr int OC = ObsStencil<GEO>::OC;
     constexpr int KP = (PN + 255) / 256, KS = (SN + 255) / 256;
     static_assert(SN >= TN, "s tile covers the node tile");
+    static_assert(NS >= 2, "the copy pipeline needs two stages");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& S = *reinterpret_cast<SM*>(smem_raw);
 
@@ -297,11 +298,14 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     for (int j = 0; j < KB; ++j) dacc[j][0] = dacc[j][1] = dacc[j][2] = dacc[j][3] = T(0);
     int st = 0;
 #pragma unroll 1
+    // Two barriers per unit: the first (after this unit's copies landed) also
+    // orders every read of the previous unit (its stage buffer, the s tile,
+    // qobs) before the refill of that buffer and the next writes.
     for (int done = 0; done < count; ++done) {
+        cp_wait<NS - 2>();
+        __syncthreads();
         issue(ahead, st == 0 ? NS - 1 : st - 1, done + NS - 1 < count);
         unit_next(ahead, tiles_x, tiles_y, tiles_t);
-        cp_wait<NS - 1>();
-        __syncthreads();
         if (MODE == M_CHEB0) {      // staged b -> x1 = c0 D^-1 b in place
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
@@ -368,15 +372,16 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             }
         }
         // A^T R^-1 A p at the observed nodes of the tile: entry e (one node's
-        // 3^k-point stencil) is evaluated by thread e, so only the first
+        // 3^k-point stencil) is evaluated by thread 255 - e, so only the last
         // ceil(entries / 32) warps run the loop
-        if (has_obs && tid < L.ocap) {
+        const int oe = 255 - tid;      // entries go to the last warps (the first ones hold extra s rows)
+        if (has_obs && oe < L.ocap) {
             const unsigned char* ob = obs_smem + (size_t)st * ostage;
-            const int nd = reinterpret_cast<const int16_t*>(ob + TN * 2 + (size_t)L.ocap * OC * sizeof(T))[tid];
+            const int nd = reinterpret_cast<const int16_t*>(ob + TN * 2 + (size_t)L.ocap * OC * sizeof(T))[oe];
             if (nd >= 0) {
                 const int ex = nd % TX, ey = (nd / TX) % TY, et = nd / (TX * TY);
                 const int pb = ((et + HT) * PY + (ey + HY)) * PX + (ex + 2);
-                const T* c = reinterpret_cast<const T*>(ob + TN * 2) + tid * OC;
+                const T* c = reinterpret_cast<const T*>(ob + TN * 2) + oe * OC;
                 V4<T> v[KB];
 #pragma unroll
                 for (int j = 0; j < KB; ++j) v[j] = v4zero<T>();
@@ -485,7 +490,6 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 }
             }
         }
-        __syncthreads();
         cur = nxt;
         st = st + 1 == NS ? 0 : st + 1;
     }
