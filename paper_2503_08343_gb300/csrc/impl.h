@@ -61,6 +61,7 @@ struct LevelView {
     const T* oent;
     int ocap;          // entries per tile (0: no observation rows)
     int ostride;       // bytes per tile of oent (multiple of 16)
+    int obs_direct;    // 1: read the tables from global memory instead of staging them (set per launch)
 };
 
 struct Level {

@@ -58,6 +58,7 @@ template <typename T> LevelView<T> Level::view() const {
     if constexpr (sizeof(T) == 4) { v.oent = d_oent32; v.ostride = ostride32; }
     else { v.oent = d_oent64; v.ostride = ostride64; }
     v.ocap = d_omap ? ocap : 0;
+    v.obs_direct = 0;
     return v;
 }
 
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     const int lx = tid % TX, ly = (tid / TX) % TY, lt = tid / (TX * TY);
     const int G = gridDim.x;
     const bool has_obs = L.ocap > 0;
+    const bool obs_staged = has_obs && !L.obs_direct;
     const int ostage = TN * 2 + L.ostride;     // bytes of one stage of observation tables
     unsigned char* obs_smem = smem_raw + sizeof(SM);
 
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                     cp_v4<T>(&S.d[MODE == M_CHEB ? st : 0][tid][j], A.d + boff + node * RW, ok);
             }
             if (MODE == M_CHEB) cp_scalar<T>(&S.dinv[MODE == M_CHEB ? st : 0][tid], A.dinv + node, own);
-            if (has_obs) {
+            if (obs_staged) {
                 unsigned char* dst = obs_smem + (size_t)st * ostage;
                 const unsigned char* gmap = reinterpret_cast<const unsigned char*>(L.omap + (size_t)tile * TN);
                 const unsigned char* gent = reinterpret_cast<const unsigned char*>(L.oent) + (size_t)tile * L.ostride;
@@ -374,14 +376,27 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         // A^T R^-1 A p at the observed nodes of the tile: entry e (one node's
         // 3^k-point stencil) is evaluated by thread 255 - e, so only the last
         // ceil(entries / 32) warps run the loop
+        // this tile's tables: the staged copy, or global memory when a level's
+        // tables are too large to stage (small, heavily observed coarse levels)
+        const int16_t* omap_t = nullptr;
+        const unsigned char* oent_t = nullptr;
+        if (has_obs) {
+            if (obs_staged) {
+                omap_t = reinterpret_cast<const int16_t*>(obs_smem + (size_t)st * ostage);
+                oent_t = obs_smem + (size_t)st * ostage + TN * 2;
+            } else {
+                const int tile = (cur.tt * tiles_y + cur.ty) * tiles_x + cur.tx;
+                omap_t = L.omap + (size_t)tile * TN;
+                oent_t = reinterpret_cast<const unsigned char*>(L.oent) + (size_t)tile * L.ostride;
+            }
+        }
         const int oe = 255 - tid;      // entries go to the last warps (the first ones hold extra s rows)
         if (has_obs && oe < L.ocap) {
-            const unsigned char* ob = obs_smem + (size_t)st * ostage;
-            const int nd = reinterpret_cast<const int16_t*>(ob + TN * 2 + (size_t)L.ocap * OC * sizeof(T))[oe];
+            const int nd = reinterpret_cast<const int16_t*>(oent_t + (size_t)L.ocap * OC * sizeof(T))[oe];
             if (nd >= 0) {
                 const int ex = nd % TX, ey = (nd / TX) % TY, et = nd / (TX * TY);
                 const int pb = ((et + HT) * PY + (ey + HY)) * PX + (ex + 2);
-                const T* c = reinterpret_cast<const T*>(ob + TN * 2) + oe * OC;
+                const T* c = reinterpret_cast<const T*>(oent_t) + oe * OC;
                 V4<T> v[KB];
 #pragma unroll
                 for (int j = 0; j < KB; ++j) v[j] = v4zero<T>();
@@ -439,8 +454,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 }
             }
             if (has_obs) {
-                const unsigned char* ob = obs_smem + (size_t)st * ostage;
-                if (reinterpret_cast<const int16_t*>(ob)[tid] >= 0) {
+                if (omap_t[tid] >= 0) {
 #pragma unroll
                     for (int j = 0; j < KB; ++j) q[j] = q[j] + S.qobs[tid][j];
                 }
@@ -513,10 +527,11 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
     using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
     auto kern = k_stencil<GEO, T, MODE, COL, NS, KB>;
     static int attr_smem = 0;
-    static int sms = 0;
+    static int sms = 0, optin = 0;
     static std::map<size_t, int> per_sm;       // resident CTAs per SM by dynamic shared memory
     static std::mutex mu;                      // solves of independent posteriors may run on several host threads
-    const size_t smem = sizeof(SM) + (a.L.ocap > 0 ? (size_t)NS * (SM::TN * 2 + a.L.ostride) : 0);
+    StencilArgs<T> args = a;
+    size_t smem = sizeof(SM);
     int resident = 0;
     {
         std::lock_guard<std::mutex> lock(mu);
@@ -524,7 +539,17 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
             int dev = 0;
             cuda_ok(cudaGetDevice(&dev));
             cuda_ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            cuda_ok(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         }
+        // stage the observation tables with the inputs when they fit beside
+        // them (with the 1 KB the block reduction's static array may take)
+        const size_t staged = sizeof(SM) + (size_t)NS * (SM::TN * 2 + a.L.ostride);
+        args.L.obs_direct = 0;
+        if (a.L.ocap > 0) {
+            if (staged + 1024 <= (size_t)optin) smem = staged;
+            else args.L.obs_direct = 1;
+        }
+        if (smem + 1024 > (size_t)optin) throw std::runtime_error("stencil kernel does not fit in shared memory");
         if ((int)smem > attr_smem) {
             cuda_ok(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_smem = (int)smem;
@@ -541,7 +566,7 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
     const long long ntiles = (long long)a.L.tiles_x * a.L.tiles_y * a.L.tiles_t;
     const long long nunits = ntiles * ((a.nblk + KB - 1) / KB);
     const int grid = (int)std::min<long long>(std::min<long long>(nunits, (long long)resident), kMaxStencilGrid);
-    { kern<<<(unsigned)grid, 256, smem, s>>>(a, (int)nunits); note_launch(); }
+    { kern<<<(unsigned)grid, 256, smem, s>>>(args, (int)nunits); note_launch(); }
     return grid;
 }
 

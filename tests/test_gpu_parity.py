@@ -160,6 +160,20 @@ def test_plain_fp64_single_rhs_path_agrees():
     assert _rel(mu, infer.posterior_mean(orc)) < MEAN_TOL
 
 
+def test_plain_fp64_path_on_densely_observed_coarse_levels():
+    # 32^3 space-time grid with 5000 observations: on the 16^3 coarse level
+    # every node of a tile carries an observation entry, and the FP64 tables
+    # (256 x 27 coefficients per tile) no longer fit in shared memory beside
+    # the staged inputs, so the kernel reads them from global memory
+    pr, ob = W.c5_st2d(n=32, nt=32, m=5000, seed=8)
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    assert [lv[:3] for lv in post.level_info()][:2] == [(32, 32, 32), (16, 16, 16)]
+    mu32, info32 = post.solve_mean()
+    mu64, info64 = post.solve_mean(opts=gmrf.default_opts(precision=1, batched=0, max_inner=2000))
+    assert info32["converged"] == 1 and info64["converged"] == 1
+    assert _rel(mu64, mu32) < 1e-8
+
+
 def test_invalid_arguments_are_rejected():
     bad = W.prior_matern2d(2, 4.0)
     with pytest.raises(gmrf.GmrfError) as e:
