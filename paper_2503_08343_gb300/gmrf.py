@@ -307,3 +307,73 @@ def normals(seed, stream, sample0, count, n):
     out = np.empty((count, n))
     _check(load().gmrf_normals(seed, stream, sample0, count, n, _ptr(out)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Log marginal likelihood as a differentiable torch function of the
+# hyper-parameters theta = (log kappa, log tau, log sigma_obs, c, nu).
+
+HYPER = ("log_kappa", "log_tau", "log_sigma", "c", "nu")
+
+
+def with_hyper(prior: dict, obs: dict, theta) -> tuple[dict, dict]:
+    """Copies of (prior, obs) at hyper-parameters theta (sequence in HYPER
+    order).  kappa is the initial-block kappa0 of the space-time priors,
+    sigma_obs is one noise level for all point observations and c the x
+    velocity; the Matern kind ignores c and nu."""
+    lk, lt, ls, c, nu = (float(v) for v in theta)
+    pr, ob = dict(prior), dict(obs)
+    pr["kappa"] = float(np.exp(lk))
+    if pr["kind"].startswith("advdiff_st"):
+        pr["kappa0"] = pr["kappa"]
+    pr["tau"] = float(np.exp(lt))
+    pr["cx"], pr["nu"] = c, nu
+    ob["sigma"] = np.full(len(obs["y"]), float(np.exp(ls)))
+    return pr, ob
+
+
+def hyper_of(prior: dict, obs: dict) -> np.ndarray:
+    """theta of (prior, obs) in HYPER order (inverse of with_hyper)."""
+    k = prior["kappa0"] if prior["kind"].startswith("advdiff_st") else prior["kappa"]
+    return np.array([np.log(k), np.log(prior["tau"]), np.log(float(np.asarray(obs["sigma"])[0])),
+                     prior.get("cx", 0.0), prior.get("nu", 0.0)])
+
+
+def _loglik_function():
+    import torch
+
+    class LogMarginalLikelihood(torch.autograd.Function):
+        """Forward: the data-fit part 1/2 b^T mu - 1/2 y^T R^-1 y of the log
+        marginal likelihood at theta (the log-determinant terms are not
+        evaluated).  Backward: the gradient of the full log marginal
+        likelihood, with the trace terms estimated by Hutchinson probes from
+        the same batched solves (gmrf_loglik_grad); no graph through the
+        solver is recorded."""
+
+        @staticmethod
+        def forward(ctx, theta, prior, obs, nprobes, seed, opts):
+            pr, ob = with_hyper(prior, obs, theta.detach().cpu().tolist())
+            post = Posterior(Prior(pr), ob)
+            ll, g, se, info = post.loglik_grad(nprobes, seed, opts=opts)
+            ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
+            ctx.info = dict(info, grad_stderr=se.tolist())
+            return theta.new_tensor(ll)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return grad_out * g, None, None, None, None, None
+
+    return LogMarginalLikelihood
+
+
+_LOGLIK = None
+
+
+def log_marginal_likelihood(theta, prior: dict, obs: dict, nprobes: int = 32, seed: int = 0, opts=None):
+    """Differentiable in theta (a float64 torch tensor of 5 entries in HYPER
+    order); see LogMarginalLikelihood for what the value and the gradient are."""
+    global _LOGLIK
+    if _LOGLIK is None:
+        _LOGLIK = _loglik_function()
+    return _LOGLIK.apply(theta, prior, obs, nprobes, seed, opts)

@@ -59,3 +59,22 @@ def test_gradient_matches_oracle_estimator_and_exact_gradient(name):
     mu = infer.posterior_mean(post_o)
     fit = 0.5 * post_o.b @ mu - 0.5 * np.sum(post_o.rinv * post_o.y ** 2)
     assert ll == pytest.approx(fit, rel=1e-7, abs=1e-9)
+
+
+def test_autograd_function_returns_the_library_gradient():
+    import torch
+    pr, ob = CASES["st1d_24x20"]()
+    theta0 = gmrf.hyper_of(pr, ob)
+    pr2, ob2 = gmrf.with_hyper(pr, ob, theta0)
+    assert pr2["kappa0"] == pytest.approx(pr["kappa0"]) and pr2["tau"] == pytest.approx(pr["tau"])
+    theta = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+    ll = gmrf.log_marginal_likelihood(theta, pr, ob, nprobes=16, seed=5)
+    (3.0 * ll).backward()
+    want_ll, want_g, _, _ = gmrf.Posterior(gmrf.Prior(pr2), ob2).loglik_grad(16, 5)
+    assert ll.item() == pytest.approx(want_ll, rel=1e-12)
+    assert np.allclose(theta.grad.numpy(), 3.0 * want_g, rtol=1e-12, atol=0)
+    # one gradient-ascent step on the hyper-parameters moves the exact gradient's objective up
+    exact0 = infer.log_marginal_likelihood(pr2, ob2)
+    step = 1e-3 * theta.grad.numpy() / np.linalg.norm(theta.grad.numpy())
+    pr3, ob3 = gmrf.with_hyper(pr, ob, theta0 + step)
+    assert infer.log_marginal_likelihood(pr3, ob3) > exact0
