@@ -82,13 +82,16 @@ template <typename T> __device__ __forceinline__ T comp(const V4<T>& v, int i) {
 // absent, ny = 1); GEO_XYT: 2D space x time.  A CTA of 256 threads owns one
 // TX x TY x TT tile of nodes for one block of four right-hand sides.  The
 // input vector is staged with a halo of 2 in x and y (the stacked stencil
-// B^T B reaches two nodes) and 1 in t.
+// B^T B reaches two nodes) and 1 in t.  GEO_XYT tiles are single time levels
+// of a 32 x 8 plane tile: its stencil kernel marches through time with
+// rolling planes in shared memory, and the observation tables and tile lists
+// are kept per plane tile.
 enum Geometry { GEO_XY = 0, GEO_XT = 1, GEO_XYT = 2 };
 
 template <int GEO> struct Geo;
 template <> struct Geo<GEO_XY>  { static constexpr int TX = 32, TY = 8, TT = 1, HY = 2, HT = 0; };
 template <> struct Geo<GEO_XT>  { static constexpr int TX = 32, TY = 1, TT = 8, HY = 0, HT = 1; };
-template <> struct Geo<GEO_XYT> { static constexpr int TX = 16, TY = 4, TT = 4, HY = 2, HT = 1; };
+template <> struct Geo<GEO_XYT> { static constexpr int TX = 32, TY = 8, TT = 1, HY = 2, HT = 1; };
 
 // Offsets of the observation stencil A^T R^-1 A: all (dx, dy, dt) in
 // {-1, 0, 1} over the axes the geometry has (9 points in 2D, 27 in 3D).
@@ -101,9 +104,9 @@ __host__ __device__ constexpr int obs_dy(int geo, int a) { return geo == GEO_XT 
 __host__ __device__ constexpr int obs_dt(int geo, int a) { return geo == GEO_XY ? 0 : (geo == GEO_XT ? a / 3 - 1 : a / 9 - 1); }
 inline int obs_oc(int g) { return g == GEO_XYT ? 27 : 9; }
 
-inline int geo_tx(int g) { return g == GEO_XY ? 32 : (g == GEO_XT ? 32 : 16); }
-inline int geo_ty(int g) { return g == GEO_XY ? 8 : (g == GEO_XT ? 1 : 4); }
-inline int geo_tt(int g) { return g == GEO_XY ? 1 : (g == GEO_XT ? 8 : 4); }
+inline int geo_tx(int) { return 32; }
+inline int geo_ty(int g) { return g == GEO_XT ? 1 : 8; }
+inline int geo_tt(int g) { return g == GEO_XT ? 8 : 1; }
 
 // Stencil taps of the root B (dx, dy, dt): 0 centre, 1 x-1, 2 x+1, 3 y-1,
 // 4 y+1, 5 (x-1, y-1), 6 (x+1, y+1), 7 t-1.
@@ -192,6 +195,39 @@ __device__ __forceinline__ void block_sum4(A v[4], double* out /* 4 doubles, glo
         out[threadIdx.x] = s;
     }
     __syncthreads();   // the scratch may be reused by the next call
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async; a false predicate copies
+// zero bytes and zero-fills the destination) and the Dirichlet test of the
+// space boundary (App. B).
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 8 : 0));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <typename T> __device__ __forceinline__ void cp_v4(V4<T>* smem, const T* gmem, bool pred) {
+    cp_async16(smem, gmem, pred);
+    if (sizeof(T) == 8) cp_async16(reinterpret_cast<char*>(smem) + 16, reinterpret_cast<const char*>(gmem) + 16, pred);
+}
+template <typename T> __device__ __forceinline__ void cp_scalar(T* smem, const T* gmem, bool pred) {
+    if (sizeof(T) == 8) cp_async8(smem, gmem, pred);
+    else cp_async4(smem, gmem, pred);
+}
+
+__device__ __forceinline__ bool is_dirichlet(int x, int y, int nx, int ny) {
+    return x == 0 || x == nx - 1 || (ny > 1 && (y == 0 || y == ny - 1));
 }
 
 }  // namespace gmrf

@@ -65,9 +65,6 @@ template <typename T> LevelView<T> Level::view() const {
 template LevelView<float> Level::view<float>() const;
 template LevelView<double> Level::view<double>() const;
 
-__device__ __forceinline__ bool is_dirichlet(int x, int y, int nx, int ny) {
-    return x == 0 || x == nx - 1 || (ny > 1 && (y == 0 || y == ny - 1));
-}
 
 template <typename T> __device__ __forceinline__ T obs_w(const ObsRow& o, int n);
 template <> __device__ __forceinline__ float obs_w<float>(const ObsRow& o, int n) { return o.wf[n]; }
@@ -96,30 +93,6 @@ __device__ __forceinline__ void jcoef(const Colloc& c, T mu_c, T mu_l, T mu_r, T
 // A cp.async pipeline of NS stages keeps the next units' input tiles (with
 // halo), right-hand sides, directions and inverse diagonals in flight while
 // the current unit runs its B / B^T / observation phases.
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 16 : 0));
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 4 : 0));
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 8 : 0));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-template <typename T> __device__ __forceinline__ void cp_v4(V4<T>* smem, const T* gmem, bool pred) {
-    cp_async16(smem, gmem, pred);
-    if (sizeof(T) == 8) cp_async16(reinterpret_cast<char*>(smem) + 16, reinterpret_cast<const char*>(gmem) + 16, pred);
-}
-template <typename T> __device__ __forceinline__ void cp_scalar(T* smem, const T* gmem, bool pred) {
-    if (sizeof(T) == 8) cp_async8(smem, gmem, pred);
-    else cp_async4(smem, gmem, pred);
-}
 
 template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct StencilSmem {
     using G = Geo<GEO>;
@@ -588,7 +561,7 @@ static int launch_geo(int mode, const StencilArgs<T>& a, cudaStream_t s) {
 template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s) {
     if (geo == GEO_XY) return launch_geo<T, GEO_XY>(mode, a, s);
     if (geo == GEO_XT) return launch_geo<T, GEO_XT>(mode, a, s);
-    return launch_geo<T, GEO_XYT>(mode, a, s);
+    return launch_march<T>(mode, a, s);
 }
 template int launch_stencil<float>(int, int, const StencilArgs<float>&, cudaStream_t);
 template int launch_stencil<double>(int, int, const StencilArgs<double>&, cudaStream_t);

@@ -34,6 +34,8 @@ struct StencilArgs {
 // Dot partials written to `partial` as [nblk][grid][4] (APPLY x.Qx, RESID
 // |r|^2, CHEB b.x_new); returns the grid size, i.e. the partial count per block.
 template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s);
+// 2D space x time: the 2.5D-blocked kernel of stencil_march.cu (called by launch_stencil)
+template <typename T> int launch_march(int mode, const StencilArgs<T>& a, cudaStream_t s);
 int stencil_max_grid();
 
 // reduce [nblk][nparts][4] partials into out[nblk * 4]
