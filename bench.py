@@ -8,6 +8,7 @@ relative residual of 1e-10, and form the Rao-Blackwellised marginal variances.
 Metric: RHS x unknowns solved per second (whole job, all GPUs).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --stencil-timing c2|c5      # per-kernel stencil timings
 
 N > 1 runs under torchrun, one process per GPU: each rank solves its own
 replica (the workload is one posterior; it has no data-parallel split), so
@@ -125,6 +126,22 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# Chebyshev stencil on this workload, from one ncu capture
+# (profiles/stencil_chebyshev_matern512_rhs65.md), valid only for the kernel
+# sources it was taken on: SHA-256 of kernels.cu + common.cuh.
+CHEB_TRAFFIC = {"sources_sha256": "310a381c486d8e787c15718db515486ac0ff36bb36e0a552576f98676859033c", "bytes": 369905407}
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2503_08343_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def measured_peak_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -235,7 +252,8 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": 16 * N},
         "gpu_launches": int(l1 - l0),
         "roofline": {"bound": "hbm", "achieved": dom["GB/s"], "peak": peak, "unit": "GB/s",
-                     "frac": dom["frac"], "traffic": None,
+                     "frac": dom["frac"],
+                     "traffic": CHEB_TRAFFIC["bytes"] if CHEB_TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None,
                      "kernel": "k_stencil<GEO_XY,float,M_CHEB> (fused Q_u|y Chebyshev step, finest level)",
                      "peak_kind": f"{peak_kind} burst copy bandwidth", "kernel_ms": dom["ms"],
                      "algorithmic_bytes": 21.0 * units, "kernels": kern},
@@ -252,6 +270,40 @@ def run_ours(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
+STENCIL_BYTES = {0: 8.0, 1: 12.0, 2: 21.0}      # algorithmic bytes per RHS x unknown (FP32): apply, residual, Chebyshev
+
+
+def run_stencil_timing(which: str, iters: int) -> None:
+    """Per-kernel timing of the fused posterior-precision stencil on the
+    finest level (CUDA events inside the library, after warm-up), one JSON
+    line per mode.  One further launch of each mode runs inside the NVTX
+    range "stencil_<mode>" for a profiler filter.  Shapes: c2 = 2D Matern
+    512^2 with 65 right-hand sides; c5 = 2D space-time 128^2 x 64 with 33
+    (the marching kernel)."""
+    import torch
+    from paper_2503_08343_gb300 import gmrf, workloads as W
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peak = float(json.load(f)["hbm_gbs"])
+    if which == "c2":
+        pr, ob = W.c2_matern(n=N_SIDE, m=M_OBS)
+        k = NS + 1
+    else:
+        pr, ob = W.c5_st2d(n=128, nt=64, m=20000, seed=5)
+        k = 33
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    slots = 4 * ((k + 3) // 4)
+    for mode, name in ((0, "apply"), (1, "residual"), (2, "chebyshev")):
+        ms = post.time_stencil(mode, k, iters)
+        gbs = STENCIL_BYTES[mode] * slots * post.N / (ms * 1e-3) / 1e9
+        print(json.dumps({"workload": which, "kernel": name, "rhs": k, "slots": slots, "unknowns": post.N,
+                          "ms": ms, "GB/s": gbs, "frac_of_measured_hbm": gbs / peak}), flush=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(f"stencil_{name}")
+        post.time_stencil(mode, k, 1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -259,7 +311,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stencil-timing", choices=["c2", "c5"], default=None,
+                    help="time the stencil kernels alone (one JSON line per mode) instead of the step")
     args = ap.parse_args()
+    if args.stencil_timing:
+        run_stencil_timing(args.stencil_timing, 50)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "ours":
