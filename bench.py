@@ -246,7 +246,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 inner / f64 refinement", "data": "synthetic",
-        "config": dict(CONFIG, parallelism=f"replicas{world}", pcg_iterations=iters, fp64_residuals=refs),
+        "config": dict(CONFIG, parallelism=f"replicas{world}", pcg_iterations=iters, refinement_residuals=refs),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(ob["y"]),
                 "d2h_bytes_per_step": 16 * N},

@@ -625,8 +625,6 @@ void launch_pcg_scalar(int kind, const double* red, double* sc, int nblk, double
     { k_pcg_scalar<<<(P + 127) / 128, 128, 0, s>>>(kind, red, sc, P, tol2); note_launch(); }
 }
 
-constexpr int EPT = 4;                  // nodes per thread in elementwise kernels
-constexpr int ECHUNK = 256 * EPT;       // nodes per CTA
 int elem_parts(long long N) { return (int)((N + ECHUNK - 1) / ECHUNK); }
 
 template <typename T>

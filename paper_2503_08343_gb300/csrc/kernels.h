@@ -61,7 +61,20 @@ template <typename T> void launch_pcg_update_xr(T* x, T* r, const T* p, const T*
                                                 int nblk, double* partial, int nparts, cudaStream_t s);
 template <typename T> void launch_pcg_update_p(T* p, const T* z, const double* sc, long long N, int nblk, cudaStream_t s);
 void launch_pcg_scalar(int kind, const double* red, double* sc, int nblk, double tol2, cudaStream_t s);
+constexpr int EPT = 4;                  // nodes per thread in elementwise kernels
+constexpr int ECHUNK = 256 * EPT;       // nodes per CTA
 int elem_parts(long long N);
+
+// Refinement residual r = b - Q x in double-float arithmetic (resid_df.cu),
+// for 2D and 1D space-time levels without collocation rows: r is stored as
+// float pairs (hi, lo) in the FP64 slots of `out`; the partials hold the
+// rweight-weighted |r|^2 ([nblk][grid][4]); returns the grid size.
+bool resid_df_applicable(const Level& L);
+int launch_resid_df(const Level& L, const double* x, const double* b, double* out, const double* rweight,
+                    double* partial, int nblk, cudaStream_t s);
+// |r|^2 per right-hand side of a pair-stored residual, and r / norm as FP32
+void launch_norm2_df(const double* r, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
+void launch_scale_cast_df(const double* r, const double* norms, float* r32, long long N, int nblk, cudaStream_t s);
 
 // mixed precision refinement
 void launch_scale_cast(const double* r64, const double* norms, float* r32, long long N, int nblk, cudaStream_t s);

@@ -473,10 +473,17 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
     SolveStats st;
     const int ne = elem_parts(L.N);
     for (int ref = 0; ref <= o.max_refine; ++ref) {
+        // r64 holds FP64 values, or (r_pairs) double-float pairs (hi, lo)
+        bool r_pairs = false;
         if (ref == 0 && x_zero) {   // r = b
             GCK(cudaMemcpyAsync(W.r64, b64, sizeof(double) * (size_t)nblk * L.N * 4, cudaMemcpyDeviceToDevice, s));
             launch_norm2w(W.r64, L.d_dinv64, L.N, nblk, W.partial, ne, s);
             launch_reduce(W.partial, ne, nblk, W.red, s);
+        } else if (!fp64 && resid_df_applicable(L)) {
+            // double-float residual: GB300's FP64 rate makes the FP64 stencil compute-bound
+            const int ng = launch_resid_df(L, x64, b64, W.r64, L.d_dinv64, W.partial, nblk, s);
+            launch_reduce(W.partial, ng, nblk, W.red, s);
+            r_pairs = true;
         } else {
             StencilArgs<double> a{};
             a.L = L.view<double>();
@@ -512,7 +519,8 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
         if (conv) { st.converged = true; break; }
         if (ref == o.max_refine) break;
         // the inner solve works on r / |r| (unweighted norm keeps FP32 in range)
-        launch_norm2<double>(W.r64, L.N, nblk, W.partial, ne, s);
+        if (r_pairs) launch_norm2_df(W.r64, L.N, nblk, W.partial, ne, s);
+        else launch_norm2<double>(W.r64, L.N, nblk, W.partial, ne, s);
         launch_reduce(W.partial, ne, nblk, W.red2, s);
         GCK(cudaMemcpyAsync(W.h_red + P4, W.red2, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
         GCK(cudaStreamSynchronize(s));
@@ -524,7 +532,8 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
             st.inner += pcg<double>(P, W, inner_tol, o.max_inner, s, graph, &brk, has_dl ? &dl : nullptr);
             launch_axpy_scaled64(x64, W.norms, (const double*)W.v64.pcg[0], L.N, nblk, W.partial, s);
         } else {
-            launch_scale_cast(W.r64, W.norms, (float*)W.v32.pcg[1], L.N, nblk, s);
+            if (r_pairs) launch_scale_cast_df(W.r64, W.norms, (float*)W.v32.pcg[1], L.N, nblk, s);
+            else launch_scale_cast(W.r64, W.norms, (float*)W.v32.pcg[1], L.N, nblk, s);
             st.inner += pcg<float>(P, W, inner_tol, o.max_inner, s, graph, &brk, has_dl ? &dl : nullptr);
             launch_axpy_mixed(x64, W.norms, (const float*)W.v32.pcg[0], L.N, nblk, W.partial, s);
         }
