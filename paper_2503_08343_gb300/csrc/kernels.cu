@@ -602,8 +602,6 @@ __global__ void k_pcg_scalar(int kind, const double* __restrict__ red, double* _
         const bool ok = v > 0.0 && isfinite(v) && isfinite(rz[r]);
         if (active[r] != 0.0 && !ok) { brk[r] = 1.0; active[r] = 0.0; }
         alpha[r] = (active[r] != 0.0) ? rz[r] / v : 0.0;
-    } else if (kind == 1) {
-        rr[r] = v;
     } else if (kind == 2) {
         beta[r] = (active[r] != 0.0 && rz[r] != 0.0) ? v / rz[r] : 0.0;
         rz[r] = v;
@@ -648,7 +646,7 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
         dot[0] += rv.a * rv.a; dot[1] += rv.b * rv.b;
         dot[2] += rv.c * rv.c; dot[3] += rv.d * rv.d;
     }
-    block_sum4<256, T>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
+    if (partial != nullptr) block_sum4<256, T>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
 }
 
 template <typename T>

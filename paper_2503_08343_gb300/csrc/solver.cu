@@ -357,9 +357,7 @@ static void pcg_iteration(Posterior& P, Workspace& W, Workspace::Vecs& V, double
     const int ng = launch_stencil<T>(L.geo, M_APPLY, a, s);
     launch_reduce(W.partial, ng, nblk, W.red, s);
     launch_pcg_scalar(0, W.red, sc, nblk, tol2, s);
-    launch_pcg_update_xr<T>(x, r, p, q, sc, L.N, nblk, W.partial, ne, s);
-    launch_reduce(W.partial, ne, nblk, W.red, s);
-    launch_pcg_scalar(1, W.red, sc, nblk, tol2, s);
+    launch_pcg_update_xr<T>(x, r, p, q, sc, L.N, nblk, nullptr, ne, s);   // stopping uses r^T z, not |r|
     const int nz = vcycle<T>(P, W, V, 0, r, z, W.partial, s);
     launch_reduce(W.partial, nz, nblk, W.red, s);
     launch_pcg_scalar(2, W.red, sc, nblk, tol2, s);
