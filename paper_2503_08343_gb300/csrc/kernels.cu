@@ -12,10 +12,13 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <stdexcept>
 #include <string>
+
+#include <cuda.h>
 
 #include "kernels.h"
 
@@ -94,7 +97,7 @@ __device__ __forceinline__ void jcoef(const Colloc& c, T mu_c, T mu_l, T mu_r, T
 // halo), right-hand sides, directions and inverse diagonals in flight while
 // the current unit runs its B / B^T / observation phases.
 
-template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct StencilSmem {
+template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct alignas(128) StencilSmem {
     using G = Geo<GEO>;
     static constexpr int TX = G::TX, TY = G::TY, TT = G::TT, HY = G::HY, HT = G::HT;
     static constexpr int PX = TX + 4, PY = TY + 2 * HY, PT = TT + 2 * HT;
@@ -103,15 +106,25 @@ template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct Stencil
     static constexpr int NB = MODE == M_APPLY ? 1 : NS;
     static constexpr int ND = MODE == M_CHEB ? NS : 1;
     static constexpr int NH = MODE == M_CHEB0 ? NS : 1, PH = MODE == M_CHEB0 ? PN : 1;
+    // TMA destinations (p, b, d) first: every stage buffer starts on a
+    // 128-byte boundary
     V4<T> p[NS][PN][KB];
     V4<T> b[NB][TN][KB];
     V4<T> d[ND][TN][KB];
+    T dinv[ND][TN];
     V4<T> s[SN][KB];
     V4<T> sj[COL ? SN : 1][KB];
     V4<T> qobs[TN][KB];        // A^T R^-1 A p at the tile's observed nodes
-    T dinv[ND][TN];
     T dinvh[NH][PH];           // CHEB0: D^-1 on the staged nodes
     T mu[COL == 2 ? NS : 1][COL == 2 ? PN : 1];
+    static_assert((PN * sizeof(V4<T>)) % 128 == 0 && (TN * sizeof(V4<T>)) % 128 == 0,
+                  "stage buffers of the TMA boxes keep 128-byte alignment");
+};
+
+// Tensor maps of one launch: the input tile with its halo, and the own tiles
+// of the right-hand side and the direction (unused maps stay zero).
+struct StencilMaps {
+    CUtensorMap p, b, d;
 };
 
 // Flat shared-memory offsets of the taps: in the staged input (row r reads
@@ -151,8 +164,13 @@ __device__ __forceinline__ void unit_next(UnitPos& p, int tiles_x, int tiles_y, 
 // One work unit is (tile, group of KB consecutive blocks of four right-hand
 // sides): all per-node index work, staging addresses and checks are shared
 // by the 4 KB right-hand sides of the group.
+// Set when a stencil CTA gave up waiting for a staged tile (bounded mbarrier
+// wait); the solver checks and clears it after every solve.
+__device__ int g_stencil_abort = 0;
+constexpr int kMbarSpinCap = 1 << 22;
+
 template <int GEO, typename T, int MODE, int COL, int NS, int KB>
-__global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nunits) {
+__global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nunits, const __grid_constant__ StencilMaps maps) {
     using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
     constexpr int TX = SM::TX, TY = SM::TY, TT = SM::TT, HY = SM::HY, HT = SM::HT;
     constexpr int PX = SM::PX, PY = SM::PY, PN = SM::PN, TN = SM::TN;
@@ -162,8 +180,12 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     constexpr int KP = (PN + 255) / 256, KS = (SN + 255) / 256;
     static_assert(SN >= TN, "s tile covers the node tile");
     static_assert(NS >= 2, "the copy pipeline needs two stages");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SM& S = *reinterpret_cast<SM*>(smem_raw);
+    static_assert(KB == 1, "the input tile is one TMA box of one block");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem_base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // TMA destinations: 128 B
+    SM& S = *reinterpret_cast<SM*>(smem_base);
+    __shared__ uint64_t bars[NS];
+    __shared__ int abort_unit;
 
     const LevelView<T>& L = A.L;
     const int nx = L.nx, ny = L.ny, nt = L.nt;
@@ -176,7 +198,14 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     const bool has_obs = L.ocap > 0;
     const bool obs_staged = has_obs && !L.obs_direct;
     const int ostage = TN * 2 + L.ostride;     // bytes of one stage of observation tables
-    unsigned char* obs_smem = smem_raw + sizeof(SM);
+    unsigned char* obs_smem = smem_base + sizeof(SM);
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
+        mbar_fence_init();
+        abort_unit = 0;
+    }
+    __syncthreads();
+    unsigned phbits = 0;                       // parity of the next completion of each stage's barrier
 
     T c0[NTAP], c1[NTAP];
 #pragma unroll
@@ -216,39 +245,38 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             const int grp = P.grp;
             const int tile = (P.tt * tiles_y + P.ty) * tiles_x + P.tx;
             const int tx0 = P.tx * TX, ty0 = P.ty * TY, tt0 = P.tt * TT;
+            // TMA boxes (zero outside the grid): the input tile with its halo,
+            // the own tiles of b, d and D^-1
+            if (tid == 0) {
+                const int row0 = HY > 0 ? ty0 : tt0, hrow = HY > 0 ? HY : HT;
+                const bool with_d = MODE == M_CHEB && A.d != nullptr;
+                const unsigned bytes = (unsigned)(PN * sizeof(V4<T>)) + (MODE != M_APPLY ? (unsigned)(TN * sizeof(V4<T>)) : 0u) +
+                                       (with_d ? (unsigned)(TN * sizeof(V4<T>)) : 0u);
+                mbar_expect_tx(&bars[st], bytes);
+                tma_load_3d(&S.p[st][0][0], &maps.p, 4 * (tx0 - 2), row0 - hrow, grp, &bars[st]);
+                if (MODE != M_APPLY) tma_load_3d(&S.b[MODE != M_APPLY ? st : 0][0][0], &maps.b, 4 * tx0, row0, grp, &bars[st]);
+                if (with_d) tma_load_3d(&S.d[MODE == M_CHEB ? st : 0][0][0], &maps.d, 4 * tx0, row0, grp, &bars[st]);
+            }
+            // D^-1 is one value per node: its rows (4 nx bytes) need not be 16-byte
+            // multiples, which a tensor map requires, so it is copied per thread
+            if (MODE == M_CHEB) {
+                const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
+                const bool own = gx < nx && gy < ny && gt < nt;
+                cp_scalar<T>(&S.dinv[MODE == M_CHEB ? st : 0][tid], A.dinv + (own ? (gt * ny + gy) * nx + gx : 0), own);
+            }
             const int tbase = (tt0 * ny + ty0) * nx + tx0;
-            const T* xb[KB];
-            bool bok[KB];
+            if (COL == 2 || MODE == M_CHEB0) {      // per-node scalars of the tile and halo
 #pragma unroll
-            for (int j = 0; j < KB; ++j) {
-                const int blk = grp * KB + j;
-                bok[j] = blk < nblk;
-                xb[j] = (MODE == M_CHEB0 ? A.b : A.x) + (size_t)(bok[j] ? blk : 0) * N * RW;
+                for (int k = 0; k < KP; ++k) {
+                    const int e = tid + 256 * k;
+                    if (KP * 256 > PN && e >= PN) break;
+                    const int gx = tx0 + p_dx[k], gy = ty0 + p_dy[k], gt = tt0 + p_dt[k];
+                    const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gt >= 0 && gt < nt;
+                    const int node = in ? tbase + p_rel[k] : 0;
+                    if (COL == 2) cp_scalar<T>(&S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0], L.mu + node, in);
+                    if (MODE == M_CHEB0) cp_scalar<T>(&S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? e : 0], A.dinv + node, in);
+                }
             }
-#pragma unroll
-            for (int k = 0; k < KP; ++k) {
-                const int e = tid + 256 * k;
-                if (KP * 256 > PN && e >= PN) break;
-                const int gx = tx0 + p_dx[k], gy = ty0 + p_dy[k], gt = tt0 + p_dt[k];
-                const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gt >= 0 && gt < nt;
-                const int node = in ? tbase + p_rel[k] : 0;
-#pragma unroll
-                for (int j = 0; j < KB; ++j) cp_v4<T>(&S.p[st][e][j], xb[j] + node * RW, in && bok[j]);
-                if (COL == 2) cp_scalar<T>(&S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0], L.mu + node, in);
-                if (MODE == M_CHEB0) cp_scalar<T>(&S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? e : 0], A.dinv + node, in);
-            }
-            const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
-            const bool own = gx < nx && gy < ny && gt < nt;
-            const int node = own ? (gt * ny + gy) * nx + gx : 0;
-#pragma unroll
-            for (int j = 0; j < KB; ++j) {
-                const bool ok = own && bok[j];
-                const size_t boff = (size_t)(xb[j] - (MODE == M_CHEB0 ? A.b : A.x));
-                if (MODE != M_APPLY) cp_v4<T>(&S.b[MODE != M_APPLY ? st : 0][tid][j], A.b + boff + node * RW, ok);
-                if (MODE == M_CHEB && A.d != nullptr)
-                    cp_v4<T>(&S.d[MODE == M_CHEB ? st : 0][tid][j], A.d + boff + node * RW, ok);
-            }
-            if (MODE == M_CHEB) cp_scalar<T>(&S.dinv[MODE == M_CHEB ? st : 0][tid], A.dinv + node, own);
             if (obs_staged) {
                 unsigned char* dst = obs_smem + (size_t)st * ostage;
                 const unsigned char* gmap = reinterpret_cast<const unsigned char*>(L.omap + (size_t)tile * TN);
@@ -277,8 +305,17 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     // orders every read of the previous unit (its stage buffer, the s tile,
     // qobs) before the refill of that buffer and the next writes.
     for (int done = 0; done < count; ++done) {
+        fence_proxy_async();           // generic accesses of the last unit before the TMA refill below
         cp_wait<NS - 2>();
+        {                              // this unit's input tile (bounded wait)
+            int spins = 0;
+            while (!mbar_try_wait(&bars[st], (phbits >> st) & 1u)) {
+                if (++spins > kMbarSpinCap) { abort_unit = 1; break; }
+            }
+            phbits ^= 1u << st;
+        }
         __syncthreads();
+        if (abort_unit) break;
         issue(ahead, st == 0 ? NS - 1 : st - 1, done + NS - 1 < count);
         unit_next(ahead, tiles_x, tiles_y, tiles_t);
         if (MODE == M_CHEB0) {      // staged b -> x1 = c0 D^-1 b in place
@@ -481,6 +518,59 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         st = st + 1 == NS ? 0 : st + 1;
     }
     cp_wait<0>();
+    if (tid == 0 && abort_unit) atomicExch(&g_stencil_abort, 1);
+}
+
+// Tensor map of a blocked vector [nblk][N][4] seen as a 3D array (4 nx
+// values, rows, blocks) whose rows are y (2D) or t (1D space x time); the box
+// is one tile's input with its halo.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiled encode_tiled() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cuda_ok(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || f == nullptr) throw std::runtime_error("cuTensorMapEncodeTiled not available");
+        fn = reinterpret_cast<EncodeTiled>(f);
+    });
+    return fn;
+}
+
+template <int GEO, typename T>
+static CUtensorMap tile_map(const T* v, const LevelView<T>& L, int nblk, bool halo) {
+    using G = Geo<GEO>;
+    static_assert(G::HY == 0 || G::TT == 1, "2D tiles have one time level");
+    constexpr int PX = G::TX + 4, PR = G::HY > 0 ? G::TY + 2 * G::HY : G::TT + 2 * G::HT;
+    constexpr int TR = G::HY > 0 ? G::TY : G::TT;
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    const cuuint64_t rows = G::HY > 0 ? (cuuint64_t)L.ny : (cuuint64_t)L.nt;
+    const cuuint64_t dims[3] = {(cuuint64_t)4 * L.nx, rows, (cuuint64_t)nblk};
+    const cuuint64_t strides[2] = {(cuuint64_t)4 * L.nx * sizeof(T), (cuuint64_t)L.N * 4 * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)(4 * (halo ? PX : G::TX)), (cuuint32_t)(halo ? PR : TR), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode_tiled()(&m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                      3, const_cast<T*>(v), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw std::runtime_error("tensor map of a stencil operand: error " + std::to_string((int)r));
+    return m;
+}
+
+int stencil_abort_take(cudaStream_t s) {
+    int v = 0;
+    cuda_ok(cudaMemcpyFromSymbolAsync(&v, g_stencil_abort, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    cuda_ok(cudaStreamSynchronize(s));
+    if (v) {
+        static const int zero = 0;
+        cuda_ok(cudaMemcpyToSymbolAsync(g_stencil_abort, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+        cuda_ok(cudaStreamSynchronize(s));
+    }
+    return v;
 }
 
 // Largest persistent grid any stencil launch uses (sizes the partial buffers).
@@ -504,7 +594,7 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
     static std::map<size_t, int> per_sm;       // resident CTAs per SM by dynamic shared memory
     static std::mutex mu;                      // solves of independent posteriors may run on several host threads
     StencilArgs<T> args = a;
-    size_t smem = sizeof(SM);
+    size_t smem = sizeof(SM) + 128;            // + alignment slack of the TMA destinations
     int resident = 0;
     {
         std::lock_guard<std::mutex> lock(mu);
@@ -516,7 +606,7 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
         }
         // stage the observation tables with the inputs when they fit beside
         // them (with the 1 KB the block reduction's static array may take)
-        const size_t staged = sizeof(SM) + (size_t)NS * (SM::TN * 2 + a.L.ostride);
+        const size_t staged = sizeof(SM) + 128 + (size_t)NS * (SM::TN * 2 + a.L.ostride);
         args.L.obs_direct = 0;
         if (a.L.ocap > 0) {
             if (staged + 1024 <= (size_t)optin) smem = staged;
@@ -539,7 +629,12 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
     const long long ntiles = (long long)a.L.tiles_x * a.L.tiles_y * a.L.tiles_t;
     const long long nunits = ntiles * ((a.nblk + KB - 1) / KB);
     const int grid = (int)std::min<long long>(std::min<long long>(nunits, (long long)resident), kMaxStencilGrid);
-    { kern<<<(unsigned)grid, 256, smem, s>>>(args, (int)nunits); note_launch(); }
+    StencilMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    maps.p = tile_map<GEO, T>(MODE == M_CHEB0 ? a.b : a.x, a.L, a.nblk, true);
+    if (MODE != M_APPLY) maps.b = tile_map<GEO, T>(a.b, a.L, a.nblk, false);
+    if (MODE == M_CHEB && a.d != nullptr) maps.d = tile_map<GEO, T>(a.d, a.L, a.nblk, false);
+    { kern<<<(unsigned)grid, 256, smem, s>>>(args, (int)nunits, maps); note_launch(); }
     return grid;
 }
 

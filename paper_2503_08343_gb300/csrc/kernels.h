@@ -37,6 +37,9 @@ template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>
 // 2D space x time: the 2.5D-blocked kernel of stencil_march.cu (called by launch_stencil)
 template <typename T> int launch_march(int mode, const StencilArgs<T>& a, cudaStream_t s);
 int stencil_max_grid();
+// 1 if a stencil CTA gave up waiting for a staged input tile since the last
+// call (the flag is cleared)
+int stencil_abort_take(cudaStream_t s);
 
 // reduce [nblk][nparts][4] partials into out[nblk * 4]
 void launch_reduce(const double* partial, int nparts, int nblk, double* out, cudaStream_t s);

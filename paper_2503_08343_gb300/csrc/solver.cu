@@ -548,6 +548,7 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
         }
         st.breakdown |= brk;
     }
+    if (stencil_abort_take(s)) throw Error(GMRF_E_CUDA, "stencil kernel: staged input tile did not arrive (bounded wait)");
     return st;
 }
 
