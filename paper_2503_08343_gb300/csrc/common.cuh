@@ -248,6 +248,24 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0,
     asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
                  ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)) : "memory");
 }
+// Bounded wait for the completion of phase `parity` of a barrier: false when
+// it did not come within `cap` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int cap) {
+    for (int i = 0; i < cap; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// Before a CTA that gave up on a wait returns: wait (bounded again) for the
+// copies still in flight on the barriers whose bits are set in `pending`, so
+// that no bulk copy writes shared memory after the CTA ended.
+__device__ __forceinline__ void mbar_drain(uint64_t* bars, int nbars, unsigned pending, unsigned phbits, int cap) {
+    for (int i = 0; i < nbars; ++i)
+        if ((pending >> i) & 1u) mbar_wait_bounded(&bars[i], (phbits >> i) & 1u, cap);
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3, uint64_t* bar) {
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
+                 ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar)) : "memory");
+}
 // orders this thread's generic-proxy shared-memory accesses before later
 // async-proxy (TMA) accesses to the same buffers
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }

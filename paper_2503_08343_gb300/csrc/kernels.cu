@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     }
     __syncthreads();
     unsigned phbits = 0;                       // parity of the next completion of each stage's barrier
+    unsigned pend = 0;                         // stages with copies issued and not yet waited for
 
     T c0[NTAP], c1[NTAP];
 #pragma unroll
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 const unsigned bytes = (unsigned)(PN * sizeof(V4<T>)) + (MODE != M_APPLY ? (unsigned)(TN * sizeof(V4<T>)) : 0u) +
                                        (with_d ? (unsigned)(TN * sizeof(V4<T>)) : 0u);
                 mbar_expect_tx(&bars[st], bytes);
+                pend |= 1u << st;
                 tma_load_3d(&S.p[st][0][0], &maps.p, 4 * (tx0 - 2), row0 - hrow, grp, &bars[st]);
                 if (MODE != M_APPLY) tma_load_3d(&S.b[MODE != M_APPLY ? st : 0][0][0], &maps.b, 4 * tx0, row0, grp, &bars[st]);
                 if (with_d) tma_load_3d(&S.d[MODE == M_CHEB ? st : 0][0][0], &maps.d, 4 * tx0, row0, grp, &bars[st]);
@@ -307,12 +309,11 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     for (int done = 0; done < count; ++done) {
         fence_proxy_async();           // generic accesses of the last unit before the TMA refill below
         cp_wait<NS - 2>();
-        {                              // this unit's input tile (bounded wait)
-            int spins = 0;
-            while (!mbar_try_wait(&bars[st], (phbits >> st) & 1u)) {
-                if (++spins > kMbarSpinCap) { abort_unit = 1; break; }
-            }
+        if (mbar_wait_bounded(&bars[st], (phbits >> st) & 1u, kMbarSpinCap)) {   // this unit's input tile
             phbits ^= 1u << st;
+            pend &= ~(1u << st);
+        } else {
+            abort_unit = 1;
         }
         __syncthreads();
         if (abort_unit) break;
@@ -518,7 +519,10 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         st = st + 1 == NS ? 0 : st + 1;
     }
     cp_wait<0>();
-    if (tid == 0 && abort_unit) atomicExch(&g_stencil_abort, 1);
+    if (tid == 0 && abort_unit) {
+        mbar_drain(bars, NS, pend, phbits, kMbarSpinCap);
+        atomicExch(&g_stencil_abort, 1);
+    }
 }
 
 // Tensor map of a blocked vector [nblk][N][4] seen as a 3D array (4 nx
@@ -540,24 +544,29 @@ static EncodeTiled encode_tiled() {
     return fn;
 }
 
+void encode_tensor_map(CUtensorMap* m, bool f64, int rank, const void* base, const cuuint64_t* dims,
+                       const cuuint64_t* strides, const cuuint32_t* box) {
+    std::memset(m, 0, sizeof(*m));
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode_tiled()(m, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                      (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, estr,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw std::runtime_error("tensor map of a stencil operand: error " + std::to_string((int)r));
+}
+
 template <int GEO, typename T>
 static CUtensorMap tile_map(const T* v, const LevelView<T>& L, int nblk, bool halo) {
     using G = Geo<GEO>;
     static_assert(G::HY == 0 || G::TT == 1, "2D tiles have one time level");
     constexpr int PX = G::TX + 4, PR = G::HY > 0 ? G::TY + 2 * G::HY : G::TT + 2 * G::HT;
     constexpr int TR = G::HY > 0 ? G::TY : G::TT;
-    CUtensorMap m;
-    std::memset(&m, 0, sizeof(m));
     const cuuint64_t rows = G::HY > 0 ? (cuuint64_t)L.ny : (cuuint64_t)L.nt;
     const cuuint64_t dims[3] = {(cuuint64_t)4 * L.nx, rows, (cuuint64_t)nblk};
     const cuuint64_t strides[2] = {(cuuint64_t)4 * L.nx * sizeof(T), (cuuint64_t)L.N * 4 * sizeof(T)};
     const cuuint32_t box[3] = {(cuuint32_t)(4 * (halo ? PX : G::TX)), (cuuint32_t)(halo ? PR : TR), 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = encode_tiled()(&m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                                      3, const_cast<T*>(v), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) throw std::runtime_error("tensor map of a stencil operand: error " + std::to_string((int)r));
+    CUtensorMap m;
+    encode_tensor_map(&m, sizeof(T) == 8, 3, v, dims, strides, box);
     return m;
 }
 
@@ -570,7 +579,7 @@ int stencil_abort_take(cudaStream_t s) {
         cuda_ok(cudaMemcpyToSymbolAsync(g_stencil_abort, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
         cuda_ok(cudaStreamSynchronize(s));
     }
-    return v;
+    return v | march_abort_take(s);
 }
 
 // Largest persistent grid any stencil launch uses (sizes the partial buffers).

@@ -1,6 +1,8 @@
 // Host-callable launchers of the GMRF kernels (implemented in kernels.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "impl.h"
 
 namespace gmrf {
@@ -38,8 +40,14 @@ template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>
 template <typename T> int launch_march(int mode, const StencilArgs<T>& a, cudaStream_t s);
 int stencil_max_grid();
 // 1 if a stencil CTA gave up waiting for a staged input tile since the last
-// call (the flag is cleared)
+// call (the flags of both stencil kernels are cleared)
 int stencil_abort_take(cudaStream_t s);
+int march_abort_take(cudaStream_t s);
+// cuTensorMapEncodeTiled of a dense FP32 (f64 = false) or FP64 array of
+// `rank` dimensions (innermost first; strides of dimensions 1.. in bytes),
+// no interleave or swizzle, zero fill outside; throws on an error.
+void encode_tensor_map(CUtensorMap* m, bool f64, int rank, const void* base, const cuuint64_t* dims,
+                       const cuuint64_t* strides, const cuuint32_t* box);
 
 // reduce [nblk][nparts][4] partials into out[nblk * 4]
 void launch_reduce(const double* partial, int nparts, int nblk, double* out, cudaStream_t s);

@@ -22,6 +22,10 @@
 #include <stdexcept>
 #include <string>
 
+#include <cstring>
+
+#include <cuda.h>
+
 #include "kernels.h"
 
 namespace gmrf {
@@ -36,15 +40,27 @@ constexpr int OC = ObsStencil<GEO_XYT>::OC;
 static_assert(MX * MY == 256 && Geo<GEO_XYT>::TT == 1, "one thread per node of a 32 x 8 plane tile");
 static_assert(tap_dt(7) == -1 && tap_dx(7) == 0 && tap_dy(7) == 0, "tap 7 is the previous time level");
 
-template <typename T, int MODE> struct MarchSmem {
+// TMA destinations (input planes, own b and d) first, each stage buffer on a
+// 128-byte boundary.
+template <typename T, int MODE> struct alignas(128) MarchSmem {
     V4<T> p[4][PP];
-    V4<T> s[2][SP];
     V4<T> b[MODE != M_APPLY ? 2 : 1][256];
     V4<T> d[MODE == M_CHEB ? 2 : 1][256];
+    V4<T> s[2][SP];
     T dinv[MODE == M_CHEB ? 2 : 1][256];
     T dinvh[MODE == M_CHEB0 ? 4 : 1][MODE == M_CHEB0 ? PP : 1];
     V4<T> qobs[256];
+    static_assert((PP * sizeof(V4<T>)) % 128 == 0 && (256 * sizeof(V4<T>)) % 128 == 0, "128-byte stage buffers");
 };
+
+// Tensor maps of a blocked space-time vector seen as (4 nx values, ny, nt,
+// blocks): the input plane with its halo, and the own plane tile.
+struct MarchMaps {
+    CUtensorMap p, b, d;
+};
+
+__device__ int g_march_abort = 0;
+constexpr int kSpinCap = 1 << 22;
 
 void ok(cudaError_t e) {
     if (e != cudaSuccess) throw std::runtime_error(std::string("kernel setup: ") + cudaGetErrorString(e));
@@ -60,10 +76,14 @@ struct MUnit {
 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunits, int tc, int nchunks) {
+__global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunits, int tc, int nchunks,
+                                                const __grid_constant__ MarchMaps maps) {
     using SM = MarchSmem<T, MODE>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SM& S = *reinterpret_cast<SM*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem_base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    SM& S = *reinterpret_cast<SM*>(smem_base);
+    __shared__ uint64_t bars[4];               // one per input-plane slot
+    __shared__ int aborted;
     const LevelView<T>& L = A.L;
     const int nx = L.nx, ny = L.ny, nt = L.nt;
     const long long N = L.N;
@@ -75,7 +95,15 @@ __global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunit
     const bool has_obs = L.ocap > 0;
     const bool obs_staged = has_obs && !L.obs_direct;
     const int ostage = 256 * 2 + L.ostride;
-    unsigned char* obs_smem = smem_raw + sizeof(SM);
+    unsigned char* obs_smem = smem_base + sizeof(SM);
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+        mbar_fence_init();
+        aborted = 0;
+    }
+    __syncthreads();
+    unsigned phbits = 0;                       // parity of the next completion of each slot's barrier
+    unsigned pend = 0;                         // slots with copies issued and not yet waited for (thread 0)
 
     T c0[NTAP], c1[NTAP];
 #pragma unroll
@@ -112,42 +140,60 @@ __global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunit
         return m;
     };
 
-    // input plane of level tau into slot tau & 3 (zero outside the grid)
-    auto stage_p = [&](int grp, int tx0, int ty0, int tau) {
+    // Input plane of level tau into slot tau & 3 (TMA, zero outside the grid),
+    // with level tau - 1's own tiles of b and d when with_own; both complete
+    // on the slot's barrier.  The per-node scalars (D^-1 for CHEB0 with halo,
+    // D^-1 and the observation tables of level tau - 1) go by cp.async.
+    auto stage = [&](int grp, const MUnit& u, int tau, bool with_own) {
         const int slot = tau & 3;
-        const bool lv = tau >= 0 && tau < nt;
-        const size_t lvl = (size_t)(lv ? tau : 0) * plane;
-        const T* src = (MODE == M_CHEB0 ? A.b : A.x) + ((size_t)grp * N + lvl) * RW;
+        const int tx0 = u.tx * MX, ty0 = u.ty * MY;
+        if (tid == 0) {
+            const bool with_b = with_own && MODE != M_APPLY;
+            const bool with_d = with_own && MODE == M_CHEB && A.d != nullptr;
+            const unsigned bytes = (unsigned)(PP * sizeof(V4<T>)) + (with_b ? 256u * (unsigned)sizeof(V4<T>) : 0u) +
+                                   (with_d ? 256u * (unsigned)sizeof(V4<T>) : 0u);
+            mbar_expect_tx(&bars[slot], bytes);
+            pend |= 1u << slot;
+            tma_load_4d(&S.p[slot][0], &maps.p, 4 * (tx0 - 2), ty0 - 2, tau, grp, &bars[slot]);
+            if (with_b) tma_load_4d(&S.b[MODE != M_APPLY ? (tau - 1) & 1 : 0][0], &maps.b, 4 * tx0, ty0, tau - 1, grp, &bars[slot]);
+            if (with_d) tma_load_4d(&S.d[MODE == M_CHEB ? (tau - 1) & 1 : 0][0], &maps.d, 4 * tx0, ty0, tau - 1, grp, &bars[slot]);
+        }
+        if (MODE == M_CHEB0) {
+            const bool lv = tau >= 0 && tau < nt;
+            const size_t lvl = (size_t)(lv ? tau : 0) * plane;
 #pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            const int e = tid + 256 * k;
-            if (KP * 256 > PP && e >= PP) break;
-            const int gx = tx0 + p_dx[k], gy = ty0 + p_dy[k];
-            const bool in = lv && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-            const int node = in ? gy * nx + gx : 0;
-            cp_v4<T>(&S.p[slot][e], src + (size_t)node * RW, in);
-            if (MODE == M_CHEB0)
-                cp_scalar<T>(&S.dinvh[MODE == M_CHEB0 ? slot : 0][MODE == M_CHEB0 ? e : 0], A.dinv + lvl + node, in);
+            for (int k = 0; k < KP; ++k) {
+                const int e = tid + 256 * k;
+                if (KP * 256 > PP && e >= PP) break;
+                const int gx = tx0 + p_dx[k], gy = ty0 + p_dy[k];
+                const bool in = lv && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+                cp_scalar<T>(&S.dinvh[MODE == M_CHEB0 ? slot : 0][MODE == M_CHEB0 ? e : 0], A.dinv + lvl + (in ? gy * nx + gx : 0), in);
+            }
+        }
+        if (with_own) {
+            const int lvo = tau - 1, oslot = lvo & 1;
+            const int gx = tx0 + lx, gy = ty0 + ly;
+            const bool own = gx < nx && gy < ny;
+            if (MODE == M_CHEB)
+                cp_scalar<T>(&S.dinv[MODE == M_CHEB ? oslot : 0][tid], A.dinv + (own ? (size_t)lvo * plane + (size_t)gy * nx + gx : 0), own);
+            if (obs_staged) {
+                const int tile = (lvo * tiles_y + u.ty) * tiles_x + u.tx;
+                unsigned char* dst = obs_smem + (size_t)oslot * ostage;
+                const unsigned char* gmap = reinterpret_cast<const unsigned char*>(L.omap + (size_t)tile * 256);
+                const unsigned char* gent = reinterpret_cast<const unsigned char*>(L.oent) + (size_t)tile * L.ostride;
+                for (int c = tid; c < 256 * 2 / 16; c += 256) cp_async16(dst + c * 16, gmap + c * 16, true);
+                for (int c = tid; c < L.ostride / 16; c += 256) cp_async16(dst + 256 * 2 + c * 16, gent + c * 16, true);
+            }
         }
     };
-    // right-hand side, direction, diagonal and observation tables of level
-    // tau into slot tau & 1
-    auto stage_own = [&](int grp, const MUnit& u, int tau) {
-        const int slot = tau & 1;
-        const int gx = u.tx * MX + lx, gy = u.ty * MY + ly;
-        const bool own = gx < nx && gy < ny;
-        const size_t node = own ? (size_t)tau * plane + (size_t)gy * nx + gx : 0;
-        const size_t off = ((size_t)grp * N + node) * RW;
-        if (MODE != M_APPLY) cp_v4<T>(&S.b[MODE != M_APPLY ? slot : 0][tid], A.b + off, own);
-        if (MODE == M_CHEB && A.d != nullptr) cp_v4<T>(&S.d[MODE == M_CHEB ? slot : 0][tid], A.d + off, own);
-        if (MODE == M_CHEB) cp_scalar<T>(&S.dinv[MODE == M_CHEB ? slot : 0][tid], A.dinv + node, own);
-        if (obs_staged) {
-            const int tile = (tau * tiles_y + u.ty) * tiles_x + u.tx;
-            unsigned char* dst = obs_smem + (size_t)slot * ostage;
-            const unsigned char* gmap = reinterpret_cast<const unsigned char*>(L.omap + (size_t)tile * 256);
-            const unsigned char* gent = reinterpret_cast<const unsigned char*>(L.oent) + (size_t)tile * L.ostride;
-            for (int c = tid; c < 256 * 2 / 16; c += 256) cp_async16(dst + c * 16, gmap + c * 16, true);
-            for (int c = tid; c < L.ostride / 16; c += 256) cp_async16(dst + 256 * 2 + c * 16, gent + c * 16, true);
+    // bounded wait for the plane of level tau (and what rides on its barrier)
+    auto wait_plane = [&](int tau) {
+        const int slot = tau & 3;
+        if (mbar_wait_bounded(&bars[slot], (phbits >> slot) & 1u, kSpinCap)) {
+            phbits ^= 1u << slot;
+            pend &= ~(1u << slot);
+        } else {
+            aborted = 1;
         }
     };
     // CHEB0: staged b -> x1 = c0 D^-1 b in place (after the plane landed)
@@ -200,16 +246,19 @@ __global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunit
         const int tx0 = cur.tx * MX, ty0 = cur.ty * MY;
         const int ta = cur.chunk * tc, tb = min(ta + tc, nt);
         // prologue: planes ta - 1, ta (s_ta) and ta + 1 with level ta's own data
+        fence_proxy_async();                   // this thread's accesses of the last unit before the TMA refills
         __syncthreads();                       // the previous unit's reads are done
-        stage_p(grp, tx0, ty0, ta - 1);
+        stage(grp, cur, ta - 1, false);
         cp_commit();
-        stage_p(grp, tx0, ty0, ta);
+        stage(grp, cur, ta, false);
         cp_commit();
-        stage_p(grp, tx0, ty0, ta + 1);
-        stage_own(grp, cur, ta);
+        stage(grp, cur, ta + 1, true);
         cp_commit();
         cp_wait<1>();
+        wait_plane(ta - 1);
+        wait_plane(ta);
         __syncthreads();
+        if (aborted) break;
         if (MODE == M_CHEB0) {
             scale_plane(ta - 1);
             scale_plane(ta);
@@ -218,10 +267,12 @@ __global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunit
         spass(tx0, ty0, ta);
 #pragma unroll 1
         for (int t = ta; t < tb; ++t) {
+            fence_proxy_async();
             cp_wait<0>();                      // plane t + 1 and level t's own data landed
+            wait_plane(t + 1);
             __syncthreads();
-            if (t + 2 <= tb) stage_p(grp, tx0, ty0, t + 2);
-            if (t + 1 < tb) stage_own(grp, cur, t + 1);
+            if (aborted) break;
+            if (t + 2 <= tb) stage(grp, cur, t + 2, t + 1 < tb);
             cp_commit();
             if (MODE == M_CHEB0) {
                 scale_plane(t + 1);
@@ -300,6 +351,7 @@ __global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunit
                 }
             }
         }
+        if (aborted) break;
         // dot partials of this unit's block: add to the CTA's entry
         if (A.partial != nullptr) {
             double* dst = A.partial + ((size_t)grp * G + blockIdx.x) * 4;
@@ -311,7 +363,41 @@ __global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunit
         }
     }
     cp_wait<0>();
+    if (tid == 0 && aborted) {
+        mbar_drain(bars, 4, pend, phbits, kSpinCap);
+        atomicExch(&g_march_abort, 1);
+    }
 }
+
+// Tensor map of a blocked space-time vector [nblk][nt][ny][nx][4] as the 4D
+// array (4 nx values, ny, nt, nblk); the box is one 32 x 8 plane tile, with
+// the 2-node halo when `halo` (zero outside the grid and outside [0, nt)).
+template <typename T>
+CUtensorMap march_map(const T* v, const LevelView<T>& L, int nblk, bool halo) {
+    const cuuint64_t dims[4] = {(cuuint64_t)4 * L.nx, (cuuint64_t)L.ny, (cuuint64_t)L.nt, (cuuint64_t)nblk};
+    const cuuint64_t strides[3] = {(cuuint64_t)4 * L.nx * sizeof(T), (cuuint64_t)L.nx * L.ny * 4 * sizeof(T),
+                                   (cuuint64_t)L.N * 4 * sizeof(T)};
+    const cuuint32_t box[4] = {(cuuint32_t)(4 * (halo ? PX : MX)), (cuuint32_t)(halo ? PY : MY), 1, 1};
+    CUtensorMap m;
+    encode_tensor_map(&m, sizeof(T) == 8, 4, v, dims, strides, box);
+    return m;
+}
+
+}  // namespace
+
+int march_abort_take(cudaStream_t s) {
+    int v = 0;
+    ok(cudaMemcpyFromSymbolAsync(&v, g_march_abort, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    ok(cudaStreamSynchronize(s));
+    if (v) {
+        static const int zero = 0;
+        ok(cudaMemcpyToSymbolAsync(g_march_abort, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+        ok(cudaStreamSynchronize(s));
+    }
+    return v;
+}
+
+namespace {
 
 // Largest persistent grid (the dot-partial buffers are sized for it).
 constexpr int kMaxMarchGrid = 4096;
@@ -324,7 +410,7 @@ int launch_march_mode(const StencilArgs<T>& a, cudaStream_t s) {
     static std::map<size_t, int> per_sm;
     static std::mutex mu;
     StencilArgs<T> args = a;
-    size_t smem = sizeof(SM);
+    size_t smem = sizeof(SM) + 128;            // + slack to put the stage buffers on 128 bytes
     int resident = 0;
     {
         std::lock_guard<std::mutex> lock(mu);
@@ -334,7 +420,7 @@ int launch_march_mode(const StencilArgs<T>& a, cudaStream_t s) {
             ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             ok(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         }
-        const size_t staged = sizeof(SM) + 2 * (size_t)(256 * 2 + a.L.ostride);
+        const size_t staged = smem + 2 * (size_t)(256 * 2 + a.L.ostride);
         args.L.obs_direct = 0;
         if (a.L.ocap > 0) {
             if (staged + 1024 <= (size_t)optin) smem = staged;
@@ -364,7 +450,12 @@ int launch_march_mode(const StencilArgs<T>& a, cudaStream_t s) {
     nchunks = (nt + tc - 1) / tc;
     const long long nunits = base * nchunks;
     const int grid = (int)std::min<long long>(std::min<long long>(nunits, resident), kMaxMarchGrid);
-    { kern<<<(unsigned)grid, 256, smem, s>>>(args, (int)nunits, tc, nchunks); note_launch(); }
+    MarchMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    maps.p = march_map<T>(MODE == M_CHEB0 ? a.b : a.x, a.L, a.nblk, true);
+    if (MODE != M_APPLY) maps.b = march_map<T>(a.b, a.L, a.nblk, false);
+    if (MODE == M_CHEB && a.d != nullptr) maps.d = march_map<T>(a.d, a.L, a.nblk, false);
+    { kern<<<(unsigned)grid, 256, smem, s>>>(args, (int)nunits, tc, nchunks, maps); note_launch(); }
     return grid;
 }
 
