@@ -129,14 +129,14 @@ def run_reference(args, rank, world):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # Chebyshev stencil on this workload, from one ncu capture
 # (profiles/stencil_chebyshev_matern512_rhs65.md), valid only for the kernel
-# sources it was taken on: SHA-256 of kernels.cu + common.cuh.
+# sources it was taken on: SHA-256 of stencil.cu + common.cuh.
 CHEB_TRAFFIC = {"sources_sha256": "310a381c486d8e787c15718db515486ac0ff36bb36e0a552576f98676859033c", "bytes": 369905407}
 
 
 def kernel_sources_sha256() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels.cu", "common.cuh"):
+    for f in ("stencil.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2503_08343_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

@@ -1,14 +1,7 @@
-// Kernels of the GB300 GMRF solver.
-//
-// The posterior precision Q_u|y = B^T B + J^T Q_eps J + A^T R^-1 A
-// (Sec. 3.1 eq. posterior-mean; B the stacked root of the SPDE prior,
-// Sec. 2.2 eq. sparse-prec-matrix and App. A; J the collocation rows,
-// Sec. 3.3) is never stored.  One CTA stages a tile of the input vector
-// with its halo in shared memory, forms s = B p on the tile plus a one-node
-// ring, applies B^T back onto the tile, adds the observation rows of the
-// tile from a per-tile list, and finishes with a mode-specific epilogue.
-// All traffic is HBM-bound (about 3 flop per byte), so nothing here uses
-// tensor cores.
+// Vector, transfer, reduction, sampling and variance kernels of the GB300
+// GMRF solver (the posterior-precision stencils are in stencil.cu and
+// stencil_march.cu).  All of them are HBM-bound elementwise or gather
+// passes over blocked right-hand-side batches [nblk][N][4].
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -68,608 +61,6 @@ template <typename T> LevelView<T> Level::view() const {
 template LevelView<float> Level::view<float>() const;
 template LevelView<double> Level::view<double>() const;
 
-
-template <typename T> __device__ __forceinline__ T obs_w(const ObsRow& o, int n);
-template <> __device__ __forceinline__ float obs_w<float>(const ObsRow& o, int n) { return o.wf[n]; }
-template <> __device__ __forceinline__ double obs_w<double>(const ObsRow& o, int n) { return o.wd[n]; }
-template <typename T> __device__ __forceinline__ T obs_rinv(const ObsRow& o);
-template <> __device__ __forceinline__ float obs_rinv<float>(const ObsRow& o) { return o.rinvf; }
-template <> __device__ __forceinline__ double obs_rinv<double>(const ObsRow& o) { return o.rinv; }
-
-// Collocation row coefficients at row (rx, rt): centre, x-1, x+1, t-1.
-template <typename T, int COL>
-__device__ __forceinline__ void jcoef(const Colloc& c, T mu_c, T mu_l, T mu_r, T& cC, T& cL, T& cR) {
-    const T inv_2h = (T)c.inv_2h, nu_h2 = (T)c.nu_h2;
-    T a, da;
-    if (COL == 1) { a = (T)c.c; da = T(0); }
-    else { a = mu_c; da = (mu_r - mu_l) * inv_2h; }
-    cC = (T)c.inv_dt + da + T(2) * nu_h2;
-    cL = -a * inv_2h - nu_h2;
-    cR = a * inv_2h - nu_h2;
-}
-
-// ---------------------------------------------------------------------------
-// fused posterior-precision stencil
-//
-// Persistent grid: CTA c walks the work units u = c, c + G, ... where a unit
-// is one (tile, block of four right-hand sides) pair, u = blk * ntiles + tile.
-// A cp.async pipeline of NS stages keeps the next units' input tiles (with
-// halo), right-hand sides, directions and inverse diagonals in flight while
-// the current unit runs its B / B^T / observation phases.
-
-template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct alignas(128) StencilSmem {
-    using G = Geo<GEO>;
-    static constexpr int TX = G::TX, TY = G::TY, TT = G::TT, HY = G::HY, HT = G::HT;
-    static constexpr int PX = TX + 4, PY = TY + 2 * HY, PT = TT + 2 * HT;
-    static constexpr int SX = TX + 2, SY = TY + HY, ST = TT + HT;
-    static constexpr int TN = TX * TY * TT, PN = PX * PY * PT, SN = SX * SY * ST;
-    static constexpr int NB = MODE == M_APPLY ? 1 : NS;
-    static constexpr int ND = MODE == M_CHEB ? NS : 1;
-    static constexpr int NH = MODE == M_CHEB0 ? NS : 1, PH = MODE == M_CHEB0 ? PN : 1;
-    // TMA destinations (p, b, d) first: every stage buffer starts on a
-    // 128-byte boundary
-    V4<T> p[NS][PN][KB];
-    V4<T> b[NB][TN][KB];
-    V4<T> d[ND][TN][KB];
-    T dinv[ND][TN];
-    V4<T> s[SN][KB];
-    V4<T> sj[COL ? SN : 1][KB];
-    V4<T> qobs[TN][KB];        // A^T R^-1 A p at the tile's observed nodes
-    T dinvh[NH][PH];           // CHEB0: D^-1 on the staged nodes
-    T mu[COL == 2 ? NS : 1][COL == 2 ? PN : 1];
-    static_assert((PN * sizeof(V4<T>)) % 128 == 0 && (TN * sizeof(V4<T>)) % 128 == 0,
-                  "stage buffers of the TMA boxes keep 128-byte alignment");
-};
-
-// Tensor maps of one launch: the input tile with its halo, and the own tiles
-// of the right-hand side and the direction (unused maps stay zero).
-struct StencilMaps {
-    CUtensorMap p, b, d;
-};
-
-// Flat shared-memory offsets of the taps: in the staged input (row r reads
-// p at r + o) and in the s tile (node i gathers s at row i - o).
-template <int PX, int PY> __host__ __device__ constexpr int poff(int o) { return (tap_dt(o) * PY + tap_dy(o)) * PX + tap_dx(o); }
-template <int SX, int SY> __host__ __device__ constexpr int soff(int o) { return -((tap_dt(o) * SY + tap_dy(o)) * SX + tap_dx(o)); }
-
-// Position of a work unit: tile coordinates (tx, ty, tt) in tile units and
-// the block group.  Units are numbered group-major (u = grp * ntiles + tile);
-// each CTA takes one contiguous chunk of units, so it crosses few group
-// boundaries (where the dot partials are flushed), and steps through its
-// chunk with carry-adds (no integer division inside the unit loop).
-struct UnitPos {
-    int tx, ty, tt, grp;
-};
-__device__ __forceinline__ UnitPos unit_decompose(long long u, int tiles_x, int tiles_y, int tiles_t) {
-    UnitPos p;
-    const long long ntiles = (long long)tiles_x * tiles_y * tiles_t;
-    p.grp = (int)(u / ntiles);
-    const long long tile = u - (long long)p.grp * ntiles;
-    p.tx = (int)(tile % tiles_x);
-    const long long r = tile / tiles_x;
-    p.ty = (int)(r % tiles_y);
-    p.tt = (int)(r / tiles_y);
-    return p;
-}
-__device__ __forceinline__ void unit_next(UnitPos& p, int tiles_x, int tiles_y, int tiles_t) {
-    if (++p.tx == tiles_x) {
-        p.tx = 0;
-        if (++p.ty == tiles_y) {
-            p.ty = 0;
-            if (++p.tt == tiles_t) { p.tt = 0; ++p.grp; }
-        }
-    }
-}
-
-// One work unit is (tile, group of KB consecutive blocks of four right-hand
-// sides): all per-node index work, staging addresses and checks are shared
-// by the 4 KB right-hand sides of the group.
-// Set when a stencil CTA gave up waiting for a staged tile (bounded mbarrier
-// wait); the solver checks and clears it after every solve.
-__device__ int g_stencil_abort = 0;
-constexpr int kMbarSpinCap = 1 << 22;
-
-template <int GEO, typename T, int MODE, int COL, int NS, int KB>
-__global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nunits, const __grid_constant__ StencilMaps maps) {
-    using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
-    constexpr int TX = SM::TX, TY = SM::TY, TT = SM::TT, HY = SM::HY, HT = SM::HT;
-    constexpr int PX = SM::PX, PY = SM::PY, PN = SM::PN, TN = SM::TN;
-    constexpr int SX = SM::SX, SY = SM::SY, SN = SM::SN;
-    constexpr int HYS = HY / 2;
-    constexpr int OC = ObsStencil<GEO>::OC;
-    constexpr int KP = (PN + 255) / 256, KS = (SN + 255) / 256;
-    static_assert(SN >= TN, "s tile covers the node tile");
-    static_assert(NS >= 2, "the copy pipeline needs two stages");
-    static_assert(KB == 1, "the input tile is one TMA box of one block");
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* smem_base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // TMA destinations: 128 B
-    SM& S = *reinterpret_cast<SM*>(smem_base);
-    __shared__ uint64_t bars[NS];
-    __shared__ int abort_unit;
-
-    const LevelView<T>& L = A.L;
-    const int nx = L.nx, ny = L.ny, nt = L.nt;
-    const int N = (int)L.N;
-    const int nblk = A.nblk;
-    const int ntiles = L.tiles_x * L.tiles_y * L.tiles_t;
-    const int tid = threadIdx.x;
-    const int lx = tid % TX, ly = (tid / TX) % TY, lt = tid / (TX * TY);
-    const int G = gridDim.x;
-    const bool has_obs = L.ocap > 0;
-    const bool obs_staged = has_obs && !L.obs_direct;
-    const int ostage = TN * 2 + L.ostride;     // bytes of one stage of observation tables
-    unsigned char* obs_smem = smem_base + sizeof(SM);
-    if (tid == 0) {
-        for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
-        mbar_fence_init();
-        abort_unit = 0;
-    }
-    __syncthreads();
-    unsigned phbits = 0;                       // parity of the next completion of each stage's barrier
-    unsigned pend = 0;                         // stages with copies issued and not yet waited for
-
-    T c0[NTAP], c1[NTAP];
-#pragma unroll
-    for (int o = 0; o < NTAP; ++o) { c0[o] = L.cf[0][o]; c1[o] = L.cf[1][o]; }
-    auto tap_used = [](int o) { return !(HY == 0 && tap_dy(o) != 0) && !(HT == 0 && tap_dt(o) != 0); };
-
-    // per-thread geometry of the staged items and the s items (same every unit)
-    int p_dx[KP], p_dy[KP], p_dt[KP], p_rel[KP];
-#pragma unroll
-    for (int k = 0; k < KP; ++k) {
-        const int e = tid + 256 * k;
-        const int px = e % PX, py = (e / PX) % PY, pt = e / (PX * PY);
-        p_dx[k] = px - 2; p_dy[k] = py - HY; p_dt[k] = pt - HT;
-        p_rel[k] = (p_dt[k] * ny + p_dy[k]) * nx + p_dx[k];
-    }
-    int s_dx[KS], s_dy[KS], s_dt[KS], s_base[KS];
-#pragma unroll
-    for (int k = 0; k < KS; ++k) {
-        const int e = tid + 256 * k;
-        const int sx = e % SX, sy = (e / SX) % SY, stt = e / (SX * SY);
-        s_dx[k] = sx - 1; s_dy[k] = sy - HYS; s_dt[k] = stt;
-        s_base[k] = ((stt + HT) * PY + (sy + HY - HYS)) * PX + (sx + 1);
-    }
-    const int pbase = ((lt + HT) * PY + (ly + HY)) * PX + (lx + 2);
-    const int sbase = (lt * SY + (ly + HYS)) * SX + (lx + 1);
-
-    if (A.partial != nullptr)
-        for (int i = tid; i < nblk * 4; i += 256) A.partial[((size_t)(i >> 2) * G + blockIdx.x) * 4 + (i & 3)] = 0.0;
-
-    const int tiles_x = L.tiles_x, tiles_y = L.tiles_y, tiles_t = L.tiles_t;
-    const long long chunk = ((long long)nunits + G - 1) / G;
-    const long long u0 = (long long)blockIdx.x * chunk;
-    const int count = (int)std::max<long long>(0, std::min<long long>(chunk, (long long)nunits - u0));
-
-    auto issue = [&](const UnitPos& P, int st, bool valid) {
-        if (valid) {
-            const int grp = P.grp;
-            const int tile = (P.tt * tiles_y + P.ty) * tiles_x + P.tx;
-            const int tx0 = P.tx * TX, ty0 = P.ty * TY, tt0 = P.tt * TT;
-            // TMA boxes (zero outside the grid): the input tile with its halo,
-            // the own tiles of b, d and D^-1
-            if (tid == 0) {
-                const int row0 = HY > 0 ? ty0 : tt0, hrow = HY > 0 ? HY : HT;
-                const bool with_d = MODE == M_CHEB && A.d != nullptr;
-                const unsigned bytes = (unsigned)(PN * sizeof(V4<T>)) + (MODE != M_APPLY ? (unsigned)(TN * sizeof(V4<T>)) : 0u) +
-                                       (with_d ? (unsigned)(TN * sizeof(V4<T>)) : 0u);
-                mbar_expect_tx(&bars[st], bytes);
-                pend |= 1u << st;
-                tma_load_3d(&S.p[st][0][0], &maps.p, 4 * (tx0 - 2), row0 - hrow, grp, &bars[st]);
-                if (MODE != M_APPLY) tma_load_3d(&S.b[MODE != M_APPLY ? st : 0][0][0], &maps.b, 4 * tx0, row0, grp, &bars[st]);
-                if (with_d) tma_load_3d(&S.d[MODE == M_CHEB ? st : 0][0][0], &maps.d, 4 * tx0, row0, grp, &bars[st]);
-            }
-            // D^-1 is one value per node: its rows (4 nx bytes) need not be 16-byte
-            // multiples, which a tensor map requires, so it is copied per thread
-            if (MODE == M_CHEB) {
-                const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
-                const bool own = gx < nx && gy < ny && gt < nt;
-                cp_scalar<T>(&S.dinv[MODE == M_CHEB ? st : 0][tid], A.dinv + (own ? (gt * ny + gy) * nx + gx : 0), own);
-            }
-            const int tbase = (tt0 * ny + ty0) * nx + tx0;
-            if (COL == 2 || MODE == M_CHEB0) {      // per-node scalars of the tile and halo
-#pragma unroll
-                for (int k = 0; k < KP; ++k) {
-                    const int e = tid + 256 * k;
-                    if (KP * 256 > PN && e >= PN) break;
-                    const int gx = tx0 + p_dx[k], gy = ty0 + p_dy[k], gt = tt0 + p_dt[k];
-                    const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gt >= 0 && gt < nt;
-                    const int node = in ? tbase + p_rel[k] : 0;
-                    if (COL == 2) cp_scalar<T>(&S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0], L.mu + node, in);
-                    if (MODE == M_CHEB0) cp_scalar<T>(&S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? e : 0], A.dinv + node, in);
-                }
-            }
-            if (obs_staged) {
-                unsigned char* dst = obs_smem + (size_t)st * ostage;
-                const unsigned char* gmap = reinterpret_cast<const unsigned char*>(L.omap + (size_t)tile * TN);
-                const unsigned char* gent = reinterpret_cast<const unsigned char*>(L.oent) + (size_t)tile * L.ostride;
-                for (int c = tid; c < TN * 2 / 16; c += 256) cp_async16(dst + c * 16, gmap + c * 16, true);
-                for (int c = tid; c < L.ostride / 16; c += 256) cp_async16(dst + TN * 2 + c * 16, gent + c * 16, true);
-            }
-        }
-        cp_commit();
-    };
-
-    UnitPos cur = unit_decompose(u0 < nunits ? u0 : 0, tiles_x, tiles_y, tiles_t);
-    UnitPos ahead = cur;
-#pragma unroll 1
-    for (int k = 0; k < NS - 1; ++k) {
-        issue(ahead, k, k < count);
-        unit_next(ahead, tiles_x, tiles_y, tiles_t);
-    }
-
-    T dacc[KB][4];
-#pragma unroll
-    for (int j = 0; j < KB; ++j) dacc[j][0] = dacc[j][1] = dacc[j][2] = dacc[j][3] = T(0);
-    int st = 0;
-#pragma unroll 1
-    // Two barriers per unit: the first (after this unit's copies landed) also
-    // orders every read of the previous unit (its stage buffer, the s tile,
-    // qobs) before the refill of that buffer and the next writes.
-    for (int done = 0; done < count; ++done) {
-        fence_proxy_async();           // generic accesses of the last unit before the TMA refill below
-        cp_wait<NS - 2>();
-        if (mbar_wait_bounded(&bars[st], (phbits >> st) & 1u, kMbarSpinCap)) {   // this unit's input tile
-            phbits ^= 1u << st;
-            pend &= ~(1u << st);
-        } else {
-            abort_unit = 1;
-        }
-        __syncthreads();
-        if (abort_unit) break;
-        issue(ahead, st == 0 ? NS - 1 : st - 1, done + NS - 1 < count);
-        unit_next(ahead, tiles_x, tiles_y, tiles_t);
-        if (MODE == M_CHEB0) {      // staged b -> x1 = c0 D^-1 b in place
-#pragma unroll
-            for (int k = 0; k < KP; ++k) {
-                const int e = tid + 256 * k;
-                if (KP * 256 > PN && e >= PN) break;
-                const T f = A.c0 * S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? e : 0];
-#pragma unroll
-                for (int j = 0; j < KB; ++j) S.p[st][e][j] = f * S.p[st][e][j];
-            }
-            __syncthreads();
-        }
-        const int grp = cur.grp;
-        const int tx0 = cur.tx * TX, ty0 = cur.ty * TY, tt0 = cur.tt * TT;
-        const V4<T>(*sp)[KB] = S.p[st];
-        auto smu = [&](int e) -> T { return COL == 2 ? S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0] : T(0); };
-
-        // s = B p on the rows of the tile plus a one-node ring.  Dirichlet rows
-        // are zero; rows next to the boundary skip the Dirichlet columns
-        // (App. B column elimination), all other rows take every tap.
-#pragma unroll
-        for (int k = 0; k < KS; ++k) {
-            const int e = tid + 256 * k;
-            if (KS * 256 > SN && e >= SN) break;
-            const int rx = tx0 + s_dx[k], ry = ty0 + s_dy[k], rt = tt0 + s_dt[k];
-            const bool inrow = rx >= 0 && rx < nx && ry >= 0 && ry < ny && rt < nt;
-            const int base = s_base[k];
-            V4<T> sv[KB];
-#pragma unroll
-            for (int j = 0; j < KB; ++j) sv[j] = v4zero<T>();
-            if (inrow && !is_dirichlet(rx, ry, nx, ny)) {
-                const bool first = HT > 0 && nt > 1 && rt == 0;
-                // a tap of a non-Dirichlet row reaches a Dirichlet column only
-                // from the second or second-last node of an axis
-                const bool xl = rx == 1, xr = rx == nx - 2;
-                const bool yl = HY > 0 && ry == 1, yr = HY > 0 && ry == ny - 2;
-#pragma unroll
-                for (int o = 0; o < NTAP; ++o) {
-                    if (!tap_used(o)) continue;
-                    const T c = first ? c1[o] : c0[o];
-                    if (c == T(0)) continue;
-                    const bool hit = (tap_dx(o) < 0 && xl) || (tap_dx(o) > 0 && xr) || (tap_dy(o) < 0 && yl) ||
-                                     (tap_dy(o) > 0 && yr);
-                    if (hit) continue;
-#pragma unroll
-                    for (int j = 0; j < KB; ++j) sv[j] = fma4(c, sp[base + poff<PX, PY>(o)][j], sv[j]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < KB; ++j) S.s[e][j] = sv[j];
-            if (COL) {
-#pragma unroll
-                for (int j = 0; j < KB; ++j) {
-                    V4<T> sjv = v4zero<T>();
-                    if (inrow && rx >= 1 && rx <= nx - 2 && rt >= 1) {
-                        T cC, cL, cR;
-                        jcoef<T, COL>(L.col, smu(base), smu(base - 1), smu(base + 1), cC, cL, cR);
-                        sjv = cC * sp[base][j];
-                        sjv = fma4(cL, sp[base - 1][j], sjv);
-                        sjv = fma4(cR, sp[base + 1][j], sjv);
-                        sjv = fma4((T)(-L.col.inv_dt), sp[base - PY * PX][j], sjv);
-                    }
-                    S.sj[COL ? e : 0][j] = sjv;
-                }
-            }
-        }
-        // A^T R^-1 A p at the observed nodes of the tile: entry e (one node's
-        // 3^k-point stencil) is evaluated by thread 255 - e, so only the last
-        // ceil(entries / 32) warps run the loop
-        // this tile's tables: the staged copy, or global memory when a level's
-        // tables are too large to stage (small, heavily observed coarse levels)
-        const int16_t* omap_t = nullptr;
-        const unsigned char* oent_t = nullptr;
-        if (has_obs) {
-            if (obs_staged) {
-                omap_t = reinterpret_cast<const int16_t*>(obs_smem + (size_t)st * ostage);
-                oent_t = obs_smem + (size_t)st * ostage + TN * 2;
-            } else {
-                const int tile = (cur.tt * tiles_y + cur.ty) * tiles_x + cur.tx;
-                omap_t = L.omap + (size_t)tile * TN;
-                oent_t = reinterpret_cast<const unsigned char*>(L.oent) + (size_t)tile * L.ostride;
-            }
-        }
-        const int oe = 255 - tid;      // entries go to the last warps (the first ones hold extra s rows)
-        if (has_obs && oe < L.ocap) {
-            const int nd = reinterpret_cast<const int16_t*>(oent_t + (size_t)L.ocap * OC * sizeof(T))[oe];
-            if (nd >= 0) {
-                const int ex = nd % TX, ey = (nd / TX) % TY, et = nd / (TX * TY);
-                const int pb = ((et + HT) * PY + (ey + HY)) * PX + (ex + 2);
-                const T* c = reinterpret_cast<const T*>(oent_t) + oe * OC;
-                V4<T> v[KB];
-#pragma unroll
-                for (int j = 0; j < KB; ++j) v[j] = v4zero<T>();
-#pragma unroll
-                for (int a = 0; a < OC; ++a) {
-                    const int po = pb + (obs_dt(GEO, a) * PY + obs_dy(GEO, a)) * PX + obs_dx(GEO, a);
-#pragma unroll
-                    for (int j = 0; j < KB; ++j) v[j] = fma4(c[a], sp[po][j], v[j]);
-                }
-#pragma unroll
-                for (int j = 0; j < KB; ++j) S.qobs[nd][j] = v[j];
-            }
-        }
-        __syncthreads();
-
-        // q = B^T s (+ J^T Q_eps sj + A^T R^-1 A p) at the thread's own node
-        const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
-        const bool own = gx < nx && gy < ny && gt < nt;
-        const int node = own ? (gt * ny + gy) * nx + gx : 0;
-        V4<T> q[KB], pown[KB];
-#pragma unroll
-        for (int j = 0; j < KB; ++j) { q[j] = v4zero<T>(); pown[j] = sp[pbase][j]; }
-        if (own) {
-            if (is_dirichlet(gx, gy, nx, ny)) {
-#pragma unroll
-                for (int j = 0; j < KB; ++j) q[j] = L.inv_eps2 * pown[j];
-            } else {
-#pragma unroll
-                for (int o = 0; o < NTAP; ++o) {
-                    if (!tap_used(o)) continue;
-                    const bool first = HT > 0 && nt > 1 && gt - tap_dt(o) == 0;
-                    const T c = first ? c1[o] : c0[o];
-                    if (c == T(0)) continue;
-#pragma unroll
-                    for (int j = 0; j < KB; ++j) q[j] = fma4(c, S.s[sbase + soff<SX, SY>(o)][j], q[j]);
-                }
-            }
-            if (COL) {
-                // rows touching this column: itself (centre), x-1 row (its x+1 tap),
-                // x+1 row (its x-1 tap), t+1 row (its t-1 tap)
-                const int sb = lt * SX + (lx + 1);
-                T cC, cL, cR, tC, tL, tR, uC, uL, uR;
-                const T m0 = smu(pbase), mm1 = smu(pbase - 1), mp1 = smu(pbase + 1);
-                const T mm2 = smu(pbase - 2), mp2 = smu(pbase + 2);
-                jcoef<T, COL>(L.col, m0, mm1, mp1, cC, cL, cR);
-                jcoef<T, COL>(L.col, mm1, mm2, m0, tC, tL, tR);
-                jcoef<T, COL>(L.col, mp1, m0, mp2, uC, uL, uR);
-#pragma unroll
-                for (int j = 0; j < KB; ++j) {
-                    V4<T> acc = cC * S.sj[COL ? sb : 0][j];
-                    acc = fma4(tR, S.sj[COL ? sb - 1 : 0][j], acc);
-                    acc = fma4(uL, S.sj[COL ? sb + 1 : 0][j], acc);
-                    acc = fma4((T)(-L.col.inv_dt), S.sj[COL ? sb + SX : 0][j], acc);
-                    q[j] = fma4((T)L.col.qeps, acc, q[j]);
-                }
-            }
-            if (has_obs) {
-                if (omap_t[tid] >= 0) {
-#pragma unroll
-                    for (int j = 0; j < KB; ++j) q[j] = q[j] + S.qobs[tid][j];
-                }
-            }
-        }
-
-        // epilogue
-#pragma unroll
-        for (int j = 0; j < KB; ++j) {
-            const int blk = grp * KB + j;
-            if (!own || blk >= nblk) continue;
-            const size_t off = ((size_t)blk * N + node) * RW;
-            if (MODE == M_APPLY) {
-                v4store(A.out + off, q[j]);
-                dacc[j][0] += pown[j].a * q[j].a; dacc[j][1] += pown[j].b * q[j].b;
-                dacc[j][2] += pown[j].c * q[j].c; dacc[j][3] += pown[j].d * q[j].d;
-            } else if (MODE == M_RESID) {
-                const V4<T> r = S.b[MODE != M_APPLY ? st : 0][tid][j] - q[j];
-                v4store(A.out + off, r);
-                const T w = A.rweight != nullptr ? A.rweight[node] : T(1);
-                dacc[j][0] += w * r.a * r.a; dacc[j][1] += w * r.b * r.b;
-                dacc[j][2] += w * r.c * r.c; dacc[j][3] += w * r.d * r.d;
-            } else {
-                const V4<T> bb = S.b[MODE != M_APPLY ? st : 0][tid][j];
-                const V4<T> r = bb - q[j];
-                const T di = MODE == M_CHEB0 ? S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? pbase : 0]
-                                             : S.dinv[MODE == M_CHEB ? st : 0][tid];
-                V4<T> dn = (A.c2 * di) * r;
-                if (MODE == M_CHEB0) dn = fma4(A.c1, pown[j], dn);          // d = x1
-                else if (A.d != nullptr) dn = fma4(A.c1, S.d[MODE == M_CHEB ? st : 0][tid][j], dn);
-                const V4<T> xn = pown[j] + dn;
-                v4store(A.out + off, xn);
-                v4store(A.out2 + off, dn);
-                dacc[j][0] += bb.a * xn.a; dacc[j][1] += bb.b * xn.b; dacc[j][2] += bb.c * xn.c; dacc[j][3] += bb.d * xn.d;
-            }
-        }
-        // dot partials: one entry per (block, CTA), flushed when the group changes
-        UnitPos nxt = cur;
-        unit_next(nxt, tiles_x, tiles_y, tiles_t);
-        if (A.partial != nullptr) {
-            if (nxt.grp != grp || done + 1 == count) {
-#pragma unroll
-                for (int j = 0; j < KB; ++j) {
-                    const int blk = grp * KB + j;
-                    if (blk < nblk) block_sum4<256, T>(dacc[j], A.partial + ((size_t)blk * G + blockIdx.x) * 4);
-                    dacc[j][0] = dacc[j][1] = dacc[j][2] = dacc[j][3] = T(0);
-                }
-            }
-        }
-        cur = nxt;
-        st = st + 1 == NS ? 0 : st + 1;
-    }
-    cp_wait<0>();
-    if (tid == 0 && abort_unit) {
-        mbar_drain(bars, NS, pend, phbits, kMbarSpinCap);
-        atomicExch(&g_stencil_abort, 1);
-    }
-}
-
-// Tensor map of a blocked vector [nblk][N][4] seen as a 3D array (4 nx
-// values, rows, blocks) whose rows are y (2D) or t (1D space x time); the box
-// is one tile's input with its halo.
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-static EncodeTiled encode_tiled() {
-    static EncodeTiled fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        cuda_ok(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
-        if (q != cudaDriverEntryPointSuccess || f == nullptr) throw std::runtime_error("cuTensorMapEncodeTiled not available");
-        fn = reinterpret_cast<EncodeTiled>(f);
-    });
-    return fn;
-}
-
-void encode_tensor_map(CUtensorMap* m, bool f64, int rank, const void* base, const cuuint64_t* dims,
-                       const cuuint64_t* strides, const cuuint32_t* box) {
-    std::memset(m, 0, sizeof(*m));
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    const CUresult r = encode_tiled()(m, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                                      (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, estr,
-                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) throw std::runtime_error("tensor map of a stencil operand: error " + std::to_string((int)r));
-}
-
-template <int GEO, typename T>
-static CUtensorMap tile_map(const T* v, const LevelView<T>& L, int nblk, bool halo) {
-    using G = Geo<GEO>;
-    static_assert(G::HY == 0 || G::TT == 1, "2D tiles have one time level");
-    constexpr int PX = G::TX + 4, PR = G::HY > 0 ? G::TY + 2 * G::HY : G::TT + 2 * G::HT;
-    constexpr int TR = G::HY > 0 ? G::TY : G::TT;
-    const cuuint64_t rows = G::HY > 0 ? (cuuint64_t)L.ny : (cuuint64_t)L.nt;
-    const cuuint64_t dims[3] = {(cuuint64_t)4 * L.nx, rows, (cuuint64_t)nblk};
-    const cuuint64_t strides[2] = {(cuuint64_t)4 * L.nx * sizeof(T), (cuuint64_t)L.N * 4 * sizeof(T)};
-    const cuuint32_t box[3] = {(cuuint32_t)(4 * (halo ? PX : G::TX)), (cuuint32_t)(halo ? PR : TR), 1};
-    CUtensorMap m;
-    encode_tensor_map(&m, sizeof(T) == 8, 3, v, dims, strides, box);
-    return m;
-}
-
-int stencil_abort_take(cudaStream_t s) {
-    int v = 0;
-    cuda_ok(cudaMemcpyFromSymbolAsync(&v, g_stencil_abort, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
-    cuda_ok(cudaStreamSynchronize(s));
-    if (v) {
-        static const int zero = 0;
-        cuda_ok(cudaMemcpyToSymbolAsync(g_stencil_abort, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
-        cuda_ok(cudaStreamSynchronize(s));
-    }
-    return v | march_abort_take(s);
-}
-
-// Largest persistent grid any stencil launch uses (sizes the partial buffers).
-constexpr int kMaxStencilGrid = 4096;
-
-#ifndef GMRF_STENCIL_STAGES
-#define GMRF_STENCIL_STAGES 2
-#endif
-#ifndef GMRF_STENCIL_KB
-#define GMRF_STENCIL_KB 1
-#endif
-
-template <int GEO, typename T, int MODE, int COL>
-static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
-    constexpr int NS = sizeof(T) == 8 ? 2 : GMRF_STENCIL_STAGES;
-    constexpr int KB = sizeof(T) == 8 ? 1 : GMRF_STENCIL_KB;
-    using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
-    auto kern = k_stencil<GEO, T, MODE, COL, NS, KB>;
-    static int attr_smem = 0;
-    static int sms = 0, optin = 0;
-    static std::map<size_t, int> per_sm;       // resident CTAs per SM by dynamic shared memory
-    static std::mutex mu;                      // solves of independent posteriors may run on several host threads
-    StencilArgs<T> args = a;
-    size_t smem = sizeof(SM) + 128;            // + alignment slack of the TMA destinations
-    int resident = 0;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (sms == 0) {
-            int dev = 0;
-            cuda_ok(cudaGetDevice(&dev));
-            cuda_ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            cuda_ok(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        }
-        // stage the observation tables with the inputs when they fit beside
-        // them (with the 1 KB the block reduction's static array may take)
-        const size_t staged = sizeof(SM) + 128 + (size_t)NS * (SM::TN * 2 + a.L.ostride);
-        args.L.obs_direct = 0;
-        if (a.L.ocap > 0) {
-            if (staged + 1024 <= (size_t)optin) smem = staged;
-            else args.L.obs_direct = 1;
-        }
-        if (smem + 1024 > (size_t)optin) throw std::runtime_error("stencil kernel does not fit in shared memory");
-        if ((int)smem > attr_smem) {
-            cuda_ok(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_smem = (int)smem;
-        }
-        auto itp = per_sm.find(smem);
-        if (itp == per_sm.end()) {
-            int per = 0;
-            cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem));
-            if (per <= 0) throw std::runtime_error("stencil kernel does not fit on an SM (shared memory)");
-            itp = per_sm.emplace(smem, per).first;
-        }
-        resident = sms * itp->second;
-    }
-    const long long ntiles = (long long)a.L.tiles_x * a.L.tiles_y * a.L.tiles_t;
-    const long long nunits = ntiles * ((a.nblk + KB - 1) / KB);
-    const int grid = (int)std::min<long long>(std::min<long long>(nunits, (long long)resident), kMaxStencilGrid);
-    StencilMaps maps;
-    std::memset(&maps, 0, sizeof(maps));
-    maps.p = tile_map<GEO, T>(MODE == M_CHEB0 ? a.b : a.x, a.L, a.nblk, true);
-    if (MODE != M_APPLY) maps.b = tile_map<GEO, T>(a.b, a.L, a.nblk, false);
-    if (MODE == M_CHEB && a.d != nullptr) maps.d = tile_map<GEO, T>(a.d, a.L, a.nblk, false);
-    { kern<<<(unsigned)grid, 256, smem, s>>>(args, (int)nunits, maps); note_launch(); }
-    return grid;
-}
-
-template <int GEO, typename T, int MODE>
-static int launch_geo_mode(const StencilArgs<T>& a, cudaStream_t s) {
-    if (GEO == GEO_XT && a.L.col.kind == 1) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 1 : 0)>(a, s);
-    if (GEO == GEO_XT && a.L.col.kind == 2) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0)>(a, s);
-    return launch_one<GEO, T, MODE, 0>(a, s);
-}
-
-template <typename T, int GEO>
-static int launch_geo(int mode, const StencilArgs<T>& a, cudaStream_t s) {
-    if (mode == M_APPLY) return launch_geo_mode<GEO, T, M_APPLY>(a, s);
-    if (mode == M_RESID) return launch_geo_mode<GEO, T, M_RESID>(a, s);
-    if (mode == M_CHEB0) return launch_geo_mode<GEO, T, M_CHEB0>(a, s);
-    return launch_geo_mode<GEO, T, M_CHEB>(a, s);
-}
-
-template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s) {
-    if (geo == GEO_XY) return launch_geo<T, GEO_XY>(mode, a, s);
-    if (geo == GEO_XT) return launch_geo<T, GEO_XT>(mode, a, s);
-    return launch_march<T>(mode, a, s);
-}
-template int launch_stencil<float>(int, int, const StencilArgs<float>&, cudaStream_t);
-template int launch_stencil<double>(int, int, const StencilArgs<double>&, cudaStream_t);
-int stencil_max_grid() { return kMaxStencilGrid; }
 
 // ---------------------------------------------------------------------------
 // reductions and PCG scalars

@@ -1,4 +1,5 @@
-// Host-callable launchers of the GMRF kernels (implemented in kernels.cu).
+// Host-callable launchers of the GMRF kernels (stencil.cu, stencil_march.cu,
+// resid_df.cu and kernels.cu).
 #pragma once
 
 #include <cuda.h>
