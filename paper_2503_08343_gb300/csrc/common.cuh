@@ -153,8 +153,10 @@ __device__ __forceinline__ void philox_normal_pair(uint64_t seed, uint32_t strea
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
     const double u1 = u53(w.x, w.y), u2 = u53(w.z, w.w);
     const double r = sqrt(-2.0 * log(u1));
-    z0 = r * cospi(2.0 * u2);
-    z1 = r * sinpi(2.0 * u2);
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);           // one shared reduction of the angle
+    z0 = r * cs;
+    z1 = r * sn;
 }
 
 __device__ __forceinline__ double philox_rademacher(uint64_t seed, uint32_t sample, uint64_t idx) {

@@ -210,11 +210,11 @@ __global__ void __launch_bounds__(256) k_restrict_axis(const T* __restrict__ in,
     const int ox = axis == 0 ? nc : nx, oy = axis == 1 ? nc : ny, ot = axis == 2 ? nc : nt;
     const long long Nout = (long long)ox * oy * ot, Nin = (long long)nx * ny * nt;
     const int blk = blockIdx.y;
-    const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
-    if (n >= Nout) return;
-    const int x = (int)(n % ox);
-    const long long r = n / ox;
-    const int y = (int)(r % oy), t = (int)(r / oy);
+    const unsigned n = blockIdx.x * 256u + threadIdx.x;      // levels hold fewer than 2^31 nodes
+    if (n >= (unsigned long long)Nout) return;
+    const int x = (int)(n % (unsigned)ox);
+    const unsigned r = n / (unsigned)ox;
+    const int y = (int)(r % (unsigned)oy), t = (int)(r / (unsigned)oy);
     const int J = axis == 0 ? x : (axis == 1 ? y : t);
     const long long stride = axis == 0 ? 1 : (axis == 1 ? (long long)nx : (long long)nx * ny);
     const long long base = ((long long)(axis == 2 ? 0 : t) * ny + (axis == 1 ? 0 : y)) * nx + (axis == 0 ? 0 : x);
@@ -233,6 +233,7 @@ template <typename T>
 void launch_restrict_axis(const T* in, T* out, int nx, int ny, int nt, int axis, int ncoarse, const int32_t* rs,
                           const int32_t* rc, const int32_t* pj, const T* pw, int nblk, cudaStream_t s) {
     const long long Nout = (long long)(axis == 0 ? ncoarse : nx) * (axis == 1 ? ncoarse : ny) * (axis == 2 ? ncoarse : nt);
+    if ((long long)nx * ny * nt >= (1LL << 31)) throw std::runtime_error("restriction: a level holds 2^31 or more nodes");
     { k_restrict_axis<T><<<dim3((unsigned)((Nout + 255) / 256), nblk), 256, 0, s>>>(in, out, nx, ny, nt, axis, ncoarse, rs, rc, pj, pw); note_launch(); }
 }
 template void launch_restrict_axis<float>(const float*, float*, int, int, int, int, int, const int32_t*, const int32_t*, const int32_t*, const float*, int, cudaStream_t);
@@ -277,9 +278,12 @@ __global__ void __launch_bounds__(256) k_restrict_xy(const T* __restrict__ in, T
     const long long Nin = (long long)nx * ny * nt;
     const T* src = in + ((size_t)blk * Nin + (size_t)t * nx * ny) * RW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // asynchronous copies: every load of the region is in flight at once
     for (int y = fy0 + warp; y < fy1; y += 8)
         for (int x = fx0 + lane; x < fx1; x += 32)
-            tile[(y - fy0) * W + (x - fx0)] = v4load(src + ((size_t)y * nx + x) * RW);
+            cp_v4<T>(&tile[(y - fy0) * W + (x - fx0)], src + ((size_t)y * nx + x) * RW, true);
+    cp_commit();
+    cp_wait<0>();
     __syncthreads();
     const int Jx = Jx0 + (threadIdx.x % kRestrictTX), Jy = Jy0 + (threadIdx.x / kRestrictTX);
     if (Jx >= Jx1 || Jy >= Jy1) return;
@@ -325,11 +329,11 @@ __global__ void __launch_bounds__(256) k_prolong_add(T* __restrict__ xf, const T
                                                      int cx, int cy, int ct, AxisMap ax, AxisMap ay, AxisMap at, bool p1) {
     const long long Nf = (long long)nx * ny * nt, Nc = (long long)cx * cy * ct;
     const int blk = blockIdx.y;
-    const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
-    if (n >= Nf) return;
-    const int x = (int)(n % nx);
-    const long long r = n / nx;
-    const int y = (int)(r % ny), t = (int)(r / ny);
+    const unsigned n = blockIdx.x * 256u + threadIdx.x;      // levels hold fewer than 2^31 nodes
+    if (n >= (unsigned long long)Nf) return;
+    const int x = (int)(n % (unsigned)nx);
+    const unsigned r = n / (unsigned)nx;
+    const int y = (int)(r % (unsigned)ny), t = (int)(r / (unsigned)ny);
     int jx = x, jy = y, jt = t;
     T wx = T(0), wy = T(0), wt = T(0);
     if (ax.on) { jx = ax.j[x]; wx = ((const T*)ax.w)[x]; }
@@ -361,38 +365,59 @@ void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, bool
     AxisMap ax{f.d_pj[0], dbl ? (const void*)f.d_pwd[0] : (const void*)f.d_pw[0], f.coarsen[0]};
     AxisMap ay{f.d_pj[1], dbl ? (const void*)f.d_pwd[1] : (const void*)f.d_pw[1], f.coarsen[1]};
     AxisMap at{f.d_pj[2], dbl ? (const void*)f.d_pwd[2] : (const void*)f.d_pw[2], f.coarsen[2]};
+    if (f.N >= (1LL << 31)) throw std::runtime_error("prolongation: a level holds 2^31 or more nodes");
     { k_prolong_add<T><<<dim3((unsigned)((f.N + 255) / 256), nblk), 256, 0, s>>>(xf, xc, f.nx, f.ny, f.nt, c.nx, c.ny, c.nt, ax, ay, at, p1); note_launch(); }
 }
 template void launch_prolong_add<float>(float*, const float*, const Level&, const Level&, bool, int, cudaStream_t);
 template void launch_prolong_add<double>(double*, const double*, const Level&, const Level&, bool, int, cudaStream_t);
 
 // coarsest level: x = Q_c^-1 b with the stored dense inverse.  The inverse is
-// stored exactly symmetric, so thread i walks column i (A[j][i] = A[i][j]) and
-// a warp's loads of one j are contiguous.
+// stored exactly symmetric, so lane i walks column i (A[j][i] = A[i][j]) and
+// a warp's loads of one j are contiguous.  A CTA owns 32 rows of one block;
+// its eight warps split the columns and add their partial sums in a fixed
+// order through shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_solve(const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x, int n) {
     extern __shared__ unsigned char dsm[];
-    V4<T>* sb = reinterpret_cast<V4<T>*>(dsm);
-    const int blk = blockIdx.x;
-    for (int i = threadIdx.x; i < n; i += 256) sb[i] = v4load(b + ((size_t)blk * n + i) * RW);
+    V4<T>* sb = reinterpret_cast<V4<T>*>(dsm);          // b of the block [n]
+    V4<T>* part = sb + n;                                // warp partial sums [8][32]
+    const int blk = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    for (int k = threadIdx.x; k < n; k += 256) sb[k] = v4load(b + ((size_t)blk * n + k) * RW);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += 256) {
-        V4<T> acc = v4zero<T>();
-        int j = 0;
-        for (; j + 8 <= n; j += 8) {         // eight independent loads in flight
+    const int per = (n + 7) / 8;
+    const int j0 = min(n, warp * per), j1 = min(n, j0 + per);
+    V4<T> acc = v4zero<T>();
+    if (i < n) {
+        int j = j0;
+        for (; j + 8 <= j1; j += 8) {        // eight independent loads in flight
             T a[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) a[u] = Ainv[(size_t)(j + u) * n + i];
 #pragma unroll
             for (int u = 0; u < 8; ++u) acc = fma4(a[u], sb[j + u], acc);
         }
-        for (; j < n; ++j) acc = fma4(Ainv[(size_t)j * n + i], sb[j], acc);
-        v4store(x + ((size_t)blk * n + i) * RW, acc);
+        for (; j < j1; ++j) acc = fma4(Ainv[(size_t)j * n + i], sb[j], acc);
+    }
+    part[warp * 32 + lane] = acc;
+    __syncthreads();
+    if (warp == 0 && i < n) {
+        V4<T> sum = part[lane];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) sum = sum + part[w * 32 + lane];
+        v4store(x + ((size_t)blk * n + i) * RW, sum);
     }
 }
 
 template <typename T> void launch_dense_solve(const T* Ainv, const T* b, T* x, int n, int nblk, cudaStream_t s) {
-    { k_dense_solve<T><<<nblk, 256, (size_t)n * sizeof(V4<T>), s>>>(Ainv, b, x, n); note_launch(); }
+    const size_t smem = ((size_t)n + 256) * sizeof(V4<T>);
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cuda_ok(cudaFuncSetAttribute(k_dense_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    });
+    if (smem > 200 * 1024) throw std::runtime_error("coarsest level too large for the dense solve");
+    { k_dense_solve<T><<<dim3((unsigned)((n + 31) / 32), (unsigned)nblk), 256, smem, s>>>(Ainv, b, x, n); note_launch(); }
 }
 template void launch_dense_solve<float>(const float*, const float*, float*, int, int, cudaStream_t);
 template void launch_dense_solve<double>(const double*, const double*, double*, int, int, cudaStream_t);
