@@ -120,60 +120,59 @@ void launch_pcg_scalar(int kind, const double* red, double* sc, int nblk, double
 
 int elem_parts(long long N) { return (int)((N + ECHUNK - 1) / ECHUNK); }
 
+// r -= alpha q (the stopping test uses r^T z, so no |r|^2 here)
 template <typename T>
-__global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                                                   const T* __restrict__ q, const double* __restrict__ sc, long long N,
-                                                   double* __restrict__ partial, int nparts) {
+__global__ void __launch_bounds__(256) k_update_r(T* __restrict__ r, const T* __restrict__ q, const double* __restrict__ sc,
+                                                  long long N) {
     const int blk = blockIdx.y;
     const double* alpha = sc + 2 * (gridDim.y * RW) + blk * RW;
     const T a0 = (T)alpha[0], a1 = (T)alpha[1], a2 = (T)alpha[2], a3 = (T)alpha[3];
-    T dot[4] = {T(0), T(0), T(0), T(0)};
     for (int k = 0; k < EPT; ++k) {
         const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
         if (n >= N) break;
         const size_t off = ((size_t)blk * N + n) * RW;
-        const V4<T> pv = v4load(p + off), qv = v4load(q + off);
-        V4<T> xv = v4load(x + off), rv = v4load(r + off);
-        xv.a = fma(a0, pv.a, xv.a); xv.b = fma(a1, pv.b, xv.b); xv.c = fma(a2, pv.c, xv.c); xv.d = fma(a3, pv.d, xv.d);
+        const V4<T> qv = v4load(q + off);
+        V4<T> rv = v4load(r + off);
         rv.a = fma(-a0, qv.a, rv.a); rv.b = fma(-a1, qv.b, rv.b); rv.c = fma(-a2, qv.c, rv.c); rv.d = fma(-a3, qv.d, rv.d);
-        v4store(x + off, xv);
         v4store(r + off, rv);
-        dot[0] += rv.a * rv.a; dot[1] += rv.b * rv.b;
-        dot[2] += rv.c * rv.c; dot[3] += rv.d * rv.d;
     }
-    if (partial != nullptr) block_sum4<256, T>(dot, partial + ((size_t)blk * nparts + blockIdx.x) * 4);
 }
 
 template <typename T>
-void launch_pcg_update_xr(T* x, T* r, const T* p, const T* q, const double* sc, long long N, int nblk,
-                          double* partial, int nparts, cudaStream_t s) {
-    { k_update_xr<T><<<dim3(nparts, nblk), 256, 0, s>>>(x, r, p, q, sc, N, partial, nparts); note_launch(); }
+void launch_pcg_update_r(T* r, const T* q, const double* sc, long long N, int nblk, cudaStream_t s) {
+    { k_update_r<T><<<dim3(elem_parts(N), nblk), 256, 0, s>>>(r, q, sc, N); note_launch(); }
 }
-template void launch_pcg_update_xr<float>(float*, float*, const float*, const float*, const double*, long long, int, double*, int, cudaStream_t);
-template void launch_pcg_update_xr<double>(double*, double*, const double*, const double*, const double*, long long, int, double*, int, cudaStream_t);
+template void launch_pcg_update_r<float>(float*, const float*, const double*, long long, int, cudaStream_t);
+template void launch_pcg_update_r<double>(double*, const double*, const double*, long long, int, cudaStream_t);
 
+// x += alpha p with the iteration's p, then p = z + beta p: one pass over p
 template <typename T>
-__global__ void __launch_bounds__(256) k_update_p(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ sc, long long N) {
+__global__ void __launch_bounds__(256) k_update_xp(T* __restrict__ x, T* __restrict__ p, const T* __restrict__ z,
+                                                   const double* __restrict__ sc, long long N) {
     const int blk = blockIdx.y;
+    const double* alpha = sc + 2 * (gridDim.y * RW) + blk * RW;
     const double* beta = sc + 3 * (gridDim.y * RW) + blk * RW;
+    const T a0 = (T)alpha[0], a1 = (T)alpha[1], a2 = (T)alpha[2], a3 = (T)alpha[3];
     const T b0 = (T)beta[0], b1 = (T)beta[1], b2 = (T)beta[2], b3 = (T)beta[3];
     for (int k = 0; k < EPT; ++k) {
         const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
         if (n >= N) break;
         const size_t off = ((size_t)blk * N + n) * RW;
         const V4<T> zv = v4load(z + off);
-        V4<T> pv = v4load(p + off);
+        V4<T> pv = v4load(p + off), xv = v4load(x + off);
+        xv.a = fma(a0, pv.a, xv.a); xv.b = fma(a1, pv.b, xv.b); xv.c = fma(a2, pv.c, xv.c); xv.d = fma(a3, pv.d, xv.d);
         pv.a = fma(b0, pv.a, zv.a); pv.b = fma(b1, pv.b, zv.b); pv.c = fma(b2, pv.c, zv.c); pv.d = fma(b3, pv.d, zv.d);
+        v4store(x + off, xv);
         v4store(p + off, pv);
     }
 }
 
 template <typename T>
-void launch_pcg_update_p(T* p, const T* z, const double* sc, long long N, int nblk, cudaStream_t s) {
-    { k_update_p<T><<<dim3(elem_parts(N), nblk), 256, 0, s>>>(p, z, sc, N); note_launch(); }
+void launch_pcg_update_xp(T* x, T* p, const T* z, const double* sc, long long N, int nblk, cudaStream_t s) {
+    { k_update_xp<T><<<dim3(elem_parts(N), nblk), 256, 0, s>>>(x, p, z, sc, N); note_launch(); }
 }
-template void launch_pcg_update_p<float>(float*, const float*, const double*, long long, int, cudaStream_t);
-template void launch_pcg_update_p<double>(double*, const double*, const double*, long long, int, cudaStream_t);
+template void launch_pcg_update_xp<float>(float*, float*, const float*, const double*, long long, int, cudaStream_t);
+template void launch_pcg_update_xp<double>(double*, double*, const double*, const double*, long long, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // multigrid pieces
@@ -464,23 +463,28 @@ void launch_scale64(const double* r64, const double* norms, double* out, long lo
 template <typename T>
 __global__ void __launch_bounds__(256) k_axpy_norm(double* __restrict__ x64, const double* __restrict__ norms,
                                                    const T* __restrict__ d, long long N, double* __restrict__ partial) {
+    // x += norm * d in FP64 (one rounding).  For the forward-error stopping
+    // test: |d|^2 of the inner solution d (the increment is norm * d; the
+    // host applies the norm), accumulated in T within the CTA, and |x|^2 in
+    // FP64 (x may lie anywhere in the FP64 range).
     const int blk = blockIdx.y;
     const double* nm = norms + blk * RW;
-    double dd[4] = {0, 0, 0, 0}, xx[4] = {0, 0, 0, 0};
+    T dd[4] = {0, 0, 0, 0};
+    double xx[4] = {0, 0, 0, 0};
     for (int k = 0; k < EPT; ++k) {
         const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
         if (n >= N) break;
         const size_t off = ((size_t)blk * N + n) * RW;
         const V4<T> dv = v4load(d + off);
         V4<double> xv = v4load(x64 + off);
-        const double d0 = nm[0] * (double)dv.a, d1 = nm[1] * (double)dv.b, d2 = nm[2] * (double)dv.c, d3 = nm[3] * (double)dv.d;
-        xv.a += d0; xv.b += d1; xv.c += d2; xv.d += d3;
+        xv.a = fma(nm[0], (double)dv.a, xv.a); xv.b = fma(nm[1], (double)dv.b, xv.b);
+        xv.c = fma(nm[2], (double)dv.c, xv.c); xv.d = fma(nm[3], (double)dv.d, xv.d);
         v4store(x64 + off, xv);
-        dd[0] += d0 * d0; dd[1] += d1 * d1; dd[2] += d2 * d2; dd[3] += d3 * d3;
+        dd[0] += dv.a * dv.a; dd[1] += dv.b * dv.b; dd[2] += dv.c * dv.c; dd[3] += dv.d * dv.d;
         xx[0] += xv.a * xv.a; xx[1] += xv.b * xv.b; xx[2] += xv.c * xv.c; xx[3] += xv.d * xv.d;
     }
     const size_t np = gridDim.x;
-    block_sum4<256, double>(dd, partial + ((size_t)blk * np + blockIdx.x) * 4);
+    block_sum4<256, T>(dd, partial + ((size_t)blk * np + blockIdx.x) * 4);
     block_sum4<256, double>(xx, partial + (size_t)gridDim.y * np * 4 + ((size_t)blk * np + blockIdx.x) * 4);
 }
 void launch_axpy_mixed(double* x64, const double* norms, const float* d32, long long N, int nblk, double* partial, cudaStream_t s) {
@@ -719,26 +723,33 @@ template <typename QT>
 __global__ void k_rbmc(const QT* __restrict__ Qx, const double* __restrict__ x, const double* __restrict__ diag,
                        const int32_t* __restrict__ slot_sample, long long N, int nblk, int ns, double* __restrict__ var,
                        double* __restrict__ se) {
+    // e = ((Q x)_n - d x_n) / d = (Q x)_n / d - x_n per sample slot, in the
+    // precision of Q x (an FP32 product carries no more digits than FP32
+    // arithmetic keeps); the sums over the slots are widened at the end
     const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
     if (n >= N) return;
     const double d = diag[n];
-    double s1 = 0.0, s2 = 0.0;
+    const QT invd = (QT)(1.0 / d);
+    QT s1 = QT(0), s2 = QT(0);
     for (int blk = 0; blk < nblk; ++blk) {
         const size_t off = ((size_t)blk * N + n) * RW;
         const V4<QT> qx = v4load(Qx + off);
         const V4<double> xv = v4load(x + off);
-        const double a[4] = {qx.a, qx.b, qx.c, qx.d}, b[4] = {xv.a, xv.b, xv.c, xv.d};
+        const QT a[4] = {qx.a, qx.b, qx.c, qx.d};
+        const QT b[4] = {(QT)xv.a, (QT)xv.b, (QT)xv.c, (QT)xv.d};
+#pragma unroll
         for (int c = 0; c < 4; ++c) {
             if (slot_sample[blk * RW + c] < 0) continue;
-            const double e = (a[c] - d * b[c]) / d;
-            s1 += e * e;
-            s2 += e * e * e * e;
+            const QT e = a[c] * invd - b[c];
+            const QT e2 = e * e;
+            s1 += e2;
+            s2 += e2 * e2;
         }
     }
-    const double m = s1 / ns;
+    const double m = (double)s1 / ns;
     var[n] = 1.0 / d + m;
     if (se != nullptr) {
-        const double v = ns > 1 ? (s2 - ns * m * m) / (ns - 1) : 0.0;
+        const double v = ns > 1 ? ((double)s2 - ns * m * m) / (ns - 1) : 0.0;
         se[n] = sqrt(fmax(v, 0.0) / ns);
     }
 }

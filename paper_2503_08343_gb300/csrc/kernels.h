@@ -69,9 +69,10 @@ template <typename T> void launch_dense_solve(const T* Ainv, const T* b, T* x, i
 //   sc[0*P + r] = rz, sc[1*P + r] = pq, sc[2*P + r] = alpha, sc[3*P + r] = beta,
 //   sc[4*P + r] = rr, sc[5*P + r] = rr0, sc[6*P + r] = active (0/1), sc[7*P + r] = breakdown
 // with P = nblk * 4.
-template <typename T> void launch_pcg_update_xr(T* x, T* r, const T* p, const T* q, const double* sc, long long N,
-                                                int nblk, double* partial, int nparts, cudaStream_t s);
-template <typename T> void launch_pcg_update_p(T* p, const T* z, const double* sc, long long N, int nblk, cudaStream_t s);
+// r -= alpha q; then, after z = M r and beta: x += alpha p, p = z + beta p
+template <typename T> void launch_pcg_update_r(T* r, const T* q, const double* sc, long long N, int nblk, cudaStream_t s);
+template <typename T> void launch_pcg_update_xp(T* x, T* p, const T* z, const double* sc, long long N, int nblk,
+                                                cudaStream_t s);
 void launch_pcg_scalar(int kind, const double* red, double* sc, int nblk, double tol2, cudaStream_t s);
 constexpr int EPT = 4;                  // nodes per thread in elementwise kernels
 constexpr int ECHUNK = 256 * EPT;       // nodes per CTA

@@ -342,7 +342,8 @@ template <typename T> static double* scal(Workspace& W);
 template <> double* scal<float>(Workspace& W) { return W.sc32; }
 template <> double* scal<double>(Workspace& W) { return W.sc64; }
 
-// one PCG iteration: q = Q p, alpha, x += alpha p, r -= alpha q, z = M r, beta, p = z + beta p
+// one PCG iteration: q = Q p, alpha, r -= alpha q, z = M r, beta, then x += alpha p and
+// p = z + beta p in one pass
 template <typename T>
 static void pcg_iteration(Posterior& P, Workspace& W, Workspace::Vecs& V, double tol2, cudaStream_t s) {
     Level& L = P.levels[0];
@@ -357,11 +358,11 @@ static void pcg_iteration(Posterior& P, Workspace& W, Workspace::Vecs& V, double
     const int ng = launch_stencil<T>(L.geo, M_APPLY, a, s);
     launch_reduce(W.partial, ng, nblk, W.red, s);
     launch_pcg_scalar(0, W.red, sc, nblk, tol2, s);
-    launch_pcg_update_xr<T>(x, r, p, q, sc, L.N, nblk, nullptr, ne, s);   // stopping uses r^T z, not |r|
+    launch_pcg_update_r<T>(r, q, sc, L.N, nblk, s);
     const int nz = vcycle<T>(P, W, V, 0, r, z, W.partial, s);
     launch_reduce(W.partial, nz, nblk, W.red, s);
     launch_pcg_scalar(2, W.red, sc, nblk, tol2, s);
-    launch_pcg_update_p<T>(p, z, sc, L.N, nblk, s);
+    launch_pcg_update_xp<T>(x, p, z, sc, L.N, nblk, s);     // x += alpha p with this iteration's p
 }
 
 static const int kItersPerGraph = 2;
@@ -543,7 +544,7 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
         for (int i = 0; i < P4; ++i) {
             if (nrm[(size_t)i] == 0.0) continue;
             dxp[(size_t)i] = dxn[(size_t)i];
-            dxn[(size_t)i] = std::sqrt(std::max(W.h_red[i], 0.0));
+            dxn[(size_t)i] = nrm[(size_t)i] * std::sqrt(std::max(W.h_red[i], 0.0));   // |norm d|
             xn[(size_t)i] = std::sqrt(std::max(W.h_red[P4 + i], 0.0));
         }
         st.breakdown |= brk;
