@@ -373,8 +373,14 @@ static SolveStats run_batch(Posterior& P, const Batch& b, uint64_t seed, const g
     Workspace& W = workspace(P, b.nblk);
     GCK(cudaMemcpyAsync(W.slot_a, b.sample.data(), sizeof(int32_t) * b.sample.size(), cudaMemcpyHostToDevice, s));
     const bool draws = b.nrhs > b.off;     // any sample slot (t64 is free until the solve ends)
+    const long long orows = std::max<long long>(P.nrows, 1);    // observation rows (stream-1 normals)
+    if (draws && W.z2_n < (size_t)b.nblk * orows * 4) {
+        dev_free(W.z2);
+        W.z2_n = (size_t)b.nblk * orows * 4;
+        W.z2 = dev_alloc<double>(W.z2_n);
+    }
     launch_sample_rhs(P.levels[0].geo, P.levels[0].view<double>(), seed, W.slot_a, P.linearised ? P.d_blin : P.d_bdata,
-                      W.b64, draws ? W.t64 : nullptr, b.nblk, s);
+                      W.b64, draws ? W.t64 : nullptr, draws ? W.z2 : nullptr, orows, b.nblk, s);
     GCK(cudaMemsetAsync(W.x64, 0, sizeof(double) * b.nblk * P.levels[0].N * 4, s));
     if (o.batched || b.nblk == 1) return solve_blocked(P, b.nblk, W.b64, W.x64, o, s, true);
     // one right-hand side per solve (the comparison path): the batch is

@@ -131,32 +131,16 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
+// Uniform in (0, 1]: RN(k + 1/2) 2^-53 with k the 53-bit integer
+// (a >> 5) 2^26 + (b >> 6).  Formed with integer operations and one exact
+// integer-to-double conversion: below 2^52, k + 1/2 is exact; from 2^52 on it
+// is a tie that rounds to the even neighbour of k; w = 2 RN(k + 1/2) is an
+// exact integer and the result is w 2^-54 (exponent lowered by 54).
 __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
-    return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6) + 0.5) * (1.0 / 9007199254740992.0);
-}
-
-// Standard normal number `idx` of (seed, stream, sample): pair j = idx / 2 of
-// counter (j, sample, stream, 0), Box-Muller on two 53-bit uniforms.
-__device__ __forceinline__ double philox_normal(uint64_t seed, uint32_t stream, uint32_t sample, uint64_t idx) {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)(idx >> 1), sample, stream, 0u),
-                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    const double u1 = u53(w.x, w.y), u2 = u53(w.z, w.w);
-    const double r = sqrt(-2.0 * log(u1));
-    return (idx & 1) ? r * sinpi(2.0 * u2) : r * cospi(2.0 * u2);
-}
-
-// Both numbers of pair j: z0 = number 2j (cosine branch), z1 = number 2j + 1
-// (sine branch), bit-identical to philox_normal for those indices.
-__device__ __forceinline__ void philox_normal_pair(uint64_t seed, uint32_t stream, uint32_t sample, uint64_t j,
-                                                   double& z0, double& z1) {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, sample, stream, 0u),
-                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    const double u1 = u53(w.x, w.y), u2 = u53(w.z, w.w);
-    const double r = sqrt(-2.0 * log(u1));
-    double sn, cs;
-    sincospi(2.0 * u2, &sn, &cs);           // one shared reduction of the angle
-    z0 = r * cs;
-    z1 = r * sn;
+    const unsigned long long k = ((unsigned long long)(a >> 5) << 26) | (unsigned long long)(b >> 6);
+    const unsigned long long w = k < (1ull << 52) ? 2 * k + 1 : 2 * k + 2 * (k & 1);
+    const long long bits = __double_as_longlong((double)w) - (54ll << 52);
+    return __longlong_as_double(bits);
 }
 
 __device__ __forceinline__ double philox_rademacher(uint64_t seed, uint32_t sample, uint64_t idx) {

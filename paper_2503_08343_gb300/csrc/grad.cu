@@ -196,7 +196,7 @@ SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, co
     pid[0] = -1;
     for (int i = 1; i < nrhs; ++i) pid[(size_t)i] = i - 1;
     GCK(cudaMemcpyAsync(W.slot_a, sid.data(), sizeof(int32_t) * sid.size(), cudaMemcpyHostToDevice, s));
-    launch_sample_rhs(F.geo, F.view<double>(), seed, W.slot_a, P.d_bdata, W.b64, nullptr, nblk, s);
+    launch_sample_rhs(F.geo, F.view<double>(), seed, W.slot_a, P.d_bdata, W.b64, nullptr, nullptr, 0, nblk, s);
     GCK(cudaMemcpyAsync(W.slot_b, pid.data(), sizeof(int32_t) * pid.size(), cudaMemcpyHostToDevice, s));
     k_rademacher_slots<<<dim3(nb256(N), nblk), 256, 0, s>>>(seed, W.slot_b, W.b64, N);
     note_launch();

@@ -98,6 +98,9 @@ struct Workspace {
     int nblk = 0;
     // FP64 refinement vectors (blocked)
     double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr;
+    // observation-row normals of the drawn samples [nblk][rows][4], sized on first use
+    double* z2 = nullptr;
+    size_t z2_n = 0;
     // partial sums and per-RHS scalars
     double* partial = nullptr;
     size_t npartial = 0;

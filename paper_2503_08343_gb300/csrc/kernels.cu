@@ -35,6 +35,109 @@ static void cuda_ok(cudaError_t e) {
     if (e != cudaSuccess) throw std::runtime_error(std::string("kernel setup: ") + cudaGetErrorString(e));
 }
 
+// ---------------------------------------------------------------------------
+// Standard normals: the Box-Muller transform of two 53-bit uniforms of one
+// Philox draw (normal 2j: cosine branch, 2j + 1: sine branch of counter
+// (j, sample, stream, 0)).  The FP64 pipe of GB300 is narrow, so the
+// logarithm and the sine / cosine are table-driven with short polynomials:
+//   ln u, Tang's table-driven method (ACM TOMS 16(4), 1990): u = 2^e m with m
+//     in [1, 2); F = 1 + j/128 keeps the leading 7 fraction bits of m and
+//     f = m - F is exact; ln u = e ln 2 + ln F + ln(1 + q) with q = f / F in
+//     [0, 2^-7), by the series of ln(1 + q) through q^7 (remainder below
+//     2^-59).  Within 2^-7 of 1 the series runs on the exact t = u - 1, so
+//     that ln u keeps its relative accuracy as u -> 1.
+//   sin and cos of 2 pi u: j = nearest integer to 256 u, g = u - j/256 exact
+//     (|g| <= 1/512), phi = 2 pi g; the addition theorem combines the table
+//     values sin, cos(2 pi j / 256) with the Taylor series of sin phi through
+//     phi^7 and of cos phi through phi^8 (remainders below 1e-19).
+struct BoxMullerTables {
+    double inv_f[128];   // 1 / (1 + j/128)
+    double ln_f[128];    // ln(1 + j/128)
+    double sn[256];      // sin(pi j / 128)
+    double cs[256];      // cos(pi j / 128)
+};
+__device__ BoxMullerTables g_bm;
+constexpr double kLn2 = 0.693147180559945309417232121458;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__global__ void k_bm_tables() {
+    const int j = threadIdx.x;
+    if (j < 128) {
+        g_bm.inv_f[j] = 1.0 / (1.0 + j / 128.0);
+        g_bm.ln_f[j] = log1p(j / 128.0);
+    }
+    g_bm.sn[j] = sinpi(j / 128.0);
+    g_bm.cs[j] = cospi(j / 128.0);
+}
+
+// Fills the tables once per process (the library drives one GPU per process).
+static void bm_tables_ready() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        k_bm_tables<<<1, 256>>>();
+        note_launch();
+        cuda_ok(cudaGetLastError());
+        cuda_ok(cudaDeviceSynchronize());
+    });
+}
+
+__device__ __forceinline__ double bm_log(double u) {          // u in (0, 1]
+    const int hi = __double2hiint(u), lo = __double2loint(u);
+    const int e = ((hi >> 20) & 0x7ff) - 1023;
+    const int j = (hi >> 13) & 0x7f;
+    const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);
+    const double F = __hiloint2double((hi & 0x000fe000) | 0x3ff00000, 0);
+    const bool near1 = u >= 1.0 - 1.0 / 128.0;
+    const double q = near1 ? u - 1.0 : (m - F) * __ldg(&g_bm.inv_f[j]);
+    const double base = near1 ? 0.0 : fma((double)e, kLn2, __ldg(&g_bm.ln_f[j]));
+    double s = 1.0 / 7.0;
+    s = fma(s, q, -1.0 / 6.0);
+    s = fma(s, q, 1.0 / 5.0);
+    s = fma(s, q, -0.25);
+    s = fma(s, q, 1.0 / 3.0);
+    s = fma(s, q, -0.5);
+    s = fma(s, q, 1.0);
+    return fma(q, s, base);
+}
+
+__device__ __forceinline__ void bm_sincos2pi(double u, double& sn, double& cs) {
+    const int j = __double2int_rn(u * 256.0);
+    const double g = fma((double)j, -1.0 / 256.0, u);
+    const double phi = g * kTwoPi;
+    const double p2 = phi * phi;
+    double ss = -1.0 / 5040.0;
+    ss = fma(ss, p2, 1.0 / 120.0);
+    ss = fma(ss, p2, -1.0 / 6.0);
+    const double sp = fma(phi * p2, ss, phi);
+    double cc = 1.0 / 40320.0;
+    cc = fma(cc, p2, -1.0 / 720.0);
+    cc = fma(cc, p2, 1.0 / 24.0);
+    cc = fma(cc, p2, -0.5);
+    const double cp = fma(cc, p2, 1.0);
+    const int k = j & 255;
+    const double S = __ldg(&g_bm.sn[k]), C = __ldg(&g_bm.cs[k]);
+    sn = fma(S, cp, C * sp);
+    cs = fma(C, cp, -(S * sp));
+}
+
+__device__ __forceinline__ void philox_normal_pair(uint64_t seed, uint32_t stream, uint32_t sample, uint64_t j,
+                                                   double& z0, double& z1) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, sample, stream, 0u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const double u1 = u53(w.x, w.y), u2 = u53(w.z, w.w);
+    const double r = sqrt(-2.0 * bm_log(u1));
+    double sn, cs;
+    bm_sincos2pi(u2, sn, cs);
+    z0 = r * cs;
+    z1 = r * sn;
+}
+
+__device__ __forceinline__ double philox_normal(uint64_t seed, uint32_t stream, uint32_t sample, uint64_t idx) {
+    double z0, z1;
+    philox_normal_pair(seed, stream, sample, idx >> 1, z0, z1);
+    return (idx & 1) ? z1 : z0;
+}
+
 
 template <typename T> LevelView<T> Level::view() const {
     LevelView<T> v;
@@ -501,30 +604,38 @@ void launch_axpy_scaled64(double* x64, const double* norms, const double* d64, l
 // >= 0 draws sample `id`.  With use_probe the slot holds a Rademacher probe.
 
 // z1[blk][n][c]: the prior-row normals (stream 0) of the sample in slot
-// (blk, c), zero for slots without a sample.  One thread per Box-Muller
-// pair of rows (2j, 2j + 1), so each pair's transcendentals run once.
+// (blk, c), and z2[blk][row][c] those of the observation rows (stream 1);
+// zero for slots without a sample.  One thread per Box-Muller pair of rows
+// (2j, 2j + 1), so each pair's transcendentals run once; threads past the
+// N / 2 pairs of stream 0 take the pairs of stream 1.
 __global__ void __launch_bounds__(256) k_sample_normals(uint64_t seed, const int32_t* __restrict__ slot_sample,
-                                                        long long N, double* __restrict__ z1) {
+                                                        long long N, double* __restrict__ z1, long long rows,
+                                                        double* __restrict__ z2) {
     const int blk = blockIdx.y;
-    const long long j = (long long)blockIdx.x * 256 + threadIdx.x;
+    const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+    const long long p0 = (N + 1) / 2;
+    const bool s1 = t >= p0;
+    const long long j = s1 ? t - p0 : t;
+    const long long M = s1 ? rows : N;
     const long long n0 = 2 * j;
-    if (n0 >= N) return;
+    if (n0 >= M) return;
     double a[4], b[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const int sid = slot_sample[blk * RW + c];
         a[c] = b[c] = 0.0;
-        if (sid >= 0) philox_normal_pair(seed, 0u, (uint32_t)sid, (uint64_t)j, a[c], b[c]);
+        if (sid >= 0) philox_normal_pair(seed, s1 ? 1u : 0u, (uint32_t)sid, (uint64_t)j, a[c], b[c]);
     }
-    double* p = z1 + ((size_t)blk * N + n0) * RW;
+    double* p = (s1 ? z2 : z1) + ((size_t)blk * M + n0) * RW;
     v4store(p, V4<double>{a[0], a[1], a[2], a[3]});
-    if (n0 + 1 < N) v4store(p + RW, V4<double>{b[0], b[1], b[2], b[3]});
+    if (n0 + 1 < M) v4store(p + RW, V4<double>{b[0], b[1], b[2], b[3]});
 }
 
 template <int GEO>
 __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, uint64_t seed,
                                                     const int32_t* __restrict__ slot_sample,
                                                     const double* __restrict__ bdata, const double* __restrict__ z1,
+                                                    const double* __restrict__ z2, long long rows,
                                                     double* __restrict__ b64) {
     using G = Geo<GEO>;
     constexpr int TX = G::TX, TY = G::TY, TT = G::TT, HY = G::HY, HT = G::HT;
@@ -599,7 +710,9 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
                 const uint64_t orow = (uint64_t)L.col.row0 + (uint64_t)(rt - 1) * (nx - 2) + (rx - 1);
                 double v[4];
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) v[cc] = sid[cc] >= 0 ? philox_normal(seed, 1u, (uint32_t)sid[cc], orow) : 0.0;
+                const double* zr = z2 + ((size_t)blk * rows + orow) * RW;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) v[cc] = (sid[cc] >= 0 && z2 != nullptr) ? zr[cc] : 0.0;
                 q = fma4(c * sq_eps, V4<double>{v[0], v[1], v[2], v[3]}, q);
             }
         }
@@ -612,7 +725,9 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
             const ObsRow& o = L.obs[L.tile_idx[k]];
             double v[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = sid[c] >= 0 ? philox_normal(seed, 1u, (uint32_t)sid[c], (uint64_t)o.row) : 0.0;
+            const double* zr = z2 + ((size_t)blk * rows + o.row) * RW;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = (sid[c] >= 0 && z2 != nullptr) ? zr[c] : 0.0;
             const double sr = sqrt(o.rinv);
             for (int n = 0; n < o.nn; ++n) {
                 const long long nd = o.node[n];
@@ -645,16 +760,20 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
 }
 
 void launch_sample_rhs(int geo, const LevelView<double>& L, uint64_t seed, const int32_t* slot_sample,
-                       const double* bdata, double* b64, double* z1, int nblk, cudaStream_t s) {
+                       const double* bdata, double* b64, double* z1, double* z2, long long rows, int nblk,
+                       cudaStream_t s) {
+    if ((z1 == nullptr) != (z2 == nullptr)) throw std::runtime_error("sample right-hand sides: z1 and z2 go together");
     if (z1 != nullptr) {
-        const long long pairs = (L.N + 1) / 2;
-        k_sample_normals<<<dim3((unsigned)((pairs + 255) / 256), (unsigned)nblk), 256, 0, s>>>(seed, slot_sample, L.N, z1);
+        bm_tables_ready();
+        const long long pairs = (L.N + 1) / 2 + (rows + 1) / 2;
+        k_sample_normals<<<dim3((unsigned)((pairs + 255) / 256), (unsigned)nblk), 256, 0, s>>>(seed, slot_sample, L.N, z1,
+                                                                                                rows, z2);
         note_launch();
     }
     const dim3 grid((unsigned)((long long)L.tiles_x * L.tiles_y * L.tiles_t), (unsigned)nblk);
-    if (geo == GEO_XY) { k_sample_rhs<GEO_XY><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, z1, b64); note_launch(); }
-    else if (geo == GEO_XT) { k_sample_rhs<GEO_XT><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, z1, b64); note_launch(); }
-    else { k_sample_rhs<GEO_XYT><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, z1, b64); note_launch(); }
+    if (geo == GEO_XY) { k_sample_rhs<GEO_XY><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, z1, z2, rows, b64); note_launch(); }
+    else if (geo == GEO_XT) { k_sample_rhs<GEO_XT><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, z1, z2, rows, b64); note_launch(); }
+    else { k_sample_rhs<GEO_XYT><<<grid, 256, 0, s>>>(L, seed, slot_sample, bdata, z1, z2, rows, b64); note_launch(); }
 }
 
 // Rademacher probes: slot id >= 0 holds probe `id` (stream 2), -1 the data rhs.
@@ -868,6 +987,7 @@ __global__ void k_normals(uint64_t seed, int stream, int sample0, int count, lon
     out[(size_t)s * n + i] = philox_normal(seed, (uint32_t)stream, (uint32_t)(sample0 + s), (uint64_t)i);
 }
 void launch_normals(uint64_t seed, int stream, int sample0, int count, long long n, double* out, cudaStream_t s) {
+    bm_tables_ready();
     { k_normals<<<dim3((unsigned)((n + 255) / 256), count), 256, 0, s>>>(seed, stream, sample0, count, n, out); note_launch(); }
 }
 
@@ -1000,6 +1120,7 @@ __global__ void k_fill_random(float* __restrict__ v, long long N, uint64_t seed,
     v4store(v + n * RW, V4<float>{r[0], r[1], r[2], r[3]});
 }
 void launch_fill_random(float* v, long long N, uint64_t seed, cudaStream_t s, const float* dinv) {
+    bm_tables_ready();
     { k_fill_random<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(v, N, seed, dinv); note_launch(); }
 }
 

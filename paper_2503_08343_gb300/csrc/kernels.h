@@ -97,9 +97,12 @@ void launch_scale64(const double* r64, const double* norms, double* out, long lo
 
 // right-hand sides, layout conversion, variances
 // b64 slots: sample RHS, data RHS or zero by slot id; z1 ([nblk][N][4] FP64
-// scratch) receives the prior-row normals, NULL when no slot draws a sample
+// scratch) receives the prior-row normals and z2 ([nblk][rows][4]) those of
+// the observation rows (point, initial-condition and collocation rows,
+// numbered as in the posterior); both NULL when no slot draws a sample
 void launch_sample_rhs(int geo, const LevelView<double>& L, uint64_t seed, const int32_t* slot_sample,
-                       const double* bdata, double* b64, double* z1, int nblk, cudaStream_t s);
+                       const double* bdata, double* b64, double* z1, double* z2, long long rows, int nblk,
+                       cudaStream_t s);
 void launch_obs_scatter(const ObsRow* obs, int nobs, const double* y, double* b, cudaStream_t s);
 void launch_pack(const double* src, double* dst, const int32_t* slot_src, long long N, int nblk, cudaStream_t s);
 void launch_unpack(const double* src, double* dst, const int32_t* slot_dst, long long N, int nblk, cudaStream_t s);

@@ -209,7 +209,7 @@ static void free_vecs(Workspace::Vecs& V) {
 
 void workspace_free(Workspace* w) {
     if (!w) return;
-    dev_free(w->b64); dev_free(w->x64); dev_free(w->r64); dev_free(w->t64);
+    dev_free(w->b64); dev_free(w->x64); dev_free(w->r64); dev_free(w->t64); dev_free(w->z2);
     dev_free(w->partial); dev_free(w->red); dev_free(w->red2); dev_free(w->norms); dev_free(w->sc32); dev_free(w->sc64);
     dev_free(w->slot_a); dev_free(w->slot_b);
     if (w->h_red) cudaFreeHost(w->h_red);
