@@ -360,17 +360,26 @@ __device__ __forceinline__ T p1_weight(int dx, int dy, T wx, T wy) {
 // the P1 interpolation when p1, else of the bilinear one):
 // out[.., Jy, Jx] = sum P(x, y; Jx, Jy) in[.., y, x] over the fine ranges of
 // Jx and Jy.  A CTA owns kRestrictTX x kRestrictTY coarse nodes of one time
-// level and block: it stages the fine region under them (span W x H, rows
-// read contiguously) in shared memory, then each thread sums its node.
+// level and block: it stages the fine region under them (span W x H, all
+// rows in flight at once) and the transfer tables of its columns and rows in
+// shared memory.  Each thread then sums its node: it keeps the (offset,
+// weight) data of its up to kRestrictMax fine columns in registers and walks
+// its fine rows, without branches (a zero weight adds zero).
+constexpr int kRestrictMax = 8;      // fine nodes under one coarse node per axis (2:1 coarsening: <= 7)
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_xy(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nt,
                                                      int cx, int cy, const int32_t* __restrict__ rsx,
                                                      const int32_t* __restrict__ rcx, const int32_t* __restrict__ pjx,
                                                      const T* __restrict__ pwx, const int32_t* __restrict__ rsy,
                                                      const int32_t* __restrict__ rcy, const int32_t* __restrict__ pjy,
-                                                     const T* __restrict__ pwy, bool p1, int W, int tiles_cy) {
+                                                     const T* __restrict__ pwy, bool p1, int W, int H, int tiles_cy) {
     extern __shared__ __align__(16) unsigned char rsm[];
     V4<T>* tile = reinterpret_cast<V4<T>*>(rsm);
+    T* twx = reinterpret_cast<T*>(rsm + (size_t)W * H * sizeof(V4<T>));   // weights first: aligned for T
+    T* twy = twx + W;
+    int* tjx = reinterpret_cast<int*>(twy + H);
+    int* tjy = tjx + W;
     const int blk = blockIdx.z;
     const int t = blockIdx.y / tiles_cy;
     const int Jx0 = blockIdx.x * kRestrictTX, Jy0 = (blockIdx.y - t * tiles_cy) * kRestrictTY;
@@ -380,26 +389,50 @@ __global__ void __launch_bounds__(256) k_restrict_xy(const T* __restrict__ in, T
     const long long Nin = (long long)nx * ny * nt;
     const T* src = in + ((size_t)blk * Nin + (size_t)t * nx * ny) * RW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // asynchronous copies: every load of the region is in flight at once
     for (int y = fy0 + warp; y < fy1; y += 8)
         for (int x = fx0 + lane; x < fx1; x += 32)
             cp_v4<T>(&tile[(y - fy0) * W + (x - fx0)], src + ((size_t)y * nx + x) * RW, true);
     cp_commit();
+    for (int i = threadIdx.x; i < fx1 - fx0; i += 256) { tjx[i] = pjx[fx0 + i]; twx[i] = pwx[fx0 + i]; }
+    for (int i = threadIdx.x; i < fy1 - fy0; i += 256) { tjy[i] = pjy[fy0 + i]; twy[i] = pwy[fy0 + i]; }
     cp_wait<0>();
     __syncthreads();
     const int Jx = Jx0 + (threadIdx.x % kRestrictTX), Jy = Jy0 + (threadIdx.x / kRestrictTX);
     if (Jx >= Jx1 || Jy >= Jy1) return;
+    const int x0 = rsx[Jx] - fx0, kx = rcx[Jx], y0 = rsy[Jy] - fy0, ky = rcy[Jy];
+    // per fine column: offset dx = Jx - pj and weight w (bilinear: the x factor)
+    int dxs[kRestrictMax];
+    T wxs[kRestrictMax];
+#pragma unroll
+    for (int a = 0; a < kRestrictMax; ++a) {
+        const bool on = a < kx;
+        const int xx = on ? x0 + a : x0;
+        const int dx = Jx - tjx[xx];
+        const T wx = twx[xx];
+        dxs[a] = dx;
+        wxs[a] = p1 ? wx : (dx == 0 ? T(1) - wx : (dx == 1 ? wx : T(0)));
+    }
     V4<T> acc = v4zero<T>();
-    const int x0 = rsx[Jx], x1 = x0 + rcx[Jx], y0 = rsy[Jy], y1 = y0 + rcy[Jy];
-    for (int y = y0; y < y1; ++y) {
-        const int dy = Jy - pjy[y];
-        const T wy = pwy[y];
-        for (int x = x0; x < x1; ++x) {
-            const int dx = Jx - pjx[x];
-            const T wx = pwx[x];
-            const T w = p1 ? p1_weight<T>(dx, dy, wx, wy)
-                           : (dx == 0 ? T(1) - wx : (dx == 1 ? wx : T(0))) * (dy == 0 ? T(1) - wy : (dy == 1 ? wy : T(0)));
-            if (w != T(0)) acc = fma4(w, tile[(y - fy0) * W + (x - fx0)], acc);
+    for (int b = 0; b < ky; ++b) {
+        const int yy = y0 + b;
+        const int dy = Jy - tjy[yy];
+        const T wy = twy[yy];
+        const V4<T>* row = tile + (size_t)yy * W + x0;
+        if (p1) {
+#pragma unroll
+            for (int a = 0; a < kRestrictMax; ++a) {
+                if (a >= kx) break;
+                acc = fma4(p1_weight<T>(dxs[a], dy, wxs[a], wy), row[a], acc);
+            }
+        } else {
+            const T ay = dy == 0 ? T(1) - wy : (dy == 1 ? wy : T(0));
+            V4<T> r = v4zero<T>();
+#pragma unroll
+            for (int a = 0; a < kRestrictMax; ++a) {
+                if (a >= kx) break;
+                r = fma4(wxs[a], row[a], r);
+            }
+            acc = fma4(ay, r, acc);
         }
     }
     const long long Nout = (long long)cx * cy * nt;
@@ -412,14 +445,14 @@ void launch_restrict_xy(const T* in, T* out, int nx, int ny, int nt, int cx, int
                         const int span[2], int nblk, cudaStream_t s) {
     static_assert(kRestrictTX * kRestrictTY == 256, "one thread per coarse node of the tile");
     const int tiles_cx = (cx + kRestrictTX - 1) / kRestrictTX, tiles_cy = (cy + kRestrictTY - 1) / kRestrictTY;
-    const size_t smem = (size_t)span[0] * span[1] * sizeof(V4<T>);
+    const size_t smem = (size_t)span[0] * span[1] * sizeof(V4<T>) + (size_t)(span[0] + span[1]) * (sizeof(int) + sizeof(T));
     static std::once_flag once;
     std::call_once(once, [] {
         cuda_ok(cudaFuncSetAttribute(k_restrict_xy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     });
     if (smem > 200 * 1024) throw std::runtime_error("restriction tile exceeds shared memory");
     const dim3 grid((unsigned)tiles_cx, (unsigned)(tiles_cy * nt), (unsigned)nblk);
-    { k_restrict_xy<T><<<grid, 256, smem, s>>>(in, out, nx, ny, nt, cx, cy, rs[0], rc[0], pj[0], pw[0], rs[1], rc[1], pj[1], pw[1], p1, span[0], tiles_cy); note_launch(); }
+    { k_restrict_xy<T><<<grid, 256, smem, s>>>(in, out, nx, ny, nt, cx, cy, rs[0], rc[0], pj[0], pw[0], rs[1], rc[1], pj[1], pw[1], p1, span[0], span[1], tiles_cy); note_launch(); }
 }
 template void launch_restrict_xy<float>(const float*, float*, int, int, int, int, int, const int32_t* const[2], const int32_t* const[2], const int32_t* const[2], const float* const[2], bool, const int[2], int, cudaStream_t);
 template void launch_restrict_xy<double>(const double*, double*, int, int, int, int, int, const int32_t* const[2], const int32_t* const[2], const int32_t* const[2], const double* const[2], bool, const int[2], int, cudaStream_t);

@@ -68,6 +68,17 @@ def test_normal_draws_match_the_oracle_generator():
             assert np.max(np.abs(g[s] - o)) < 1e-12
 
 
+def test_normal_draws_match_the_oracle_generator_in_volume():
+    # 2^20 draws per (stream, sample): the table-driven logarithm's branch
+    # next to u = 1 (about 1 uniform in 128) and every table entry are hit
+    for (seed, stream, s0) in [(31, 0, 2), (2 ** 33 + 5, 1, 17)]:
+        g = gmrf.normals(seed, stream, s0, 2, 1 << 20)
+        for s in range(2):
+            o = rng.normals(seed, stream, s0 + s, 1 << 20)
+            assert np.max(np.abs(g[s] - o)) < 1e-12
+            assert np.min(np.abs(o)) < 1e-4 and np.max(np.abs(o)) > 4.5
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp64_apply_matches_assembled_posterior_precision(built, name):
     pr, ob, gp, post, orc, _ = built[name]
