@@ -189,12 +189,9 @@ void launch_reduce(const double* partial, int nparts, int nblk, double* out, cud
 //         invariant under diagonal scaling of the system)
 // kind 3: initial: rz reduced, rz_0 = rz, active = rz_0 > 0
 // kind 4: rr reduced -> rr
-__global__ void k_pcg_scalar(int kind, const double* __restrict__ red, double* __restrict__ sc, int P, double tol2) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= P) return;
+__device__ __forceinline__ void pcg_scalar_update(int kind, int r, double v, double* __restrict__ sc, int P, double tol2) {
     double* rz = sc, *pq = sc + P, *alpha = sc + 2 * P, *beta = sc + 3 * P;
     double* rr = sc + 4 * P, *rr0 = sc + 5 * P, *active = sc + 6 * P, *brk = sc + 7 * P;
-    const double v = red[r];
     if (kind == 0) {
         pq[r] = v;
         const bool ok = v > 0.0 && isfinite(v) && isfinite(rz[r]);
@@ -214,6 +211,35 @@ __global__ void k_pcg_scalar(int kind, const double* __restrict__ red, double* _
         beta[r] = 0.0;
         alpha[r] = 0.0;
     }
+}
+
+__global__ void k_pcg_scalar(int kind, const double* __restrict__ red, double* __restrict__ sc, int P, double tol2) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= P) return;
+    pcg_scalar_update(kind, r, red[r], sc, P, tol2);
+}
+
+// k_reduce and k_pcg_scalar in one launch: CTA blk sums the partials of its
+// block, and its threads 0..3 update the scalars of the block's four
+// right-hand sides (the update of a right-hand side reads only its own).
+__global__ void k_reduce_scalar(int kind, const double* __restrict__ partial, int nparts, double* __restrict__ red,
+                                double* __restrict__ sc, int P, double tol2) {
+    const int blk = blockIdx.x;
+    double v[4] = {0, 0, 0, 0};
+    for (int i = threadIdx.x; i < nparts; i += 256) {
+        const double* p = partial + ((size_t)blk * nparts + i) * 4;
+        v[0] += p[0]; v[1] += p[1]; v[2] += p[2]; v[3] += p[3];
+    }
+    block_sum4<256, double>(v, red + (size_t)blk * 4);   // threads 0..3 wrote red[blk * 4 + tid]
+    if (threadIdx.x < 4) {
+        const int r = blk * 4 + threadIdx.x;
+        pcg_scalar_update(kind, r, red[r], sc, P, tol2);
+    }
+}
+
+void launch_reduce_scalar(int kind, const double* partial, int nparts, int nblk, double* red, double* sc, double tol2,
+                          cudaStream_t s) {
+    { k_reduce_scalar<<<nblk, 256, 0, s>>>(kind, partial, nparts, red, sc, nblk * 4, tol2); note_launch(); }
 }
 
 void launch_pcg_scalar(int kind, const double* red, double* sc, int nblk, double tol2, cudaStream_t s) {

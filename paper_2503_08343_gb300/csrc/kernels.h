@@ -74,6 +74,9 @@ template <typename T> void launch_pcg_update_r(T* r, const T* q, const double* s
 template <typename T> void launch_pcg_update_xp(T* x, T* p, const T* z, const double* sc, long long N, int nblk,
                                                 cudaStream_t s);
 void launch_pcg_scalar(int kind, const double* red, double* sc, int nblk, double tol2, cudaStream_t s);
+// launch_reduce into `red` followed by launch_pcg_scalar on it, as one kernel
+void launch_reduce_scalar(int kind, const double* partial, int nparts, int nblk, double* red, double* sc, double tol2,
+                          cudaStream_t s);
 constexpr int EPT = 4;                  // nodes per thread in elementwise kernels
 constexpr int ECHUNK = 256 * EPT;       // nodes per CTA
 int elem_parts(long long N);

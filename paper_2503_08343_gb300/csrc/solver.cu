@@ -356,12 +356,10 @@ static void pcg_iteration(Posterior& P, Workspace& W, Workspace::Vecs& V, double
     a.nblk = nblk;
     a.x = p; a.out = q; a.partial = W.partial;
     const int ng = launch_stencil<T>(L.geo, M_APPLY, a, s);
-    launch_reduce(W.partial, ng, nblk, W.red, s);
-    launch_pcg_scalar(0, W.red, sc, nblk, tol2, s);
+    launch_reduce_scalar(0, W.partial, ng, nblk, W.red, sc, tol2, s);
     launch_pcg_update_r<T>(r, q, sc, L.N, nblk, s);
     const int nz = vcycle<T>(P, W, V, 0, r, z, W.partial, s);
-    launch_reduce(W.partial, nz, nblk, W.red, s);
-    launch_pcg_scalar(2, W.red, sc, nblk, tol2, s);
+    launch_reduce_scalar(2, W.partial, nz, nblk, W.red, sc, tol2, s);
     launch_pcg_update_xp<T>(x, p, z, sc, L.N, nblk, s);     // x += alpha p with this iteration's p
 }
 
@@ -381,11 +379,9 @@ static int pcg(Posterior& P, Workspace& W, double tol, int maxit, cudaStream_t s
     const double tol2 = tol * tol;
     GCK(cudaMemsetAsync(x, 0, bytes, s));
     launch_norm2<T>(r, L.N, nblk, W.partial, ne, s);
-    launch_reduce(W.partial, ne, nblk, W.red, s);
-    launch_pcg_scalar(4, W.red, sc, nblk, tol2, s);
+    launch_reduce_scalar(4, W.partial, ne, nblk, W.red, sc, tol2, s);
     const int nz = vcycle<T>(P, W, V, 0, r, z, W.partial, s);
-    launch_reduce(W.partial, nz, nblk, W.red, s);
-    launch_pcg_scalar(3, W.red, sc, nblk, tol2, s);
+    launch_reduce_scalar(3, W.partial, nz, nblk, W.red, sc, tol2, s);
     GCK(cudaMemcpyAsync(p, z, bytes, cudaMemcpyDeviceToDevice, s));
     const int P4 = nblk * 4;
     if (use_graph && V.graph == nullptr) {
