@@ -9,6 +9,7 @@ Metric: RHS x unknowns solved per second (whole job, all GPUs).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --stencil-timing c2|c5      # per-kernel stencil timings
+  python bench.py --config c1|c3|c4|c5        # the other workloads, one JSON line each
 
 N > 1 runs under torchrun, one process per GPU: each rank solves its own
 replica (the workload is one posterior; it has no data-parallel split), so
@@ -304,6 +305,76 @@ def run_stencil_timing(which: str, iters: int) -> None:
         torch.cuda.nvtx.range_pop()
 
 
+def run_config(which: str) -> None:
+    """Wall time of the other workloads through the library API (warm; one
+    GPU), one JSON line:
+      c1  1D space-time 64 x 64, 50 observations: mean + 256 samples + RBMC
+          variances (257 right-hand sides), 10 timed calls;
+      c3  Burgers 1024 x 1024: data-only mean, then 5 x (Gauss-Newton step +
+          mean and 32 Laplace samples at the linearisation), and the mode's
+          distance from the Cole-Hopf solution on 8 time levels;
+      c4  256 uneven 2D instances: mean + 16 samples + RBMC each, one batch
+          call on 8 host threads;
+      c5  2D space-time 256^3 with 50 000 observations: log-likelihood
+          gradient with 32 probes (65 right-hand sides), rtol 1e-6."""
+    import numpy as np
+    import torch
+    from paper_2503_08343_gb300 import gmrf, workloads as W
+    out = {"config": which}
+    if which == "c1":
+        pr, ob = W.c1_st1d()
+        post = gmrf.Posterior(gmrf.Prior(pr), ob)
+        for _ in range(2):
+            post.marginal_var(256, W.DRAW_SEED["c1"])
+        torch.cuda.synchronize()
+        t, k = time.perf_counter(), 10
+        for _ in range(k):
+            _, _, _, info = post.marginal_var(256, W.DRAW_SEED["c1"])
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t) / k
+        out.update({"unknowns": post.N, "rhs": 257, "ms": dt * 1e3, "rhs_unknowns_per_s": 257 * post.N / dt,
+                    "refinements": info["refinements"], "inner_iterations": info["inner_iterations"]})
+    elif which == "c3":
+        n = 1024
+        pr, ob = W.c3_burgers(nx=n, nt=n)
+        post = gmrf.Posterior(gmrf.Prior(pr), ob)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u, _ = post.solve_mean()
+        d = np.zeros_like(u)
+        for k in range(5):
+            post.gauss_newton_step(u, d)
+            post.sample(32, W.DRAW_SEED["c3"] + k)
+        torch.cuda.synchronize()
+        total = time.perf_counter() - t0
+        ts = np.linspace(0, 1, n)[:: n // 8][:8]
+        X = np.tile(np.linspace(-1, 1, n), len(ts))
+        T = np.repeat(ts, n)
+        err = float(np.abs(u.reshape(n, n)[:: n // 8][:8].ravel() - W.cole_hopf_burgers(X, T, 0.01)).max())
+        out.update({"unknowns": post.N, "s": total, "rhs_unknowns_per_s": 5 * 34 * post.N / total,
+                    "max_err_vs_cole_hopf": err})
+    elif which == "c4":
+        insts = W.c4_instances(count=256)
+        posts = [gmrf.Posterior(gmrf.Prior(pr), ob) for pr, ob in insts]
+        for rep in range(2):
+            t = time.perf_counter()
+            _, _, infos = gmrf.marginal_var_batch(posts, 16, 1004, nthreads=8)
+            dt = time.perf_counter() - t
+        units = 17 * sum(p.N for p in posts)
+        out.update({"instances": len(posts), "unknowns_total": sum(p.N for p in posts), "s": dt,
+                    "rhs_unknowns_per_s": units / dt, "converged": all(i["converged"] for i in infos)})
+    else:
+        pr, ob = W.c5_st2d(n=256, nt=256, m=50000)
+        post = gmrf.Posterior(gmrf.Prior(pr), ob)
+        for rep in range(2):
+            t = time.perf_counter()
+            _, _, _, info = post.loglik_grad(32, 1005, opts=gmrf.default_opts(rtol=1e-6))
+            dt = time.perf_counter() - t
+        out.update({"unknowns": post.N, "rhs": 65, "s": dt, "refinements": info["refinements"],
+                    "inner_iterations": info["inner_iterations"]})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,7 +384,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stencil-timing", choices=["c2", "c5"], default=None,
                     help="time the stencil kernels alone (one JSON line per mode) instead of the step")
+    ap.add_argument("--config", choices=["c1", "c3", "c4", "c5"], default=None,
+                    help="time one of the other workloads through the library API (one JSON line)")
     args = ap.parse_args()
+    if args.config:
+        run_config(args.config)
+        return
     if args.stencil_timing:
         run_stencil_timing(args.stencil_timing, 50)
         return
