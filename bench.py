@@ -131,7 +131,7 @@ def run_reference(args, rank, world):
 # Chebyshev stencil on this workload, from one ncu capture
 # (profiles/stencil_chebyshev_matern512_rhs65.md), valid only for the kernel
 # sources it was taken on: SHA-256 of stencil.cu + common.cuh.
-CHEB_TRAFFIC = {"sources_sha256": "310a381c486d8e787c15718db515486ac0ff36bb36e0a552576f98676859033c", "bytes": 369905407}
+CHEB_TRAFFIC = {"sources_sha256": "68e8a29cb9a75845c613189a3f1156c9dd111d82ab5ed3b4a55737ca0d821fab", "bytes": 369288960}
 
 
 def kernel_sources_sha256() -> str:
@@ -342,17 +342,21 @@ def run_config(which: str) -> None:
         t0 = time.perf_counter()
         u, _ = post.solve_mean()
         d = np.zeros_like(u)
+        steps = []
         for k in range(5):
-            post.gauss_newton_step(u, d)
-            post.sample(32, W.DRAW_SEED["c3"] + k)
-        torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, _, ig = post.gauss_newton_step(u, d)
+            _, _, isamp = post.sample(32, W.DRAW_SEED["c3"] + k)
+            torch.cuda.synchronize()
+            steps.append({"s": round(time.perf_counter() - t, 3), "gn_inner": ig["inner_iterations"],
+                          "sample_inner": isamp["inner_iterations"]})
         total = time.perf_counter() - t0
         ts = np.linspace(0, 1, n)[:: n // 8][:8]
         X = np.tile(np.linspace(-1, 1, n), len(ts))
         T = np.repeat(ts, n)
         err = float(np.abs(u.reshape(n, n)[:: n // 8][:8].ravel() - W.cole_hopf_burgers(X, T, 0.01)).max())
         out.update({"unknowns": post.N, "s": total, "rhs_unknowns_per_s": 5 * 34 * post.N / total,
-                    "max_err_vs_cole_hopf": err})
+                    "max_err_vs_cole_hopf": err, "steps": steps})
     elif which == "c4":
         insts = W.c4_instances(count=256)
         posts = [gmrf.Posterior(gmrf.Prior(pr), ob) for pr, ob in insts]
