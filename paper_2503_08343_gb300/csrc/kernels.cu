@@ -627,26 +627,25 @@ __global__ void __launch_bounds__(256) k_axpy_norm(double* __restrict__ x64, con
                                                    const T* __restrict__ d, long long N, double* __restrict__ partial) {
     // x += norm * d in FP64 (one rounding).  For the forward-error stopping
     // test: |d|^2 of the inner solution d (the increment is norm * d; the
-    // host applies the norm), accumulated in T within the CTA, and |x|^2 in
-    // FP64 (x may lie anywhere in the FP64 range).
+    // host applies the norm) and |x|^2, both in FP64: d and x may lie far
+    // outside the FP32 range of squares (linearised Burgers systems do).
     const int blk = blockIdx.y;
     const double* nm = norms + blk * RW;
-    T dd[4] = {0, 0, 0, 0};
-    double xx[4] = {0, 0, 0, 0};
+    double dd[4] = {0, 0, 0, 0}, xx[4] = {0, 0, 0, 0};
     for (int k = 0; k < EPT; ++k) {
         const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
         if (n >= N) break;
         const size_t off = ((size_t)blk * N + n) * RW;
         const V4<T> dv = v4load(d + off);
+        const double d0 = dv.a, d1 = dv.b, d2 = dv.c, d3 = dv.d;
         V4<double> xv = v4load(x64 + off);
-        xv.a = fma(nm[0], (double)dv.a, xv.a); xv.b = fma(nm[1], (double)dv.b, xv.b);
-        xv.c = fma(nm[2], (double)dv.c, xv.c); xv.d = fma(nm[3], (double)dv.d, xv.d);
+        xv.a = fma(nm[0], d0, xv.a); xv.b = fma(nm[1], d1, xv.b); xv.c = fma(nm[2], d2, xv.c); xv.d = fma(nm[3], d3, xv.d);
         v4store(x64 + off, xv);
-        dd[0] += dv.a * dv.a; dd[1] += dv.b * dv.b; dd[2] += dv.c * dv.c; dd[3] += dv.d * dv.d;
+        dd[0] = fma(d0, d0, dd[0]); dd[1] = fma(d1, d1, dd[1]); dd[2] = fma(d2, d2, dd[2]); dd[3] = fma(d3, d3, dd[3]);
         xx[0] += xv.a * xv.a; xx[1] += xv.b * xv.b; xx[2] += xv.c * xv.c; xx[3] += xv.d * xv.d;
     }
     const size_t np = gridDim.x;
-    block_sum4<256, T>(dd, partial + ((size_t)blk * np + blockIdx.x) * 4);
+    block_sum4<256, double>(dd, partial + ((size_t)blk * np + blockIdx.x) * 4);
     block_sum4<256, double>(xx, partial + (size_t)gridDim.y * np * 4 + ((size_t)blk * np + blockIdx.x) * 4);
 }
 void launch_axpy_mixed(double* x64, const double* norms, const float* d32, long long N, int nblk, double* partial, cudaStream_t s) {
