@@ -8,7 +8,7 @@ relative residual of 1e-10, and form the Rao-Blackwellised marginal variances.
 Metric: RHS x unknowns solved per second (whole job, all GPUs).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --stencil-timing c2|c5      # per-kernel stencil timings
+  python bench.py --stencil-timing c2|c3|c5   # per-kernel stencil timings
   python bench.py --config c1|c3|c4|c5        # the other workloads, one JSON line each
 
 N > 1 runs under torchrun, one process per GPU: each rank solves its own
@@ -279,23 +279,36 @@ def run_stencil_timing(which: str, iters: int) -> None:
     finest level (CUDA events inside the library, after warm-up), one JSON
     line per mode.  One further launch of each mode runs inside the NVTX
     range "stencil_<mode>" for a profiler filter.  Shapes: c2 = 2D Matern
-    512^2 with 65 right-hand sides; c5 = 2D space-time 128^2 x 64 with 33
-    (the marching kernel)."""
+    512^2 with 65 right-hand sides; c3 = Burgers 1024 x 1024 with 33,
+    linearised by one Gauss-Newton step so that the collocation rows are
+    active (apply and residual only: its preconditioner is the
+    time-stepping one, not Chebyshev smoothing; 1 B per RHS x unknown more for
+    the linearisation point); c5 = 2D space-time 128^2 x 64 with 33 (the
+    marching kernel)."""
     import torch
     from paper_2503_08343_gb300 import gmrf, workloads as W
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
         peak = float(json.load(f)["hbm_gbs"])
+    extra = 0.0
+    modes = ((0, "apply"), (1, "residual"), (2, "chebyshev"))
     if which == "c2":
         pr, ob = W.c2_matern(n=N_SIDE, m=M_OBS)
         k = NS + 1
+    elif which == "c3":
+        pr, ob = W.c3_burgers(nx=1024, nt=1024)
+        k, extra, modes = 33, 1.0, modes[:2]
     else:
         pr, ob = W.c5_st2d(n=128, nt=64, m=20000, seed=5)
         k = 33
     post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    if which == "c3":
+        import numpy as np
+        u, _ = post.solve_mean()
+        post.gauss_newton_step(u, np.zeros_like(u))
     slots = 4 * ((k + 3) // 4)
-    for mode, name in ((0, "apply"), (1, "residual"), (2, "chebyshev")):
+    for mode, name in modes:
         ms = post.time_stencil(mode, k, iters)
-        gbs = STENCIL_BYTES[mode] * slots * post.N / (ms * 1e-3) / 1e9
+        gbs = (STENCIL_BYTES[mode] + extra) * slots * post.N / (ms * 1e-3) / 1e9
         print(json.dumps({"workload": which, "kernel": name, "rhs": k, "slots": slots, "unknowns": post.N,
                           "ms": ms, "GB/s": gbs, "frac_of_measured_hbm": gbs / peak}), flush=True)
         torch.cuda.synchronize()
@@ -305,7 +318,59 @@ def run_stencil_timing(which: str, iters: int) -> None:
         torch.cuda.nvtx.range_pop()
 
 
-def run_config(which: str) -> None:
+def oracle_config_baseline(which: str) -> dict:
+    """The oracle as it stands, timed on the host cores on a bounded sample of
+    the configuration (the cpu_baseline leg of --config):
+      c1  the full workload: assemble, banded Cholesky, mean, 256 samples, RBMC;
+      c3  one relinearisation at 512 x 512 (at full size it takes minutes):
+          condition at the data-only mean, banded Cholesky of H, the
+          Gauss-Newton direction and mean + 32 samples with the same factor
+          (34 right-hand sides); per unknown, the smaller problem is the
+          faster one for the oracle (bandwidth 512 instead of 1024);
+      c4  8 of the 256 instances (every 32nd), mean + 16 samples + RBMC each;
+      c5  the 16^3 replica (full size, ~7e16 flops of banded Cholesky, is not
+          run): the exact-solve Hutchinson gradient with 32 probes."""
+    import numpy as np
+    from oracle import infer, linalg
+    from paper_2503_08343_gb300 import workloads as W
+    if which == "c1":
+        pr, ob = W.c1_st1d()
+        t = time.perf_counter()
+        oracle_step(pr, ob, W.DRAW_SEED["c1"], 256)
+        dt = time.perf_counter() - t
+        n = W.n_nodes(pr)
+        return {"value": 257 * n / dt, "unit": UNIT, "s": dt, "sample": "full workload (257 RHS x 4096)"}
+    if which == "c3":
+        pr, ob = W.c3_burgers(nx=512, nt=512)
+        post0 = infer.condition(pr, ob)
+        u = infer.posterior_mean(post0, linalg.cholesky(post0.Qpost))
+        t = time.perf_counter()
+        post = infer.condition(pr, ob, linearise_at=u)
+        L = linalg.cholesky(post.Qpost)
+        linalg.solve(L, post.Qpost @ u - post.b)
+        infer.posterior_mean(post, L)
+        infer.perturbation_samples(post, W.DRAW_SEED["c3"], range(32), L)
+        dt = time.perf_counter() - t
+        n = W.n_nodes(pr)
+        return {"value": 34 * n / dt, "unit": UNIT, "s": dt,
+                "sample": "one relinearisation at 512 x 512 (condition, Cholesky, direction, mean, 32 samples)"}
+    if which == "c4":
+        insts = W.c4_instances(count=256)[::32]
+        t = time.perf_counter()
+        for pr, ob in insts:
+            oracle_step(pr, ob, W.DRAW_SEED["c4"], 16)
+        dt = time.perf_counter() - t
+        units = 17 * sum(W.n_nodes(pr) for pr, _ in insts)
+        return {"value": units / dt, "unit": UNIT, "s": dt, "sample": f"{len(insts)} of the 256 instances"}
+    pr, ob = W.c5_st2d(n=16, nt=16, m=500)
+    t = time.perf_counter()
+    infer.hutchinson_grad(pr, ob, W.DRAW_SEED["c5"], 32)
+    dt = time.perf_counter() - t
+    return {"value": dt, "unit": "s per gradient", "s": dt,
+            "sample": "16^3 replica, 500 observations, 32 probes (full size not run: ~7e16 flops)"}
+
+
+def run_config(which: str, cpu: bool = True) -> None:
     """Wall time of the other workloads through the library API (warm; one
     GPU), one JSON line:
       c1  1D space-time 64 x 64, 50 observations: mean + 256 samples + RBMC
@@ -376,6 +441,8 @@ def run_config(which: str) -> None:
             dt = time.perf_counter() - t
         out.update({"unknowns": post.N, "rhs": 65, "s": dt, "refinements": info["refinements"],
                     "inner_iterations": info["inner_iterations"]})
+    if cpu:
+        out["cpu_baseline"] = {**oracle_config_baseline(which), "cores": cpu_cores(), "kind": "oracle"}
     print(json.dumps(out), flush=True)
 
 
@@ -386,13 +453,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--stencil-timing", choices=["c2", "c5"], default=None,
+    ap.add_argument("--stencil-timing", choices=["c2", "c3", "c5"], default=None,
                     help="time the stencil kernels alone (one JSON line per mode) instead of the step")
     ap.add_argument("--config", choices=["c1", "c3", "c4", "c5"], default=None,
                     help="time one of the other workloads through the library API (one JSON line)")
     args = ap.parse_args()
     if args.config:
-        run_config(args.config)
+        run_config(args.config, cpu=not args.no_cpu_baseline)
         return
     if args.stencil_timing:
         run_stencil_timing(args.stencil_timing, 50)
