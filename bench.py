@@ -151,6 +151,25 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself on one
+    rank.  NCCL reduces a device tensor, gloo a host one."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput: every rank processes units_per_rank in at most
+    `seconds` (the slowest rank's time)."""
+    return world * units_per_rank / seconds
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -202,13 +221,9 @@ def run_ours(args, rank, world):
     l1 = lib.gmrf_launch_count()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     units = (NS + 1) * N
-    value = world * units / (ms * 1e-3)
+    value = whole_job_value(units, ms * 1e-3, world)
     iters, refs = info.inner_iterations, info.refinements
 
     # end to end through the C ABI with host buffers: data in, mean and variances out
@@ -224,11 +239,8 @@ def run_ours(args, rank, world):
         gmrf._check(lib.gmrf_marginal_var(post.h, NS, seed, gmrf._ptr(mean_h), gmrf._ptr(var_h), None,
                                           C.byref(opts), C.byref(info)))
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ke2e
-    t = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * units / float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / ke2e, world)
+    e2e_value = whole_job_value(units, e2e_s, world)
 
     # roofline of the dominant kernel (the FP32 Chebyshev smoothing step on the
     # finest level; by the ncu launch list it takes the largest share of the
