@@ -27,6 +27,10 @@
  *    own handle and every posterior built on it are destroyed.
  *  - Handles own all device scratch.  Scratch for a batch of k right-hand
  *    sides is allocated at the first call that needs k and reused after.
+ *  - The first call in a process that draws normals (gmrf_sample,
+ *    gmrf_marginal_var, gmrf_normals, gmrf_condition's eigenvalue bound)
+ *    fills a 6 KB device table of the Box-Muller transform: one kernel and a
+ *    device synchronisation, once.  The library drives one GPU per process.
  */
 #ifndef GMRF_H
 #define GMRF_H
