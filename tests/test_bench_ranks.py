@@ -64,3 +64,14 @@ def test_single_rank_helpers_need_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.whole_job_value(100.0, 0.5, 1) == 200.0
+
+
+@pytest.mark.parametrize("which", ["c1", "c5"])
+def test_config_oracle_baselines_report_their_sample(which):
+    # the cpu_baseline leg of `bench.py --config` (no GPU): a bounded oracle
+    # sample with its throughput (c1) or seconds per gradient (c5)
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.oracle_config_baseline(which)
+    assert r["value"] > 0 and r["s"] > 0 and r["sample"]
+    assert r["unit"] == ("RHS*unknowns/s" if which == "c1" else "s per gradient")
