@@ -124,6 +124,9 @@ struct Workspace;
 
 constexpr double kP1DataShare = 0.5;
 constexpr int kRestrictTX = 32, kRestrictTY = 8;
+// fine nodes under one coarse node per axis that the plane restriction keeps
+// in registers (full coarsening n -> (n - 1)/2 + 1 with n >= 9 gives at most 5)
+constexpr int kRestrictMax = 8;
 
 struct Posterior {
     Prior* prior = nullptr;

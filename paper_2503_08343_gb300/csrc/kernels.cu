@@ -391,7 +391,6 @@ __device__ __forceinline__ T p1_weight(int dx, int dy, T wx, T wy) {
 // shared memory.  Each thread then sums its node: it keeps the (offset,
 // weight) data of its up to kRestrictMax fine columns in registers and walks
 // its fine rows, without branches (a zero weight adds zero).
-constexpr int kRestrictMax = 8;      // fine nodes under one coarse node per axis (2:1 coarsening: <= 7)
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_xy(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nt,

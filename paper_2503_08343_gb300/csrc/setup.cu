@@ -378,6 +378,8 @@ void build_transfer(Level& f, const Level& c) {
         for (int J = 0; J < m; ++J) {
             if (re[(size_t)J] < rs[(size_t)J]) { rs[(size_t)J] = 0; rc[(size_t)J] = 0; }
             else rc[(size_t)J] = re[(size_t)J] - rs[(size_t)J] + 1;
+            if (a < 2 && rc[(size_t)J] > kRestrictMax)
+                throw std::runtime_error("grid transfer: a coarse node collects more fine nodes than the restriction holds");
         }
         if (a < 2) {
             const int T = a == 0 ? kRestrictTX : kRestrictTY;
