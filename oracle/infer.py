@@ -292,15 +292,23 @@ def log_marginal_likelihood_grad(prior: dict, obs: dict) -> dict:
 def hutchinson_grad(prior: dict, obs: dict, seed: int, nprobe: int) -> dict:
     """The same gradient with both trace terms replaced by Hutchinson
     estimates on Rademacher probes v_s (Philox stream 2, sample s):
-    tr(X^-1 dX) ~ (1/S) sum_s (X^-1 v_s)^T dX v_s, exact solves.
-    parity unpinned by itself: it is pinned through its expectation, the
-    exact gradient, within 4 standard errors."""
+    tr(X^-1 dX) ~ (1/S) sum_s (X^-1 v_s)^T dX v_s, exact solves.  Pinned
+    through hutchinson_grad_probes: over all 2^N sign vectors of a tiny
+    problem the estimate is the exact gradient."""
+    N = condition(prior, obs).Q.shape[0]
+    V = np.stack([rng.rademacher(seed, s, N) for s in range(nprobe)])
+    return hutchinson_grad_probes(prior, obs, V)
+
+
+def hutchinson_grad_probes(prior: dict, obs: dict, V: np.ndarray) -> dict:
+    """The Hutchinson gradient on given probe vectors V [S][N]: the mean over
+    the probes of the gradient terms with tr(X^-1 dX) replaced by
+    v^T X^-1 dX v, and its standard error."""
     post = condition(prior, obs)
     Lq = linalg.cholesky(post.Q)
     Lp = linalg.cholesky(post.Qpost)
     mu = linalg.solve(Lp, post.b)
-    N = post.Q.shape[0]
-    V = np.stack([rng.rademacher(seed, s, N) for s in range(nprobe)])
+    nprobe = V.shape[0]
     Wq = linalg.solve(Lq, V.T).T
     Wp = linalg.solve(Lp, V.T).T
     A = post.A

@@ -252,6 +252,22 @@ def test_hutchinson_gradient_unbiased_within_stderr():
         assert abs(est[name] - exact[name]) <= 4.0 * se[name] + 1e-9, name
 
 
+def test_hutchinson_estimator_over_all_sign_vectors_is_exact():
+    # sum over all 2^N Rademacher vectors of v v^T is 2^N I exactly, so the
+    # estimator averaged over the full enumeration equals the exact gradient:
+    # a dropped term, a wrong sign or a transposed solve fails here
+    prior = W.prior_st1d(4, 3, 0.5, 0.05)
+    ob = W.point_obs(prior, 5, 0.2, lambda z: np.sin(3 * z[:, 0]) + z[:, 1], seed=4)
+    N = W.n_nodes(prior)
+    assert N == 12
+    k = np.arange(2 ** N)[:, None]
+    V = 1.0 - 2.0 * ((k >> np.arange(N)[None, :]) & 1)
+    est, _ = infer.hutchinson_grad_probes(prior, ob, V)
+    exact = infer.log_marginal_likelihood_grad(prior, ob)
+    for name in infer.HYPER:
+        assert abs(est[name] - exact[name]) <= 1e-9 * max(1.0, abs(exact[name])), (name, est[name], exact[name])
+
+
 def test_burgers_jacobian_matches_finite_differences():
     prior = W.prior_st1d(9, 6, 1.0, 0.01, x0=-1.0, x1=1.0)
     u = np.random.default_rng(2).normal(size=9 * 6)
