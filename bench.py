@@ -393,7 +393,10 @@ def run_config(which: str, cpu: bool = True) -> None:
       c4  256 uneven 2D instances: mean + 16 samples + RBMC each, one batch
           call on 8 host threads;
       c5  2D space-time 256^3 with 50 000 observations: log-likelihood
-          gradient with 32 probes (65 right-hand sides), rtol 1e-6."""
+          gradient with 32 probes (65 right-hand sides), rtol 1e-6;
+      c5plain  the same gradient by the batched FP32-refinement path and by
+          the plain path (each right-hand side alone, FP64 throughout, same
+          rtol and stopping rule), in one run: their time ratio (minutes)."""
     import numpy as np
     import torch
     from paper_2503_08343_gb300 import gmrf, workloads as W
@@ -449,10 +452,18 @@ def run_config(which: str, cpu: bool = True) -> None:
         post = gmrf.Posterior(gmrf.Prior(pr), ob)
         for rep in range(2):
             t = time.perf_counter()
-            _, _, _, info = post.loglik_grad(32, 1005, opts=gmrf.default_opts(rtol=1e-6))
+            _, g, _, info = post.loglik_grad(32, 1005, opts=gmrf.default_opts(rtol=1e-6))
             dt = time.perf_counter() - t
         out.update({"unknowns": post.N, "rhs": 65, "s": dt, "refinements": info["refinements"],
                     "inner_iterations": info["inner_iterations"]})
+        if which == "c5plain":
+            t = time.perf_counter()
+            _, gp, _, infop = post.loglik_grad(32, 1005, opts=gmrf.default_opts(rtol=1e-6, precision=1, batched=0,
+                                                                                 max_inner=2000))
+            dtp = time.perf_counter() - t
+            out.update({"plain_s": dtp, "ratio": dtp / dt, "plain_converged": infop["converged"],
+                        "max_rel_grad_diff": float(max(abs(a - b) / max(abs(b), 1e-300) for a, b in zip(g, gp)))})
+            cpu = False
     if cpu:
         out["cpu_baseline"] = {**oracle_config_baseline(which), "cores": cpu_cores(), "kind": "oracle"}
     print(json.dumps(out), flush=True)
@@ -467,7 +478,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stencil-timing", choices=["c2", "c3", "c5"], default=None,
                     help="time the stencil kernels alone (one JSON line per mode) instead of the step")
-    ap.add_argument("--config", choices=["c1", "c3", "c4", "c5"], default=None,
+    ap.add_argument("--config", choices=["c1", "c3", "c4", "c5", "c5plain"], default=None,
                     help="time one of the other workloads through the library API (one JSON line)")
     args = ap.parse_args()
     if args.config:
