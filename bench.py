@@ -128,9 +128,9 @@ def run_reference(args, rank, world):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# Chebyshev stencil on this workload, from one ncu capture
-# (profiles/stencil_chebyshev_matern512_rhs65.md), valid only for the kernel
-# sources it was taken on: SHA-256 of stencil.cu + common.cuh.
+# Chebyshev stencil on this workload, from one ncu capture of
+# `bench.py --stencil-timing c2`, valid only for the kernel sources it was
+# taken on: SHA-256 of stencil.cu + common.cuh.
 CHEB_TRAFFIC = {"sources_sha256": "68e8a29cb9a75845c613189a3f1156c9dd111d82ab5ed3b4a55737ca0d821fab", "bytes": 369288960}
 
 

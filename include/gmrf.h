@@ -213,7 +213,8 @@ gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t see
                              gmrf_solve_info* info);
 
 /* y = Q_u|y x in FP64 for a batch of k vectors x, y: [k][N].  Test hook for
- * the fused stencil. */
+ * the fused stencil.  GMRF_E_CUDA if a stencil CTA gave up its bounded wait
+ * for a staged input tile. */
 gmrf_status gmrf_apply_posterior(gmrf_posterior* post, int32_t k, const double* x, double* y);
 
 /* Allocation-free y = Q_u|y x for one vector (FP64), with x^T Q_u|y x.
@@ -228,11 +229,16 @@ gmrf_status gmrf_apply_posterior(gmrf_posterior* post, int32_t k, const double* 
  *  x, y: device memory, [N], N <= 262144 unknowns (a 512 x 512 grid); larger
  *        posteriors are rejected with GMRF_E_INVALID and a message naming the
  *        limit.  xQx: host or device, may be NULL.
- *  The first call on a device looks up the scratch address for that device
- *  (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  Set-up happens in gmrf_condition, on the posterior's device, for every
+ *  posterior within the limit: it looks up the scratch address
+ *  (cudaGetSymbolAddress), which loads the library module that holds the
+ *  array, and loads the kernels this call launches.  The call itself then
+ *  loads and allocates nothing.
  *  All calls share the one scratch array: calls that overlap on the GPU (other
  *  host threads, other streams) race and must be serialised by the caller.
- *  Runs on the posterior's stream and returns after it has finished. */
+ *  Runs on the posterior's stream and returns after it has finished.  If a
+ *  stencil CTA gave up its bounded wait for a staged input tile, the call
+ *  returns GMRF_E_CUDA (y and xQx are then incomplete). */
 gmrf_status gmrf_apply_posterior_noalloc(gmrf_posterior* post, const double* x, double* y, double* xQx);
 
 /* Normal draws of the sample stream: out[s][i] = z(seed, stream, sample0 + s, i)

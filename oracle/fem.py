@@ -2,7 +2,7 @@
 
 Test infrastructure (see the package docstring): float64, slow, explicit.
 
-Readings of the paper used here (each is listed in the design notes):
+Readings of the paper used here (where it is silent or ambiguous):
 
 * n nodes per axis include the boundary; h = (hi - lo) / (n - 1).  Time
   levels include t = 0, dt = T / (nt - 1).
@@ -167,7 +167,8 @@ def prior_root(prior: dict) -> sp.csr_matrix:
     """Square sparse root B with Q = B^T B.
 
     Spatial priors (Sec. 2.2): B = tau Ml^-1/2 Kc, Kc the constrained
-    K = kappa^2 Ml + nu S + Badv; boundary rows are e_k / eps.
+    K = kappa^2 Ml + S (Matern) or kappa^2 Ml + nu S + Badv (steady
+    advection-diffusion); boundary rows are e_k / eps.
 
     Space-time (Sec. 2.4, App. A), block rows in time:
       t = 0:  (tau0 / tau) Ml^-1/2 K0c, K0 = kappa0^2 Ml + S
@@ -181,7 +182,10 @@ def prior_root(prior: dict) -> sp.csr_matrix:
     sbnd = spatial_boundary(prior)
     inv_eps = 1.0 / math.sqrt(prior["eps2"])
     if kind in ("matern2d", "steady_advdiff2d"):
-        K = prior["kappa"] ** 2 * sp.diags(ml) + prior["nu"] * S + Badv
+        if kind == "matern2d":      # (kappa^2 - Laplacian): no diffusion or advection coefficient
+            K = prior["kappa"] ** 2 * sp.diags(ml) + S
+        else:
+            K = prior["kappa"] ** 2 * sp.diags(ml) + prior["nu"] * S + Badv
         Kc = constrain(K, sbnd)
         d = np.where(sbnd, inv_eps, prior["tau"] / np.sqrt(ml))
         return (sp.diags(d) @ Kc).tocsr()
@@ -208,6 +212,89 @@ def prior_root(prior: dict) -> sp.csr_matrix:
                 blocks[k][l] = sp.csr_matrix((Ns, Ns))
     B = sp.bmat(blocks, format="csr")
     return B
+
+
+def _zero_boundary(X: sp.spmatrix, bnd: np.ndarray) -> sp.csr_matrix:
+    """keep X keep: the derivative of constrain(X) (the unit diagonal it adds
+    on the boundary does not depend on any parameter)."""
+    keep = sp.diags((~bnd).astype(float))
+    return (keep @ X @ keep).tocsr()
+
+
+def prior_root_derivative(prior: dict, name: str) -> sp.csr_matrix:
+    """dB/dtheta of the root of prior_root, exactly, for theta in
+    (log_kappa, log_tau, c, nu) (c: the x velocity).  B is affine in
+    kappa^2, c and nu inside K or G, carries tau as a row scale (tau for the
+    spatial priors, 1/tau for space-time), and in the space-time t = 0 block
+    the unit-variance scale tau0(kappa0) as well; boundary rows e_k / eps do
+    not depend on any parameter.  The Matern kind has no c or nu.
+    Space-time priors: kappa means kappa0 (the initial block)."""
+    kind = prior["kind"]
+    S, ml, _, dim = spatial_mesh(prior)
+    sbnd = spatial_boundary(prior)
+    nx, ny, _ = prior["n"]
+    xs = axis_nodes(prior["lo"][0], prior["hi"][0], nx)
+    if dim == 1:
+        Bx = p1_1d(xs, 1.0)[2]
+    else:
+        Bx = p1_2d(xs, axis_nodes(prior["lo"][1], prior["hi"][1], ny), 1.0, 0.0)[2]
+    Ml = sp.diags(ml)
+    if kind in ("matern2d", "steady_advdiff2d"):
+        d = np.where(sbnd, 0.0, prior["tau"] / np.sqrt(ml))      # interior row scale
+        if name == "log_tau":
+            return (sp.diags(d) @ constrain(prior_root_K(prior), sbnd)).tocsr()
+        if name == "log_kappa":
+            dK = 2.0 * prior["kappa"] ** 2 * Ml
+        elif kind == "matern2d":
+            return sp.csr_matrix((len(ml), len(ml)))
+        elif name == "c":
+            dK = Bx
+        else:
+            dK = S
+        return (sp.diags(d) @ _zero_boundary(dK, sbnd)).tocsr()
+    nt = prior["n"][2]
+    Ns = len(ml)
+    dt = (prior["hi"][2] - prior["lo"][2]) / (nt - 1)
+    tau, k0 = prior["tau"], prior["kappa0"]
+    tau0 = matern_tau_unit(k0, dim)
+    d0 = np.where(sbnd, 0.0, (tau0 / tau) / np.sqrt(ml))
+    dk = np.where(sbnd, 0.0, 1.0 / (tau * math.sqrt(dt) * np.sqrt(ml)))
+    zero = sp.csr_matrix((Ns, Ns))
+    blocks = [[None] * nt for _ in range(nt)]
+    if name == "log_tau":
+        # every interior row scales as 1/tau
+        K0c = constrain(k0 ** 2 * Ml + S, sbnd)
+        Gc = constrain(Ml + dt * (prior["nu"] * S + spatial_mesh(prior)[2]), sbnd)
+        Mlc = sp.diags(np.where(sbnd, 0.0, ml))
+        blocks[0][0] = -(sp.diags(d0) @ K0c)
+        for k in range(1, nt):
+            blocks[k][k] = -(sp.diags(dk) @ Gc)
+            blocks[k][k - 1] = sp.diags(dk) @ Mlc
+    elif name == "log_kappa":
+        # d/dlog kappa0 of diag(d0) K0c: d0 ~ tau0(kappa0) with the exponent
+        # of matern_tau_unit (tau0 ~ kappa0^-3/2 in 1D, kappa0^-1 in 2D), and
+        # K0 = kappa0^2 Ml + S
+        dlog_tau0 = -1.5 if dim == 1 else -1.0
+        K0c = constrain(k0 ** 2 * Ml + S, sbnd)
+        blocks[0][0] = dlog_tau0 * (sp.diags(d0) @ K0c) + sp.diags(d0) @ _zero_boundary(2.0 * k0 ** 2 * Ml, sbnd)
+    else:
+        dG = dt * (Bx if name == "c" else S)
+        for k in range(1, nt):
+            blocks[k][k] = sp.diags(dk) @ _zero_boundary(dG, sbnd)
+    for k in range(nt):
+        for l in range(nt):
+            if blocks[k][l] is None and (k == l or k == l + 1):
+                blocks[k][l] = zero
+    return sp.bmat(blocks, format="csr")
+
+
+def prior_root_K(prior: dict) -> sp.spmatrix:
+    """The unconstrained operator K of a spatial prior (Matern:
+    kappa^2 Ml + S; steady advection-diffusion: kappa^2 Ml + nu S + Badv)."""
+    S, ml, Badv, _ = spatial_mesh(prior)
+    if prior["kind"] == "matern2d":
+        return prior["kappa"] ** 2 * sp.diags(ml) + S
+    return prior["kappa"] ** 2 * sp.diags(ml) + prior["nu"] * S + Badv
 
 
 def prior_precision(prior: dict) -> sp.csr_matrix:

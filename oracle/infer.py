@@ -241,21 +241,12 @@ def hyper_of(prior: dict, obs: dict) -> dict:
             "c": prior["cx"], "nu": prior["nu"]}
 
 
-def dQ_dtheta(prior: dict, name: str, h: float = 1e-6) -> sp.csr_matrix:
-    """Derivative of the prior precision with respect to one hyper-parameter.
-    Q = B^T B is a polynomial in (kappa^2, c, nu) entries and scales with
-    tau, so dQ = dB^T B + B^T dB with dB from a central difference of the
-    (entrywise polynomial) root; exact up to rounding for the linear
-    dependence of B on c and nu, O(h^2) for kappa and tau."""
-    base = hyper_of(prior, {"sigma": [1.0]})
-    tp = dict(base)
-    tm = dict(base)
-    tp[name] += h
-    tm[name] -= h
-    Bp = fem.prior_root(with_hyper(prior, {"y": [0.0], "sigma": [1.0]}, tp)[0])
-    Bm = fem.prior_root(with_hyper(prior, {"y": [0.0], "sigma": [1.0]}, tm)[0])
+def dQ_dtheta(prior: dict, name: str) -> sp.csr_matrix:
+    """Derivative of the prior precision Q = B^T B with respect to one
+    hyper-parameter: dQ = dB^T B + B^T dB with the exact root derivative
+    fem.prior_root_derivative."""
     B = fem.prior_root(prior)
-    dB = (Bp - Bm) / (2.0 * h)
+    dB = fem.prior_root_derivative(prior, name)
     return (dB.T @ B + B.T @ dB).tocsr()
 
 

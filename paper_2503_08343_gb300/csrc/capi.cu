@@ -302,6 +302,7 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
         P.d_ypoint = dev_alloc<double>((size_t)std::max<int64_t>(P.m, 1));
         if (P.m) GCK(cudaMemcpyAsync(P.d_ypoint, P.y_point.data(), sizeof(double) * P.m, cudaMemcpyHostToDevice, s));
         rebuild_bdata(P, s);
+        noalloc_prepare(P);
         GCK(cudaStreamSynchronize(s));
         *out = post;
     });
@@ -503,6 +504,7 @@ gmrf_status gmrf_marginal_var(gmrf_posterior* post, int32_t ns, uint64_t seed, d
         copy_out(var, W.t64, (size_t)N, s);
         if (stderr_) copy_out(stderr_, W.t64 + N, (size_t)N, s);
         GCK(cudaStreamSynchronize(s));
+        if (stencil_abort_take(s)) throw Error(GMRF_E_CUDA, "stencil kernel: staged input tile did not arrive (bounded wait)");
         rc = finish(ss, info, b.nrhs, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     });
     return st != GMRF_OK ? st : rc;
@@ -591,6 +593,7 @@ gmrf_status gmrf_apply_posterior(gmrf_posterior* post, int32_t k, const double* 
         launch_unpack(W.r64, W.t64, W.slot_b, N, nblk, s);
         copy_out(y, W.t64, (size_t)N * k, s);
         GCK(cudaStreamSynchronize(s));
+        if (stencil_abort_take(s)) throw Error(GMRF_E_CUDA, "stencil kernel: staged input tile did not arrive (bounded wait)");
     });
 }
 

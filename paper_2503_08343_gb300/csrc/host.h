@@ -74,6 +74,9 @@ Workspace& workspace(Posterior& P, int nblk);
 void workspace_free(Workspace* w);
 double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s);
 
+// noalloc.cu: loads what gmrf_apply_posterior_noalloc uses for this posterior
+void noalloc_prepare(const Posterior& P);
+
 // tsp.cu
 bool tsp_applicable(const Level& L, int nic);
 template <typename T>

@@ -178,6 +178,11 @@ __global__ void k_reduce(const double* __restrict__ partial, int nparts, double*
     block_sum4<256, double>(v, out + (size_t)blk * 4);
 }
 
+void reduce_prepare() {
+    cudaFuncAttributes fa;
+    cuda_ok(cudaFuncGetAttributes(&fa, k_reduce));
+}
+
 void launch_reduce(const double* partial, int nparts, int nblk, double* out, cudaStream_t s) {
     { k_reduce<<<nblk, 256, 0, s>>>(partial, nparts, out); note_launch(); }
 }

@@ -40,6 +40,14 @@ template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>
 // 2D space x time: the 2.5D-blocked kernel of stencil_march.cu (called by launch_stencil)
 template <typename T> int launch_march(int mode, const StencilArgs<T>& a, cudaStream_t s);
 int stencil_max_grid();
+int march_max_grid();
+// One-time set-up of the stencil instantiation that launch_stencil would use
+// for (geo, mode, a): function attributes and occupancy, which also load the
+// kernel's code on the current device.  Launches nothing.
+template <typename T> void stencil_prepare(int geo, int mode, const StencilArgs<T>& a);
+template <typename T> void march_prepare(int mode, const StencilArgs<T>& a);
+// loads the code of the partial-sum reduction kernel on the current device
+void reduce_prepare();
 // 1 if a stencil CTA gave up waiting for a staged input tile since the last
 // call (the flags of both stencil kernels are cleared)
 int stencil_abort_take(cudaStream_t s);

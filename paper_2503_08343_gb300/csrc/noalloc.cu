@@ -10,6 +10,7 @@
 // library's blocked four-wide layout and the per-CTA partial sums of
 // x^T Q_u|y x) lives in one file-scope device array of fixed size.  The call
 // makes no cudaMalloc, cudaFree or other allocating call.
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -38,6 +39,9 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 std::mutex g_mu;
 double* g_addr[1024] = {};
 
+// Device address of the scratch array on the current device (looked up once
+// per device; the first lookup loads this file's module, whose load is what
+// places the array in device memory).
 double* scratch_address() {
     int dev = 0;
     gmrf::cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
@@ -76,11 +80,34 @@ __global__ void k_unpack_one(const double* __restrict__ yb, double* __restrict__
     if (n < N) y[n] = yb[n * 4];
 }
 
+// The CTA-partial region holds the largest grid either stencil kernel launches.
+static_assert(kNoAllocMaxParts >= 4096, "partial-sum scratch below the stencil grid caps");
+
 }  // namespace
 
 namespace gmrf {
 void set_last_error(const std::string& msg);
+
+// Set-up of the allocation-free apply for one posterior, run by
+// gmrf_condition on the posterior's device: loads everything the entry point
+// will touch (this file's module with the scratch array, the pack/unpack
+// kernels, the FP64 apply instantiation of the posterior's stencil and the
+// reduction kernel), so that gmrf_apply_posterior_noalloc itself loads and
+// allocates nothing.  Posteriors above the size limit skip it.
+void noalloc_prepare(const Posterior& P) {
+    const Level& L = P.levels[0];
+    if (L.N > kNoAllocMaxN) return;
+    scratch_address();
+    cudaFuncAttributes fa;
+    cuda_check(cudaFuncGetAttributes(&fa, k_pack_one), "loading the allocation-free apply");
+    cuda_check(cudaFuncGetAttributes(&fa, k_unpack_one), "loading the allocation-free apply");
+    StencilArgs<double> a{};
+    a.L = L.view<double>();
+    a.nblk = 1;
+    stencil_prepare<double>(L.geo, M_APPLY, a);
+    reduce_prepare();
 }
+}  // namespace gmrf
 
 extern "C" gmrf_status gmrf_apply_posterior_noalloc(gmrf_posterior* post, const double* x, double* y, double* xQx) {
     try {
@@ -92,7 +119,7 @@ extern "C" gmrf_status gmrf_apply_posterior_noalloc(gmrf_posterior* post, const 
             throw gmrf::Error(GMRF_E_INVALID, "gmrf_apply_posterior_noalloc: " + std::to_string(N) +
                                                   " unknowns exceed the fixed scratch limit of " +
                                                   std::to_string(kNoAllocMaxN));
-        if (gmrf::stencil_max_grid() > kNoAllocMaxParts)
+        if (std::max(gmrf::stencil_max_grid(), gmrf::march_max_grid()) > kNoAllocMaxParts)
             throw gmrf::Error(GMRF_E_INVALID, "gmrf_apply_posterior_noalloc: partial-sum scratch too small");
         if (!is_device_memory(x) || !is_device_memory(y))
             throw gmrf::Error(GMRF_E_INVALID, "gmrf_apply_posterior_noalloc: x and y must be device memory");
@@ -112,12 +139,19 @@ extern "C" gmrf_status gmrf_apply_posterior_noalloc(gmrf_posterior* post, const 
         a.out = yb;
         a.partial = part;     // every CTA clears its own entries before use
         const int nparts = gmrf::launch_stencil<double>(L.geo, gmrf::M_APPLY, a, s);
+        if (nparts > kNoAllocMaxParts)
+            throw gmrf::Error(GMRF_E_CUDA, "gmrf_apply_posterior_noalloc: stencil grid beyond the partial-sum scratch");
         gmrf::launch_reduce(part, nparts, 1, sum, s);
         k_unpack_one<<<g, 256, 0, s>>>(yb, y, N);
         gmrf::note_launch();
         gmrf::cuda_check(cudaGetLastError(), "gmrf_apply_posterior_noalloc launch");
         if (xQx) gmrf::cuda_check(cudaMemcpyAsync(xQx, sum, sizeof(double), cudaMemcpyDefault, s), "copy x^T Q x");
         gmrf::cuda_check(cudaStreamSynchronize(s), "gmrf_apply_posterior_noalloc");
+        // a CTA that gave up its bounded wait for a staged tile left y and
+        // x^T Q x incomplete: report it (this also clears the flag, so the
+        // next solve does not inherit it)
+        if (gmrf::stencil_abort_take(s))
+            throw gmrf::Error(GMRF_E_CUDA, "gmrf_apply_posterior_noalloc: staged input tile did not arrive (bounded wait)");
         return GMRF_OK;
     } catch (const gmrf::Error& e) {
         gmrf::set_last_error(e.what());

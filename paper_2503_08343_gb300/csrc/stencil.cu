@@ -548,8 +548,10 @@ constexpr int kMaxStencilGrid = 4096;
 #define GMRF_STENCIL_KB 1
 #endif
 
+// dry: only the one-time set-up of this instantiation (function attributes,
+// occupancy query, which also loads the kernel's code), no launch
 template <int GEO, typename T, int MODE, int COL>
-static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
+static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false) {
     constexpr int NS = sizeof(T) == 8 ? 2 : GMRF_STENCIL_STAGES;
     constexpr int KB = sizeof(T) == 8 ? 1 : GMRF_STENCIL_KB;
     using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
@@ -591,6 +593,7 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
         }
         resident = sms * itp->second;
     }
+    if (dry) return 0;
     const long long ntiles = (long long)a.L.tiles_x * a.L.tiles_y * a.L.tiles_t;
     const long long nunits = ntiles * ((a.nblk + KB - 1) / KB);
     const int grid = (int)std::min<long long>(std::min<long long>(nunits, (long long)resident), kMaxStencilGrid);
@@ -604,18 +607,18 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s) {
 }
 
 template <int GEO, typename T, int MODE>
-static int launch_geo_mode(const StencilArgs<T>& a, cudaStream_t s) {
-    if (GEO == GEO_XT && a.L.col.kind == 1) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 1 : 0)>(a, s);
-    if (GEO == GEO_XT && a.L.col.kind == 2) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0)>(a, s);
-    return launch_one<GEO, T, MODE, 0>(a, s);
+static int launch_geo_mode(const StencilArgs<T>& a, cudaStream_t s, bool dry) {
+    if (GEO == GEO_XT && a.L.col.kind == 1) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 1 : 0)>(a, s, dry);
+    if (GEO == GEO_XT && a.L.col.kind == 2) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0)>(a, s, dry);
+    return launch_one<GEO, T, MODE, 0>(a, s, dry);
 }
 
 template <typename T, int GEO>
-static int launch_geo(int mode, const StencilArgs<T>& a, cudaStream_t s) {
-    if (mode == M_APPLY) return launch_geo_mode<GEO, T, M_APPLY>(a, s);
-    if (mode == M_RESID) return launch_geo_mode<GEO, T, M_RESID>(a, s);
-    if (mode == M_CHEB0) return launch_geo_mode<GEO, T, M_CHEB0>(a, s);
-    return launch_geo_mode<GEO, T, M_CHEB>(a, s);
+static int launch_geo(int mode, const StencilArgs<T>& a, cudaStream_t s, bool dry = false) {
+    if (mode == M_APPLY) return launch_geo_mode<GEO, T, M_APPLY>(a, s, dry);
+    if (mode == M_RESID) return launch_geo_mode<GEO, T, M_RESID>(a, s, dry);
+    if (mode == M_CHEB0) return launch_geo_mode<GEO, T, M_CHEB0>(a, s, dry);
+    return launch_geo_mode<GEO, T, M_CHEB>(a, s, dry);
 }
 
 template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s) {
@@ -625,6 +628,14 @@ template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>
 }
 template int launch_stencil<float>(int, int, const StencilArgs<float>&, cudaStream_t);
 template int launch_stencil<double>(int, int, const StencilArgs<double>&, cudaStream_t);
+
+template <typename T> void stencil_prepare(int geo, int mode, const StencilArgs<T>& a) {
+    if (geo == GEO_XY) launch_geo<T, GEO_XY>(mode, a, 0, true);
+    else if (geo == GEO_XT) launch_geo<T, GEO_XT>(mode, a, 0, true);
+    else march_prepare<T>(mode, a);
+}
+template void stencil_prepare<float>(int, int, const StencilArgs<float>&);
+template void stencil_prepare<double>(int, int, const StencilArgs<double>&);
 int stencil_max_grid() { return kMaxStencilGrid; }
 
 }  // namespace gmrf

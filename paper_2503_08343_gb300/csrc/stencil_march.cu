@@ -403,7 +403,7 @@ namespace {
 constexpr int kMaxMarchGrid = 4096;
 
 template <typename T, int MODE>
-int launch_march_mode(const StencilArgs<T>& a, cudaStream_t s) {
+int launch_march_mode(const StencilArgs<T>& a, cudaStream_t s, bool dry = false) {
     using SM = MarchSmem<T, MODE>;
     auto kern = k_march<T, MODE>;
     static int sms = 0, optin = 0, attr = 0;
@@ -440,6 +440,7 @@ int launch_march_mode(const StencilArgs<T>& a, cudaStream_t s) {
         }
         resident = sms * it->second;
     }
+    if (dry) return 0;
     if (a.L.col.kind != 0) throw std::runtime_error("space-time stencil: collocation rows are 1D space only");
     // split time into chunks when tiles x blocks alone do not fill the grid twice
     const long long tiles = (long long)a.L.tiles_x * a.L.tiles_y;
@@ -469,5 +470,15 @@ template <typename T> int launch_march(int mode, const StencilArgs<T>& a, cudaSt
 }
 template int launch_march<float>(int, const StencilArgs<float>&, cudaStream_t);
 template int launch_march<double>(int, const StencilArgs<double>&, cudaStream_t);
+
+template <typename T> void march_prepare(int mode, const StencilArgs<T>& a) {
+    if (mode == M_APPLY) launch_march_mode<T, M_APPLY>(a, 0, true);
+    else if (mode == M_RESID) launch_march_mode<T, M_RESID>(a, 0, true);
+    else if (mode == M_CHEB0) launch_march_mode<T, M_CHEB0>(a, 0, true);
+    else launch_march_mode<T, M_CHEB>(a, 0, true);
+}
+template void march_prepare<float>(int, const StencilArgs<float>&);
+template void march_prepare<double>(int, const StencilArgs<double>&);
+int march_max_grid() { return kMaxMarchGrid; }
 
 }  // namespace gmrf

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances (written here, derived in the design notes):
+Tolerances:
 * FP64 operator apply: relative 1e-12 (same arithmetic, different summation order);
 * posterior means and same-draw samples: relative 1e-6 (max-norm);
 * same-draw Rao-Blackwellised variances: relative 1e-3 (sample count stated per test);

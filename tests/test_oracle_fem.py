@@ -164,6 +164,89 @@ def test_matern_variance_tends_to_one_in_the_interior():
     assert abs(v - 1.0) < 0.03
 
 
+def _t0_block(prior):
+    """The t = 0 block of the space-time root and its precision B0^T B0."""
+    nx, ny, _ = prior["n"]
+    Ns = nx * ny
+    B0 = fem.prior_root(prior).tocsr()[:Ns, :Ns]
+    return (B0.T @ B0).tocsr()
+
+
+def test_initial_block_unit_variance_1d():
+    # tau0 of the space-time initial block (App. A Q1; unit-variance Matern
+    # alpha = 2 with kappa0, Lindgren et al. 2011: sigma^2 = 1/(4 kappa^3 tau^2)
+    # in 1D).  Wide grid: kappa0 h = 0.05 on [0, 4], centre 2 = 5.8 ranges
+    # (range sqrt(12)/kappa0) from the boundary.  The discrete variance there
+    # is given independently by the sine series of the Dirichlet
+    # tridiagonal Laplacian: Q1_int = (tau0^2/h) K^2, K = kappa0^2 h I + T/h,
+    # T = tridiag(-1, 2, -1) with eigenvalues 4 sin^2(pi k / (2(n-1))) and
+    # normalised eigenvectors sqrt(2/(n-1)) sin(pi k j / (n-1)).  Measured:
+    # 1.00031 (discretisation error 3e-4); a kappa^3 <-> kappa^2 slip or a
+    # wrong constant moves it by a factor of kappa0 or more.
+    nx, k0 = 801, 10.0
+    prior = W.prior_st1d(nx, 2, 0.5, 0.01, kappa0=k0, x0=0.0, x1=4.0)
+    var = linalg.takahashi_diag(linalg.cholesky(_t0_block(prior)))
+    c = (nx - 1) // 2
+    h = 4.0 / (nx - 1)
+    k = np.arange(1, nx - 1)
+    mu = k0 * k0 * h + 4.0 * np.sin(np.pi * k / (2 * (nx - 1))) ** 2 / h
+    series_tau1 = h * np.sum((2.0 / (nx - 1)) * np.sin(np.pi * k * c / (nx - 1)) ** 2 / mu ** 2)
+    tau0 = fem.matern_tau_unit(k0, 1)
+    assert var[c] == pytest.approx(series_tau1 / tau0 ** 2, rel=1e-9)
+    assert abs(var[c] - 1.0) < 1e-3
+
+
+def test_initial_block_unit_variance_2d():
+    # as above in 2D (sigma^2 = 1/(4 pi kappa^2 tau^2)): kappa0 h = 0.05 on
+    # [0, 1.7]^2, centre 3 ranges (sqrt(8)/kappa0) from the boundary; the
+    # centre variance of the assembled t = 0 block by one sparse solve
+    # e_c^T Q1^-1 e_c, against the Dirichlet 5-point sine series and against
+    # the continuum value 1.  Measured: 1.0023.
+    n, k0, side = 341, 10.0, 1.7
+    prior = W.prior_st2d(n, 2, 0.5, 0.0, 0.01, k0)
+    prior["hi"] = (side, side, 1.0)
+    Q1 = _t0_block(prior).tocsc()
+    c = (n - 1) // 2
+    e = np.zeros(n * n)
+    e[c * n + c] = 1.0
+    import scipy.sparse.linalg as spl
+    v = spl.spsolve(Q1, e)[c * n + c]
+    h = side / (n - 1)
+    j = np.arange(1, n - 1)
+    lam1 = 4.0 * np.sin(j * np.pi / (2 * (n - 1))) ** 2
+    lam = k0 * k0 * h * h + lam1[:, None] + lam1[None, :]
+    sj = np.sin(j * np.pi * c / (n - 1))
+    v2 = (2.0 / (n - 1)) ** 2 * (sj[:, None] * sj[None, :]) ** 2
+    series_tau1 = h * h * np.sum(v2 / lam ** 2)
+    tau0 = fem.matern_tau_unit(k0, 2)
+    assert v == pytest.approx(series_tau1 / tau0 ** 2, rel=1e-8)
+    assert abs(v - 1.0) < 5e-3
+
+
+@pytest.mark.parametrize("prior", [W.prior_st2d(6, 5, 0.5, 0.2, 0.03, 7.0), W.prior_st1d(9, 6, 0.5, 0.05),
+                                   W.prior_matern2d(8, 5.0), W.prior_steady_advdiff2d(8, 5.0, 0.05, 1.2)],
+                         ids=lambda p: p["kind"])
+def test_root_derivative_matches_central_differences(prior):
+    # the exact dB/dtheta against central differences of the assembled root
+    # (h = 1e-5: truncation O(h^2) and rounding ~1e-16/h, far below 1e-8)
+    from oracle import infer
+    th = infer.hyper_of(prior, {"sigma": [1.0]})
+    for name in ("log_kappa", "log_tau", "c", "nu"):
+        h = 1e-5
+        tp, tm = dict(th), dict(th)
+        tp[name] += h
+        tm[name] -= h
+        dummy = {"y": [0.0], "sigma": [1.0]}
+        Bp = fem.prior_root(infer.with_hyper(prior, dummy, tp)[0])
+        Bm = fem.prior_root(infer.with_hyper(prior, dummy, tm)[0])
+        fd = ((Bp - Bm) / (2 * h)).toarray()
+        ex = fem.prior_root_derivative(prior, name).toarray()
+        if prior["kind"] == "matern2d" and name in ("c", "nu"):
+            assert not ex.any() and not fd.any()
+            continue
+        assert np.abs(fd - ex).max() <= 1e-8 * np.abs(ex).max(), name
+
+
 def test_takahashi_matches_dense_inverse_on_random_band():
     rng = np.random.default_rng(0)
     N, bw = 40, 5

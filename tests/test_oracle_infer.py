@@ -5,6 +5,7 @@ the Rao-Blackwellised estimator in expectation, Philox statistics, the
 Gaussian marginal likelihood with finite-difference gradients, and the
 Burgers Jacobian by finite differences."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -197,6 +198,18 @@ def test_philox_streams_statistics():
     assert np.array_equal(rng.normals(1234, 0, 3, 11), z[:11])
     v = rng.rademacher(9, 2, 100000)
     assert set(np.unique(v)) == {-1.0, 1.0} and abs(v.mean()) < 0.02
+
+
+def test_philox_known_answer_vectors():
+    # published known-answer vectors (tests/golden/philox4x32_10_kat.txt):
+    # a wrong multiplier, round constant, word order or round count fails
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(w, 16) for w in r]
+        out = rng.philox4x32_10(*v[:6])
+        assert [int(o) for o in out] == v[6:]
 
 
 def test_philox_is_a_bijection_on_counters():
