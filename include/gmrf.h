@@ -254,6 +254,23 @@ gmrf_status gmrf_normals(uint64_t seed, int32_t stream, int32_t sample0, int32_t
  * (d' = c1 d + c2 D^-1 (b - Q_u|y x), x' = x + d'). */
 gmrf_status gmrf_time_stencil(gmrf_posterior* post, int32_t kernel, int32_t k, int32_t iters, double* ms);
 
+/* One launch of the fused stencil kernel on multigrid level `level`
+ * (0 = finest) in FP32 (precision 0) or FP64 (1), for k right-hand sides.
+ * Test hook for the kernel modes the solver uses (the FP32 ones only
+ * precondition, so wrong arithmetic there would show as slower convergence,
+ * not as wrong results).  Inputs x, b, d and outputs out, out2 are [k][N_l]
+ * FP64, host or device (inputs are rounded to the kernel precision); N_l the
+ * level's unknowns; D the diagonal of the level's operator Q_l:
+ *  mode 0 apply:      out = Q_l x,                        dots = x^T out
+ *  mode 1 residual:   out = b - Q_l x,                    dots = |out|^2
+ *  mode 2 Chebyshev:  out2 = c1 d + c2 D^-1 (b - Q_l x),  out = x + out2,
+ *                     dots = b^T out (d may be NULL: taken as 0)
+ *  mode 3 Chebyshev from zero: x1 = c0 D^-1 b, then mode 2 with x = d = x1.
+ * dots: [k] host.  Allocates its own scratch. */
+gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t precision, int32_t mode, int32_t k,
+                              const double* x, const double* b, const double* d, double c0, double c1, double c2,
+                              double* out, double* out2, double* dots);
+
 /* Number of kernels this library has launched in the process so far
  * (kernels inside replayed CUDA graphs included). */
 uint64_t gmrf_launch_count(void);

@@ -617,6 +617,45 @@ gmrf_status gmrf_time_stencil(gmrf_posterior* post, int32_t kernel, int32_t k, i
     });
 }
 
+gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t precision, int32_t mode, int32_t k,
+                              const double* x, const double* b, const double* d, double c0, double c1, double c2,
+                              double* out, double* out2, double* dots) {
+    return guard([&] {
+        require(post && k >= 1 && out && dots, "bad argument");
+        require(level >= 0 && level < (int32_t)post->impl.levels.size(), "level out of range");
+        require(precision == 0 || precision == 1, "precision must be 0 or 1");
+        require(mode >= 0 && mode <= 3, "mode must be 0..3");
+        require(mode == 3 || x, "x is required");
+        require(mode == 0 || b, "b is required");
+        require(mode < 2 || out2, "out2 is required for the Chebyshev modes");
+        enter(post->prior);
+        Posterior& P = post->impl;
+        const cudaStream_t s = P.prior->stream;
+        const long long N = P.levels[(size_t)level].N;
+        const size_t n = (size_t)N * k;
+        double* buf = dev_alloc<double>(5 * n);
+        const double* src[3] = {x, b, d};
+        const double* din[3] = {nullptr, nullptr, nullptr};
+        for (int i = 0; i < 3; ++i)
+            if (src[i]) {
+                copy_in(buf + i * n, src[i], n, s);
+                din[i] = buf + i * n;
+            }
+        try {
+            stencil_step(P, level, precision, mode, k, din[0], mode == 0 ? nullptr : din[1], mode == 2 ? din[2] : nullptr,
+                         c0, c1, c2, buf + 3 * n, mode >= 2 ? buf + 4 * n : nullptr, dots, s);
+            copy_out(out, buf + 3 * n, n, s);
+            if (mode >= 2) copy_out(out2, buf + 4 * n, n, s);
+            GCK(cudaStreamSynchronize(s));
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            dev_free(buf);
+            throw;
+        }
+        dev_free(buf);
+    });
+}
+
 uint64_t gmrf_launch_count(void) { return launch_count(); }
 
 gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* delta_prev, double* newton_decrement,

@@ -153,9 +153,11 @@ __device__ __forceinline__ double philox_rademacher(uint64_t seed, uint32_t samp
 // ---------------------------------------------------------------------------
 // Block reduction of four partial sums (one per right-hand side of the
 // block) over a 256-thread CTA; threads 0..3 write the totals as FP64.
-// Every thread of the CTA must call it.  FP32
-// kernels accumulate in FP32 inside the CTA (the FP64 pipe of GB300 is
-// narrow) and widen the CTA totals.
+// Every thread of the CTA must call it.  Each thread's own partial stays in
+// the kernel's precision (an FP32 kernel sums a few dozen FP32 terms per
+// thread: the FP64 pipe of GB300 is too narrow for one FP64 add per node);
+// everything above it -- the warp shuffles, the sum over warps and the sum
+// over CTAs -- runs in FP64.
 
 template <typename A> __device__ __forceinline__ A warp_sum(A v) {
 #pragma unroll
@@ -165,19 +167,20 @@ template <typename A> __device__ __forceinline__ A warp_sum(A v) {
 
 template <int NT, typename A>
 __device__ __forceinline__ void block_sum4(A v[4], double* out /* 4 doubles, global */) {
-    __shared__ A red[NT / 32][4];
+    __shared__ double red[NT / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double w[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = warp_sum(v[i]);
+    for (int i = 0; i < 4; ++i) w[i] = warp_sum((double)v[i]);
     if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) red[warp][i] = v[i];
+        for (int i = 0; i < 4; ++i) red[warp][i] = w[i];
     }
     __syncthreads();
     if (threadIdx.x < 4) {
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < NT / 32; ++w) s += (double)red[w][threadIdx.x];
+        for (int k = 0; k < NT / 32; ++k) s += red[k][threadIdx.x];
         out[threadIdx.x] = s;
     }
     __syncthreads();   // the scratch may be reused by the next call

@@ -73,6 +73,12 @@ void apply64(Posterior& P, int nblk, const double* x64, double* y64, cudaStream_
 Workspace& workspace(Posterior& P, int nblk);
 void workspace_free(Workspace* w);
 double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s);
+// One launch of the fused stencil on `level` in FP32 (prec 0) or FP64 (1):
+// device FP64 [k][N_level] inputs x (unused by mode 3), b (modes 1-3),
+// d (mode 2, may be null) and outputs out, out2 (modes 2-3); dots[k] (host)
+// receives the kernel's per-RHS dot products.
+void stencil_step(Posterior& P, int level, int prec, int mode, int k, const double* x, const double* b, const double* d,
+                  double c0, double c1, double c2, double* out, double* out2, double* dots, cudaStream_t s);
 
 // noalloc.cu: loads what gmrf_apply_posterior_noalloc uses for this posterior
 void noalloc_prepare(const Posterior& P);

@@ -1088,6 +1088,17 @@ namespace gmrf {
 // small helpers of the solver driver
 
 template <typename T>
+__global__ void k_widen(const T* __restrict__ in, double* __restrict__ out, long long n) {
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
+}
+template <typename T> void launch_widen(const T* in, double* out, long long n, cudaStream_t s) {
+    { k_widen<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n); note_launch(); }
+}
+template void launch_widen<float>(const float*, double*, long long, cudaStream_t);
+template void launch_widen<double>(const double*, double*, long long, cudaStream_t);
+
+template <typename T>
 __global__ void k_norm2(const T* __restrict__ v, long long N, double* __restrict__ partial, int nparts) {
     const int blk = blockIdx.y;
     T dot[4] = {T(0), T(0), T(0), T(0)};

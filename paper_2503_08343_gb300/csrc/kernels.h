@@ -126,6 +126,7 @@ void launch_max_share(const double* prior, const double* total, long long N, uns
 void launch_finish_diag(const double* diag, float* dinv32, double* dinv64, long long N, cudaStream_t s);
 void launch_normals(uint64_t seed, int stream, int sample0, int count, long long n, double* out, cudaStream_t s);
 template <typename T> void launch_cast(const double* in, T* out, long long n, cudaStream_t s);
+template <typename T> void launch_widen(const T* in, double* out, long long n, cudaStream_t s);
 void launch_rademacher_fill(uint64_t seed, const int32_t* slot_sample, double* b64, long long N, int nblk, cudaStream_t s);
 void launch_dot_blocked(const double* a, const double* b, long long N, int nblk, double* partial, int nparts, cudaStream_t s);
 

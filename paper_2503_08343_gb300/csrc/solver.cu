@@ -584,4 +584,73 @@ double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s)
     return ms / iters;
 }
 
+
+template <typename T>
+static void stencil_step_t(Posterior& P, int level, int mode, int k, const double* x, const double* b, const double* d,
+                           double c0, double c1, double c2, double* out, double* out2, double* dots, cudaStream_t s) {
+    Level& L = P.levels[(size_t)level];
+    const long long N = L.N;
+    const int nblk = (k + 3) / 4;
+    const size_t nv = (size_t)nblk * N * 4;
+    std::vector<int32_t> rows((size_t)nblk * 4, -1);
+    for (int i = 0; i < k; ++i) rows[(size_t)i] = i;
+    int32_t* drows = dev_alloc<int32_t>(rows.size());
+    double* b64 = dev_alloc<double>(nv);
+    T* v[5];
+    for (int i = 0; i < 5; ++i) v[i] = dev_alloc<T>(nv);   // x, b, d, out, out2 (blocked)
+    const int parts = std::max(stencil_max_grid(), march_max_grid());
+    double* part = dev_alloc<double>((size_t)nblk * parts * 4);
+    double* red = dev_alloc<double>((size_t)nblk * 4);
+    GCK(cudaMemcpyAsync(drows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s));
+    const double* src[3] = {x, b, d};
+    for (int i = 0; i < 3; ++i) {
+        GCK(cudaMemsetAsync(v[i], 0, sizeof(T) * nv, s));
+        if (!src[i]) continue;
+        if (sizeof(T) == 8) {
+            launch_pack(src[i], reinterpret_cast<double*>(v[i]), drows, N, nblk, s);
+        } else {
+            launch_pack(src[i], b64, drows, N, nblk, s);
+            launch_cast<T>(b64, v[i], (long long)nv, s);
+        }
+    }
+    StencilArgs<T> a{};
+    a.L = L.view<T>();
+    a.nblk = nblk;
+    a.x = v[0];
+    if (mode != M_APPLY) a.b = v[1];
+    if (mode == M_CHEB && d) a.d = v[2];
+    a.dinv = sizeof(T) == 8 ? reinterpret_cast<const T*>(L.d_dinv64) : reinterpret_cast<const T*>(L.d_dinv32);
+    a.out = v[3];
+    a.out2 = v[4];
+    a.c0 = (T)c0;
+    a.c1 = (T)c1;
+    a.c2 = (T)c2;
+    a.partial = part;
+    const int nparts = launch_stencil<T>(L.geo, mode, a, s);
+    launch_reduce(part, nparts, nblk, red, s);
+    double* dst[2] = {out, out2};
+    for (int i = 0; i < 2; ++i) {
+        if (!dst[i]) continue;
+        launch_widen<T>(v[3 + i], b64, (long long)nv, s);
+        launch_unpack(b64, dst[i], drows, N, nblk, s);
+    }
+    std::vector<double> h((size_t)nblk * 4);
+    GCK(cudaMemcpyAsync(h.data(), red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    GCK(cudaStreamSynchronize(s));
+    const int aborted = stencil_abort_take(s);
+    for (int i = 0; i < k; ++i) dots[i] = h[(size_t)i];
+    dev_free(drows);
+    dev_free(b64);
+    for (int i = 0; i < 5; ++i) dev_free(v[i]);
+    dev_free(part);
+    dev_free(red);
+    if (aborted) throw Error(GMRF_E_CUDA, "stencil kernel: staged input tile did not arrive (bounded wait)");
+}
+
+void stencil_step(Posterior& P, int level, int prec, int mode, int k, const double* x, const double* b, const double* d,
+                  double c0, double c1, double c2, double* out, double* out2, double* dots, cudaStream_t s) {
+    if (prec == 1) stencil_step_t<double>(P, level, mode, k, x, b, d, c0, c1, c2, out, out2, dots, s);
+    else stencil_step_t<float>(P, level, mode, k, x, b, d, c0, c1, c2, out, out2, dots, s);
+}
+
 }  // namespace gmrf

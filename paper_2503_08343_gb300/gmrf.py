@@ -91,6 +91,7 @@ def load(build_if_missing: bool = False):
                                           C.POINTER(SolveOpts), C.POINTER(SolveInfo), I32]),
         "gmrf_normals": (I32, [U64, I32, I32, I32, I64, P]),
         "gmrf_time_stencil": (I32, [P, I32, I32, I32, DP]),
+        "gmrf_stencil_step": (I32, [P, I32, I32, I32, I32, P, P, P, D, D, D, P, P, DP]),
         "gmrf_level_info": (I32, [P, I32, C.POINTER(C.c_int32), DP]),
         "gmrf_transfer_info": (I32, [P, C.POINTER(C.c_int32), DP]),
         "gmrf_num_unknowns": (I64, [P]),
@@ -257,6 +258,21 @@ class Posterior:
         y = np.empty_like(x)
         _check(load().gmrf_apply_posterior(self.h, x.shape[0], _ptr(x), _ptr(y)))
         return y
+
+    def stencil_step(self, mode, x=None, b=None, d=None, level=0, precision=0, c0=0.0, c1=0.0, c2=0.0):
+        """One launch of the fused stencil kernel (gmrf_stencil_step): mode 0
+        apply, 1 residual, 2 Chebyshev step, 3 Chebyshev from zero; inputs
+        [k][N_level].  Returns (out, out2 or None, dots)."""
+        ref = next(v for v in (x, b) if v is not None)
+        k, n = np.atleast_2d(ref).shape
+        prep = lambda v: None if v is None else np.ascontiguousarray(np.atleast_2d(v), dtype=np.float64)
+        x, b, d = prep(x), prep(b), prep(d)
+        out = np.empty((k, n))
+        out2 = np.empty((k, n)) if mode >= 2 else None
+        dots = np.empty(k)
+        _check(load().gmrf_stencil_step(self.h, level, precision, mode, k, _ptr(x), _ptr(b), _ptr(d),
+                                        c0, c1, c2, _ptr(out), _ptr(out2), _dptr(dots)))
+        return out, out2, dots
 
     def level_info(self):
         """[(nx, ny, nt, chebyshev lambda_max bound)] from finest to coarsest."""

@@ -52,6 +52,28 @@ def test_gauss_newton_iterates_match_the_oracle(n, nt, nu):
         u_or = u_next
 
 
+@pytest.mark.slow
+def test_gauss_newton_step_at_512_squared_matches_the_oracle():
+    # one relinearisation of the Burgers workload at 512 x 512 (262 144
+    # unknowns; the oracle's banded Cholesky of H takes seconds): the first
+    # step from the data-only mean, with the C3 noise levels (collocation and
+    # initial condition sigma = 1e-6, nu = 0.01)
+    pr, ob = W.c3_burgers(nx=512, nt=512, m=200, seed=3)
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    u0_gpu, info = post.solve_mean()
+    assert info["converged"] == 1
+    u0 = infer.posterior_mean(infer.condition(pr, ob))
+    assert _rel(u0_gpu, u0) < 1e-6
+    u1_or, d_or, alpha_or, dec_or = infer.gauss_newton_step(pr, ob, u0)
+    u_gpu, d_gpu = u0.copy(), np.zeros_like(u0)
+    dec, alpha, info = post.gauss_newton_step(u_gpu, d_gpu)
+    assert info["converged"] == 1
+    assert alpha == alpha_or
+    assert dec == pytest.approx(dec_or, rel=1e-6)
+    assert np.max(np.abs(d_gpu - d_or)) < 1e-6 * np.max(np.abs(u0))
+    assert _rel(u_gpu, u1_or) < 1e-6
+
+
 def test_laplace_samples_at_the_mode_match_the_oracle():
     pr, ob = W.c3_burgers(nx=65, nt=33, m=60, seed=3, nu=0.05)
     post = gmrf.Posterior(gmrf.Prior(pr), ob)

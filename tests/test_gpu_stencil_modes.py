@@ -1,0 +1,180 @@
+"""Every mode of the fused stencil kernels, FP32 and FP64, element by element
+against the oracle's assembled operator (gmrf_stencil_step through the C ABI).
+
+In the FP32-inner / FP64-refinement solver the FP32 stencil modes only
+precondition: a wrong FP32 apply or Chebyshev step would still give correct
+means, just after more iterations.  So each mode is checked here directly:
+
+  apply             out = Q x
+  residual          out = b - Q x
+  Chebyshev         out2 = c1 d + c2 D^-1 (b - Q x),  out = x + out2
+  Chebyshev-from-0  x1 = c0 D^-1 b, then the Chebyshev step with x = d = x1
+
+with Q the level's posterior precision (Sec. 3.1: Q + A^T Q_eps A, collocation
+rows included) and D its diagonal.  The reference is computed in FP64 from the
+inputs as the kernel sees them (rounded to FP32 for the FP32 kernels).  The
+tolerance is the forward-error bound of the arithmetic, element by element:
+|out - ref| <= gamma * m, where m is the same expression evaluated on
+absolute values (|B|^T |B| |x| + |A|^T Q_eps |A| |x| for Q x, since the kernel
+forms B^T (B x) and the observation term) and gamma = 64 u (u = 2^-24 in FP32,
+2^-53 in FP64): a few dozen roundings on each path.  The per-RHS dot products
+the kernel also returns (x^T Q x, |r|^2, b^T x_new) get gamma_dot = 128 u on
+the sum of absolute terms (each thread adds a few dozen FP32 terms before
+the FP64 reduction).
+
+Geometries: the tiled 2D and 1D space-time kernel, the marching 2D space-time
+kernel, ragged tiles, dense observations, linear and linearised Burgers
+collocation rows, the full-size 2D Matern workload (512^2, 10 000
+observations, 65 right-hand sides) and the first coarse multigrid level
+(rediscretised prior with the point data interpolated on the coarse mesh).
+"""
+import zlib
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import infer
+from paper_2503_08343_gb300 import gmrf
+from paper_2503_08343_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+U = {0: 2.0 ** -24, 1: 2.0 ** -53}
+C0, C1, C2 = 0.37, 0.61, 0.83
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2503_08343_gb300 import build
+    build.build()
+    return gmrf.load()
+
+
+def _linear_colloc():
+    pr, ob = W.c1_st1d(nx=37, nt=21, m=30, seed=5)
+    f = np.random.default_rng(3).normal(size=(37 - 2) * (21 - 1))
+    return pr, dict(ob, colloc_sigma=0.05, colloc_c=0.5, burgers_nu=0.01, colloc_f=f)
+
+
+CASES = {
+    "matern45_ragged": (lambda: W.c2_matern(n=45, m=150, seed=7, kappa=8.0), 5),
+    "steady_advdiff40": (lambda: (W.prior_steady_advdiff2d(40, 10.0, nu=0.05, c=1.0),
+                                  W.node_obs(W.prior_steady_advdiff2d(40, 10.0, nu=0.05, c=1.0), 0.03, 0.05,
+                                             W.fourier_modes(np.random.default_rng(1), 8, 2, 4), seed=3)), 4),
+    "st1d_37x21_ragged": (lambda: W.c1_st1d(nx=37, nt=21, m=30, seed=5), 6),
+    "st1d_linear_collocation": (_linear_colloc, 3),
+    "st2d_20x20x12_march": (lambda: W.c5_st2d(n=20, nt=12, m=300, seed=5), 3),
+    "st2d_24x24x10_dense_obs": (lambda: W.c5_st2d(n=24, nt=10, m=5000, seed=3), 2),
+}
+
+
+def _bound_matrix(post):
+    """|B|^T |B| + |A|^T Q_eps |A|: the absolute-value form of how the
+    kernel evaluates Q (the stacked root twice, then the observation rows)."""
+    aB = abs(post.B)
+    aA = abs(post.A)
+    return (aB.T @ aB + aA.T @ sp.diags(post.rinv) @ aA).tocsr()
+
+
+def _check_modes(post_gpu, post_o, k, level, prec, seed, modes=(0, 1, 2, 3)):
+    rng = np.random.default_rng(seed)
+    N = post_o.Q.shape[0]
+    rnd = lambda: rng.normal(size=(k, N))
+    x, b, d = rnd(), rnd(), rnd()
+    if prec == 0:
+        f32 = lambda v: v.astype(np.float32).astype(np.float64)
+        x, b, d = f32(x), f32(b), f32(d)
+        c0, c1, c2 = (float(np.float32(c)) for c in (C0, C1, C2))
+    else:
+        c0, c1, c2 = C0, C1, C2
+    Q = post_o.Qpost
+    M = _bound_matrix(post_o)
+    dinv = 1.0 / Q.diagonal()
+    g, gd = 64 * U[prec], 128 * U[prec]
+    Qx = (Q @ x.T).T
+    Mx = (M @ np.abs(x).T).T
+
+    def close(got, want, bound, what):
+        err = np.abs(got - want)
+        bad = err > g * bound + 1e-300
+        assert not bad.any(), (what, float((err / np.maximum(bound, 1e-300)).max()), int(bad.sum()))
+
+    if 0 in modes:
+        out, _, dots = post_gpu.stencil_step(0, x=x, level=level, precision=prec)
+        close(out, Qx, Mx, "apply")
+        assert np.all(np.abs(dots - np.sum(x * Qx, axis=1)) <= gd * np.sum(np.abs(x) * Mx, axis=1))
+    if 1 in modes:
+        out, _, dots = post_gpu.stencil_step(1, x=x, b=b, level=level, precision=prec)
+        r = b - Qx
+        br = np.abs(b) + Mx
+        close(out, r, br, "residual")
+        assert np.all(np.abs(dots - np.sum(r * r, axis=1)) <= gd * np.sum(2 * (np.abs(r) + g * br) * br, axis=1))
+    if 2 in modes:
+        out, out2, dots = post_gpu.stencil_step(2, x=x, b=b, d=d, level=level, precision=prec, c1=c1, c2=c2)
+        dn = c1 * d + c2 * dinv * (b - Qx)
+        bdn = abs(c1) * np.abs(d) + abs(c2) * dinv * (np.abs(b) + Mx)
+        close(out2, dn, bdn, "chebyshev d")
+        close(out, x + dn, np.abs(x) + 2 * bdn, "chebyshev x")
+        assert np.all(np.abs(dots - np.sum(b * (x + dn), axis=1))
+                      <= gd * np.sum(np.abs(b) * (np.abs(x) + 2 * bdn), axis=1))
+    if 3 in modes:
+        out, out2, dots = post_gpu.stencil_step(3, b=b, level=level, precision=prec, c0=c0, c1=c1, c2=c2)
+        x1 = c0 * dinv * b
+        ax1 = np.abs(x1)
+        Qx1 = (Q @ x1.T).T
+        dn = c1 * x1 + c2 * dinv * (b - Qx1)
+        bdn = abs(c1) * ax1 + abs(c2) * dinv * (np.abs(b) + (M @ ax1.T).T)
+        close(out2, dn, bdn + ax1, "chebyshev-from-zero d")
+        close(out, x1 + dn, 2 * (ax1 + bdn), "chebyshev-from-zero x")
+        assert np.all(np.abs(dots - np.sum(b * (x1 + dn), axis=1))
+                      <= gd * np.sum(np.abs(b) * 2 * (ax1 + bdn), axis=1))
+
+
+def _coarse_prior(pr, dims):
+    pc = dict(pr)
+    pc["n"] = tuple(int(v) for v in dims)
+    return pc
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "fp64"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_stencil_modes_match_the_oracle_operator(name, prec):
+    mk, k = CASES[name]
+    pr, ob = mk()
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    _check_modes(post, infer.condition(pr, ob), k, 0, prec, seed=zlib.crc32(name.encode()) % 1000)
+
+
+@pytest.mark.parametrize("name", ["matern45_ragged", "steady_advdiff40", "st1d_37x21_ragged",
+                                  "st2d_20x20x12_march", "st2d_24x24x10_dense_obs"])
+def test_stencil_modes_on_the_first_coarse_level(name):
+    # the coarse operator is the rediscretised prior with the same point data
+    # interpolated on the coarse mesh
+    mk, k = CASES[name]
+    pr, ob = mk()
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    dims = post.level_info()[1][:3]
+    orc = infer.condition(_coarse_prior(pr, dims), ob)
+    assert orc.Q.shape[0] == int(np.prod(dims))
+    _check_modes(post, orc, k, 1, 0, seed=11)
+
+
+def test_stencil_modes_burgers_linearised():
+    # collocation rows of the Burgers residual linearised at the Gauss-Newton
+    # iterate the library holds after one step (Sec. 3.3)
+    pr, ob = W.c3_burgers(nx=65, nt=33, m=40)
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    u, _ = post.solve_mean()
+    d = np.zeros_like(u)
+    post.gauss_newton_step(u, d)
+    orc = infer.condition(pr, ob, linearise_at=u)
+    for prec in (0, 1):
+        _check_modes(post, orc, 5, 0, prec, seed=21 + prec, modes=(0, 1))
+
+
+def test_stencil_modes_full_size_matern_65_rhs():
+    # the bench workload: 512^2, 10 000 observations, 65 right-hand sides (FP32)
+    pr, ob = W.c2_matern()
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    _check_modes(post, infer.condition(pr, ob), 65, 0, 0, seed=5)
