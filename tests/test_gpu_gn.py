@@ -54,10 +54,21 @@ def test_gauss_newton_iterates_match_the_oracle(n, nt, nu):
 
 @pytest.mark.slow
 def test_gauss_newton_step_at_512_squared_matches_the_oracle():
-    # one relinearisation of the Burgers workload at 512 x 512 (262 144
+    # One relinearisation of the Burgers workload at 512 x 512 (262 144
     # unknowns; the oracle's banded Cholesky of H takes seconds): the first
     # step from the data-only mean, with the C3 noise levels (collocation and
-    # initial condition sigma = 1e-6, nu = 0.01)
+    # initial condition sigma = 1e-6, nu = 0.01).
+    #
+    # H = Q + 1e12 J^T J + ... is ill-conditioned enough here that FP64 fixes
+    # the direction only in the norm the step is defined in (the energy norm
+    # |v|_H = sqrt(v^T H v) of the quadratic model of Sec. 3.3): the gradient
+    # is a cancellation of terms of size 1e17, and one FP64 refinement step of
+    # the oracle's own Cholesky solution moves it by ~4e-6 of its max-norm
+    # (measured), while in the energy norm the same change is ~5e-10.  So the
+    # direction and the iterate are held to 1e-6 in the energy norm, and to
+    # the oracle's own FP64 uncertainty (4x its refinement correction) in the
+    # max-norm.
+    from oracle import linalg as ol
     pr, ob = W.c3_burgers(nx=512, nt=512, m=200, seed=3)
     post = gmrf.Posterior(gmrf.Prior(pr), ob)
     u0_gpu, info = post.solve_mean()
@@ -70,8 +81,16 @@ def test_gauss_newton_step_at_512_squared_matches_the_oracle():
     assert info["converged"] == 1
     assert alpha == alpha_or
     assert dec == pytest.approx(dec_or, rel=1e-6)
-    assert np.max(np.abs(d_gpu - d_or)) < 1e-6 * np.max(np.abs(u0))
-    assert _rel(u_gpu, u1_or) < 1e-6
+    H = infer.condition(pr, ob, linearise_at=u0).Qpost
+    hn = lambda v: float(np.sqrt(v @ (H @ v)))
+    assert hn(d_gpu - d_or) <= 1e-6 * hn(d_or)
+    assert hn(u_gpu - u1_or) <= 1e-6 * hn(u1_or - u0)
+    L = ol.cholesky(H)
+    g = H @ u0 - infer.condition(pr, ob, linearise_at=u0).b
+    corr = np.max(np.abs(ol.solve(L, -g - H @ d_or)))      # one FP64 refinement step of the oracle's direction
+    tol = 1e-6 * np.max(np.abs(u0)) + 4.0 * corr
+    assert np.max(np.abs(d_gpu - d_or)) <= tol
+    assert np.max(np.abs(u_gpu - u1_or)) <= tol
 
 
 def test_laplace_samples_at_the_mode_match_the_oracle():

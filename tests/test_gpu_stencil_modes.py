@@ -16,11 +16,11 @@ inputs as the kernel sees them (rounded to FP32 for the FP32 kernels).  The
 tolerance is the forward-error bound of the arithmetic, element by element:
 |out - ref| <= gamma * m, where m is the same expression evaluated on
 absolute values (|B|^T |B| |x| + |A|^T Q_eps |A| |x| for Q x, since the kernel
-forms B^T (B x) and the observation term) and gamma = 64 u (u = 2^-24 in FP32,
-2^-53 in FP64): a few dozen roundings on each path.  The per-RHS dot products
-the kernel also returns (x^T Q x, |r|^2, b^T x_new) get gamma_dot = 128 u on
-the sum of absolute terms (each thread adds a few dozen FP32 terms before
-the FP64 reduction).
+forms B^T (B x) and the observation term) and gamma = 64 u in FP32 (u = 2^-24:
+a few dozen roundings on each path) and 1e-12 in FP64 (see GAMMA).  The per-RHS
+dot products the kernel also returns (x^T Q x, |r|^2, b^T x_new) get twice
+gamma on the sum of absolute terms (each thread adds a few dozen FP32 terms
+before the FP64 reduction).
 
 Geometries: the tiled 2D and 1D space-time kernel, the marching 2D space-time
 kernel, ragged tiles, dense observations, linear and linearised Burgers
@@ -41,6 +41,14 @@ from paper_2503_08343_gb300 import workloads as W
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
 
 U = {0: 2.0 ** -24, 1: 2.0 ** -53}
+# bound factor per unit roundoff: FP32 64 u; FP64 1e-12 / u (~4500), since the
+# library and the oracle compute the observation weights from the coordinates
+# by different formulas: they agree to a few ulps of x / h (~1e-14 here), and
+# an observation placed on a node can get a rounding-level weight on a
+# neighbour in one of them and exactly zero in the other, which the |A| in the
+# bound cannot see (measured up to 1.9e-13 of the bound; without observations
+# the FP64 kernel stays within 4e-15)
+GAMMA = {0: 64 * 2.0 ** -24, 1: 1e-12}
 C0, C1, C2 = 0.37, 0.61, 0.83
 
 
@@ -91,7 +99,7 @@ def _check_modes(post_gpu, post_o, k, level, prec, seed, modes=(0, 1, 2, 3)):
     Q = post_o.Qpost
     M = _bound_matrix(post_o)
     dinv = 1.0 / Q.diagonal()
-    g, gd = 64 * U[prec], 128 * U[prec]
+    g, gd = GAMMA[prec], 2 * GAMMA[prec]
     Qx = (Q @ x.T).T
     Mx = (M @ np.abs(x).T).T
 
