@@ -202,15 +202,51 @@ gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* d
                                    double* newton_decrement, double* alpha,
                                    const gmrf_solve_opts* opts, gmrf_solve_info* info);
 
-/* Gradient of the log marginal likelihood of the point data with respect to
- * (log kappa, log tau, log sigma, cx, nu), by one batched solve of the
- * posterior system for the mean and nprobes Rademacher probes plus the same
- * probes against the prior (Hutchinson trace estimates).  loglik (host, may
- * be NULL) receives the data-fit part 1/2 b^T mu - 1/2 y^T R^-1 y (the
- * log-determinants are not estimated).  grad[5], grad_stderr[5]: host. */
+/* Log marginal likelihood l = log N(y; 0, A Q^-1 A^T + R) of the point
+ * data and its gradient with respect to (log kappa, log tau, log sigma, cx,
+ * nu) (not in the paper, which fixes its hyper-parameters; Gaussian
+ * identities with b = A^T R^-1 y, mu = Q_u|y^-1 b):
+ *   l = 1/2 log det Q - 1/2 log det Q_u|y - 1/2 log det R - 1/2 y^T R^-1 y
+ *       + 1/2 b^T mu - (M/2) log 2 pi.
+ * One batched solve of the posterior system for the mean and nprobes
+ * Rademacher probes (Philox stream 2, seed).  The prior terms are exact
+ * (log det Q and 1/2 tr(Q^-1 dQ), as gmrf_prior_logdet, computed on host
+ * threads while the GPU solves and cached in the prior handle); the
+ * posterior trace 1/2 tr(Q_u|y^-1 dQ_u|y) is the Hutchinson estimate over
+ * the probes, log det Q_u|y the stochastic Lanczos quadrature estimate over
+ * the same probes (Jacobi-scaled operator, at most max_lanczos steps, <= 0:
+ * 400).  loglik (host, may be NULL: then no Lanczos run) receives l;
+ * li (may be NULL) its standard error and parts; grad[5], grad_stderr[5]
+ * (host; stderr of the Hutchinson part, the exact parts have none). */
+typedef struct gmrf_loglik_info {
+    double loglik_stderr;      /* standard error of loglik (half that of the log det Q_u|y estimate) */
+    double logdet_prior;       /* log det Q, exact */
+    double logdet_post;        /* estimate of log det Q_u|y */
+    int32_t lanczos_steps;     /* Lanczos steps run for every probe */
+    int32_t lanczos_converged; /* 1 if every probe's quadrature settled before max_lanczos */
+} gmrf_loglik_info;
+
+gmrf_status gmrf_loglik_grad_ex(gmrf_posterior* post, int32_t nprobes, uint64_t seed, int32_t max_lanczos,
+                                double* loglik, gmrf_loglik_info* li, double* grad, double* grad_stderr,
+                                const gmrf_solve_opts* opts, gmrf_solve_info* info);
+
+/* gmrf_loglik_grad_ex with the default Lanczos cap and no gmrf_loglik_info. */
 gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t seed, double* loglik,
                              double* grad, double* grad_stderr, const gmrf_solve_opts* opts,
                              gmrf_solve_info* info);
+
+/* Exact log det Q of the prior and the prior trace terms of the
+ * log-likelihood gradient, trace[p] = 1/2 tr(Q^-1 dQ/dtheta_p) for
+ * theta = (log kappa, log tau, cx, nu) (kappa: kappa0 of the initial level
+ * for space-time priors).  Not in the paper (hyper-parameter learning;
+ * Gaussian identities).  Q = B^T B with B block lower bidiagonal in time, so
+ * log det Q = 2 sum_k log|det B_kk| and 1/2 tr(Q^-1 dQ) = sum_k
+ * tr(B_kk^-1 dB_kk) over the diagonal blocks: at most two distinct interior
+ * operators (the spatial / initial block and the transition block), by the
+ * sine-transform closed form when symmetric, else by banded LU and the band of
+ * the inverse, O(N_s (n_x)^2) host work for N_s spatial nodes.  Runs on the
+ * host only (no GPU, no handle).  logdet or trace may be NULL. */
+gmrf_status gmrf_prior_logdet(const gmrf_prior_desc* desc, double* logdet, double* trace);
 
 /* y = Q_u|y x in FP64 for a batch of k vectors x, y: [k][N].  Test hook for
  * the fused stencil.  GMRF_E_CUDA if a stencil CTA gave up its bounded wait

@@ -280,21 +280,32 @@ def log_marginal_likelihood_grad(prior: dict, obs: dict) -> dict:
     return grad
 
 
-def hutchinson_grad(prior: dict, obs: dict, seed: int, nprobe: int) -> dict:
-    """The same gradient with both trace terms replaced by Hutchinson
+def hutchinson_grad(prior: dict, obs: dict, seed: int, nprobe: int, prior_trace: str = "hutchinson") -> dict:
+    """The same gradient with the trace terms replaced by Hutchinson
     estimates on Rademacher probes v_s (Philox stream 2, sample s):
-    tr(X^-1 dX) ~ (1/S) sum_s (X^-1 v_s)^T dX v_s, exact solves.  Pinned
+    tr(X^-1 dX) ~ (1/S) sum_s (X^-1 v_s)^T dX v_s, exact solves.  With
+    prior_trace="exact" only the posterior trace is estimated and the prior
+    one, 1/2 tr(Q^-1 dQ), is taken exactly (dense, tiny grids).  Pinned
     through hutchinson_grad_probes: over all 2^N sign vectors of a tiny
     problem the estimate is the exact gradient."""
     N = condition(prior, obs).Q.shape[0]
     V = np.stack([rng.rademacher(seed, s, N) for s in range(nprobe)])
-    return hutchinson_grad_probes(prior, obs, V)
+    return hutchinson_grad_probes(prior, obs, V, prior_trace)
 
 
-def hutchinson_grad_probes(prior: dict, obs: dict, V: np.ndarray) -> dict:
+def prior_trace_terms(prior: dict) -> dict:
+    """1/2 tr(Q^-1 dQ/dtheta) for theta in (log_kappa, log_tau, c, nu), by a
+    dense inverse (tiny grids only)."""
+    Qi = np.linalg.inv(fem.prior_precision(prior).toarray())
+    return {name: 0.5 * float(np.sum(Qi * dQ_dtheta(prior, name).toarray()))
+            for name in ("log_kappa", "log_tau", "c", "nu")}
+
+
+def hutchinson_grad_probes(prior: dict, obs: dict, V: np.ndarray, prior_trace: str = "hutchinson") -> dict:
     """The Hutchinson gradient on given probe vectors V [S][N]: the mean over
     the probes of the gradient terms with tr(X^-1 dX) replaced by
-    v^T X^-1 dX v, and its standard error."""
+    v^T X^-1 dX v, and its standard error.  prior_trace="exact" keeps the
+    prior trace exact (see hutchinson_grad)."""
     post = condition(prior, obs)
     Lq = linalg.cholesky(post.Q)
     Lp = linalg.cholesky(post.Qpost)
@@ -304,6 +315,7 @@ def hutchinson_grad_probes(prior: dict, obs: dict, V: np.ndarray) -> dict:
     Wp = linalg.solve(Lp, V.T).T
     A = post.A
     y = post.y
+    exact_prior = prior_trace_terms(prior) if prior_trace == "exact" else None
     grad, stderr = {}, {}
     for name in HYPER:
         if name == "log_sigma":
@@ -315,9 +327,12 @@ def hutchinson_grad_probes(prior: dict, obs: dict, V: np.ndarray) -> dict:
                    - 0.5 * np.sum(drinv * y * y) + 0.5 * np.sum(drinv / post.rinv))
         else:
             dQ = dQ_dtheta(prior, name)
-            tq = np.array([Wq[s] @ (dQ @ V[s]) for s in range(nprobe)])
             tp = np.array([Wp[s] @ (dQ @ V[s]) for s in range(nprobe)])
-            val = 0.5 * tq - 0.5 * tp - 0.5 * mu @ (dQ @ mu)
+            if exact_prior is None:
+                tq = 0.5 * np.array([Wq[s] @ (dQ @ V[s]) for s in range(nprobe)])
+            else:
+                tq = np.full(nprobe, exact_prior[name])
+            val = tq - 0.5 * tp - 0.5 * mu @ (dQ @ mu)
         grad[name] = float(np.mean(val))
         stderr[name] = float(np.std(val, ddof=1) / math.sqrt(nprobe)) if nprobe > 1 else float("inf")
     return grad, stderr

@@ -324,7 +324,6 @@ void gmrf_posterior_destroy(gmrf_posterior* post) {
     dev_free(P.d_blin);
     dev_free(P.d_gn);
     dev_free(P.d_grad_part);
-    if (P.prior_only) gmrf_posterior_destroy(static_cast<gmrf_posterior*>(P.prior_only));
     gmrf_prior* pr = post->prior;
     delete post;
     if (pr) prior_release(pr);
@@ -656,6 +655,22 @@ gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t preci
     });
 }
 
+gmrf_status gmrf_prior_logdet(const gmrf_prior_desc* desc, double* logdet, double* trace) {
+    return guard([&] {
+        require(desc && (logdet || trace), "null argument");
+        const gmrf_prior_desc& d = *desc;
+        require(d.kind >= 0 && d.kind <= 3, "unknown prior kind");
+        require(d.nx >= 3 && (d.kind == GMRF_ADVDIFF_ST_1D ? d.ny == 1 : d.ny >= 3), "bad grid");
+        require(d.eps2 > 0 && d.tau > 0, "eps2 and tau must be positive");
+        std::vector<Level> lv;
+        build_hierarchy(d, lv);
+        const PriorDet r = prior_logdet(d, lv[0]);
+        if (logdet) *logdet = r.logdet;
+        if (trace)
+            for (int q = 0; q < 4; ++q) trace[q] = r.tr[q];
+    });
+}
+
 uint64_t gmrf_launch_count(void) { return launch_count(); }
 
 gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* delta_prev, double* newton_decrement,
@@ -676,8 +691,9 @@ gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* d
     return st != GMRF_OK ? st : rc;
 }
 
-gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t seed, double* loglik, double* grad,
-                             double* grad_stderr, const gmrf_solve_opts* opts, gmrf_solve_info* info) {
+gmrf_status gmrf_loglik_grad_ex(gmrf_posterior* post, int32_t nprobes, uint64_t seed, int32_t max_lanczos,
+                                double* loglik, gmrf_loglik_info* li, double* grad, double* grad_stderr,
+                                const gmrf_solve_opts* opts, gmrf_solve_info* info) {
     gmrf_status rc = GMRF_OK;
     const gmrf_status st = guard([&] {
         require(post && grad && nprobes >= 1, "bad argument");
@@ -686,24 +702,31 @@ gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t see
         enter(post->prior);
         const gmrf_solve_opts o = resolve_opts(opts);
         const auto t0 = std::chrono::steady_clock::now();
-        if (!P.prior_only) {
-            gmrf_obs_desc none;
-            std::memset(&none, 0, sizeof(none));
-            gmrf_posterior* q = nullptr;
-            const gmrf_status s2 = gmrf_condition(post->prior, &none, &q);
-            if (s2 != GMRF_OK) throw Error(s2, std::string("prior-only operator: ") + g_err);
-            P.prior_only = q;
-        }
         double g[5], se[5];
-        const SolveStats ss = loglik_grad(P, static_cast<gmrf_posterior*>(P.prior_only)->impl, nprobes, seed, o, loglik,
+        LoglikOut out;
+        const bool value = loglik != nullptr || li != nullptr;
+        const SolveStats ss = loglik_grad(P, nprobes, seed, o, max_lanczos > 0 ? max_lanczos : 400, value ? &out : nullptr,
                                           g, se, P.prior->stream);
         for (int i = 0; i < 5; ++i) {
             grad[i] = g[i];
             if (grad_stderr) grad_stderr[i] = se[i];
         }
-        rc = finish(ss, info, 2 * nprobes + 1, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+        if (loglik) *loglik = out.loglik;
+        if (li) {
+            li->loglik_stderr = out.loglik_se;
+            li->logdet_prior = out.logdet_prior;
+            li->logdet_post = out.logdet_post;
+            li->lanczos_steps = out.lanczos_steps;
+            li->lanczos_converged = out.lanczos_converged ? 1 : 0;
+        }
+        rc = finish(ss, info, nprobes + 1, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     });
     return st != GMRF_OK ? st : rc;
+}
+
+gmrf_status gmrf_loglik_grad(gmrf_posterior* post, int32_t nprobes, uint64_t seed, double* loglik, double* grad,
+                             double* grad_stderr, const gmrf_solve_opts* opts, gmrf_solve_info* info) {
+    return gmrf_loglik_grad_ex(post, nprobes, seed, 0, loglik, nullptr, grad, grad_stderr, opts, info);
 }
 
 }  // extern "C"

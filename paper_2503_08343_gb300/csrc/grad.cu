@@ -5,12 +5,19 @@
 //   dl = 1/2 tr(Q^-1 dQ) - 1/2 tr(Q_u|y^-1 dQ_u|y) - 1/2 mu^T dQ_u|y mu
 //        + mu^T db - 1/2 y^T d(R^-1) y + 1/2 tr(R d(R^-1)),
 // with dQ = dB^T B + B^T dB for the prior parameters and, for log sigma,
-// d(R^-1) = -2 R^-1, dQ_u|y = A^T d(R^-1) A, db = A^T d(R^-1) y.  Both traces
-// are Hutchinson estimates tr(X^-1 dX) ~ mean_s (X^-1 v_s)^T dX v_s over the
-// same Rademacher probes v_s (Philox stream 2), from one batched posterior
-// solve [mean, probes] and one batched prior solve [probes].
+// d(R^-1) = -2 R^-1, dQ_u|y = A^T d(R^-1) A, db = A^T d(R^-1) y.  The prior
+// trace 1/2 tr(Q^-1 dQ) is exact (prior_det.cu: the block lower-bidiagonal
+// root gives it from the diagonal blocks alone); the posterior trace is the
+// Hutchinson estimate tr(Q_u|y^-1 dX) ~ mean_s (Q_u|y^-1 v_s)^T dX v_s over
+// Rademacher probes v_s (Philox stream 2) from one batched posterior solve
+// [mean, probes].  The value
+//   l = 1/2 log det Q - 1/2 log det Q_u|y - 1/2 log det R - 1/2 y^T R^-1 y
+//       + 1/2 b^T mu - (M/2) log 2 pi
+// takes log det Q exactly and log det Q_u|y by stochastic Lanczos quadrature
+// on the same probes (slq.cu).
 #include <cmath>
 #include <cstring>
+#include <future>
 #include <vector>
 
 #include "handles.h"
@@ -20,10 +27,6 @@ namespace gmrf {
 namespace {
 
 constexpr int NPAR = 4;   // prior parameters handled by the stencil contraction: log kappa, log tau, cx, nu
-
-struct DerivTaps {
-    double d[NPAR][2][NTAP];   // dB / dtheta per row class
-};
 
 // (dB w)^T (B v) + (B w)^T (dB v) summed over rows, per parameter and slot;
 // also (B w)^T (B v) for reference.  Rows are nodes; Dirichlet rows have no
@@ -131,6 +134,8 @@ __global__ void k_copy_slot(const double* __restrict__ src, int src_slot, double
 
 unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
 
+}  // namespace
+
 // derivative taps of the prior root B for the level (the same closed forms as
 // level_coefficients, differentiated)
 DerivTaps derivative_taps(const gmrf_prior_desc& d, const Level& L) {
@@ -180,14 +185,37 @@ DerivTaps derivative_taps(const gmrf_prior_desc& d, const Level& L) {
     return D;
 }
 
-}  // namespace
+
+// The prior's exact log det Q and trace terms, computed once per prior on
+// host threads (cached in the prior; Q does not change).
+static PriorDet cached_prior_det(Prior& pr, const Level& F) {
+    std::lock_guard<std::mutex> lock(pr.det_mu);
+    if (!pr.det_ready) {
+        const PriorDet d = prior_logdet(pr.desc, F);
+        pr.det_logdet = d.logdet;
+        for (int q = 0; q < 4; ++q) pr.det_tr[q] = d.tr[q];
+        pr.det_ready = true;
+    }
+    PriorDet d;
+    d.logdet = pr.det_logdet;
+    for (int q = 0; q < 4; ++q) d.tr[q] = pr.det_tr[q];
+    return d;
+}
 
 // Runs the gradient computation; grad/stderr indexed as (log kappa, log tau, log sigma, cx, nu).
-SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, const gmrf_solve_opts& o, double* loglik,
+SolveStats loglik_grad(Posterior& P, int S, uint64_t seed, const gmrf_solve_opts& o, int max_lanczos, LoglikOut* ll,
                        double grad[5], double gse[5], cudaStream_t s) {
     Level& F = P.levels[0];
     const long long N = F.N;
     const int m = (int)P.m;
+    // 0. the exact prior terms on host threads, while the GPU solves
+    std::future<PriorDet> pdet = std::async(std::launch::async, [&P, &F] { return cached_prior_det(*P.prior, F); });
+    struct Join {          // the host work reads P and F: finish it before any exit from here
+        std::future<PriorDet>& f;
+        ~Join() {
+            if (f.valid()) f.wait();
+        }
+    } join{pdet};
     // 1. posterior batch: slot 0 = data right-hand side, slots 1..S = probes 0..S-1
     const int nrhs = S + 1, nblk = (nrhs + 3) / 4;
     Workspace& W = workspace(P, nblk);
@@ -202,22 +230,7 @@ SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, co
     note_launch();
     GCK(cudaMemsetAsync(W.x64, 0, sizeof(double) * nblk * N * 4, s));
     SolveStats st = solve_blocked(P, nblk, W.b64, W.x64, o, s, true);
-    // 2. prior batch on the same slots (slot 0 holds probe 0 twice: harmless, ignored)
-    Workspace& Wp = workspace(Pprior, nblk);
-    std::vector<int32_t> pidp = pid;
-    pidp[0] = 0;
-    GCK(cudaMemcpyAsync(Wp.slot_b, pidp.data(), sizeof(int32_t) * pidp.size(), cudaMemcpyHostToDevice, s));
-    GCK(cudaMemsetAsync(Wp.b64, 0, sizeof(double) * nblk * N * 4, s));
-    k_rademacher_slots<<<dim3(nb256(N), nblk), 256, 0, s>>>(seed, Wp.slot_b, Wp.b64, N);
-    note_launch();
-    GCK(cudaMemsetAsync(Wp.x64, 0, sizeof(double) * nblk * N * 4, s));
-    const SolveStats sp = solve_blocked(Pprior, nblk, Wp.b64, Wp.x64, o, s, true);
-    st.refinements += sp.refinements;
-    st.inner += sp.inner;
-    st.converged = st.converged && sp.converged;
-    st.breakdown = st.breakdown || sp.breakdown;
-    st.max_rel = std::max(st.max_rel, sp.max_rel);
-    // 3. contractions (probe slots: V = probes (W.b64 holds them), solutions in W.x64 / Wp.x64)
+    // 2. contractions (probe slots: V = probes (W.b64 holds them), solutions in W.x64)
     const DerivTaps D = derivative_taps(P.prior->desc, F);
     const unsigned nbx = nb256(N);
     const size_t pstride = (size_t)nblk * nbx * 4;   // doubles per parameter
@@ -238,9 +251,8 @@ SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, co
         }
         GCK(cudaStreamSynchronize(s));
     };
-    std::vector<double> tpost, tprior, quadv;
+    std::vector<double> tpost, quadv;
     contract(W.x64, W.b64, nblk, tpost);    // (Q_u|y^-1 v)^T dQ v per slot (slot 0 unused)
-    contract(Wp.x64, W.b64, nblk, tprior);  // (Q^-1 v)^T dQ v per slot (slot 0 unused)
     // mu^T dQ mu: broadcast mu (slot 0) into a one-block batch
     Workspace& W1 = workspace(P, 1);
     k_copy_slot<<<dim3(nb256(N), 1), 256, 0, s>>>(W.x64, 0, W1.t64, N, 1);
@@ -264,25 +276,38 @@ SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, co
     GCK(cudaMemcpyAsync(W1.h_red, W1.red, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
     GCK(cudaStreamSynchronize(s));
     const double mu_dR_mu = W1.h_red[0];
+    // data-fit part 1/2 b^T mu (needed for the value only)
+    double btmu = 0.0;
+    if (ll) {
+        launch_dot_blocked(W.b64, W.x64, N, nblk, part, elem_parts(N), s);
+        launch_reduce(part, elem_parts(N), nblk, W.red, s);
+        GCK(cudaMemcpyAsync(W.h_red, W.red, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+        GCK(cudaStreamSynchronize(s));
+        btmu = W.h_red[0];
+    }
+    // 3. log det Q_u|y by Lanczos quadrature on the same probes (value only)
+    SlqResult slq;
+    if (ll) slq = slq_logdet(P, S, seed, max_lanczos, s);
+    const PriorDet pd = pdet.get();
     // host assembly
-    double ydRy = 0.0, yRy = 0.0;
+    double ydRy = 0.0, yRy = 0.0, logrinv = 0.0;
     for (int k = 0; k < m; ++k) {
         const double r = P.levels[0].h_obs[(size_t)k].rinv, yk = P.y_point[(size_t)k];
         ydRy += -2.0 * r * yk * yk;
         yRy += r * yk * yk;
+        logrinv += std::log(r);
     }
     const int map[NPAR] = {0, 1, 3, 4};       // stencil parameter -> gradient index
     for (int p = 0; p < NPAR; ++p) {
         std::vector<double> est((size_t)S);
-        for (int i = 1; i < nrhs; ++i)
-            est[(size_t)i - 1] = 0.5 * tprior[(size_t)p * nblk * 4 + i] - 0.5 * tpost[(size_t)p * nblk * 4 + i];
+        for (int i = 1; i < nrhs; ++i) est[(size_t)i - 1] = -0.5 * tpost[(size_t)p * nblk * 4 + i];
         double mean = 0.0;
         for (double e : est) mean += e;
         mean /= S;
         double var = 0.0;
         for (double e : est) var += (e - mean) * (e - mean);
         var = S > 1 ? var / (S - 1) : 0.0;
-        grad[map[p]] = mean - 0.5 * quad[(size_t)p];
+        grad[map[p]] = pd.tr[p] + mean - 0.5 * quad[(size_t)p];
         gse[map[p]] = S > 1 ? std::sqrt(var / S) : INFINITY;
     }
     {
@@ -297,13 +322,14 @@ SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, co
         grad[2] = mean - 0.5 * mu_dR_mu + o2[0] - 0.5 * ydRy - (double)m;
         gse[2] = S > 1 ? std::sqrt(var / S) : INFINITY;
     }
-    if (loglik) {
-        // data-fit part 1/2 b^T mu - 1/2 y^T R^-1 y
-        launch_dot_blocked(W.b64, W.x64, N, nblk, part, elem_parts(N), s);
-        launch_reduce(part, elem_parts(N), nblk, W.red, s);
-        GCK(cudaMemcpyAsync(W.h_red, W.red, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
-        GCK(cudaStreamSynchronize(s));
-        *loglik = 0.5 * W.h_red[0] - 0.5 * yRy;
+    if (ll) {
+        const double log2pi = std::log(2.0 * 3.14159265358979323846);
+        ll->logdet_prior = pd.logdet;
+        ll->logdet_post = slq.logdet;
+        ll->loglik = 0.5 * pd.logdet - 0.5 * slq.logdet + 0.5 * logrinv - 0.5 * yRy + 0.5 * btmu - 0.5 * (double)m * log2pi;
+        ll->loglik_se = 0.5 * slq.stderr_;
+        ll->lanczos_steps = slq.steps;
+        ll->lanczos_converged = slq.converged;
     }
     return st;
 }

@@ -99,8 +99,48 @@ GnResult gauss_newton_step(Posterior& P, double* u_io, double* d_io, bool u_dev,
                            cudaStream_t s);
 
 // grad.cu
-SolveStats loglik_grad(Posterior& P, Posterior& Pprior, int S, uint64_t seed, const gmrf_solve_opts& o, double* loglik,
+// dB/dtheta taps of the prior root per row class (0 interior / t >= 1,
+// 1 t = 0) for theta = (log kappa, log tau, cx, nu)
+struct DerivTaps {
+    double d[4][2][NTAP];
+};
+DerivTaps derivative_taps(const gmrf_prior_desc& d, const Level& L);
+
+// prior_det.cu: exact log det Q and 1/2 tr(Q^-1 dQ/dtheta) from the
+// diagonal blocks of the root (interior 7-point operators)
+struct Stencil7 {
+    double c[7];
+};
+struct InteriorDet {
+    double logabsdet = 0.0;
+    int sign = 1;
+    std::vector<double> tr;    // tr(A^-1 X_p)
+};
+InteriorDet interior_logdet(int mx, int my, const double a[7], const std::vector<Stencil7>& X);
+struct PriorDet {
+    double logdet = 0.0;
+    double tr[4] = {0, 0, 0, 0};   // 1/2 tr(Q^-1 dQ/dtheta), theta = (log kappa, log tau, cx, nu)
+};
+PriorDet prior_logdet(const gmrf_prior_desc& d, const Level& F);
+
+struct LoglikOut {
+    double loglik = 0.0, loglik_se = 0.0;
+    double logdet_prior = 0.0, logdet_post = 0.0;
+    int lanczos_steps = 0;
+    bool lanczos_converged = false;
+};
+// ll == nullptr: gradient only (no Lanczos quadrature)
+SolveStats loglik_grad(Posterior& P, int S, uint64_t seed, const gmrf_solve_opts& o, int max_lanczos, LoglikOut* ll,
                        double grad[5], double gse[5], cudaStream_t s);
+
+// slq.cu: log det Q_u|y by stochastic Lanczos quadrature over S Rademacher probes
+struct SlqResult {
+    double logdet = 0.0, stderr_ = 0.0;
+    int steps = 0;
+    bool converged = false;
+};
+SlqResult slq_logdet(Posterior& P, int S, uint64_t seed, int max_steps, cudaStream_t s);
+double gauss_log_quadrature(const std::vector<double>& a, const std::vector<double>& b);
 
 // scratch of one batch size
 struct Workspace {

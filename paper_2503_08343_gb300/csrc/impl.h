@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -118,6 +119,11 @@ struct Prior {
     cudaStream_t stream = 0;
     int geo = 0;
     std::vector<Level> levels;   // rebuilt per posterior (observations differ); geometry here
+    // exact log det Q and prior trace terms (computed on first use)
+    std::mutex det_mu;
+    bool det_ready = false;
+    double det_logdet = 0.0;
+    double det_tr[4] = {0, 0, 0, 0};
 };
 
 struct Workspace;
@@ -159,7 +165,6 @@ struct Posterior {
     // transfer.
     double data_share = 0.0;       // max_n (obs part of diag_n) / diag_n, fine level
     bool transfer_p1 = false;
-    void* prior_only = nullptr;    // gmrf_posterior* of the same prior without observations (gradient traces)
     double* d_grad_part = nullptr; // partial sums of the gradient contractions
     size_t grad_part_n = 0;
     double ic_rinv = 0.0;          // precision of the initial-condition rows

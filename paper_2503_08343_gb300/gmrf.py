@@ -50,6 +50,14 @@ class SolveInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class LoglikInfo(C.Structure):
+    _fields_ = [("loglik_stderr", C.c_double), ("logdet_prior", C.c_double), ("logdet_post", C.c_double),
+                ("lanczos_steps", C.c_int32), ("lanczos_converged", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GmrfError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -86,6 +94,8 @@ def load(build_if_missing: bool = False):
         "gmrf_marginal_var": (I32, [P, I32, U64, P, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "gmrf_gauss_newton_step": (I32, [P, P, P, DP, DP, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "gmrf_loglik_grad": (I32, [P, I32, U64, DP, DP, DP, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "gmrf_loglik_grad_ex": (I32, [P, I32, U64, I32, DP, C.POINTER(LoglikInfo), DP, DP, C.POINTER(SolveOpts),
+                                      C.POINTER(SolveInfo)]),
         "gmrf_apply_posterior": (I32, [P, I32, P, P]),
         "gmrf_marginal_var_batch": (I32, [C.POINTER(P), I32, I32, U64, C.POINTER(P), C.POINTER(P),
                                           C.POINTER(SolveOpts), C.POINTER(SolveInfo), I32]),
@@ -93,6 +103,7 @@ def load(build_if_missing: bool = False):
         "gmrf_time_stencil": (I32, [P, I32, I32, I32, DP]),
         "gmrf_stencil_step": (I32, [P, I32, I32, I32, I32, P, P, P, D, D, D, P, P, DP]),
         "gmrf_level_info": (I32, [P, I32, C.POINTER(C.c_int32), DP]),
+        "gmrf_prior_logdet": (I32, [C.POINTER(PriorDesc), DP, DP]),
         "gmrf_transfer_info": (I32, [P, C.POINTER(C.c_int32), DP]),
         "gmrf_num_unknowns": (I64, [P]),
         "gmrf_num_levels": (I32, [P]),
@@ -148,6 +159,16 @@ def prior_desc(prior: dict) -> PriorDesc:
     for k in ("kappa", "tau", "nu", "cx", "cy", "kappa0", "eps2"):
         setattr(d, k, float(prior[k]))
     return d
+
+
+def prior_logdet(prior: dict):
+    """Exact log det Q and 1/2 tr(Q^-1 dQ/dtheta) for theta = (log kappa,
+    log tau, c, nu) of a prior (host computation, gmrf_prior_logdet)."""
+    d = prior_desc(prior)
+    ld = C.c_double()
+    tr = np.zeros(4)
+    _check(load().gmrf_prior_logdet(C.byref(d), C.byref(ld), _dptr(tr)))
+    return ld.value, tr
 
 
 class Prior:
@@ -244,14 +265,23 @@ class Posterior:
                                              C.byref(opts or default_opts()), C.byref(info)))
         return dec.value, alpha.value, info.as_dict()
 
-    def loglik_grad(self, nprobes, seed, opts=None):
+    def loglik_grad(self, nprobes, seed, opts=None, value=True, max_lanczos=0):
+        """(log marginal likelihood or None, gradient [5], gradient stderr [5],
+        solve info); info["loglik"] holds the value's standard error and the
+        log-determinant parts (gmrf_loglik_grad_ex).  value=False skips the
+        Lanczos quadrature of the value."""
         ll = C.c_double()
+        li = LoglikInfo()
         g = np.zeros(5)
         se = np.zeros(5)
         info = SolveInfo()
-        _check(load().gmrf_loglik_grad(self.h, nprobes, seed, C.byref(ll), _dptr(g), _dptr(se),
-                                       C.byref(opts or default_opts()), C.byref(info)))
-        return ll.value, g, se, info.as_dict()
+        _check(load().gmrf_loglik_grad_ex(self.h, nprobes, seed, max_lanczos, C.byref(ll) if value else None,
+                                          C.byref(li) if value else None, _dptr(g), _dptr(se),
+                                          C.byref(opts or default_opts()), C.byref(info)))
+        d = info.as_dict()
+        if value:
+            d["loglik"] = li.as_dict()
+        return (ll.value if value else None), g, se, d
 
     def apply(self, x):
         x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
@@ -359,12 +389,12 @@ def _loglik_function():
     import torch
 
     class LogMarginalLikelihood(torch.autograd.Function):
-        """Forward: the data-fit part 1/2 b^T mu - 1/2 y^T R^-1 y of the log
-        marginal likelihood at theta (the log-determinant terms are not
-        evaluated).  Backward: the gradient of the full log marginal
-        likelihood, with the trace terms estimated by Hutchinson probes from
-        the same batched solves (gmrf_loglik_grad); no graph through the
-        solver is recorded."""
+        """Forward: the log marginal likelihood at theta (exact prior log
+        determinant, Lanczos-quadrature estimate of the posterior one; its
+        standard error is in ctx.info).  Backward: its gradient, with the
+        posterior trace terms estimated by Hutchinson probes from the same
+        batched solve and the prior trace terms exact (gmrf_loglik_grad_ex);
+        no graph through the solver is recorded."""
 
         @staticmethod
         def forward(ctx, theta, prior, obs, nprobes, seed, opts):

@@ -275,10 +275,11 @@ def test_hutchinson_estimator_over_all_sign_vectors_is_exact():
     assert N == 12
     k = np.arange(2 ** N)[:, None]
     V = 1.0 - 2.0 * ((k >> np.arange(N)[None, :]) & 1)
-    est, _ = infer.hutchinson_grad_probes(prior, ob, V)
     exact = infer.log_marginal_likelihood_grad(prior, ob)
-    for name in infer.HYPER:
-        assert abs(est[name] - exact[name]) <= 1e-9 * max(1.0, abs(exact[name])), (name, est[name], exact[name])
+    for mode in ("hutchinson", "exact"):      # both traces estimated / the prior one exact
+        est, _ = infer.hutchinson_grad_probes(prior, ob, V, prior_trace=mode)
+        for name in infer.HYPER:
+            assert abs(est[name] - exact[name]) <= 1e-9 * max(1.0, abs(exact[name])), (mode, name, est[name], exact[name])
 
 
 def test_burgers_jacobian_matches_finite_differences():
