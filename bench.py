@@ -389,6 +389,7 @@ def c5_accuracy_matched(post, probes: int = 32, seed: int = 1005, target: float 
     path the loosest rtol (1e-6, 1e-7, ...) whose gradient is within `target`
     relative (max over the five components) of the reference, and the time of
     each path at its rtol (gradient only, warm)."""
+    import numpy as np
     from paper_2503_08343_gb300 import gmrf
 
     def grad(rtol, plain):

@@ -307,6 +307,15 @@ gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t preci
                               const double* x, const double* b, const double* d, double c0, double c1, double c2,
                               double* out, double* out2, double* dots);
 
+/* Test hook for the failure path of the stencil kernels: the number of
+ * polls each CTA spends on a bounded wait for a staged input tile before it
+ * gives up (0 restores the default, 2^22).  A CTA that gives up records a
+ * device flag, still waits (with the default cap) for its copies in flight,
+ * and returns; the solver turns the flag into GMRF_E_CUDA and clears it, so
+ * the handle stays usable.  With a cap of 1 the waits give up while the
+ * copies are still landing.  Process-wide; not for production use. */
+void gmrf_test_set_wait_cap(int32_t cap);
+
 /* Number of kernels this library has launched in the process so far
  * (kernels inside replayed CUDA graphs included). */
 uint64_t gmrf_launch_count(void);

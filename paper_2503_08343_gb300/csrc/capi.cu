@@ -671,6 +671,8 @@ gmrf_status gmrf_prior_logdet(const gmrf_prior_desc* desc, double* logdet, doubl
     });
 }
 
+void gmrf_test_set_wait_cap(int32_t cap) { set_wait_cap(cap); }
+
 uint64_t gmrf_launch_count(void) { return launch_count(); }
 
 gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* delta_prev, double* newton_decrement,

@@ -160,6 +160,7 @@ struct Workspace {
     double* sc64 = nullptr;
     double* h_red = nullptr;       // pinned host mirror of `red`
     double* h_active = nullptr;    // pinned host mirror of the active flags
+    int32_t* h_abort = nullptr;    // pinned copies of the two stencil abort flags
     int32_t* slot_a = nullptr;     // per-slot ids (device)
     int32_t* slot_b = nullptr;
     // per-level vectors for each precision

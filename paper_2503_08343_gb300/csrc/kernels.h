@@ -52,6 +52,15 @@ void reduce_prepare();
 // call (the flags of both stencil kernels are cleared)
 int stencil_abort_take(cudaStream_t s);
 int march_abort_take(cudaStream_t s);
+// queue copies of both abort flags into host memory (2 ints, pinned) on s;
+// valid after the next synchronisation of s
+void stencil_abort_peek_async(int32_t* host2, cudaStream_t s);
+void march_abort_peek_async(int32_t* host1, cudaStream_t s);
+// test hook: poll cap of the staged-tile waits of both stencil kernels
+// (0: the default 2^22), a device variable read by every CTA (so captured
+// graphs follow it); the drain of in-flight copies keeps the default
+void set_wait_cap(int cap);
+void march_set_wait_cap(int cap);
 // cuTensorMapEncodeTiled of a dense FP32 (f64 = false) or FP64 array of
 // `rank` dimensions (innermost first; strides of dimensions 1.. in bytes),
 // no interleave or swizzle, zero fill outside; throws on an error.

@@ -214,6 +214,7 @@ void workspace_free(Workspace* w) {
     dev_free(w->slot_a); dev_free(w->slot_b);
     if (w->h_red) cudaFreeHost(w->h_red);
     if (w->h_active) cudaFreeHost(w->h_active);
+    if (w->h_abort) cudaFreeHost(w->h_abort);
     free_vecs(w->v32);
     free_vecs(w->v64);
     delete w;
@@ -240,6 +241,7 @@ Workspace& workspace(Posterior& P, int nblk) {
     W->slot_b = dev_alloc<int32_t>((size_t)nblk * 4);
     GCK(cudaMallocHost((void**)&W->h_red, sizeof(double) * nblk * 8));
     GCK(cudaMallocHost((void**)&W->h_active, sizeof(double) * nblk * 4));
+    GCK(cudaMallocHost((void**)&W->h_abort, sizeof(int32_t) * 2));
     P.ws[nblk] = W;
     return *W;
 }
@@ -489,8 +491,15 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
             launch_reduce(W.partial, ng, nblk, W.red, s);
         }
         GCK(cudaMemcpyAsync(W.h_red, W.red, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
+        stencil_abort_peek_async(W.h_abort, s);
         GCK(cudaStreamSynchronize(s));
         st.refinements++;
+        // a stencil CTA that gave up waiting for a staged tile left this
+        // residual (and the solve behind it) incomplete
+        if (W.h_abort[0] || W.h_abort[1]) {
+            stencil_abort_take(s);
+            throw Error(GMRF_E_CUDA, "stencil kernel: staged input tile did not arrive (bounded wait)");
+        }
         bool conv = true;
         st.max_rel = 0.0;
         for (int i = 0; i < P4; ++i) {

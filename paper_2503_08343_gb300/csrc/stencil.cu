@@ -12,6 +12,7 @@
 // mode-specific epilogue (apply, residual, Chebyshev step).  The work is
 // HBM-bound (about 3 flop per byte), so nothing here uses tensor cores.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -124,6 +125,8 @@ __device__ __forceinline__ void unit_next(UnitPos& p, int tiles_x, int tiles_y, 
 // wait); the solver checks and clears it after every solve.
 __device__ int g_stencil_abort = 0;
 constexpr int kMbarSpinCap = 1 << 22;
+// polls before a staged-tile wait gives up (0: kMbarSpinCap); a test hook
+__device__ int g_stencil_wait_cap = 0;
 
 template <int GEO, typename T, int MODE, int COL, int NS, int KB>
 __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nunits, const __grid_constant__ StencilMaps maps) {
@@ -142,6 +145,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     SM& S = *reinterpret_cast<SM*>(smem_base);
     __shared__ uint64_t bars[NS];
     __shared__ int abort_unit;
+    const int cap = g_stencil_wait_cap > 0 ? g_stencil_wait_cap : kMbarSpinCap;
 
     const LevelView<T>& L = A.L;
     const int nx = L.nx, ny = L.ny, nt = L.nt;
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     for (int done = 0; done < count; ++done) {
         fence_proxy_async();           // generic accesses of the last unit before the TMA refill below
         cp_wait<NS - 2>();
-        if (mbar_wait_bounded(&bars[st], (phbits >> st) & 1u, kMbarSpinCap)) {   // this unit's input tile
+        if (mbar_wait_bounded(&bars[st], (phbits >> st) & 1u, cap)) {   // this unit's input tile
             phbits ^= 1u << st;
             pend &= ~(1u << st);
         } else {
@@ -524,6 +528,17 @@ static CUtensorMap tile_map(const T* v, const LevelView<T>& L, int nblk, bool ha
     CUtensorMap m;
     encode_tensor_map(&m, sizeof(T) == 8, 3, v, dims, strides, box);
     return m;
+}
+
+void set_wait_cap(int cap) {
+    const int v = cap > 0 ? cap : 0;
+    cuda_ok(cudaMemcpyToSymbol(g_stencil_wait_cap, &v, sizeof(int)));
+    march_set_wait_cap(v);
+}
+
+void stencil_abort_peek_async(int32_t* host2, cudaStream_t s) {
+    cuda_ok(cudaMemcpyFromSymbolAsync(host2, g_stencil_abort, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    march_abort_peek_async(host2 + 1, s);
 }
 
 int stencil_abort_take(cudaStream_t s) {

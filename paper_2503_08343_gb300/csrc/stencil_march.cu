@@ -61,6 +61,8 @@ struct MarchMaps {
 
 __device__ int g_march_abort = 0;
 constexpr int kSpinCap = 1 << 22;
+// polls before a staged-plane wait gives up (0: kSpinCap); a test hook
+__device__ int g_march_wait_cap = 0;
 
 void ok(cudaError_t e) {
     if (e != cudaSuccess) throw std::runtime_error(std::string("kernel setup: ") + cudaGetErrorString(e));
@@ -84,6 +86,7 @@ __global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunit
     SM& S = *reinterpret_cast<SM*>(smem_base);
     __shared__ uint64_t bars[4];               // one per input-plane slot
     __shared__ int aborted;
+    const int cap = g_march_wait_cap > 0 ? g_march_wait_cap : kSpinCap;
     const LevelView<T>& L = A.L;
     const int nx = L.nx, ny = L.ny, nt = L.nt;
     const long long N = L.N;
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunit
     // bounded wait for the plane of level tau (and what rides on its barrier)
     auto wait_plane = [&](int tau) {
         const int slot = tau & 3;
-        if (mbar_wait_bounded(&bars[slot], (phbits >> slot) & 1u, kSpinCap)) {
+        if (mbar_wait_bounded(&bars[slot], (phbits >> slot) & 1u, cap)) {
             phbits ^= 1u << slot;
             pend &= ~(1u << slot);
         } else {
@@ -384,6 +387,12 @@ CUtensorMap march_map(const T* v, const LevelView<T>& L, int nblk, bool halo) {
 }
 
 }  // namespace
+
+void march_set_wait_cap(int cap) { ok(cudaMemcpyToSymbol(g_march_wait_cap, &cap, sizeof(int))); }
+
+void march_abort_peek_async(int32_t* host1, cudaStream_t s) {
+    ok(cudaMemcpyFromSymbolAsync(host1, g_march_abort, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+}
 
 int march_abort_take(cudaStream_t s) {
     int v = 0;

@@ -105,6 +105,7 @@ def load(build_if_missing: bool = False):
         "gmrf_level_info": (I32, [P, I32, C.POINTER(C.c_int32), DP]),
         "gmrf_prior_logdet": (I32, [C.POINTER(PriorDesc), DP, DP]),
         "gmrf_transfer_info": (I32, [P, C.POINTER(C.c_int32), DP]),
+        "gmrf_test_set_wait_cap": (None, [I32]),
         "gmrf_num_unknowns": (I64, [P]),
         "gmrf_num_levels": (I32, [P]),
         "gmrf_prior_destroy": (None, [P]),

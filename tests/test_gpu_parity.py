@@ -248,3 +248,30 @@ def test_full_size_matern_512_in_the_bench_configuration():
     want = infer.rbmc_variance(orc.Qpost, xs)
     assert _rel(var, want) < VAR_TOL
     assert np.all(np.abs(var - want) <= VAR_TOL * want)
+
+
+def test_bounded_tile_wait_failure_is_reported_and_the_handle_recovers():
+    # The staged-tile waits of the stencil kernels give up after one poll
+    # (gmrf_test_set_wait_cap): the copies are still landing, so the CTAs
+    # record the device flag, drain their in-flight copies with the normal cap
+    # and return.  The solve and the FP64 apply must report GMRF_E_CUDA; with
+    # the default cap restored the same handle solves correctly again.
+    lib = gmrf.load()
+    pr, ob = W.c2_matern(n=96, m=300, seed=6)
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    x = np.random.default_rng(2).normal(size=post.N)
+    try:
+        lib.gmrf_test_set_wait_cap(1)
+        with pytest.raises(gmrf.GmrfError) as e:
+            post.solve_mean()
+        assert e.value.status == 4
+        with pytest.raises(gmrf.GmrfError) as e:
+            post.apply(x)
+        assert e.value.status == 4
+    finally:
+        lib.gmrf_test_set_wait_cap(0)
+    mu, info = post.solve_mean()
+    assert info["converged"] == 1
+    orc = infer.condition(pr, ob)
+    assert _rel(mu, infer.posterior_mean(orc)) < MEAN_TOL
+    assert _rel(post.apply(x)[0], orc.Qpost @ x) < 1e-12
