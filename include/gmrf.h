@@ -26,7 +26,8 @@
  *  - Handles may be destroyed in any order: a prior stays alive until its
  *    own handle and every posterior built on it are destroyed.
  *  - Handles own all device scratch.  Scratch for a batch of k right-hand
- *    sides is allocated at the first call that needs k and reused after.
+ *    sides is allocated at the first call that needs k (or by gmrf_reserve)
+ *    and reused after.
  *  - The first call in a process that draws normals (gmrf_sample,
  *    gmrf_marginal_var, gmrf_normals, gmrf_condition's eigenvalue bound)
  *    fills a 6 KB device table of the Box-Muller transform: one kernel and a
@@ -152,6 +153,16 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
 /* Replaces the point-data values y (length m of the descriptor; host or
  * device memory) without rebuilding the observation operator. */
 gmrf_status gmrf_update_data(gmrf_posterior* post, const double* y);
+
+/* Creates the device scratch and CUDA graphs of a batch of nrhs right-hand
+ * sides (the mean and nrhs - 1 samples) for the options opts (precision,
+ * batched; NULL: defaults) by running that batch once (results discarded).
+ * Later calls of gmrf_solve_mean (nrhs = 1), gmrf_sample and
+ * gmrf_marginal_var with the same batch size and options allocate no device
+ * memory, so they can run where allocation is unwelcome (inside a memory
+ * budget, next to other work).  The paper has no counterpart: it is serving
+ * plumbing. */
+gmrf_status gmrf_reserve(gmrf_posterior* post, int32_t nrhs, const gmrf_solve_opts* opts);
 
 /* Posterior mean mu = Q_u|y^-1 A^T Q_eps y (eq. posterior-mean, prior mean 0).
  * mu: [N]. */

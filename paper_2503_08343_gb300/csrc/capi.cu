@@ -427,6 +427,21 @@ static void write_rows(Posterior& P, Workspace& W, const std::vector<int32_t>& r
     GCK(cudaStreamSynchronize(s));
 }
 
+gmrf_status gmrf_reserve(gmrf_posterior* post, int32_t nrhs, const gmrf_solve_opts* opts) {
+    return guard([&] {
+        require(post && nrhs >= 1, "bad argument");
+        enter(post->prior);
+        Posterior& P = post->impl;
+        const cudaStream_t s = P.prior->stream;
+        const gmrf_solve_opts o = resolve_opts(opts);
+        // one pass of the batch (mean + nrhs - 1 samples) creates every buffer
+        // and CUDA graph of this batch size; its results are discarded
+        const Batch b = make_batch(nrhs - 1, true);
+        run_batch(P, b, 0, o, s);
+        GCK(cudaStreamSynchronize(s));
+    });
+}
+
 gmrf_status gmrf_solve_mean(gmrf_posterior* post, double* mu, const gmrf_solve_opts* opts, gmrf_solve_info* info) {
     gmrf_status rc = GMRF_OK;
     const gmrf_status st = guard([&] {

@@ -90,6 +90,7 @@ def load(build_if_missing: bool = False):
         "gmrf_condition": (I32, [P, C.POINTER(ObsDesc), C.POINTER(P)]),
         "gmrf_update_data": (I32, [P, P]),
         "gmrf_solve_mean": (I32, [P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "gmrf_reserve": (I32, [P, I32, C.POINTER(SolveOpts)]),
         "gmrf_sample": (I32, [P, I32, U64, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "gmrf_marginal_var": (I32, [P, I32, U64, P, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "gmrf_gauss_newton_step": (I32, [P, P, P, DP, DP, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
@@ -235,6 +236,11 @@ class Posterior:
 
     def update_data(self, y):
         _check(load().gmrf_update_data(self.h, _ptr(y)))
+
+    def reserve(self, nrhs, opts=None):
+        """Pre-creates the scratch and graphs of a batch of nrhs right-hand
+        sides (gmrf_reserve)."""
+        _check(load().gmrf_reserve(self.h, nrhs, C.byref(opts or default_opts())))
 
     def solve_mean(self, out=None, opts=None):
         out = np.empty(self.N) if out is None else out

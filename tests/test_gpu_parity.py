@@ -275,3 +275,25 @@ def test_bounded_tile_wait_failure_is_reported_and_the_handle_recovers():
     orc = infer.condition(pr, ob)
     assert _rel(mu, infer.posterior_mean(orc)) < MEAN_TOL
     assert _rel(post.apply(x)[0], orc.Qpost @ x) < 1e-12
+
+
+def test_reserved_batch_allocates_nothing_later():
+    # after gmrf_reserve(17), mean + 16 samples + variances and the mean alone
+    # (a batch of 1 needs its own reservation) leave the free device memory
+    # unchanged
+    torch = pytest.importorskip("torch")
+    pr, ob = W.c2_matern(n=130, m=500, seed=11)
+    post = gmrf.Posterior(gmrf.Prior(pr), ob)
+    post.reserve(17)
+    post.reserve(1)
+    var = torch.empty(post.N, dtype=torch.float64, device="cuda")
+    mu = torch.empty_like(var)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for seed in (3, 4):
+        post.marginal_var(16, seed, out=var)
+        post.solve_mean(out=mu)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    orc = infer.condition(pr, ob)
+    assert _rel(mu.cpu().numpy(), infer.posterior_mean(orc)) < MEAN_TOL
