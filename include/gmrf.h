@@ -320,11 +320,12 @@ gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t preci
 
 /* Test hook for the failure path of the stencil kernels: the number of
  * polls each CTA spends on a bounded wait for a staged input tile before it
- * gives up (0 restores the default, 2^22).  A CTA that gives up records a
- * device flag, still waits (with the default cap) for its copies in flight,
- * and returns; the solver turns the flag into GMRF_E_CUDA and clears it, so
- * the handle stays usable.  With a cap of 1 the waits give up while the
- * copies are still landing.  Process-wide; not for production use. */
+ * gives up (0 restores the default, 2^22; a negative cap gives up without
+ * polling, so every CTA fails its first wait).  A poll may itself block for
+ * a short hardware-defined time.  A CTA that gives up records a device flag,
+ * still waits (with the default cap) for its copies in flight, and returns;
+ * the solver turns the flag into GMRF_E_CUDA and clears it, so the handle
+ * stays usable.  Process-wide; not for production use. */
 void gmrf_test_set_wait_cap(int32_t cap);
 
 /* Number of kernels this library has launched in the process so far

@@ -57,8 +57,9 @@ int march_abort_take(cudaStream_t s);
 void stencil_abort_peek_async(int32_t* host2, cudaStream_t s);
 void march_abort_peek_async(int32_t* host1, cudaStream_t s);
 // test hook: poll cap of the staged-tile waits of both stencil kernels
-// (0: the default 2^22), a device variable read by every CTA (so captured
-// graphs follow it); the drain of in-flight copies keeps the default
+// (0: the default 2^22; negative: give up without polling), a device variable
+// read by every CTA (so captured graphs follow it); the drain of in-flight
+// copies keeps the default
 void set_wait_cap(int cap);
 void march_set_wait_cap(int cap);
 // cuTensorMapEncodeTiled of a dense FP32 (f64 = false) or FP64 array of

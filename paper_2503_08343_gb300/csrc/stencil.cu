@@ -125,7 +125,8 @@ __device__ __forceinline__ void unit_next(UnitPos& p, int tiles_x, int tiles_y, 
 // wait); the solver checks and clears it after every solve.
 __device__ int g_stencil_abort = 0;
 constexpr int kMbarSpinCap = 1 << 22;
-// polls before a staged-tile wait gives up (0: kMbarSpinCap); a test hook
+// polls before a staged-tile wait gives up (0: kMbarSpinCap; negative: give
+// up without polling); a test hook
 __device__ int g_stencil_wait_cap = 0;
 
 template <int GEO, typename T, int MODE, int COL, int NS, int KB>
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     SM& S = *reinterpret_cast<SM*>(smem_base);
     __shared__ uint64_t bars[NS];
     __shared__ int abort_unit;
-    const int cap = g_stencil_wait_cap > 0 ? g_stencil_wait_cap : kMbarSpinCap;
+    const int cap = g_stencil_wait_cap > 0 ? g_stencil_wait_cap : (g_stencil_wait_cap < 0 ? 0 : kMbarSpinCap);
 
     const LevelView<T>& L = A.L;
     const int nx = L.nx, ny = L.ny, nt = L.nt;
@@ -531,7 +532,7 @@ static CUtensorMap tile_map(const T* v, const LevelView<T>& L, int nblk, bool ha
 }
 
 void set_wait_cap(int cap) {
-    const int v = cap > 0 ? cap : 0;
+    const int v = cap;
     cuda_ok(cudaMemcpyToSymbol(g_stencil_wait_cap, &v, sizeof(int)));
     march_set_wait_cap(v);
 }

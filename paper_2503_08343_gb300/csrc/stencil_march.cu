@@ -61,7 +61,8 @@ struct MarchMaps {
 
 __device__ int g_march_abort = 0;
 constexpr int kSpinCap = 1 << 22;
-// polls before a staged-plane wait gives up (0: kSpinCap); a test hook
+// polls before a staged-plane wait gives up (0: kSpinCap; negative: give up
+// without polling); a test hook
 __device__ int g_march_wait_cap = 0;
 
 void ok(cudaError_t e) {
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(256) k_march(const StencilArgs<T> A, int nunit
     SM& S = *reinterpret_cast<SM*>(smem_base);
     __shared__ uint64_t bars[4];               // one per input-plane slot
     __shared__ int aborted;
-    const int cap = g_march_wait_cap > 0 ? g_march_wait_cap : kSpinCap;
+    const int cap = g_march_wait_cap > 0 ? g_march_wait_cap : (g_march_wait_cap < 0 ? 0 : kSpinCap);
     const LevelView<T>& L = A.L;
     const int nx = L.nx, ny = L.ny, nt = L.nt;
     const long long N = L.N;

@@ -251,8 +251,8 @@ def test_full_size_matern_512_in_the_bench_configuration():
 
 
 def test_bounded_tile_wait_failure_is_reported_and_the_handle_recovers():
-    # The staged-tile waits of the stencil kernels give up after one poll
-    # (gmrf_test_set_wait_cap): the copies are still landing, so the CTAs
+    # The staged-tile waits of the stencil kernels give up without polling
+    # (gmrf_test_set_wait_cap(-1)): the copies are still landing, so the CTAs
     # record the device flag, drain their in-flight copies with the normal cap
     # and return.  The solve and the FP64 apply must report GMRF_E_CUDA; with
     # the default cap restored the same handle solves correctly again.
@@ -261,7 +261,7 @@ def test_bounded_tile_wait_failure_is_reported_and_the_handle_recovers():
     post = gmrf.Posterior(gmrf.Prior(pr), ob)
     x = np.random.default_rng(2).normal(size=post.N)
     try:
-        lib.gmrf_test_set_wait_cap(1)
+        lib.gmrf_test_set_wait_cap(-1)
         with pytest.raises(gmrf.GmrfError) as e:
             post.solve_mean()
         assert e.value.status == 4
