@@ -215,6 +215,7 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
         for (Level& L : P.levels) {   // device members are per posterior
             L.d_obs = nullptr; L.d_tile_ptr = nullptr; L.d_tile_idx = nullptr;
             L.d_omap = nullptr; L.d_oent32 = nullptr; L.d_oent64 = nullptr;
+            L.d_tsp32 = nullptr; L.d_tsp64 = nullptr;
         }
         const int dimc = d.kind == GMRF_ADVDIFF_ST_2D ? 3 : 2;
         P.m = obs->m;
@@ -296,6 +297,7 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
         posterior_setup_levels(P, s);
         if (obs->ic) P.ic_rinv = 1.0 / (obs->ic_sigma * obs->ic_sigma);
         P.use_tsp = tsp_applicable(P.levels[0], (int)P.nic);
+        if (P.use_tsp) tsp_prepare(P.levels[0], s);
         dev_upload(&P.d_bstatic, bstatic);
         if (P.nic) dev_upload(&P.d_icvals, P.ic_values);
         P.d_bdata = dev_alloc<double>((size_t)F.N);

@@ -85,6 +85,7 @@ void noalloc_prepare(const Posterior& P);
 
 // tsp.cu
 bool tsp_applicable(const Level& L, int nic);
+void tsp_prepare(Level& L, cudaStream_t s);
 template <typename T>
 void launch_tsp(const Level& L, double w_ic, double w_bnd, const T* r, T* y, T* z, int nblk, cudaStream_t s);
 

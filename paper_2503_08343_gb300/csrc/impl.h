@@ -106,6 +106,9 @@ struct Level {
     // largest fine span (x, y) under one restriction tile of kRestrictTX x
     // kRestrictTY coarse nodes (sizes the shared-memory tile)
     int rspan[2] = {0, 0};
+    // time-stepping preconditioner factors (collocation levels), device
+    float* d_tsp32 = nullptr;
+    double* d_tsp64 = nullptr;
     // coarsest level: dense inverse of Q_u|y (device, row-major)
     float* d_dense32 = nullptr;
     double* d_dense64 = nullptr;

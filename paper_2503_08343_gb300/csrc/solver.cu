@@ -54,6 +54,7 @@ void level_free(Level& L) {
         dev_free(L.d_pj[a]); dev_free(L.d_pw[a]); dev_free(L.d_pwd[a]); dev_free(L.d_rs[a]); dev_free(L.d_rc[a]);
     }
     dev_free(L.d_dense32); dev_free(L.d_dense64);
+    dev_free(L.d_tsp32); dev_free(L.d_tsp64);
     L = Level();
 }
 
