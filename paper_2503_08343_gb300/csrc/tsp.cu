@@ -17,36 +17,41 @@ namespace gmrf {
 
 namespace {
 
-constexpr int kTspRows = 31;                 // interior rows per lane: nx <= 32 (kTspRows + 1)
-constexpr int kTspMaxNx = 32 * (kTspRows + 1);
-
-// Each right-hand side is swept by one warp.  A level's tridiagonal system
-// (nx <= 32 (M + 1) rows) is solved by the partition method: lane l owns the
-// contiguous rows [l m, l m + m), m = ceil(nx / 32); the last row of each chunk
-// is a separator.  The chunk's interior rows are eliminated by a Thomas sweep
-// with three right-hand sides, giving x_i = p_i + q_i X_{l-1} + r_i X_l in
-// terms of the neighbouring separators; substituting into the separator rows
-// leaves a 32-unknown tridiagonal system, one unknown per lane, solved by
-// parallel cyclic reduction with warp shuffles; the interior rows follow by
-// back-substitution.
+// Each level's tridiagonal system (nx <= kLanes (kRows + 1) rows) is solved
+// by the partition method over kLanes = 32 kWarps lanes of one CTA: lane l
+// owns the contiguous rows [l m, l m + m), m = ceil(nx / kLanes); the last row
+// of each chunk is a separator.  The chunk's interior rows are eliminated by a
+// Thomas sweep with three right-hand sides, giving
+// x_i = p_i + q_i X_{l-1} + r_i X_l in terms of the neighbouring separators;
+// substituting into the separator rows leaves a kLanes-unknown tridiagonal
+// system, one unknown per lane, solved by parallel cyclic reduction (warp
+// shuffles for strides below 32, shared memory above); the interior rows
+// follow by back-substitution.  Spreading a level over four warps keeps each
+// lane's recurrences short (at most kRows rows): a level is a dependency
+// chain, so its latency, not the throughput, sets the time.
 //
 // Everything that depends on the matrix alone (the Thomas pivots and
 // multipliers, the interface columns q and r, the separator coefficients and
 // the cyclic-reduction multipliers) is the same for every right-hand side and
 // every application in a solve, so k_tsp_factor computes it once per
 // linearisation, for every level and both sweep directions; an application
-// (k_tsp) then runs only the right-hand-side recurrences: no divisions, one
-// dependent FMA per row and direction.  A CTA holds the four warps of one
-// block of right-hand sides; each level's inputs and factors are staged in
-// shared memory by cp.async one level ahead (double-buffered).
+// (k_tsp) then runs only the right-hand-side recurrences, without divisions,
+// on the four right-hand sides of one block at once (a lane carries them as
+// one vector).  Each level's inputs and factors are staged in shared memory
+// by cp.async one level ahead (double-buffered).
 //
 // Factors of one (direction, level), in elements of T:
-//   row fields [5][32][32] (field, chunk row j, lane): A_j/den_j, 1/den_j,
-//     c'_j (Thomas), Q_j, R_j (interface columns after back-substitution);
-//   lane fields [13][32]: separator A and C, the cyclic-reduction
-//     multipliers k1, k2 of its 5 steps, 1 / final diagonal.
-constexpr int kRowF = 5, kLaneF = 13;
-constexpr int kFactorBlock = kRowF * 32 * 32 + kLaneF * 32;
+//   row fields [5][kRows][kLanes] (field, chunk row j, lane): A_j/den_j,
+//     1/den_j, c'_j (Thomas), Q_j, R_j (interface columns after
+//     back-substitution);
+//   lane fields [3 + 2 kSteps][kLanes]: separator A and C, 1 / final
+//     diagonal, the cyclic-reduction multipliers k1 and k2 of every step.
+constexpr int kWarps = 4, kLanes = 32 * kWarps, kSteps = 7;    // 2^kSteps = kLanes
+constexpr int kRows = 8;                                        // interior rows per lane
+constexpr int kTspMaxNx = kLanes * (kRows + 1);
+constexpr int kRowF = 5, kLaneF = 3 + 2 * kSteps;
+constexpr int kFactorBlock = kRowF * kRows * kLanes + kLaneF * kLanes;
+static_assert((1 << kSteps) == kLanes, "cyclic reduction covers the lanes");
 
 // Level row coefficients of J (lower x-1, diagonal, upper x+1) at node x of
 // level k, with mu the linearisation point of the level (Burgers).
@@ -81,26 +86,28 @@ __device__ __forceinline__ void level_row(const LevelView<T>& L, const T* mu, in
     if (x < L.nx - 1) { j_row<T>(L, mu, x + 1, k, l2, d2, u2); C = l2; }
 }
 
-// One warp per (direction, level): the matrix-only part of the partition
-// solve.  blockIdx.x = dir * nt + k, dir 0 = D_k (forward sweep), 1 = D_k^T.
+// One CTA of kLanes threads per (direction, level): the matrix-only part of
+// the partition solve.  blockIdx.x = dir * nt + k, dir 0 = D_k (forward
+// sweep), 1 = D_k^T.
 template <typename T>
-__global__ void __launch_bounds__(32) k_tsp_factor(const LevelView<T> L, T* __restrict__ f) {
-    const unsigned FULL = 0xffffffffu;
+__global__ void __launch_bounds__(kLanes) k_tsp_factor(const LevelView<T> L, T* __restrict__ f) {
+    __shared__ T xa[kLanes], xb[kLanes], xc[kLanes];
     const int nx = L.nx, nt = L.nt;
     const int dir = blockIdx.x / nt, k = blockIdx.x % nt;
     const int lane = threadIdx.x;
-    const int m = (nx + 31) / 32, s = lane * m, mi = max(0, min(m, nx - s)), mint = mi - 1;
+    const int m = (nx + kLanes - 1) / kLanes, s = lane * m, mi = max(0, min(m, nx - s)), mint = mi - 1;
     const T* mu = L.col.kind == 2 ? L.mu + (size_t)k * nx : nullptr;
     T* blk = f + (size_t)blockIdx.x * kFactorBlock;
-    T* rowf = blk;                               // [field][j][lane]
-    T* lanef = blk + kRowF * 32 * 32;            // [field][lane]
+    T* rowf = blk;                                   // [field][j][lane]
+    T* lanef = blk + kRowF * kRows * kLanes;         // [field][lane]
     auto row = [&](int x, T& A, T& B, T& C) {
         if (dir == 0) level_row<T, false>(L, mu, x, k, A, B, C);
         else level_row<T, true>(L, mu, x, k, A, B, C);
     };
-    T qv[32], rv[32], cv[32];
+    T qv[kRows], rv[kRows], cv[kRows];
     T cprev = T(0), qprev = T(0);
-    for (int j = 0; j < 32; ++j) {
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
         T ainv = T(0), inv = T(0), c = T(0), q = T(0), r = T(0);
         if (j < mint) {
             T A, B, C;
@@ -114,39 +121,41 @@ __global__ void __launch_bounds__(32) k_tsp_factor(const LevelView<T> L, T* __re
             cprev = c;
             qprev = q;
         }
-        rowf[(0 * 32 + j) * 32 + lane] = ainv;
-        rowf[(1 * 32 + j) * 32 + lane] = inv;
-        rowf[(2 * 32 + j) * 32 + lane] = c;
+        rowf[(0 * kRows + j) * kLanes + lane] = ainv;
+        rowf[(1 * kRows + j) * kLanes + lane] = inv;
+        rowf[(2 * kRows + j) * kLanes + lane] = c;
         qv[j] = q;
         rv[j] = r;
         cv[j] = c;
     }
-    T qn = T(0), rn = T(0);
-    for (int j = 31; j >= 0; --j) {
+    T qn = T(0), rn = T(0), ql = T(1), rl = T(0);
+#pragma unroll
+    for (int j = kRows - 1; j >= 0; --j) {
         if (j < mint) {
             qv[j] = qv[j] - cv[j] * qn;
             rv[j] = rv[j] - cv[j] * rn;
             qn = qv[j];
             rn = rv[j];
+            if (j == mint - 1) { ql = qv[j]; rl = rv[j]; }
         }
-        rowf[(3 * 32 + j) * 32 + lane] = j < mint ? qv[j] : T(0);
-        rowf[(4 * 32 + j) * 32 + lane] = j < mint ? rv[j] : T(0);
+        rowf[(3 * kRows + j) * kLanes + lane] = j < mint ? qv[j] : T(0);
+        rowf[(4 * kRows + j) * kLanes + lane] = j < mint ? rv[j] : T(0);
     }
     // separator row: A x_{e-2} + B X_l + C x_e, with x_{e-2} = p + ql X_{l-1} + rl X_l
     // (own last interior row) and x_e = p + qf X_l + rf X_{l+1} (next lane's first row)
     T qf = mint > 0 ? qv[0] : T(0), rf = mint > 0 ? rv[0] : T(1);
     if (mi <= 0) { qf = T(0); rf = T(0); }
-    const T qnx = __shfl_down_sync(FULL, qf, 1), rnx = __shfl_down_sync(FULL, rf, 1);
+    xa[lane] = qf;
+    xb[lane] = rf;
+    __syncthreads();
+    const T qnx = lane + 1 < kLanes ? xa[lane + 1] : T(0), rnx = lane + 1 < kLanes ? xb[lane + 1] : T(0);
+    __syncthreads();
     T Asep = T(0), Csep = T(0), ra = T(0), rb = T(1), rc = T(0);
     if (mi > 0) {
         T A, B, C;
         row(s + mi - 1, A, B, C);
-        if (lane == 31 || s + mi >= nx) C = T(0);
-        T ql = T(1), rl = T(0);
-        if (mint > 0) {
-            for (int j = 0; j < 32; ++j)
-                if (j == mint - 1) { ql = qv[j]; rl = rv[j]; }
-        }
+        if (lane == kLanes - 1 || s + mi >= nx) C = T(0);
+        if (mint == 0) { ql = T(1); rl = T(0); }
         if (s == 0 && mint == 0) ql = T(0);
         Asep = A;
         Csep = C;
@@ -154,189 +163,185 @@ __global__ void __launch_bounds__(32) k_tsp_factor(const LevelView<T> L, T* __re
         rb = B + A * rl + C * qnx;
         rc = C * rnx;
     }
-    lanef[0 * 32 + lane] = Asep;
-    lanef[1 * 32 + lane] = Csep;
+    lanef[0 * kLanes + lane] = Asep;
+    lanef[1 * kLanes + lane] = Csep;
     int step = 0;
-    for (int st = 1; st < 32; st <<= 1, ++step) {
-        const T am = __shfl_up_sync(FULL, ra, st), bm = __shfl_up_sync(FULL, rb, st), cm = __shfl_up_sync(FULL, rc, st);
-        const T ap = __shfl_down_sync(FULL, ra, st), bp = __shfl_down_sync(FULL, rb, st), cp2 = __shfl_down_sync(FULL, rc, st);
-        const bool hm = lane - st >= 0, hp = lane + st < 32;
+    for (int st = 1; st < kLanes; st <<= 1, ++step) {
+        xa[lane] = ra;
+        xb[lane] = rb;
+        xc[lane] = rc;
+        __syncthreads();
+        const bool hm = lane - st >= 0, hp = lane + st < kLanes;
+        const T am = hm ? xa[lane - st] : T(0), bm = hm ? xb[lane - st] : T(1), cm = hm ? xc[lane - st] : T(0);
+        const T ap = hp ? xa[lane + st] : T(0), bp = hp ? xb[lane + st] : T(1), cp2 = hp ? xc[lane + st] : T(0);
+        __syncthreads();
         const T k1 = hm ? ra / bm : T(0), k2 = hp ? rc / bp : T(0);
         const T na = hm ? -am * k1 : T(0), nc = hp ? -cp2 * k2 : T(0);
         const T nb = rb - (hm ? cm * k1 : T(0)) - (hp ? ap * k2 : T(0));
         ra = na;
         rb = nb;
         rc = nc;
-        lanef[(2 + step) * 32 + lane] = k1;
-        lanef[(7 + step) * 32 + lane] = k2;
+        lanef[(3 + step) * kLanes + lane] = k1;
+        lanef[(3 + kSteps + step) * kLanes + lane] = k2;
     }
-    lanef[12 * 32 + lane] = T(1) / rb;
+    lanef[2 * kLanes + lane] = T(1) / rb;
 }
 
-// The right-hand-side part of one level solve for the lane's rows (interior
-// rows j < mi - 1 in xv[], the separator's right-hand side dsep, its solution
-// in X), with the factors of the level staged at rowf / lanef.
-template <typename T, int M>
-__device__ __forceinline__ void warp_tridiag_rhs(const T* rowf, const T* lanef, int mi, T (&xv)[M], T dsep, T& Xout) {
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int mint = mi - 1;
-    auto F = [&](int field, int j) { return rowf[(field * 32 + j) * 32 + lane]; };
-    // forward: p'_j = d_j / den_j - (A_j / den_j) p'_{j-1}
-    T pprev = T(0);
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        if (j < mint) {
-            pprev = xv[j] * F(1, j) - F(0, j) * pprev;
-            xv[j] = pprev;
-        }
-    }
-    const T plast = mint > 0 ? pprev : T(0);
-    // backward: P_j = p'_j - c'_j P_{j+1}
-    T pn = T(0);
-#pragma unroll
-    for (int j = M - 1; j >= 0; --j) {
-        if (j < mint) {
-            pn = xv[j] - F(2, j) * pn;
-            xv[j] = pn;
-        }
-    }
-    T pf = mint > 0 ? xv[0] : T(0);
-    if (mi <= 0) pf = T(0);
-    const T pnx = __shfl_down_sync(FULL, pf, 1);
-    T rd = mi > 0 ? dsep - lanef[0 * 32 + lane] * plast - lanef[1 * 32 + lane] * pnx : T(0);
-    int step = 0;
-#pragma unroll
-    for (int st = 1; st < 32; st <<= 1, ++step) {
-        const T dm = __shfl_up_sync(FULL, rd, st), dp = __shfl_down_sync(FULL, rd, st);
-        rd = rd - lanef[(2 + step) * 32 + lane] * dm - lanef[(7 + step) * 32 + lane] * dp;
-    }
-    const T X = rd * lanef[12 * 32 + lane];
-    T Xl = __shfl_up_sync(FULL, X, 1);
-    if (lane == 0) Xl = T(0);
-#pragma unroll
-    for (int j = 0; j < M; ++j)
-        if (j < mint) xv[j] = xv[j] + F(3, j) * Xl + F(4, j) * X;
-    Xout = X;
-}
-
-// One CTA of four warps per block of four right-hand sides; warp w sweeps
-// component w.  y is scratch of the blocked layout; r and z are blocked.
-template <typename T, int M>
-__global__ void __launch_bounds__(128) k_tsp(const LevelView<T> L, const T* __restrict__ fac, T w_ic, T w_bnd,
-                                            const T* __restrict__ r, T* __restrict__ y, T* __restrict__ z) {
+// One CTA (kLanes threads) per block of four right-hand sides.  y is scratch
+// of the blocked layout; r and z are blocked.  Shared memory: factors
+// [2][kFactorBlock], inputs [2][nx + kLanes] four-wide chunks laid out with one
+// gap after each lane's chunk (x -> x + x / m: a lane reads its rows at
+// base + j, and neighbouring lanes fall in distinct bank groups), the lane
+// exchange buffers.
+template <typename T>
+__global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* __restrict__ fac, T iw_ic, T iw_bnd,
+                                               T iw_q, const T* __restrict__ r, T* __restrict__ y, T* __restrict__ z) {
     extern __shared__ __align__(16) unsigned char tsp_smem[];
+    __shared__ V4<T> xch[2][kLanes];
     const int nx = L.nx, nt = L.nt;
     const long long N = L.N;
-    const int NXP = nx + (nx >> 5) + 1;                  // padded input row
-    const int SIN = ((4 * NXP + 3) / 4) * 4;             // elements of one stage of inputs (16-byte multiple)
+    const int NXC = nx + kLanes;                         // chunks per input row, gaps included
     T* sfac = reinterpret_cast<T*>(tsp_smem);            // [2][kFactorBlock]
-    T* sin = sfac + 2 * kFactorBlock;                    // [2][4][NXP]
-    const int blk = blockIdx.x, tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int m = (nx + 31) / 32;
-    const int s0 = lane * m, mi = max(0, min(m, nx - s0));
+    V4<T>* sin = reinterpret_cast<V4<T>*>(sfac + 2 * kFactorBlock);   // [2][NXC]
+    const int lane = threadIdx.x, wl = lane & 31;
+    const int blk = blockIdx.x;
+    const int m = (nx + kLanes - 1) / kLanes;
+    const float rm = 1.0f / (float)m;
+    const int s0 = lane * m, mi = max(0, min(m, nx - s0)), mint = mi - 1;
+    const int ibase = s0 + lane;                         // this lane's first row in the staged layout
     const T inv_dt = (T)L.col.inv_dt;
-    const T wq = (T)L.col.qeps;
     auto stage = [&](const T* src, int dir, int k, int slot) {
         if (k < 0 || k >= nt) return;
-        const T* g = src + ((size_t)blk * N + (size_t)k * nx) * RW;
-        T* d = sin + (size_t)slot * SIN;
-        for (int e = tid; e < 4 * nx; e += 128) {
-            const int x = e >> 2, c = e & 3;
-            cp_scalar<T>(d + (size_t)c * NXP + x + (x >> 5), g + e, true);
+        const char* g = reinterpret_cast<const char*>(src + ((size_t)blk * N + (size_t)k * nx) * RW);
+        V4<T>* d = sin + (size_t)slot * NXC;
+        for (int x = lane; x < nx; x += kLanes) {
+            int own = (int)((float)x * rm);          // x / m without an integer division
+            own += (own + 1) * m <= x;
+            own -= own * m > x;
+            char* dx = reinterpret_cast<char*>(d + x + own);
+            cp_async16(dx, g + (size_t)x * sizeof(V4<T>), true);
+            if (sizeof(T) == 8) cp_async16(dx + 16, g + (size_t)x * sizeof(V4<T>) + 16, true);
         }
         const char* gf = reinterpret_cast<const char*>(fac + ((size_t)dir * nt + k) * kFactorBlock);
         char* df = reinterpret_cast<char*>(sfac + (size_t)slot * kFactorBlock);
-        for (int c = tid; c < (int)(kFactorBlock * sizeof(T) / 16); c += 128) cp_async16(df + c * 16, gf + c * 16, true);
+        for (int c = lane; c < (int)(kFactorBlock * sizeof(T) / 16); c += kLanes) cp_async16(df + c * 16, gf + c * 16, true);
     };
-    T xv[M], carry[M], csep = T(0);
+    // four-wide exchange with the lane d below / above (shuffles within a warp,
+    // shared memory across warps; every thread calls it)
+    int xsel = 0;
+    auto exch = [&](V4<T> v, int d, V4<T>& up, V4<T>& dn) {
+        if (d < 32) {
+            up = V4<T>{__shfl_up_sync(0xffffffffu, v.a, d), __shfl_up_sync(0xffffffffu, v.b, d),
+                       __shfl_up_sync(0xffffffffu, v.c, d), __shfl_up_sync(0xffffffffu, v.d, d)};
+            dn = V4<T>{__shfl_down_sync(0xffffffffu, v.a, d), __shfl_down_sync(0xffffffffu, v.b, d),
+                       __shfl_down_sync(0xffffffffu, v.c, d), __shfl_down_sync(0xffffffffu, v.d, d)};
+            // the neighbour lies in the next or previous warp: through shared memory
+            const bool need_up = wl - d < 0 && lane - d >= 0, need_dn = wl + d >= 32 && lane + d < kLanes;
+            xch[xsel][lane] = v;
+            __syncthreads();
+            if (need_up) up = xch[xsel][lane - d];
+            if (need_dn) dn = xch[xsel][lane + d];
+            if (lane - d < 0) up = v4zero<T>();
+            if (lane + d >= kLanes) dn = v4zero<T>();
+        } else {
+            xch[xsel][lane] = v;
+            __syncthreads();
+            up = lane - d >= 0 ? xch[xsel][lane - d] : v4zero<T>();
+            dn = lane + d < kLanes ? xch[xsel][lane + d] : v4zero<T>();
+        }
+        xsel ^= 1;          // the next exchange writes the other buffer (no second barrier)
+    };
+    V4<T> xv[kRows], car[kRows], csep = v4zero<T>();
 #pragma unroll
-    for (int j = 0; j < M; ++j) carry[j] = T(0);
+    for (int j = 0; j < kRows; ++j) car[j] = v4zero<T>();
     const int xs = s0 + mi - 1;
     const bool xs_int = xs > 0 && xs < nx - 1;
-    // backward sweep: J^T y = r from the last level down, then y / W
-    stage(r, 1, nt - 1, 0);
-    cp_commit();
-    for (int k = nt - 1; k >= 0; --k) {
-        const int slot = (nt - 1 - k) & 1;
-        cp_wait<0>();
-        __syncthreads();                  // level k landed; level k+1's buffers are free
-        stage(r, 1, k - 1, slot ^ 1);
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        // sweep 0, backward: J^T y = r from the last level down, then y / W;
+        // sweep 1, forward: J z = W^-1 y from the first level up
+        const bool bwd = sweep == 0;
+        const T* src = bwd ? r : y;
+        T* dst = bwd ? y : z;
+        const int dir = bwd ? 1 : 0;
+        if (!bwd) {
+            __syncthreads();               // every lane's y rows written
+#pragma unroll
+            for (int j = 0; j < kRows; ++j) car[j] = v4zero<T>();
+            csep = v4zero<T>();
+        }
+        stage(src, dir, bwd ? nt - 1 : 0, 0);
         cp_commit();
-        const T* in = sin + (size_t)slot * SIN + (size_t)w * NXP;
-        const T* fk = sfac + (size_t)slot * kFactorBlock;
+        for (int i = 0; i < nt; ++i) {
+            const int k = bwd ? nt - 1 - i : i;
+            const int slot = i & 1;
+            cp_wait<0>();
+            __syncthreads();               // level k landed; the other buffers are free
+            stage(src, dir, bwd ? k - 1 : k + 1, slot ^ 1);
+            cp_commit();
+            const V4<T>* in = sin + (size_t)slot * NXC + ibase;
+            const T* rowf = sfac + (size_t)slot * kFactorBlock;
+            const T* lanef = rowf + kRowF * kRows * kLanes;
+            auto F = [&](int field, int j) { return rowf[(field * kRows + j) * kLanes + lane]; };
+            const bool couple = bwd ? k + 1 < nt : k > 0;     // the level reached by the time step
+            const int jlo = s0 > 0 ? 0 : 1;                  // x = 0 (lane 0, row 0) is a boundary node
+            // right-hand sides of the interior rows, then p'_j = d_j / den_j - (A_j / den_j) p'_{j-1}
+            V4<T> pprev = v4zero<T>();
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            if (j < mi - 1) {
-                const int x = s0 + j;
-                T v = in[x + (x >> 5)];
-                if (k + 1 < nt && x > 0 && x < nx - 1) v += inv_dt * carry[j];
-                xv[j] = v;
+            for (int j = 0; j < kRows; ++j) {
+                if (j < mint) {
+                    V4<T> v = in[j];
+                    if (couple && j >= jlo) v = fma4(inv_dt, car[j], v);
+                    pprev = fma4(-F(0, j), pprev, F(1, j) * v);
+                    xv[j] = pprev;
+                }
             }
-        }
-        T dsep = T(0), X = T(0);
-        if (mi > 0) {
-            dsep = in[xs + (xs >> 5)];
-            if (k + 1 < nt && xs_int) dsep += inv_dt * csep;
-        }
-        warp_tridiag_rhs<T, M>(fk, fk + kRowF * 32 * 32, mi, xv, dsep, X);
-        const T wi = k == 0 ? w_ic : wq;                    // interior x; boundary x gets w_bnd
+            const V4<T> plast = mint > 0 ? pprev : v4zero<T>();
+            // backward: P_j = p'_j - c'_j P_{j+1}
+            V4<T> pn = v4zero<T>();
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            if (j < mi - 1) {
-                const int x = s0 + j;
-                carry[j] = xv[j];
-                const T wt = (x == 0 || x == nx - 1) ? w_bnd : wi;
-                y[((size_t)blk * N + (size_t)k * nx + x) * RW + w] = xv[j] / wt;
+            for (int j = kRows - 1; j >= 0; --j) {
+                if (j < mint) {
+                    pn = fma4(-F(2, j), pn, xv[j]);
+                    xv[j] = pn;
+                }
             }
-        }
-        if (mi > 0) {
-            csep = X;
-            const T wt = (xs == 0 || xs == nx - 1) ? w_bnd : wi;
-            y[((size_t)blk * N + (size_t)k * nx + xs) * RW + w] = X / wt;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < M; ++j) carry[j] = T(0);
-    csep = T(0);
-    // forward sweep: J z = W^-1 y from the first level up
-    stage(y, 0, 0, 0);
-    cp_commit();
-    for (int k = 0; k < nt; ++k) {
-        const int slot = k & 1;
-        cp_wait<0>();
-        __syncthreads();
-        stage(y, 0, k + 1, slot ^ 1);
-        cp_commit();
-        const T* in = sin + (size_t)slot * SIN + (size_t)w * NXP;
-        const T* fk = sfac + (size_t)slot * kFactorBlock;
-#pragma unroll
-        for (int j = 0; j < M; ++j) {
-            if (j < mi - 1) {
-                const int x = s0 + j;
-                T v = in[x + (x >> 5)];
-                if (k > 0 && x > 0 && x < nx - 1) v += inv_dt * carry[j];
-                xv[j] = v;
+            // separator row: d - A P_{e-2} - C P_e (P_e: the next lane's first row)
+            V4<T> dsep = v4zero<T>();
+            if (mi > 0) {
+                dsep = in[mi - 1];
+                if (couple && xs_int) dsep = fma4(inv_dt, csep, dsep);
             }
-        }
-        T dsep = T(0), X = T(0);
-        if (mi > 0) {
-            dsep = in[xs + (xs >> 5)];
-            if (k > 0 && xs_int) dsep += inv_dt * csep;
-        }
-        warp_tridiag_rhs<T, M>(fk, fk + kRowF * 32 * 32, mi, xv, dsep, X);
+            const V4<T> pf = mint > 0 ? xv[0] : v4zero<T>();
+            V4<T> pup, pnx;
+            exch(pf, 1, pup, pnx);
+            V4<T> rd = v4zero<T>();
+            if (mi > 0) rd = fma4(-lanef[1 * kLanes + lane], pnx, fma4(-lanef[0 * kLanes + lane], plast, dsep));
+            int step = 0;
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            if (j < mi - 1) {
-                const int x = s0 + j;
-                carry[j] = xv[j];
-                z[((size_t)blk * N + (size_t)k * nx + x) * RW + w] = xv[j];
+            for (int st = 1; st < kLanes; st <<= 1, ++step) {
+                V4<T> dm, dp;
+                exch(rd, st, dm, dp);
+                rd = fma4(-lanef[(3 + kSteps + step) * kLanes + lane], dp, fma4(-lanef[(3 + step) * kLanes + lane], dm, rd));
             }
-        }
-        if (mi > 0) {
-            csep = X;
-            z[((size_t)blk * N + (size_t)k * nx + xs) * RW + w] = X;
+            const V4<T> X = lanef[2 * kLanes + lane] * rd;
+            V4<T> Xl, Xr;
+            exch(X, 1, Xl, Xr);
+            const T iwi = k == 0 ? iw_ic : iw_q;               // interior x; boundary x gets iw_bnd
+            T* ob = dst + ((size_t)blk * N + (size_t)k * nx + s0) * RW;
+#pragma unroll
+            for (int j = 0; j < kRows; ++j) {
+                if (j < mint) {
+                    const V4<T> xj = fma4(F(4, j), X, fma4(F(3, j), Xl, xv[j]));
+                    car[j] = xj;
+                    const T wsc = (s0 + j == 0) ? iw_bnd : iwi;
+                    v4store(ob + (size_t)j * RW, bwd ? wsc * xj : xj);
+                }
+            }
+            if (mi > 0) {
+                csep = X;
+                const T wsc = (xs == 0 || xs == nx - 1) ? iw_bnd : iwi;
+                v4store(ob + (size_t)(xs - s0) * RW, bwd ? wsc * X : X);
+            }
         }
     }
 }
@@ -354,26 +359,26 @@ void tsp_prepare(Level& L, cudaStream_t s) {
     const size_t n = (size_t)2 * L.nt * kFactorBlock;
     if (!L.d_tsp32) L.d_tsp32 = dev_alloc<float>(n);
     if (!L.d_tsp64) L.d_tsp64 = dev_alloc<double>(n);
-    k_tsp_factor<float><<<2 * L.nt, 32, 0, s>>>(L.view<float>(), L.d_tsp32);
+    k_tsp_factor<float><<<2 * L.nt, kLanes, 0, s>>>(L.view<float>(), L.d_tsp32);
     note_launch();
-    k_tsp_factor<double><<<2 * L.nt, 32, 0, s>>>(L.view<double>(), L.d_tsp64);
+    k_tsp_factor<double><<<2 * L.nt, kLanes, 0, s>>>(L.view<double>(), L.d_tsp64);
     note_launch();
     GCK(cudaGetLastError());
 }
 
 template <typename T>
 void launch_tsp(const Level& L, double w_ic, double w_bnd, const T* r, T* y, T* z, int nblk, cudaStream_t s) {
-    const int nxp = L.nx + (L.nx >> 5) + 1;
-    const size_t smem = sizeof(T) * (size_t)(2 * kFactorBlock + 2 * (((4 * nxp + 3) / 4) * 4));
+    const size_t smem = sizeof(T) * (size_t)2 * kFactorBlock + sizeof(V4<T>) * (size_t)2 * (L.nx + kLanes);
     const T* fac = sizeof(T) == 4 ? reinterpret_cast<const T*>(L.d_tsp32) : reinterpret_cast<const T*>(L.d_tsp64);
     if (!fac) throw Error(GMRF_E_INVALID, "time-stepping preconditioner: factors not prepared");
     static size_t attr = 0;
     if (smem > attr) {
-        if (cudaFuncSetAttribute(k_tsp<T, kTspRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_tsp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             throw Error(GMRF_E_CUDA, "time-stepping preconditioner: shared memory attribute");
         attr = smem;
     }
-    k_tsp<T, kTspRows><<<nblk, 128, smem, s>>>(L.view<T>(), fac, (T)w_ic, (T)w_bnd, r, y, z);
+    const double iq = L.col.qeps > 0 ? 1.0 / L.col.qeps : 0.0;
+    k_tsp<T><<<nblk, kLanes, smem, s>>>(L.view<T>(), fac, (T)(1.0 / w_ic), (T)(1.0 / w_bnd), (T)iq, r, y, z);
     note_launch();
 }
 template void launch_tsp<float>(const Level&, double, double, const float*, float*, float*, int, cudaStream_t);
