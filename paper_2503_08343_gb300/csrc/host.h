@@ -71,6 +71,7 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
                          cudaStream_t s, bool x_zero = false);
 void apply64(Posterior& P, int nblk, const double* x64, double* y64, cudaStream_t s);
 Workspace& workspace(Posterior& P, int nblk);
+void solve_graph_free(SolveGraph* g);
 void workspace_free(Workspace* w);
 double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s);
 // One launch of the fused stencil on `level` in FP32 (prec 0) or FP64 (1):
@@ -162,6 +163,7 @@ struct Workspace {
     double* h_red = nullptr;       // pinned host mirror of `red`
     double* h_active = nullptr;    // pinned host mirror of the active flags
     int32_t* h_abort = nullptr;    // pinned copies of the two stencil abort flags
+    SolveGraph* sgraph = nullptr;  // device-driven solve of this batch size (solver.cu)
     int32_t* slot_a = nullptr;     // per-slot ids (device)
     int32_t* slot_b = nullptr;
     // per-level vectors for each precision

@@ -130,6 +130,7 @@ struct Prior {
 };
 
 struct Workspace;
+struct SolveGraph;
 
 constexpr double kP1DataShare = 0.5;
 constexpr int kRestrictTX = 32, kRestrictTY = 8;

@@ -8,8 +8,10 @@
 // rediscretised on coarser grids, and a dense inverse on the coarsest level.
 // One PCG iteration is captured into a CUDA graph and replayed.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "host.h"
@@ -216,6 +218,8 @@ void workspace_free(Workspace* w) {
     if (w->h_red) cudaFreeHost(w->h_red);
     if (w->h_active) cudaFreeHost(w->h_active);
     if (w->h_abort) cudaFreeHost(w->h_abort);
+    solve_graph_free(w->sgraph);
+    w->sgraph = nullptr;
     free_vecs(w->v32);
     free_vecs(w->v64);
     delete w;
@@ -368,6 +372,35 @@ static void pcg_iteration(Posterior& P, Workspace& W, Workspace::Vecs& V, double
 
 static const int kItersPerGraph = 2;
 
+// the device-driven solve graph (on by default; GMRF_DEVICE_LOOP=0 selects the
+// host-driven loop, which also serves the plain FP64 path and timeouts)
+static bool device_loop_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("GMRF_DEVICE_LOOP");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+// x = 0, rz = r^T M r with z = M r, p = z: the start of a PCG solve on the
+// right-hand side already in V.pcg[1]
+template <typename T>
+static void pcg_prologue(Posterior& P, Workspace& W, double tol2, cudaStream_t s) {
+    Level& L = P.levels[0];
+    Workspace::Vecs& V = vecs<T>(W);
+    const int nblk = W.nblk;
+    T *x = (T*)V.pcg[0], *r = (T*)V.pcg[1], *p = (T*)V.pcg[2], *z = (T*)V.pcg[4];
+    double* sc = scal<T>(W);
+    const int ne = elem_parts(L.N);
+    const size_t bytes = (size_t)nblk * L.N * 4 * sizeof(T);
+    GCK(cudaMemsetAsync(x, 0, bytes, s));
+    launch_norm2<T>(r, L.N, nblk, W.partial, ne, s);
+    launch_reduce_scalar(4, W.partial, ne, nblk, W.red, sc, tol2, s);
+    const int nz = vcycle<T>(P, W, V, 0, r, z, W.partial, s);
+    launch_reduce_scalar(3, W.partial, nz, nblk, W.red, sc, tol2, s);
+    GCK(cudaMemcpyAsync(p, z, bytes, cudaMemcpyDeviceToDevice, s));
+}
+
 // Solves Q x = r (r already in V.pcg[1]) into V.pcg[0]; returns iterations.
 template <typename T>
 static int pcg(Posterior& P, Workspace& W, double tol, int maxit, cudaStream_t s, bool use_graph, bool* breakdown,
@@ -378,15 +411,10 @@ static int pcg(Posterior& P, Workspace& W, double tol, int maxit, cudaStream_t s
     T *x = (T*)V.pcg[0], *r = (T*)V.pcg[1], *p = (T*)V.pcg[2], *z = (T*)V.pcg[4];
     double* sc = scal<T>(W);
     const int nt = (int)L.ntiles(), ne = elem_parts(L.N);
-    const size_t bytes = (size_t)nblk * L.N * 4 * sizeof(T);
     const double tol2 = tol * tol;
-    GCK(cudaMemsetAsync(x, 0, bytes, s));
-    launch_norm2<T>(r, L.N, nblk, W.partial, ne, s);
-    launch_reduce_scalar(4, W.partial, ne, nblk, W.red, sc, tol2, s);
-    const int nz = vcycle<T>(P, W, V, 0, r, z, W.partial, s);
-    launch_reduce_scalar(3, W.partial, nz, nblk, W.red, sc, tol2, s);
-    GCK(cudaMemcpyAsync(p, z, bytes, cudaMemcpyDeviceToDevice, s));
+    pcg_prologue<T>(P, W, tol2, s);
     const int P4 = nblk * 4;
+    (void)x; (void)r; (void)p; (void)z; (void)nt; (void)ne;
     if (use_graph && V.graph == nullptr) {
         GCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         capture_begin();
@@ -444,8 +472,307 @@ void apply64(Posterior& P, int nblk, const double* x64, double* y64, cudaStream_
     launch_stencil<double>(L.geo, M_APPLY, a, s);
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven solve: the FP64 refinement loop and each PCG loop run as
+// conditional while nodes of one CUDA graph, so a whole solve is one graph
+// launch with no host round trip; kernels decide convergence on the device.
+// The controller reproduces the host loop of solve_blocked: per right-hand
+// side, the D^-1-weighted residual relative to the first one, the forward
+// error estimate rho/(1-rho) |dx| of the last correction, and the unweighted
+// residual norm that scales the FP32 inner right-hand side.
+
+namespace {
+
+// controller state: doubles [bn | dxn | dxp | xn] x P4 then max_rel;
+// ints: 0 residual evaluations, 1 inner iterations, 2 iterations of the
+// current PCG loop, 3 converged, 4 breakdown, 5 non-finite residual
+enum { IS_REF = 0, IS_INNER = 1, IS_PCG = 2, IS_CONV = 3, IS_BRK = 4, IS_NONFIN = 5, IS_N = 8 };
+
+__global__ void k_ctrl_reset(double* __restrict__ ds, int* __restrict__ is, int P4) {
+    for (int i = threadIdx.x; i < P4; i += blockDim.x) {
+        ds[0 * P4 + i] = 0.0;
+        ds[1 * P4 + i] = -1.0;
+        ds[2 * P4 + i] = -1.0;
+        ds[3 * P4 + i] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        ds[4 * P4] = 0.0;
+        for (int k = 0; k < IS_N; ++k) is[k] = 0;
+    }
+}
+
+// after a residual: red = |r|_D^2, red2 = |r|^2 per right-hand side
+__global__ void k_ctrl(const double* __restrict__ red, const double* __restrict__ red2, double* __restrict__ norms,
+                       double* __restrict__ ds, int* __restrict__ is, int P4, double rtol, double xtol, int max_refine,
+                       cudaGraphConditionalHandle h) {
+    __shared__ int s_open, s_bad;
+    __shared__ double s_max;
+    if (threadIdx.x == 0) { s_open = 0; s_bad = 0; s_max = 0.0; }
+    __syncthreads();
+    const bool first = is[IS_REF] == 0;
+    double mx = 0.0;
+    int open = 0, bad = 0;
+    for (int i = threadIdx.x; i < P4; i += blockDim.x) {
+        const double v = red[i];
+        if (!isfinite(v)) bad = 1;
+        const double rn = sqrt(fmax(v, 0.0));
+        if (first) ds[0 * P4 + i] = rn;
+        const double bn = ds[0 * P4 + i];
+        const double rel = bn > 0.0 ? rn / bn : 0.0;
+        mx = fmax(mx, rel);
+        bool done = rel <= rtol;
+        const double dxn = ds[1 * P4 + i], dxp = ds[2 * P4 + i];
+        if (done && dxn >= 0.0) {
+            double est = dxn;
+            if (dxp > 0.0) {
+                const double rho = dxn / dxp;
+                est = rho < 0.5 ? dxn * rho / (1.0 - rho) : dxn;
+            }
+            done = est <= xtol * ds[3 * P4 + i];
+        }
+        norms[i] = done ? 0.0 : sqrt(fmax(red2[i], 0.0));
+        open |= done ? 0 : 1;
+    }
+    if (open) atomicOr(&s_open, 1);
+    if (bad) atomicOr(&s_bad, 1);
+    // max of the relative residuals (non-negative: the bit patterns order like the values)
+    atomicMax(reinterpret_cast<unsigned long long*>(&s_max), (unsigned long long)__double_as_longlong(mx));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nref = ++is[IS_REF];
+        ds[4 * P4] = s_max;
+        is[IS_CONV] = s_open ? 0 : 1;
+        if (s_bad) is[IS_NONFIN] = 1;
+        const bool more = s_open && !s_bad && nref - 1 < max_refine;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
+// after a correction: red = |d|^2, red2 = |x|^2 of the FP32 correction and the iterate
+__global__ void k_ctrl_dx(const double* __restrict__ red, const double* __restrict__ red2, const double* __restrict__ norms,
+                          double* __restrict__ ds, int P4) {
+    for (int i = threadIdx.x; i < P4; i += blockDim.x) {
+        if (norms[i] == 0.0) continue;
+        ds[2 * P4 + i] = ds[1 * P4 + i];
+        ds[1 * P4 + i] = norms[i] * sqrt(fmax(red[i], 0.0));
+        ds[3 * P4 + i] = sqrt(fmax(red2[i], 0.0));
+    }
+}
+
+// PCG loop control: run while a right-hand side is active and below max_inner
+__global__ void k_pcg_start(const double* __restrict__ sc, int P4, int* __restrict__ is, int max_inner,
+                            cudaGraphConditionalHandle h) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < P4; i += blockDim.x)
+        if (sc[6 * P4 + i] != 0.0) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        is[IS_PCG] = 0;
+        cudaGraphSetConditional(h, (any && max_inner > 0) ? 1u : 0u);
+    }
+}
+
+__global__ void k_pcg_cond(const double* __restrict__ sc, int P4, int* __restrict__ is, int max_inner, int step,
+                           cudaGraphConditionalHandle h) {
+    __shared__ int any, brk;
+    if (threadIdx.x == 0) { any = 0; brk = 0; }
+    __syncthreads();
+    for (int i = threadIdx.x; i < P4; i += blockDim.x) {
+        if (sc[6 * P4 + i] != 0.0) atomicOr(&any, 1);
+        if (sc[7 * P4 + i] != 0.0) atomicOr(&brk, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        is[IS_PCG] += step;
+        is[IS_INNER] += step;
+        if (brk) is[IS_BRK] = 1;
+        cudaGraphSetConditional(h, (any && is[IS_PCG] < max_inner) ? 1u : 0u);
+    }
+}
+
+}  // namespace
+
+struct SolveGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap2 = nullptr, cap3 = nullptr;      // capture streams of the loop bodies
+    double* ds = nullptr;                             // controller state (device)
+    int* is = nullptr;
+    double* h_ds = nullptr;                           // pinned mirrors
+    int* h_is = nullptr;
+    // what the graph bakes in
+    const double* b64 = nullptr;
+    double* x64 = nullptr;
+    double rtol = -1, inner_tol = -1;
+    int max_refine = -1, max_inner = -1;
+    unsigned long long k_init = 0, k_pre = 0, k_pcg = 0, k_post = 0;    // kernels per segment
+};
+
+void solve_graph_free(SolveGraph* g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->cap2) cudaStreamDestroy(g->cap2);
+    if (g->cap3) cudaStreamDestroy(g->cap3);
+    dev_free(g->ds);
+    dev_free(g->is);
+    if (g->h_ds) cudaFreeHost(g->h_ds);
+    if (g->h_is) cudaFreeHost(g->h_is);
+    delete g;
+}
+
+// the residual of the current iterate into W.r64 with red = |r|_D^2, red2 = |r|^2
+// (double-float pairs where the level allows them)
+static bool refinement_residual(Posterior& P, Workspace& W, int nblk, const double* x64, const double* b64, cudaStream_t s) {
+    Level& L = P.levels[0];
+    const int ne = elem_parts(L.N);
+    bool pairs = false;
+    if (resid_df_applicable(L)) {
+        const int ng = launch_resid_df(L, x64, b64, W.r64, L.d_dinv64, W.partial, nblk, s);
+        launch_reduce(W.partial, ng, nblk, W.red, s);
+        launch_norm2_df(W.r64, L.N, nblk, W.partial, ne, s);
+        pairs = true;
+    } else {
+        StencilArgs<double> a{};
+        a.L = L.view<double>();
+        a.nblk = nblk;
+        a.x = x64; a.b = b64; a.out = W.r64; a.partial = W.partial;
+        a.rweight = L.d_dinv64;
+        const int ng = launch_stencil<double>(L.geo, M_RESID, a, s);
+        launch_reduce(W.partial, ng, nblk, W.red, s);
+        launch_norm2<double>(W.r64, L.N, nblk, W.partial, ne, s);
+    }
+    launch_reduce(W.partial, ne, nblk, W.red2, s);
+    return pairs;
+}
+
+// appends a while node with handle h after the work captured so far on s;
+// returns its body graph
+static cudaGraph_t add_while(cudaStream_t s, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    GCK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    GCK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
+    GCK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return prm.conditional.phGraph_out[0];
+}
+
+static void build_solve_graph(Posterior& P, Workspace& W, SolveGraph& G, const double* b64, double* x64,
+                              const gmrf_solve_opts& o, double inner_tol, cudaStream_t s) {
+    Level& L = P.levels[0];
+    const int nblk = W.nblk, P4 = nblk * 4;
+    Workspace::Vecs& V = W.v32;
+    const double tol2 = inner_tol * inner_tol;
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G.exec = nullptr;
+    G.graph = nullptr;
+    if (!G.cap2) GCK(cudaStreamCreateWithFlags(&G.cap2, cudaStreamNonBlocking));
+    if (!G.cap3) GCK(cudaStreamCreateWithFlags(&G.cap3, cudaStreamNonBlocking));
+    if (!G.ds) G.ds = dev_alloc<double>((size_t)5 * P4);
+    if (!G.is) G.is = dev_alloc<int>(IS_N);
+    if (!G.h_ds) GCK(cudaMallocHost((void**)&G.h_ds, sizeof(double) * 5 * P4));
+    if (!G.h_is) GCK(cudaMallocHost((void**)&G.h_is, sizeof(int) * IS_N));
+    const double xtol = 100.0 * o.rtol;
+    cudaGraph_t g = nullptr;
+    GCK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h_ref, h_pcg;
+    GCK(cudaGraphConditionalHandleCreate(&h_ref, g, 0, 0));
+    // initial residual and test
+    GCK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    capture_begin();
+    k_ctrl_reset<<<1, 256, 0, s>>>(G.ds, G.is, P4);
+    note_launch();
+    refinement_residual(P, W, nblk, x64, b64, s);
+    k_ctrl<<<1, 256, 0, s>>>(W.red, W.red2, W.norms, G.ds, G.is, P4, o.rtol, xtol, o.max_refine, h_ref);
+    note_launch();
+    G.k_init = capture_end();
+    cudaGraph_t body = add_while(s, h_ref);
+    GCK(cudaStreamEndCapture(s, &g));
+    // refinement step: scaled FP32 correction by PCG, update, new residual, test
+    GCK(cudaGraphConditionalHandleCreate(&h_pcg, body, 0, 0));
+    GCK(cudaStreamBeginCaptureToGraph(G.cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    capture_begin();
+    if (resid_df_applicable(L)) launch_scale_cast_df(W.r64, W.norms, (float*)V.pcg[1], L.N, nblk, G.cap2);
+    else launch_scale_cast(W.r64, W.norms, (float*)V.pcg[1], L.N, nblk, G.cap2);
+    pcg_prologue<float>(P, W, tol2, G.cap2);
+    k_pcg_start<<<1, 256, 0, G.cap2>>>(W.sc32, P4, G.is, o.max_inner, h_pcg);
+    note_launch();
+    G.k_pre = capture_end();
+    cudaGraph_t pbody = add_while(G.cap2, h_pcg);
+    capture_begin();
+    const int ne = elem_parts(L.N);
+    launch_axpy_mixed(x64, W.norms, (const float*)V.pcg[0], L.N, nblk, W.partial, G.cap2);
+    launch_reduce(W.partial, ne, nblk, W.red, G.cap2);
+    launch_reduce(W.partial + (size_t)nblk * ne * 4, ne, nblk, W.red2, G.cap2);
+    k_ctrl_dx<<<1, 256, 0, G.cap2>>>(W.red, W.red2, W.norms, G.ds, P4);
+    note_launch();
+    refinement_residual(P, W, nblk, x64, b64, G.cap2);
+    k_ctrl<<<1, 256, 0, G.cap2>>>(W.red, W.red2, W.norms, G.ds, G.is, P4, o.rtol, xtol, o.max_refine, h_ref);
+    note_launch();
+    G.k_post = capture_end();
+    GCK(cudaStreamEndCapture(G.cap2, &body));
+    // PCG body: kItersPerGraph iterations, then the loop test
+    GCK(cudaStreamBeginCaptureToGraph(G.cap3, pbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    capture_begin();
+    for (int k = 0; k < kItersPerGraph; ++k) pcg_iteration<float>(P, W, V, tol2, G.cap3);
+    k_pcg_cond<<<1, 256, 0, G.cap3>>>(W.sc32, P4, G.is, o.max_inner, kItersPerGraph, h_pcg);
+    note_launch();
+    G.k_pcg = capture_end();
+    GCK(cudaStreamEndCapture(G.cap3, &pbody));
+    GCK(cudaGraphInstantiate(&G.exec, g, 0));
+    G.graph = g;
+    G.b64 = b64;
+    G.x64 = x64;
+    G.rtol = o.rtol;
+    G.inner_tol = inner_tol;
+    G.max_refine = o.max_refine;
+    G.max_inner = o.max_inner;
+}
+
+static SolveStats solve_blocked_graph(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
+                                      cudaStream_t s) {
+    Workspace& W = workspace(P, nblk);
+    alloc_vecs<float>(P, W, W.v32);
+    const double inner_tol = o.inner_rtol;
+    if (!W.sgraph) W.sgraph = new SolveGraph();
+    SolveGraph& G = *W.sgraph;
+    if (!G.exec || G.b64 != b64 || G.x64 != x64 || G.rtol != o.rtol || G.inner_tol != inner_tol ||
+        G.max_refine != o.max_refine || G.max_inner != o.max_inner)
+        build_solve_graph(P, W, G, b64, x64, o, inner_tol, s);
+    const int P4 = nblk * 4;
+    GCK(cudaGraphLaunch(G.exec, s));
+    GCK(cudaMemcpyAsync(G.h_ds, G.ds, sizeof(double) * 5 * P4, cudaMemcpyDeviceToHost, s));
+    GCK(cudaMemcpyAsync(G.h_is, G.is, sizeof(int) * IS_N, cudaMemcpyDeviceToHost, s));
+    GCK(cudaStreamSynchronize(s));
+    SolveStats st;
+    st.refinements = G.h_is[IS_REF];
+    st.inner = G.h_is[IS_INNER];
+    st.converged = G.h_is[IS_CONV] != 0;
+    st.breakdown = G.h_is[IS_BRK] != 0;
+    st.max_rel = G.h_ds[4 * P4];
+    const unsigned long long corrections = st.refinements > 0 ? (unsigned long long)(st.refinements - 1) : 0;
+    note_graph_launch(G.k_init + corrections * (G.k_pre + G.k_post) +
+                      (unsigned long long)(st.inner / kItersPerGraph) * G.k_pcg);
+    if (stencil_abort_take(s)) throw Error(GMRF_E_CUDA, "stencil kernel: staged input tile did not arrive (bounded wait)");
+    if (G.h_is[IS_NONFIN]) throw Error(GMRF_E_NOT_SPD, "non-finite residual in refinement");
+    return st;
+}
+
 SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
                          cudaStream_t s, bool x_zero) {
+    if (o.precision != 1 && o.batched != 0 && !(o.timeout_s > 0) && device_loop_enabled())
+        return solve_blocked_graph(P, nblk, b64, x64, o, s);
+    (void)x_zero;
     Workspace& W = workspace(P, nblk);
     Level& L = P.levels[0];
     const int P4 = nblk * 4;
