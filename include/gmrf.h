@@ -192,8 +192,13 @@ gmrf_status gmrf_marginal_var(gmrf_posterior* post, int32_t ns, uint64_t seed, d
  * posts[0..count), instance i with seed + i, means[i] (NULL array or NULL
  * entry: no mean) and vars[i] (non-NULL, [N_i]) outputs as in
  * gmrf_marginal_var.  Instances whose posteriors share a prior handle run in
- * list order on that prior's stream; instances of different priors run
- * concurrently from min(nthreads, number of priors) host threads (<= 0: 16).
+ * list order on that prior's stream.  nthreads <= 1 with the FP32
+ * refinement path (precision 0, batched, no timeout): one host thread
+ * enqueues every instance (each solve is one CUDA graph whose refinement and
+ * PCG loops run on the device, so nothing is waited for until all are
+ * enqueued), then collects them; instances of different priors run
+ * concurrently on their streams.  nthreads > 1 (or other options): instances
+ * of different priors run from min(nthreads, number of priors) host threads.
  * Results equal those of calling gmrf_marginal_var on each instance alone.
  * No posterior or prior in the list may be used elsewhere during the call.
  * infos: [count] or NULL.  Returns GMRF_E_INVALID for a NULL entry before any

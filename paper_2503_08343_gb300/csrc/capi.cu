@@ -526,6 +526,125 @@ gmrf_status gmrf_marginal_var(gmrf_posterior* post, int32_t ns, uint64_t seed, d
     return st != GMRF_OK ? st : rc;
 }
 
+// One instance of the single-thread batch: the whole gmrf_marginal_var
+// enqueued on the prior's stream (sample right-hand sides, the device-driven
+// solve, the variance estimator, the mean unpacked), nothing waited for.
+// Device outputs are copied in stream order; host outputs after collect.
+struct BatchItem {
+    int i = -1;
+    Batch b;
+    double* mean = nullptr;
+    double* var = nullptr;
+    bool mean_host = false, var_host = false;
+};
+
+static void enqueue_marginal_var(Posterior& P, BatchItem& it, int ns, uint64_t seed, const gmrf_solve_opts& o) {
+    const cudaStream_t s = P.prior->stream;
+    it.b = make_batch(ns, it.mean != nullptr);
+    const Batch& b = it.b;
+    Workspace& W = workspace(P, b.nblk);
+    const long long N = P.levels[0].N;
+    GCK(cudaMemcpyAsync(W.slot_a, b.sample.data(), sizeof(int32_t) * b.sample.size(), cudaMemcpyHostToDevice, s));
+    const long long orows = std::max<long long>(P.nrows, 1);
+    if (W.z2_n < (size_t)b.nblk * orows * 4) {
+        dev_free(W.z2);
+        W.z2_n = (size_t)b.nblk * orows * 4;
+        W.z2 = dev_alloc<double>(W.z2_n);
+    }
+    launch_sample_rhs(P.levels[0].geo, P.levels[0].view<double>(), seed, W.slot_a, P.linearised ? P.d_blin : P.d_bdata,
+                      W.b64, W.t64, W.z2, orows, b.nblk, s);
+    GCK(cudaMemsetAsync(W.x64, 0, sizeof(double) * b.nblk * N * 4, s));
+    solve_graph_launch(P, b.nblk, W.b64, W.x64, o, s);
+    // Rao-Blackwellised variances from the FP32 apply of the samples (as gmrf_marginal_var)
+    float* x32 = static_cast<float*>(W.v32.pcg[0]);
+    float* q32 = static_cast<float*>(W.v32.pcg[3]);
+    launch_cast<float>(W.x64, x32, (long long)b.nblk * N * 4, s);
+    StencilArgs<float> a{};
+    a.L = P.levels[0].view<float>();
+    a.nblk = b.nblk;
+    a.x = x32;
+    a.out = q32;
+    launch_stencil<float>(P.levels[0].geo, M_APPLY, a, s);
+    launch_rbmc<float>(q32, W.x64, P.levels[0].d_diag64, W.slot_a, N, b.nblk, ns, W.t64, W.t64 + N, s);
+    it.var_host = !is_device_ptr(it.var);
+    if (!it.var_host) GCK(cudaMemcpyAsync(it.var, W.t64, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    if (it.mean) {
+        GCK(cudaMemcpyAsync(W.slot_b, b.mean_row.data(), sizeof(int32_t) * b.mean_row.size(), cudaMemcpyHostToDevice, s));
+        launch_unpack(W.x64, W.r64, W.slot_b, N, b.nblk, s);
+        it.mean_host = !is_device_ptr(it.mean);
+        if (!it.mean_host) GCK(cudaMemcpyAsync(it.mean, W.r64, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    }
+}
+
+static SolveStats collect_marginal_var(Posterior& P, BatchItem& it) {
+    const cudaStream_t s = P.prior->stream;
+    GCK(cudaStreamSynchronize(s));
+    const SolveStats st = solve_graph_collect(P, it.b.nblk, s);
+    Workspace& W = workspace(P, it.b.nblk);
+    const long long N = P.levels[0].N;
+    if (it.var_host) GCK(cudaMemcpy(it.var, W.t64, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    if (it.mean && it.mean_host) GCK(cudaMemcpy(it.mean, W.r64, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    return st;
+}
+
+// The batch on one host thread: every instance is enqueued on its prior's
+// stream before any is waited for (the device-driven solves need no host
+// round trip), then all are collected in list order.  An instance whose
+// posterior is still in flight is collected before it is enqueued again.
+static gmrf_status marginal_var_batch_async(gmrf_posterior* const* posts, int32_t count, int32_t ns, uint64_t seed,
+                                            double* const* means, double* const* vars, const gmrf_solve_opts& o,
+                                            gmrf_solve_info* infos) {
+    std::vector<BatchItem> items((size_t)count);
+    std::vector<gmrf_status> sts((size_t)count, GMRF_OK);
+    std::vector<std::string> errs((size_t)count);
+    std::map<gmrf_posterior*, int> inflight;
+    std::vector<std::chrono::steady_clock::time_point> t0((size_t)count);
+    auto collect = [&](int i) {
+        gmrf_posterior* p = posts[i];
+        inflight.erase(p);
+        const gmrf_status st = guard([&] {
+            const SolveStats ss = collect_marginal_var(p->impl, items[(size_t)i]);
+            gmrf_solve_info inf;
+            std::memset(&inf, 0, sizeof(inf));
+            const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0[(size_t)i]).count();
+            const gmrf_status rc = finish(ss, &inf, items[(size_t)i].b.nrhs, sec);
+            if (infos) infos[i] = inf;
+            if (rc != GMRF_OK) throw Error(rc, g_err);
+        });
+        sts[(size_t)i] = st;
+        if (st != GMRF_OK) errs[(size_t)i] = g_err;
+    };
+    for (int i = 0; i < count; ++i) {
+        gmrf_posterior* p = posts[i];
+        auto f = inflight.find(p);
+        if (f != inflight.end()) collect(f->second);
+        items[(size_t)i].i = i;
+        items[(size_t)i].mean = means ? means[i] : nullptr;
+        items[(size_t)i].var = vars[i];
+        t0[(size_t)i] = std::chrono::steady_clock::now();
+        const gmrf_status st = guard([&] {
+            enter(p->prior);
+            enqueue_marginal_var(p->impl, items[(size_t)i], ns, seed + (uint64_t)i, o);
+        });
+        if (st != GMRF_OK) {
+            sts[(size_t)i] = st;
+            errs[(size_t)i] = g_err;
+            cudaStreamSynchronize(p->impl.prior->stream);
+            continue;
+        }
+        inflight[p] = i;
+    }
+    for (int i = 0; i < count; ++i)
+        if (inflight.count(posts[i]) && inflight[posts[i]] == i) collect(i);
+    for (int i = 0; i < count; ++i) {       // report the first failing instance in list order
+        if (sts[(size_t)i] != GMRF_OK) {
+            g_err = "instance " + std::to_string(i) + ": " + errs[(size_t)i];
+            return sts[(size_t)i];
+        }
+    }
+    return GMRF_OK;
+}
+
 gmrf_status gmrf_marginal_var_batch(gmrf_posterior* const* posts, int32_t count, int32_t ns, uint64_t seed,
                                     double* const* means, double* const* vars, const gmrf_solve_opts* opts,
                                     gmrf_solve_info* infos, int32_t nthreads) {
@@ -538,6 +657,14 @@ gmrf_status gmrf_marginal_var_batch(gmrf_posterior* const* posts, int32_t count,
             g_err = "gmrf_marginal_var_batch: null posterior or output at instance " + std::to_string(i);
             return GMRF_E_INVALID;
         }
+    }
+    if (ns < 1) {
+        g_err = "gmrf_marginal_var_batch: ns must be >= 1";
+        return GMRF_E_INVALID;
+    }
+    {
+        const gmrf_solve_opts o = resolve_opts(opts);
+        if (nthreads <= 1 && device_loop_usable(o)) return marginal_var_batch_async(posts, count, ns, seed, means, vars, o, infos);
     }
     // Posteriors of one prior share its stream (and a posterior listed twice
     // shares its workspace), so each group of instances with the same prior

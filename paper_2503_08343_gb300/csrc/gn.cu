@@ -169,6 +169,8 @@ void linearise(Posterior& P, const double* u, cudaStream_t s) {
             V->graph = nullptr;
             V->graph_tol = -1.0;
         }
+        solve_graph_free(kv.second->sgraph);     // the device-driven solve bakes the same coefficients
+        kv.second->sgraph = nullptr;
     }
     posterior_refresh_operator(P, s);
     P.use_tsp = tsp_applicable(F, (int)P.nic);

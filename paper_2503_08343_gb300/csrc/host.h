@@ -70,6 +70,13 @@ void posterior_refresh_operator(Posterior& P, cudaStream_t s); // after the line
 SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
                          cudaStream_t s, bool x_zero = false);
 void apply64(Posterior& P, int nblk, const double* x64, double* y64, cudaStream_t s);
+// the device-driven solve (one CUDA graph per batch size with the refinement
+// and PCG loops as conditional while nodes): usable for the batched FP32
+// refinement path without a wall-clock limit; launch enqueues it without
+// waiting, collect reads its statistics once the stream has finished
+bool device_loop_usable(const gmrf_solve_opts& o);
+void solve_graph_launch(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o, cudaStream_t s);
+SolveStats solve_graph_collect(Posterior& P, int nblk, cudaStream_t s);
 Workspace& workspace(Posterior& P, int nblk);
 void solve_graph_free(SolveGraph* g);
 void workspace_free(Workspace* w);

@@ -739,8 +739,13 @@ static void build_solve_graph(Posterior& P, Workspace& W, SolveGraph& G, const d
     G.max_inner = o.max_inner;
 }
 
-static SolveStats solve_blocked_graph(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
-                                      cudaStream_t s) {
+bool device_loop_usable(const gmrf_solve_opts& o) {
+    return o.precision != 1 && o.batched != 0 && !(o.timeout_s > 0) && device_loop_enabled();
+}
+
+// Enqueues the device-driven solve on s (builds its graph on first use) and
+// the copy of the controller state to pinned host memory; nothing waits.
+void solve_graph_launch(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o, cudaStream_t s) {
     Workspace& W = workspace(P, nblk);
     alloc_vecs<float>(P, W, W.v32);
     const double inner_tol = o.inner_rtol;
@@ -753,7 +758,14 @@ static SolveStats solve_blocked_graph(Posterior& P, int nblk, const double* b64,
     GCK(cudaGraphLaunch(G.exec, s));
     GCK(cudaMemcpyAsync(G.h_ds, G.ds, sizeof(double) * 5 * P4, cudaMemcpyDeviceToHost, s));
     GCK(cudaMemcpyAsync(G.h_is, G.is, sizeof(int) * IS_N, cudaMemcpyDeviceToHost, s));
-    GCK(cudaStreamSynchronize(s));
+}
+
+// After s has finished a solve_graph_launch: its statistics (and the checks
+// of the stencil abort flags and of a non-finite residual).
+SolveStats solve_graph_collect(Posterior& P, int nblk, cudaStream_t s) {
+    Workspace& W = workspace(P, nblk);
+    SolveGraph& G = *W.sgraph;
+    const int P4 = nblk * 4;
     SolveStats st;
     st.refinements = G.h_is[IS_REF];
     st.inner = G.h_is[IS_INNER];
@@ -768,10 +780,16 @@ static SolveStats solve_blocked_graph(Posterior& P, int nblk, const double* b64,
     return st;
 }
 
+static SolveStats solve_blocked_graph(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
+                                      cudaStream_t s) {
+    solve_graph_launch(P, nblk, b64, x64, o, s);
+    GCK(cudaStreamSynchronize(s));
+    return solve_graph_collect(P, nblk, s);
+}
+
 SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
                          cudaStream_t s, bool x_zero) {
-    if (o.precision != 1 && o.batched != 0 && !(o.timeout_s > 0) && device_loop_enabled())
-        return solve_blocked_graph(P, nblk, b64, x64, o, s);
+    if (device_loop_usable(o)) return solve_blocked_graph(P, nblk, b64, x64, o, s);
     (void)x_zero;
     Workspace& W = workspace(P, nblk);
     Level& L = P.levels[0];

@@ -341,7 +341,7 @@ class Posterior:
             self.h = None
 
 
-def marginal_var_batch(posts, ns, seed, means=True, opts=None, nthreads=16):
+def marginal_var_batch(posts, ns, seed, means=True, opts=None, nthreads=1):
     """gmrf_marginal_var over independent posteriors, concurrently across
     priors (posteriors of one prior run in list order); instance i uses
     seed + i.  Returns (means, vars, infos)."""

@@ -79,10 +79,13 @@ def test_weak_point_data_keeps_bilinear_transfers():
     assert np.max(np.abs(mu - want)) < 1e-6 * np.max(np.abs(want))
 
 
-def test_batch_equals_individual_solves_and_oracle_means():
+@pytest.mark.parametrize("nthreads", [1, 6], ids=["one_thread_device_loops", "six_threads"])
+def test_batch_equals_individual_solves_and_oracle_means(nthreads):
+    # nthreads 1: every instance enqueued by one host thread (device-driven
+    # solves), collected at the end; 6: host worker threads
     insts = W.c4_instances(**INSTANCES)
     posts = [gmrf.Posterior(gmrf.Prior(pr), ob) for pr, ob in insts]
-    ms, vs, infos = gmrf.marginal_var_batch(posts, 16, 1004, nthreads=6)
+    ms, vs, infos = gmrf.marginal_var_batch(posts, 16, 1004, nthreads=nthreads)
     assert all(i["converged"] == 1 for i in infos)
     for i, (post, (pr, ob)) in enumerate(zip(posts, insts)):
         mu, var, se, info = post.marginal_var(16, 1004 + i)
@@ -91,9 +94,11 @@ def test_batch_equals_individual_solves_and_oracle_means():
         assert np.max(np.abs(mu - want)) < 1e-6 * np.max(np.abs(want)), i
 
 
-def test_batch_with_shared_prior_and_repeated_posterior():
+@pytest.mark.parametrize("nthreads", [1, 4])
+def test_batch_with_shared_prior_and_repeated_posterior(nthreads):
     # two posteriors of one prior (one stream) and one posterior listed twice:
-    # grouped onto one worker in list order, results as solo calls
+    # in list order on one stream (one thread: the repeated posterior is
+    # collected before it is enqueued again), results as solo calls
     insts = W.c4_instances(count=3, seed=9, smin=20, smax=40)
     pr, ob = insts[0]
     prior = gmrf.Prior(pr)
@@ -101,7 +106,7 @@ def test_batch_with_shared_prior_and_repeated_posterior():
     a, b = gmrf.Posterior(prior, ob), gmrf.Posterior(prior, ob2)
     c = gmrf.Posterior(gmrf.Prior(insts[1][0]), insts[1][1])
     posts = [a, c, b, a]
-    ms, vs, infos = gmrf.marginal_var_batch(posts, 8, 55, nthreads=4)
+    ms, vs, infos = gmrf.marginal_var_batch(posts, 8, 55, nthreads=nthreads)
     assert all(i["converged"] == 1 for i in infos)
     for i, post in enumerate(posts):
         mu, var, se, info = post.marginal_var(8, 55 + i)
