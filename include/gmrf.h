@@ -337,6 +337,28 @@ void gmrf_test_set_wait_cap(int32_t cap);
  * (kernels inside replayed CUDA graphs included). */
 uint64_t gmrf_launch_count(void);
 
+/* Launch-shape autotuner of the persistent stencil kernels.  Nothing in the
+ * method depends on the grid a persistent kernel runs on: it decides only
+ * how the work units (tiles x right-hand-side blocks, and time chunks of the
+ * marching space-time kernel) are shared among CTAs, and in which order the
+ * per-CTA dot partials are summed.  The first launch of a kernel on a new
+ * (instantiation, right-hand-side blocks, size bucket, observation-table
+ * bucket) key times every candidate shape (CTAs per SM; time-chunk length)
+ * on zero-filled scratch copies of its vectors, outside any graph capture,
+ * and keeps the fastest for the rest of the process.  Environment:
+ * GMRF_AUTOTUNE=0 disables measuring (default shapes); GMRF_AUTOTUNE_FILE
+ * names a file the choices are read from at first use and appended to.
+ *
+ * gmrf_autotune_mode: mode 0 off, 1 on, negative only queries; returns the
+ * mode before the call.  Process-wide.
+ * gmrf_autotune_log: copies every recorded choice (one JSON object per line:
+ * key, chosen CTAs per SM and time-chunk multiplier, measured milliseconds
+ * per launch of each candidate) into buf (NUL-terminated, truncated to
+ * cap - 1 bytes; buf may be NULL) and returns the full length in bytes, or
+ * -1 on an internal error. */
+int32_t gmrf_autotune_mode(int32_t mode);
+int64_t gmrf_autotune_log(char* buf, int64_t cap);
+
 /* Multigrid hierarchy of a posterior: grid dimensions (nx, ny, nt) of level
  * `level` (0 = finest) and the bound on the spectrum of D^-1 Q_u|y used by
  * its Chebyshev smoother (0 on the coarsest level, which is solved directly). */

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgmrf.so")
-SOURCES = ["stencil.cu", "kernels.cu", "stencil_march.cu", "resid_df.cu", "setup.cu", "solver.cu", "gn.cu", "tsp.cu", "grad.cu", "prior_det.cu", "slq.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["stencil.cu", "kernels.cu", "stencil_march.cu", "resid_df.cu", "setup.cu", "solver.cu", "gn.cu", "tsp.cu", "grad.cu", "prior_det.cu", "slq.cu", "capi.cu", "noalloc.cu", "autotune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

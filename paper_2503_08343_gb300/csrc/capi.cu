@@ -9,6 +9,7 @@
 #include <map>
 #include <thread>
 
+#include "autotune.h"
 #include "handles.h"
 
 using namespace gmrf;
@@ -818,6 +819,26 @@ gmrf_status gmrf_prior_logdet(const gmrf_prior_desc* desc, double* logdet, doubl
 void gmrf_test_set_wait_cap(int32_t cap) { set_wait_cap(cap); }
 
 uint64_t gmrf_launch_count(void) { return launch_count(); }
+
+int32_t gmrf_autotune_mode(int32_t mode) {
+    if (mode < 0) return tune_enabled() ? 1 : 0;
+    return tune_set_mode(mode);
+}
+
+int64_t gmrf_autotune_log(char* buf, int64_t cap) {
+    std::string s;
+    try {
+        s = tune_log();
+    } catch (...) {
+        return -1;
+    }
+    if (buf && cap > 0) {
+        const size_t n = std::min<size_t>(s.size(), (size_t)cap - 1);
+        std::memcpy(buf, s.data(), n);
+        buf[n] = '\0';
+    }
+    return (int64_t)s.size();
+}
 
 gmrf_status gmrf_gauss_newton_step(gmrf_posterior* post, double* mu_k, double* delta_prev, double* newton_decrement,
                                    double* alpha, const gmrf_solve_opts* opts, gmrf_solve_info* info) {

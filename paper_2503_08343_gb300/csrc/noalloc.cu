@@ -14,6 +14,7 @@
 #include <mutex>
 #include <string>
 
+#include "autotune.h"
 #include "handles.h"
 
 namespace {
@@ -111,6 +112,7 @@ void noalloc_prepare(const Posterior& P) {
 
 extern "C" gmrf_status gmrf_apply_posterior_noalloc(gmrf_posterior* post, const double* x, double* y, double* xQx) {
     try {
+        gmrf::TuneSuppress no_measuring;          // launch shapes: cached or default, never measured here
         if (!post || !x || !y) throw gmrf::Error(GMRF_E_INVALID, "gmrf_apply_posterior_noalloc: null argument");
         gmrf::Posterior& P = post->impl;
         const gmrf::Level& L = P.levels[0];

@@ -14,9 +14,10 @@
 // The Lanczos vectors and the operator apply are FP32 (the fused stencil);
 // the alpha / beta dot products are reduced in FP64 and the quadrature runs on
 // the host in FP64.  Lanczos runs for all probes as one blocked batch and
-// stops when every probe's quadrature value has settled (relative change
-// below 1e-10 between two checks, at steps 16, 32, ... growing by a quarter)
-// or after max_steps.
+// stops when every probe's quadrature value has settled between two checks
+// (at steps 16, 32, ... growing by a quarter): a change below 1e-10 of the
+// value or below 1 % of the spread of the values over the probes, so that the
+// quadrature error is small against the Monte Carlo error; or after max_steps.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -196,6 +197,7 @@ SlqResult slq_logdet(Posterior& P, int S, uint64_t seed, int max_steps, cudaStre
         note_launch();
         std::vector<double> ha, hb;
         std::vector<double> prev((size_t)S, 0.0), est((size_t)S, 0.0);
+        std::vector<char> open((size_t)S, 1);
         int steps = 0, next_check = 16;
         bool settled = false;
         for (int j = 0; j < max_steps; ++j) {
@@ -224,7 +226,6 @@ SlqResult slq_logdet(Posterior& P, int S, uint64_t seed, int max_steps, cudaStre
                 GCK(cudaMemcpyAsync(ha.data(), alpha, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s));
                 GCK(cudaMemcpyAsync(hb.data(), beta, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s));
                 GCK(cudaStreamSynchronize(s));
-                bool all = true;
                 double amax = 0.0;
                 for (double x : ha) amax = std::max(amax, std::fabs(x));
                 for (int k = 0; k < S; ++k) {
@@ -238,10 +239,21 @@ SlqResult slq_logdet(Posterior& P, int S, uint64_t seed, int max_steps, cudaStre
                     }
                     est[(size_t)k] = (double)N * gauss_log_quadrature(ta, tb);
                     if (!std::isfinite(est[(size_t)k])) throw Error(GMRF_E_NOT_SPD, "Lanczos quadrature met a non-positive node");
-                    const bool closed = (int)ta.size() < steps;
-                    if (!closed && std::fabs(est[(size_t)k] - prev[(size_t)k]) > 1e-10 * std::max(1.0, std::fabs(est[(size_t)k])))
-                        all = false;
+                    open[(size_t)k] = (int)ta.size() == steps;
                 }
+                // settled: no probe's value moved by more than 1e-10 of itself,
+                // or by more than 1 % of the spread of the values over the
+                // probes (the Monte Carlo error of one probe), since the last check
+                double em = 0.0, ev = 0.0;
+                for (double e : est) em += e;
+                em /= S;
+                for (double e : est) ev += (e - em) * (e - em);
+                const double spread = S > 1 ? std::sqrt(ev / (S - 1)) : 0.0;
+                bool all = true;
+                for (int k = 0; k < S; ++k)
+                    if (open[(size_t)k] &&
+                        std::fabs(est[(size_t)k] - prev[(size_t)k]) > std::max(1e-10 * std::max(1.0, std::fabs(est[(size_t)k])), 0.01 * spread))
+                        all = false;
                 prev = est;
                 if (all && steps >= 32) {
                     settled = true;

@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "autotune.h"
 #include "host.h"
 
 namespace gmrf {
@@ -416,13 +417,19 @@ static int pcg(Posterior& P, Workspace& W, double tol, int maxit, cudaStream_t s
     const int P4 = nblk * 4;
     (void)x; (void)r; (void)p; (void)z; (void)nt; (void)ne;
     if (use_graph && V.graph == nullptr) {
-        GCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        capture_begin();
-        for (int k = 0; k < kItersPerGraph; ++k) pcg_iteration<T>(P, W, V, tol2, s);
-        V.graph_kernels = capture_end();
-        cudaMemcpyAsync(W.h_active, sc + 6 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(W.h_red, sc + 7 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s);
-        GCK(cudaStreamEndCapture(s, &V.graph));
+        // a second capture when launch shapes were measured after the first
+        for (int pass = 0; pass < 2; ++pass) {
+            GCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            capture_begin();
+            for (int k = 0; k < kItersPerGraph; ++k) pcg_iteration<T>(P, W, V, tol2, s);
+            V.graph_kernels = capture_end();
+            cudaMemcpyAsync(W.h_active, sc + 6 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(W.h_red, sc + 7 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s);
+            GCK(cudaStreamEndCapture(s, &V.graph));
+            if (pass == 1 || !tune_flush(s)) break;
+            GCK(cudaGraphDestroy(V.graph));
+            V.graph = nullptr;
+        }
         GCK(cudaGraphInstantiate(&V.exec, V.graph, 0));
     }
     int it = 0;
@@ -753,7 +760,10 @@ void solve_graph_launch(Posterior& P, int nblk, const double* b64, double* x64, 
     SolveGraph& G = *W.sgraph;
     if (!G.exec || G.b64 != b64 || G.x64 != x64 || G.rtol != o.rtol || G.inner_tol != inner_tol ||
         G.max_refine != o.max_refine || G.max_inner != o.max_inner)
+    {
         build_solve_graph(P, W, G, b64, x64, o, inner_tol, s);
+        if (tune_flush(s)) build_solve_graph(P, W, G, b64, x64, o, inner_tol, s);   // with the measured launch shapes
+    }
     const int P4 = nblk * 4;
     GCK(cudaGraphLaunch(G.exec, s));
     GCK(cudaMemcpyAsync(G.h_ds, G.ds, sizeof(double) * 5 * P4, cudaMemcpyDeviceToHost, s));

@@ -21,6 +21,7 @@
 
 #include <cuda.h>
 
+#include "autotune.h"
 #include "kernels.h"
 
 namespace gmrf {
@@ -564,6 +565,14 @@ constexpr int kMaxStencilGrid = 4096;
 #define GMRF_STENCIL_KB 1
 #endif
 
+static const char* mode_name(int m) {
+    return m == M_APPLY ? "apply" : m == M_RESID ? "resid" : m == M_CHEB ? "cheb" : "cheb0";
+}
+template <int GEO, typename T, int MODE, int COL> static std::string stencil_name() {
+    return std::string("stencil<") + (GEO == GEO_XY ? "xy" : "xt") + (sizeof(T) == 8 ? ",f64," : ",f32,") + mode_name(MODE) +
+           ",col" + std::to_string(COL) + ">";
+}
+
 // dry: only the one-time set-up of this instantiation (function attributes,
 // occupancy query, which also loads the kernel's code), no launch
 template <int GEO, typename T, int MODE, int COL>
@@ -612,13 +621,47 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false)
     if (dry) return 0;
     const long long ntiles = (long long)a.L.tiles_x * a.L.tiles_y * a.L.tiles_t;
     const long long nunits = ntiles * ((a.nblk + KB - 1) / KB);
-    const int grid = (int)std::min<long long>(std::min<long long>(nunits, (long long)resident), kMaxStencilGrid);
-    StencilMaps maps;
-    std::memset(&maps, 0, sizeof(maps));
-    maps.p = tile_map<GEO, T>(MODE == M_CHEB0 ? a.b : a.x, a.L, a.nblk, true);
-    if (MODE != M_APPLY) maps.b = tile_map<GEO, T>(a.b, a.L, a.nblk, false);
-    if (MODE == M_CHEB && a.d != nullptr) maps.d = tile_map<GEO, T>(a.d, a.L, a.nblk, false);
-    { kern<<<(unsigned)grid, 256, smem, s>>>(args, (int)nunits, maps); note_launch(); }
+    const int per = resident / sms;
+    const int nsm = sms;
+    auto grid_of = [nunits, nsm](int k) {
+        return (int)std::min<long long>(std::min<long long>(nunits, (long long)nsm * k), kMaxStencilGrid);
+    };
+    auto run = [kern, smem, nunits](const StencilArgs<T>& aa, int grid, cudaStream_t st, bool count) {
+        StencilMaps maps;
+        std::memset(&maps, 0, sizeof(maps));
+        maps.p = tile_map<GEO, T>(MODE == M_CHEB0 ? aa.b : aa.x, aa.L, aa.nblk, true);
+        if (MODE != M_APPLY) maps.b = tile_map<GEO, T>(aa.b, aa.L, aa.nblk, false);
+        if (MODE == M_CHEB && aa.d != nullptr) maps.d = tile_map<GEO, T>(aa.d, aa.L, aa.nblk, false);
+        kern<<<(unsigned)grid, 256, smem, st>>>(aa, (int)nunits, maps);
+        if (count) note_launch();
+    };
+    int grid = grid_of(per);
+    // launch shape: measured once per key when there is more than one unit per SM
+    if (nunits > nsm && per > 1) {
+        const TuneKey key{stencil_name<GEO, T, MODE, COL>(), args.nblk, tune_units_bucket(nunits),
+                          tune_obs_bucket(args.L.ostride, args.L.ocap > 0)};
+        auto measure = [key, args, per, grid_of, run](cudaStream_t st) {
+            TuneChoice c;
+            if (tune_lookup(key, &c)) return c;
+            TuneScratch sc;
+            StencilArgs<T> t = args;
+            const size_t vb = (size_t)args.nblk * args.L.N * 4 * sizeof(T);
+            t.x = (const T*)sc.zeros(vb, st);
+            t.b = (const T*)sc.zeros(vb, st);
+            if (args.d) t.d = (const T*)sc.zeros(vb, st);
+            t.out = (T*)sc.zeros(vb, st);
+            if (args.out2) t.out2 = (T*)sc.zeros(vb, st);
+            if (args.partial) t.partial = (double*)sc.zeros(sizeof(double) * 4 * args.nblk * kMaxStencilGrid, st);
+            std::vector<TuneChoice> cands;
+            for (int k = per; k >= 1; --k) cands.push_back(TuneChoice{k, 0});
+            return tune_measure(key, cands, [&](const TuneChoice& cc, cudaStream_t s2) { run(t, grid_of(cc.ctas_per_sm), s2, false); }, st);
+        };
+        TuneChoice c;
+        if (tune_lookup(key, &c)) grid = grid_of(c.ctas_per_sm);
+        else if (tune_now(s)) grid = grid_of(measure(s).ctas_per_sm);
+        else tune_defer([measure](cudaStream_t st) { measure(st); });
+    }
+    run(args, grid, s, true);
     return grid;
 }
 

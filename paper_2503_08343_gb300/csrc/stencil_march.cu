@@ -26,6 +26,7 @@
 
 #include <cuda.h>
 
+#include "autotune.h"
 #include "kernels.h"
 
 namespace gmrf {
@@ -452,22 +453,68 @@ int launch_march_mode(const StencilArgs<T>& a, cudaStream_t s, bool dry = false)
     }
     if (dry) return 0;
     if (a.L.col.kind != 0) throw std::runtime_error("space-time stencil: collocation rows are 1D space only");
-    // split time into chunks when tiles x blocks alone do not fill the grid twice
+    // time is cut into chunks when tiles x blocks alone do not fill the grid:
+    // about `mult` units per resident CTA, at least 8 time levels per chunk
     const long long tiles = (long long)a.L.tiles_x * a.L.tiles_y;
     const long long base = tiles * a.nblk;
     const int nt = a.L.nt;
-    int nchunks = (int)std::min<long long>(std::max<long long>(1, (2LL * resident + base - 1) / base), std::max(1, nt / 8));
-    const int tc = (nt + nchunks - 1) / nchunks;
-    nchunks = (nt + tc - 1) / tc;
-    const long long nunits = base * nchunks;
-    const int grid = (int)std::min<long long>(std::min<long long>(nunits, resident), kMaxMarchGrid);
-    MarchMaps maps;
-    std::memset(&maps, 0, sizeof(maps));
-    maps.p = march_map<T>(MODE == M_CHEB0 ? a.b : a.x, a.L, a.nblk, true);
-    if (MODE != M_APPLY) maps.b = march_map<T>(a.b, a.L, a.nblk, false);
-    if (MODE == M_CHEB && a.d != nullptr) maps.d = march_map<T>(a.d, a.L, a.nblk, false);
-    { kern<<<(unsigned)grid, 256, smem, s>>>(args, (int)nunits, tc, nchunks, maps); note_launch(); }
-    return grid;
+    const int nsm = sms, per = resident / sms;
+    struct Shape { int grid, tc, nchunks; long long nunits; };
+    auto shape_of = [base, nt, nsm](int k, int mult) {
+        const long long res = (long long)nsm * k;
+        int nchunks = (int)std::min<long long>(std::max<long long>(1, (mult * res + base - 1) / base), std::max(1, nt / 8));
+        const int tc = (nt + nchunks - 1) / nchunks;
+        nchunks = (nt + tc - 1) / tc;
+        const long long nunits = base * nchunks;
+        return Shape{(int)std::min<long long>(std::min<long long>(nunits, res), kMaxMarchGrid), tc, nchunks, nunits};
+    };
+    auto run = [kern, smem](const StencilArgs<T>& aa, const Shape& sh, cudaStream_t st, bool count) {
+        MarchMaps maps;
+        std::memset(&maps, 0, sizeof(maps));
+        maps.p = march_map<T>(MODE == M_CHEB0 ? aa.b : aa.x, aa.L, aa.nblk, true);
+        if (MODE != M_APPLY) maps.b = march_map<T>(aa.b, aa.L, aa.nblk, false);
+        if (MODE == M_CHEB && aa.d != nullptr) maps.d = march_map<T>(aa.d, aa.L, aa.nblk, false);
+        kern<<<(unsigned)sh.grid, 256, smem, st>>>(aa, (int)sh.nunits, sh.tc, sh.nchunks, maps);
+        if (count) note_launch();
+    };
+    Shape sh = shape_of(per, 2);
+    // launch shape (CTAs per SM, units per resident CTA): measured once per key
+    if (base * std::max(1, nt / 8) > nsm) {
+        const TuneKey key{std::string("march<") + (sizeof(T) == 8 ? "f64," : "f32,") +
+                              (MODE == M_APPLY ? "apply" : MODE == M_RESID ? "resid" : MODE == M_CHEB ? "cheb" : "cheb0") + ">",
+                          args.nblk, tune_units_bucket(base * nt), tune_obs_bucket(args.L.ostride, args.L.ocap > 0)};
+        auto measure = [key, args, per, shape_of, run](cudaStream_t st) {
+            TuneChoice c;
+            if (tune_lookup(key, &c)) return c;
+            TuneScratch sc;
+            StencilArgs<T> t = args;
+            const size_t vb = (size_t)args.nblk * args.L.N * 4 * sizeof(T);
+            t.x = (const T*)sc.zeros(vb, st);
+            t.b = (const T*)sc.zeros(vb, st);
+            if (args.d) t.d = (const T*)sc.zeros(vb, st);
+            t.out = (T*)sc.zeros(vb, st);
+            if (args.out2) t.out2 = (T*)sc.zeros(vb, st);
+            if (args.partial) t.partial = (double*)sc.zeros(sizeof(double) * 4 * args.nblk * kMaxMarchGrid, st);
+            std::vector<TuneChoice> cands;
+            std::vector<Shape> seen;
+            for (int k = per; k >= 1; --k)
+                for (int m : {2, 1, 4}) {
+                    const Shape q = shape_of(k, m);
+                    bool dup = false;
+                    for (const Shape& o : seen) dup |= o.grid == q.grid && o.nchunks == q.nchunks;
+                    if (dup) continue;
+                    seen.push_back(q);
+                    cands.push_back(TuneChoice{k, m});
+                }
+            return tune_measure(key, cands, [&](const TuneChoice& cc, cudaStream_t s2) { run(t, shape_of(cc.ctas_per_sm, cc.aux), s2, false); }, st);
+        };
+        TuneChoice c;
+        if (tune_lookup(key, &c)) sh = shape_of(c.ctas_per_sm, c.aux);
+        else if (tune_now(s)) { c = measure(s); sh = shape_of(c.ctas_per_sm, c.aux); }
+        else tune_defer([measure](cudaStream_t st) { measure(st); });
+    }
+    run(args, sh, s, true);
+    return sh.grid;
 }
 
 }  // namespace

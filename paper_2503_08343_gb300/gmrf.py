@@ -107,6 +107,9 @@ def load(build_if_missing: bool = False):
         "gmrf_prior_logdet": (I32, [C.POINTER(PriorDesc), DP, DP]),
         "gmrf_transfer_info": (I32, [P, C.POINTER(C.c_int32), DP]),
         "gmrf_test_set_wait_cap": (None, [I32]),
+        "gmrf_launch_count": (U64, []),
+        "gmrf_autotune_mode": (I32, [I32]),
+        "gmrf_autotune_log": (I64, [C.c_char_p, I64]),
         "gmrf_num_unknowns": (I64, [P]),
         "gmrf_num_levels": (I32, [P]),
         "gmrf_prior_destroy": (None, [P]),
@@ -354,6 +357,25 @@ def marginal_var_batch(posts, ns, seed, means=True, opts=None, nthreads=1):
     infos = (SolveInfo * k)()
     _check(load().gmrf_marginal_var_batch(hp, k, ns, seed, mp, vp, C.byref(opts or default_opts()), infos, nthreads))
     return ms, vs, [i.as_dict() for i in infos]
+
+
+def autotune_mode(mode=None) -> int:
+    """Launch-shape autotuner: sets the mode (0 off, 1 on) and returns the
+    previous one; with no argument only returns the current mode."""
+    return int(load().gmrf_autotune_mode(-1 if mode is None else int(mode)))
+
+
+def autotune_log() -> list[dict]:
+    """Every launch shape the autotuner has chosen in this process: key,
+    CTAs per SM, time-chunk multiplier, milliseconds per candidate."""
+    import json
+    lib = load()
+    n = lib.gmrf_autotune_log(None, 0)
+    if n < 0:
+        raise RuntimeError("gmrf_autotune_log failed")
+    buf = C.create_string_buffer(n + 1)
+    lib.gmrf_autotune_log(buf, n + 1)
+    return [json.loads(line) for line in buf.value.decode().splitlines() if line.strip()]
 
 
 def normals(seed, stream, sample0, count, n):
