@@ -11,6 +11,17 @@ Readings of the paper used here (where it is silent or ambiguous):
 * Homogeneous Dirichlet boundary (App. B, N_k = 0): rows and columns of the
   constrained matrices are zeroed and the diagonal set to 1; the boundary
   DOF is given variance eps2 (App. B "M_kk = eps_k^2"), independent of tau.
+* Periodic boundary (App. B, N_k = 1, c_1 = 1, h(1) = mirror(k)), for the
+  spatial kinds with prior["bc"] == "periodic": the nodes on x = hi and on
+  y = hi are constrained to their mirrors on x = lo and y = lo.  App. B adds
+  column k to column mirror(k); for the FEM assembly the test functions are
+  periodic too, so row k is added to row mirror(k) (without it the rows of
+  the mirror nodes would hold half an element ring and the operator would
+  not be translation invariant).  The constrained rows become e_k with
+  M_kk = eps_k^2, and we take App. B's hard limit eps_k -> 0: u_k = 0, the
+  field at k equals the field at mirror(k), and the unknowns are the
+  (n - 1)^2 nodes of the torus.  In matrix form K_t = T^T K T and
+  ml_t = T^T ml with T the n^2 x (n - 1)^2 mirror map.
 * Space-time noise is white in space and lumped, w ~ N(0, tau^2 dt Ml)
   (App. A with Sigma = M^-1), so the whole prior scales as tau^-2.  The
   initial block is a Matern alpha = 2 precision with kappa0, normalised to
@@ -110,9 +121,37 @@ def p1_2d(xs: np.ndarray, ys: np.ndarray, vx: float = 0.0, vy: float = 0.0):
 # Dirichlet constraint (App. B)
 
 
-def spatial_boundary(prior: dict) -> np.ndarray:
-    """Boolean mask over the spatial nodes of the Dirichlet boundary."""
+def is_periodic(prior: dict) -> bool:
+    return prior.get("bc", "dirichlet") == "periodic"
+
+
+def mirror_matrix(prior: dict) -> sp.csr_matrix:
+    """T: the n_x n_y mesh nodes -> the (n_x - 1)(n_y - 1) torus nodes,
+    T[(i, j), (i mod (n_x - 1), j mod (n_y - 1))] = 1 (App. B periodic
+    boundary: a node on x = hi or y = hi is its mirror on x = lo or y = lo)."""
     nx, ny, _ = prior["n"]
+    mx, my = nx - 1, ny - 1
+    rows, cols = [], []
+    for j in range(ny):
+        for i in range(nx):
+            rows.append(j * nx + i)
+            cols.append((j % my) * mx + (i % mx))
+    return sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(nx * ny, mx * my))
+
+
+def num_unknowns(prior: dict) -> int:
+    nx, ny, nt = prior["n"]
+    if is_periodic(prior):
+        return (nx - 1) * (ny - 1)
+    return nx * ny * nt
+
+
+def spatial_boundary(prior: dict) -> np.ndarray:
+    """Boolean mask over the spatial nodes of the Dirichlet boundary (none on
+    the torus of a periodic prior)."""
+    nx, ny, _ = prior["n"]
+    if is_periodic(prior):
+        return np.zeros((nx - 1) * (ny - 1), dtype=bool)
     i = np.tile(np.arange(nx), ny)
     j = np.repeat(np.arange(ny), nx)
     bnd = (i == 0) | (i == nx - 1)
@@ -177,6 +216,15 @@ def prior_root(prior: dict) -> sp.csr_matrix:
     where Mlc is Ml with boundary rows removed; boundary rows e_k / eps.
     """
     kind = prior["kind"]
+    if is_periodic(prior):
+        # App. B periodic constraint on rows and columns, hard limit (see the
+        # module docstring): B = tau ml_t^-1/2 T^T K T
+        assert kind in ("matern2d", "steady_advdiff2d"), "periodic boundary: spatial priors only"
+        T = mirror_matrix(prior)
+        ml = spatial_mesh(prior)[1]
+        Kt = T.T @ prior_root_K(prior) @ T
+        mlt = T.T @ ml
+        return (sp.diags(prior["tau"] / np.sqrt(mlt)) @ Kt).tocsr()
     S, ml, Badv, dim = spatial_mesh(prior)
     Ns = len(ml)
     sbnd = spatial_boundary(prior)
@@ -231,8 +279,23 @@ def prior_root_derivative(prior: dict, name: str) -> sp.csr_matrix:
     Space-time priors: kappa means kappa0 (the initial block)."""
     kind = prior["kind"]
     S, ml, _, dim = spatial_mesh(prior)
-    sbnd = spatial_boundary(prior)
     nx, ny, _ = prior["n"]
+    if is_periodic(prior):
+        T = mirror_matrix(prior)
+        d = prior["tau"] / np.sqrt(T.T @ ml)
+        if name == "log_tau":
+            dK = prior_root_K(prior)
+        elif name == "log_kappa":
+            dK = 2.0 * prior["kappa"] ** 2 * sp.diags(ml)
+        elif kind == "matern2d":
+            return sp.csr_matrix((len(d), len(d)))
+        elif name == "c":
+            dK = p1_2d(axis_nodes(prior["lo"][0], prior["hi"][0], nx),
+                       axis_nodes(prior["lo"][1], prior["hi"][1], ny), 1.0, 0.0)[2]
+        else:
+            dK = S
+        return (sp.diags(d) @ (T.T @ dK @ T)).tocsr()
+    sbnd = spatial_boundary(prior)
     xs = axis_nodes(prior["lo"][0], prior["hi"][0], nx)
     if dim == 1:
         Bx = p1_1d(xs, 1.0)[2]

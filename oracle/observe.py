@@ -5,6 +5,8 @@ the Burgers residual with its Jacobian (Sec. 3.3).
 Test infrastructure (see the package docstring).
 
 Readings:
+* With a periodic prior the point data are taken on the full n x n mesh and
+  the weight of a node on x = hi or y = hi goes to its mirror on the torus.
 * Off-grid point data in space-time use P1 barycentric weights in space
   times linear interpolation in time.  A point on an element edge goes to the
   lower-index cell; inside a cell the lower triangle wins on the diagonal.
@@ -98,7 +100,11 @@ def point_matrix(prior: dict, coords: np.ndarray) -> sp.csr_matrix:
             rows.append(r)
             cols.append(c)
             vals.append(v)
-    return sp.csr_matrix((vals, (rows, cols)), shape=(m, N))
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(m, N))
+    if fem.is_periodic(prior):
+        # weights on a node of x = hi or y = hi belong to its mirror (App. B)
+        A = (A @ fem.mirror_matrix(prior)).tocsr()
+    return A
 
 
 def ic_matrix(prior: dict) -> sp.csr_matrix:

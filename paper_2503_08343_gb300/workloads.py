@@ -17,6 +17,7 @@ A prior description is a plain dict:
     lo, hi  (x0, y0, t0), (x1, y1, t1) domain corners
     kappa, tau, nu, cx, cy, kappa0, eps2   SPDE parameters (see the oracle
             and the C header for their exact role)
+    bc      optional: "dirichlet" (default) or "periodic" (spatial kinds)
 
 An observation description is a dict with "coords" [m, d] (space, then time),
 "y" [m], "sigma" [m] and optional collocation settings for Burgers.
@@ -59,8 +60,18 @@ def prior_st2d(n: int, nt: int, cx: float, cy: float, nu: float, kappa: float, t
                 kappa0=float(kappa), eps2=float(eps2))
 
 
+def periodic(prior: dict) -> dict:
+    """The same spatial prior with the periodic boundary of App. B (N_k = 1):
+    the nodes on x = hi and y = hi are the mirrors of those on x = lo and
+    y = lo, so the unknowns are the (n - 1)^2 nodes of the torus."""
+    assert prior["kind"] in ("matern2d", "steady_advdiff2d")
+    return dict(prior, bc="periodic")
+
+
 def n_nodes(prior: dict) -> int:
     nx, ny, nt = prior["n"]
+    if prior.get("bc", "dirichlet") == "periodic":
+        return (nx - 1) * (ny - 1)
     return nx * ny * nt
 
 
@@ -154,6 +165,48 @@ def node_obs(prior: dict, frac: float, sigma: float, truth, seed: int) -> dict:
     coords = np.stack([xs, ys], axis=1)
     y = truth(coords) + rng.normal(0.0, sigma, size=m)
     return dict(coords=coords, y=y, sigma=np.full(m, float(sigma)))
+
+
+def torus_node_obs(prior: dict, sigma: float, truth, seed: int) -> dict:
+    """One observation at every node of a periodic prior's torus (x = lo + i h,
+    i < n - 1), y = truth + N(0, sigma^2)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, _ = prior["n"]
+    lo, hi = prior["lo"], prior["hi"]
+    ix = np.tile(np.arange(nx - 1), ny - 1)
+    iy = np.repeat(np.arange(ny - 1), nx - 1)
+    xs = lo[0] + (hi[0] - lo[0]) * ix / (nx - 1)
+    ys = lo[1] + (hi[1] - lo[1]) * iy / (ny - 1)
+    coords = np.stack([xs, ys], axis=1)
+    y = truth(coords) + rng.normal(0.0, sigma, size=len(xs))
+    return dict(coords=coords, y=y, sigma=np.full(len(xs), float(sigma)))
+
+
+def periodic_fourier(rng: np.random.Generator, k: int = 20, wmax: int = 8):
+    """Sum of k random Fourier modes of period one in x and y (a smooth
+    periodic truth)."""
+    kx = rng.integers(-wmax, wmax + 1, size=k)
+    ky = rng.integers(-wmax, wmax + 1, size=k)
+    amp = rng.normal(size=k) / np.sqrt(k)
+    ph = rng.uniform(0.0, 2.0 * np.pi, size=k)
+
+    def f(z):
+        z = np.atleast_2d(z)
+        return np.sum(amp * np.cos(2.0 * np.pi * (np.outer(z[:, 0], kx) + np.outer(z[:, 1], ky)) + ph), axis=1)
+    return f
+
+
+def c2_matern_periodic(n: int = 513, m: int = 10000, seed: int = 2, kappa: float = 20.0, all_nodes: bool = False,
+                       sigma: float = 0.1):
+    """The 2D Matern workload on the unit torus (periodic boundary, (n-1)^2
+    unknowns): m uniform point observations of a periodic 20-mode Fourier sum
+    plus N(0, sigma^2), or with all_nodes one observation at every node."""
+    pr = periodic(prior_matern2d(n, kappa))
+    rng = np.random.default_rng(seed + 200)
+    f = periodic_fourier(rng, 20, 8)
+    if all_nodes:
+        return pr, torus_node_obs(pr, sigma, f, seed)
+    return pr, point_obs(pr, m, sigma, f, seed)
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,140 @@
+"""Pins of the oracle's periodic boundary (App. B, N_k = 1) against closed
+forms that do not go through its element loops.
+
+On the torus every operator of the structured P1 mesh is circulant, so it is
+diagonalised by the 2D DFT.  With h the mesh width, the lumped mass is h^2,
+the P1 stiffness is the 5-point stencil (4; -1 at the four axis neighbours;
+the diagonal couplings vanish on right triangles), whose symbol is
+s(w) = 4 sin^2(w_x / 2) + 4 sin^2(w_y / 2), and the x-advection matrix
+int phi_i c d/dx phi_j collects, from the six triangles around a node, the
+antisymmetric stencil (c h / 6)[x+1: 2, x-1: -2, (+1,+1): 1, (-1,-1): -1,
+y+1: -1, y-1: 1], whose symbol is i (c h / 3)(2 sin w_x + sin(w_x + w_y)
+- sin w_y).  So B = tau h^-1 (kappa^2 h^2 + nu S + c Bx) has the symbol
+b(w) = (tau / h)(kappa^2 h^2 + nu s(w) + i (c h / 3)(...)), and
+Q = B^T B has |b(w)|^2.  Pins:
+
+* B v and Q v equal their DFT forms (a row or column left out of the mirror
+  condensation, a wrong mass or a wrong sign of the advection fails);
+* the prior variance at every node equals (1/N) sum_w 1/|b(w)|^2 (Takahashi
+  on the oracle's Cholesky factor, 1e-10) and log det Q = sum_w log |b(w)|^2;
+* point rows: a point on x = hi or y = hi is its mirror on x = lo or y = lo,
+  and a point in the last cell shares its weight with column 0;
+* all torus nodes observed with equal noise: Q_u|y is circulant and the
+  posterior mean is a DFT solve (1e-10);
+* the exact derivative of B against central differences of prior_root.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fem, infer, linalg, observe
+from paper_2503_08343_gb300 import workloads as W
+
+
+def _symbol(pr):
+    m = pr["n"][0] - 1
+    h = (pr["hi"][0] - pr["lo"][0]) / m
+    w = 2.0 * np.pi * np.fft.fftfreq(m)           # frequencies along one axis
+    wy, wx = np.meshgrid(w, w, indexing="ij")     # field index j * m + i -> array [j, i]
+    s = 4.0 * np.sin(wx / 2) ** 2 + 4.0 * np.sin(wy / 2) ** 2
+    nu = 1.0 if pr["kind"] == "matern2d" else pr["nu"]
+    c = 0.0 if pr["kind"] == "matern2d" else pr["cx"]
+    adv = 1j * (c * h / 3.0) * (2.0 * np.sin(wx) + np.sin(wx + wy) - np.sin(wy))
+    return (pr["tau"] / h) * (pr["kappa"] ** 2 * h * h + nu * s + adv), m
+
+
+def _apply_symbol(sym, v, m):
+    """(C v) for the circulant C with (C v)_n = sum_d c_d v_(n+d), given its
+    symbol sum_d c_d exp(i w.d): in numpy's DFT convention a shift by +d
+    multiplies the transform by exp(+i w.d)."""
+    V = np.fft.fft2(v.reshape(m, m))
+    return np.real(np.fft.ifft2(sym * V)).ravel()
+
+
+PRIORS = {
+    "matern_24": lambda: W.periodic(W.prior_matern2d(25, 6.0)),
+    "matern_16_k20": lambda: W.periodic(W.prior_matern2d(17, 20.0)),
+    "advdiff_20": lambda: W.periodic(W.prior_steady_advdiff2d(21, 5.0, nu=0.3, c=1.7)),
+}
+
+
+@pytest.mark.parametrize("name", list(PRIORS))
+def test_root_and_precision_are_the_circulants_of_the_closed_form_symbol(name):
+    pr = PRIORS[name]()
+    b, m = _symbol(pr)
+    B = fem.prior_root(pr)
+    Q = fem.prior_precision(pr)
+    assert B.shape == (m * m, m * m)
+    v = np.random.default_rng(3).normal(size=m * m)
+    # (B v)_n = sum_d B[n, n + d] v_(n+d): the symbol uses exp(+i w.d), i.e. b
+    # as written (the advection stencil's offsets are those of the columns)
+    Bv = _apply_symbol(b, v, m)
+    assert np.max(np.abs(B @ v - Bv)) <= 1e-12 * np.max(np.abs(Bv))
+    Qv = _apply_symbol(np.abs(b) ** 2, v, m)
+    assert np.max(np.abs(Q @ v - Qv)) <= 1e-12 * np.max(np.abs(Qv))
+
+
+@pytest.mark.parametrize("name", list(PRIORS))
+def test_prior_variance_and_log_det_closed_form(name):
+    pr = PRIORS[name]()
+    b, m = _symbol(pr)
+    lam = np.abs(b) ** 2
+    L = linalg.cholesky(fem.prior_precision(pr))
+    var = linalg.takahashi_diag(L)
+    want = np.mean(1.0 / lam)
+    assert np.max(np.abs(var - want)) <= 1e-10 * want
+    assert linalg.logdet(L) == pytest.approx(float(np.sum(np.log(lam))), rel=1e-12, abs=1e-9)
+
+
+def test_point_rows_wrap_to_the_mirror_nodes():
+    pr = PRIORS["matern_24"]()
+    m = pr["n"][0] - 1
+    h = 1.0 / m
+    pts = np.array([[1.0, 0.3], [0.0, 0.3], [0.37, 1.0], [0.37, 0.0], [1.0, 1.0], [0.0, 0.0],
+                    [1.0 - 0.25 * h, 0.5 + 0.1 * h]])
+    A = observe.point_matrix(pr, pts).toarray()
+    assert A.shape == (len(pts), m * m)
+    assert np.allclose(A.sum(axis=1), 1.0, atol=1e-14)
+    for a, b in ((0, 1), (2, 3), (4, 5)):
+        assert np.max(np.abs(A[a] - A[b])) <= 1e-14, (a, b)
+    assert abs(A[5, 0] - 1.0) <= 1e-14
+    # near the seam: weight on the last column and on column 0 (the mirror of x = hi)
+    j = int(0.5 * m)
+    assert A[6, j * m + m - 1] > 0.2 and A[6, j * m + 0] > 0.5
+
+
+def test_all_nodes_observed_posterior_mean_is_a_dft_solve():
+    pr, ob = W.c2_matern_periodic(n=25, kappa=6.0, all_nodes=True, sigma=0.2, seed=4)
+    b, m = _symbol(pr)
+    post = infer.condition(pr, ob)
+    mu = infer.posterior_mean(post)
+    rinv = 1.0 / 0.2 ** 2
+    Y = np.fft.fft2((rinv * ob["y"]).reshape(m, m))
+    want = np.real(np.fft.ifft2(Y / (np.abs(b) ** 2 + rinv))).ravel()
+    assert np.max(np.abs(mu - want)) <= 1e-10 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("name", ["matern_24", "advdiff_20"])
+def test_root_derivative_against_central_differences(name):
+    pr = PRIORS[name]()
+    theta = {"log_kappa": math.log(pr["kappa"]), "log_tau": math.log(pr["tau"]), "c": pr["cx"], "nu": pr["nu"]}
+    names = ["log_kappa", "log_tau"] + (["c", "nu"] if pr["kind"] != "matern2d" else [])
+    for nm in names:
+        hstep = 1e-6
+
+        def root(v):
+            q = dict(pr)
+            if nm == "log_kappa":
+                q["kappa"] = math.exp(v)
+            elif nm == "log_tau":
+                q["tau"] = math.exp(v)
+            elif nm == "c":
+                q["cx"] = v
+            else:
+                q["nu"] = v
+            return fem.prior_root(q).toarray()
+
+        fd = (root(theta[nm] + hstep) - root(theta[nm] - hstep)) / (2 * hstep)
+        dB = fem.prior_root_derivative(pr, nm).toarray()
+        assert np.max(np.abs(dB - fd)) <= 1e-6 * max(1.0, np.max(np.abs(dB))), nm
