@@ -63,14 +63,32 @@ typedef enum gmrf_status {
  *                         G = Ml + dt (nu S + B_c), w ~ N(0, tau^2 dt Ml); the
  *                         initial level is a unit-variance Matern (kappa0).
  * Every prior is applied in the stacked form Q = B^T B with B a short stencil.
- * Boundary nodes carry a homogeneous Dirichlet condition (App. B, N_k = 0):
- * decoupled, variance eps2. */
+ * Boundary (gmrf_prior_desc.bc):
+ *  GMRF_BC_DIRICHLET  boundary nodes carry a homogeneous Dirichlet condition
+ *                     (App. B, N_k = 0): decoupled, variance eps2.
+ *  GMRF_BC_PERIODIC   spatial kinds (GMRF_MATERN2_2D, GMRF_STEADY_ADVDIFF_2D)
+ *                     only: App. B with N_k = 1, c_1 = 1, h(1) = mirror(k),
+ *                     in its hard limit.  The nodes on x = hi and y = hi are
+ *                     the nodes on x = lo and y = lo; columns and rows of the
+ *                     constrained nodes are added to those of their mirrors
+ *                     (test and trial functions periodic), so the unknowns
+ *                     are the (nx - 1) x (ny - 1) nodes of the torus, node
+ *                     (i, j) at (lo + i h_x, lo + j h_y), h = (hi - lo) / (n - 1).
+ *                     Every field the library reads or writes has that size.
+ *                     The multigrid hierarchy halves nx - 1 and ny - 1 while
+ *                     they are even and at least 8; a coarsest level above
+ *                     1024 unknowns is rejected (GMRF_E_INVALID). */
 typedef enum gmrf_prior_kind {
     GMRF_MATERN2_2D = 0,
     GMRF_ADVDIFF_ST_1D = 1,
     GMRF_ADVDIFF_ST_2D = 2,
     GMRF_STEADY_ADVDIFF_2D = 3
 } gmrf_prior_kind;
+
+typedef enum gmrf_boundary {
+    GMRF_BC_DIRICHLET = 0,
+    GMRF_BC_PERIODIC = 1
+} gmrf_boundary;
 
 typedef struct gmrf_prior_desc {
     int32_t kind;              /* gmrf_prior_kind */
@@ -82,6 +100,7 @@ typedef struct gmrf_prior_desc {
     double cx, cy;             /* advection velocity */
     double kappa0;             /* space-time: Matern kappa of the initial level */
     double eps2;               /* Dirichlet boundary variance (App. B "M_kk = eps^2") */
+    int32_t bc;                /* gmrf_boundary (0: Dirichlet) */
 } gmrf_prior_desc;
 
 /* Observations (Sec. 3.1).  All pointers are host memory, read during the call.

@@ -144,6 +144,9 @@ gmrf_status gmrf_build_prior(const gmrf_prior_desc* desc, void* stream, gmrf_pri
         else require(d.kappa > 0, "kappa must be positive");
         require((long long)d.nx * d.ny * d.nt < (1LL << 31), "grid too large for 32-bit node indices");
         require(d.nx < 32768 && d.ny < 32768 && d.nt < 32768, "axes are limited to 32767 nodes");
+        require(d.bc == GMRF_BC_DIRICHLET || d.bc == GMRF_BC_PERIODIC, "unknown boundary");
+        if (d.bc == GMRF_BC_PERIODIC)
+            require(!st && d.nx >= 5 && d.ny >= 5, "periodic boundary: spatial priors with at least 5 nodes per axis");
         gmrf_prior* p = new gmrf_prior();
         p->impl.desc = d;
         p->impl.geo = geometry_of(d);
@@ -807,6 +810,9 @@ gmrf_status gmrf_prior_logdet(const gmrf_prior_desc* desc, double* logdet, doubl
         require(d.kind >= 0 && d.kind <= 3, "unknown prior kind");
         require(d.nx >= 3 && (d.kind == GMRF_ADVDIFF_ST_1D ? d.ny == 1 : d.ny >= 3), "bad grid");
         require(d.eps2 > 0 && d.tau > 0, "eps2 and tau must be positive");
+        require(d.bc == GMRF_BC_DIRICHLET ||
+                    (d.bc == GMRF_BC_PERIODIC && d.kind != GMRF_ADVDIFF_ST_1D && d.kind != GMRF_ADVDIFF_ST_2D && d.nx >= 5 && d.ny >= 5),
+                "bad boundary");
         std::vector<Level> lv;
         build_hierarchy(d, lv);
         const PriorDet r = prior_logdet(d, lv[0]);

@@ -263,4 +263,7 @@ __device__ __forceinline__ bool is_dirichlet(int x, int y, int nx, int ny) {
     return x == 0 || x == nx - 1 || (ny > 1 && (y == 0 || y == ny - 1));
 }
 
+// index on a torus axis of n nodes, for offsets within one period
+__host__ __device__ __forceinline__ int wrap_idx(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
 }  // namespace gmrf

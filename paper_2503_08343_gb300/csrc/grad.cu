@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(256) k_probe_contract(const LevelView<double> 
         const int x = (int)(r % nx);
         const long long q = r / nx;
         const int y = (int)(q % ny), t = (int)(q / ny);
-        const bool dir = x == 0 || x == nx - 1 || (ny > 1 && (y == 0 || y == ny - 1));
+        const bool per = L.periodic != 0;       // torus: no Dirichlet rows or columns, taps wrap
+        const bool dir = !per && (x == 0 || x == nx - 1 || (ny > 1 && (y == 0 || y == ny - 1)));
         if (!dir) {
             const int cls = (nt > 1 && t == 0) ? 1 : 0;
             V4<double> bw = v4zero<double>(), bv = v4zero<double>();
@@ -53,9 +54,11 @@ __global__ void __launch_bounds__(256) k_probe_contract(const LevelView<double> 
 #pragma unroll
             for (int p = 0; p < NPAR; ++p) { dw[p] = v4zero<double>(); dv[p] = v4zero<double>(); }
             for (int o = 0; o < NTAP; ++o) {
-                const int xx = x + tap_dx(o), yy = y + tap_dy(o), tt = t + tap_dt(o);
+                int xx = x + tap_dx(o), yy = y + tap_dy(o);
+                const int tt = t + tap_dt(o);
+                if (per) { xx = wrap_idx(xx, nx); yy = wrap_idx(yy, ny); }
                 if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || tt < 0 || tt >= nt) continue;
-                if (xx == 0 || xx == nx - 1 || (ny > 1 && (yy == 0 || yy == ny - 1))) continue;   // eliminated columns
+                if (!per && (xx == 0 || xx == nx - 1 || (ny > 1 && (yy == 0 || yy == ny - 1)))) continue;   // eliminated columns
                 const double c = (double)L.cf[cls][o];
                 const long long col = ((long long)tt * ny + yy) * nx + xx;
                 const V4<double> wv = v4load(Wv + ((size_t)blk * N + col) * RW);

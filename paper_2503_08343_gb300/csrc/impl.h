@@ -63,10 +63,12 @@ struct LevelView {
     int ocap;          // entries per tile (0: no observation rows)
     int ostride;       // bytes per tile of oent (multiple of 16)
     int obs_direct;    // 1: read the tables from global memory instead of staging them (set per launch)
+    int periodic;      // 1: the (x, y) torus of a periodic prior (no Dirichlet nodes, neighbours wrap)
 };
 
 struct Level {
     int geo = 0;
+    int periodic = 0;  // (x, y) torus: nx, ny count the torus nodes, h = (hi - lo) / nx
     int nx = 1, ny = 1, nt = 1;
     long long N = 0;
     double hx = 0, hy = 0, dt = 0;

@@ -158,6 +158,7 @@ template <typename T> LevelView<T> Level::view() const {
     else { v.oent = d_oent64; v.ostride = ostride64; }
     v.ocap = d_omap ? ocap : 0;
     v.obs_direct = 0;
+    v.periodic = periodic;
     return v;
 }
 
@@ -491,7 +492,8 @@ struct AxisMap { const int32_t* j; const void* w; bool on; };
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(T* __restrict__ xf, const T* __restrict__ xc, int nx, int ny, int nt,
-                                                     int cx, int cy, int ct, AxisMap ax, AxisMap ay, AxisMap at, bool p1) {
+                                                     int cx, int cy, int ct, AxisMap ax, AxisMap ay, AxisMap at, bool p1,
+                                                     bool per) {
     const long long Nf = (long long)nx * ny * nt, Nc = (long long)cx * cy * ct;
     const int blk = blockIdx.y;
     const unsigned n = blockIdx.x * 256u + threadIdx.x;      // levels hold fewer than 2^31 nodes
@@ -515,7 +517,12 @@ __global__ void __launch_bounds__(256) k_prolong_add(T* __restrict__ xf, const T
                 const T fs = p1 ? p1_weight<T>(dx, dy, wx, wy) : (dx ? wx : T(1) - wx) * (dy ? wy : T(1) - wy);
                 const T f = ft * fs;
                 if (f == T(0)) continue;
-                const long long c = ((long long)(jt + dt) * cy + (jy + dy)) * cx + (jx + dx);
+                int ux = jx + dx, uy = jy + dy;
+                if (per) {      // coarse torus: node cx is node 0
+                    if (ux == cx) ux = 0;
+                    if (uy == cy) uy = 0;
+                }
+                const long long c = ((long long)(jt + dt) * cy + uy) * cx + ux;
                 acc = fma4(f, v4load(xb + c * RW), acc);
             }
         }
@@ -531,8 +538,53 @@ void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, bool
     AxisMap ay{f.d_pj[1], dbl ? (const void*)f.d_pwd[1] : (const void*)f.d_pw[1], f.coarsen[1]};
     AxisMap at{f.d_pj[2], dbl ? (const void*)f.d_pwd[2] : (const void*)f.d_pw[2], f.coarsen[2]};
     if (f.N >= (1LL << 31)) throw std::runtime_error("prolongation: a level holds 2^31 or more nodes");
-    { k_prolong_add<T><<<dim3((unsigned)((f.N + 255) / 256), nblk), 256, 0, s>>>(xf, xc, f.nx, f.ny, f.nt, c.nx, c.ny, c.nt, ax, ay, at, p1); note_launch(); }
+    { k_prolong_add<T><<<dim3((unsigned)((f.N + 255) / 256), nblk), 256, 0, s>>>(xf, xc, f.nx, f.ny, f.nt, c.nx, c.ny, c.nt, ax, ay, at, p1, f.periodic != 0); note_launch(); }
 }
+
+// Restriction between periodic levels (torus n -> n / 2 in x and y), the
+// transpose of the interpolation of k_prolong_add: coarse node (X, Y) sums
+// P(i, j; X, Y) in[j][i] over the fine nodes 2X - 1 .. 2X + 1 and
+// 2Y - 1 .. 2Y + 1 (mod n), where fine i lies between coarse i / 2 and
+// (i / 2 + 1) mod m with weight (i mod 2) / 2 of the second.
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_torus(const T* __restrict__ in, T* __restrict__ out, int nx, int ny,
+                                                        int cx, int cy, bool p1) {
+    const long long Nf = (long long)nx * ny, Nc = (long long)cx * cy;
+    const int blk = blockIdx.y;
+    const unsigned n = blockIdx.x * 256u + threadIdx.x;
+    if (n >= (unsigned long long)Nc) return;
+    const int X = (int)(n % (unsigned)cx), Y = (int)(n / (unsigned)cx);
+    const T* ib = in + (size_t)blk * Nf * RW;
+    V4<T> acc = v4zero<T>();
+    for (int b = -1; b <= 1; ++b) {
+        const int iy = wrap_idx(2 * Y + b, ny);
+        const int jy = iy / 2;
+        const T wy = (iy & 1) ? T(0.5) : T(0);
+        for (int a = -1; a <= 1; ++a) {
+            const int ix = wrap_idx(2 * X + a, nx);
+            const int jx = ix / 2;
+            const T wx = (ix & 1) ? T(0.5) : T(0);
+            T w = T(0);
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int ux = jx + dx == cx ? 0 : jx + dx, uy = jy + dy == cy ? 0 : jy + dy;
+                    if (ux != X || uy != Y) continue;
+                    w += p1 ? p1_weight<T>(dx, dy, wx, wy) : (dx ? wx : T(1) - wx) * (dy ? wy : T(1) - wy);
+                }
+            if (w != T(0)) acc = fma4(w, v4load(ib + ((size_t)iy * nx + ix) * RW), acc);
+        }
+    }
+    v4store(out + ((size_t)blk * Nc + n) * RW, acc);
+}
+
+template <typename T>
+void launch_restrict_torus(const T* in, T* out, const Level& f, const Level& c, bool p1, int nblk, cudaStream_t s) {
+    if (!f.periodic || c.nx * 2 != f.nx || c.ny * 2 != f.ny || f.nt != 1)
+        throw std::runtime_error("torus restriction: levels are not a periodic 2:1 pair");
+    { k_restrict_torus<T><<<dim3((unsigned)((c.N + 255) / 256), nblk), 256, 0, s>>>(in, out, f.nx, f.ny, c.nx, c.ny, p1); note_launch(); }
+}
+template void launch_restrict_torus<float>(const float*, float*, const Level&, const Level&, bool, int, cudaStream_t);
+template void launch_restrict_torus<double>(const double*, double*, const Level&, const Level&, bool, int, cudaStream_t);
 template void launch_prolong_add<float>(float*, const float*, const Level&, const Level&, bool, int, cudaStream_t);
 template void launch_prolong_add<double>(double*, const double*, const Level&, const Level&, bool, int, cudaStream_t);
 
@@ -718,7 +770,12 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
 
     for (int e = tid; e < SX * SY * ST; e += 256) {
         const int sx = e % SX, sy = (e / SX) % SY, st = e / (SX * SY);
-        const int rx = tx0 - 1 + sx, ry = ty0 - HYS + sy, rt = tt0 + st;
+        int rx = tx0 - 1 + sx, ry = ty0 - HYS + sy;
+        const int rt = tt0 + st;
+        if (L.periodic) {           // rows across the seam of the torus
+            if (rx <= nx) rx = wrap_idx(rx, nx);
+            if (ry <= ny) ry = wrap_idx(ry, ny);
+        }
         V4<double> z = v4zero<double>();
         if (z1 != nullptr && rx >= 0 && rx < nx && ry >= 0 && ry < ny && rt < nt) {
             const long long row = ((long long)rt * ny + ry) * nx + rx;
@@ -733,7 +790,8 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
     const bool own = gx < nx && gy < ny && gt < nt;
     V4<double> q = v4zero<double>();
     if (own) {
-        if (is_dirichlet(gx, gy, nx, ny)) {
+        const bool per = L.periodic != 0;
+        if (!per && is_dirichlet(gx, gy, nx, ny)) {
             q = L.inv_eps * sz[lt][ly + HYS][lx + 1];
         } else {
 #pragma unroll
@@ -741,8 +799,9 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
                 if (HY == 0 && tap_dy(o) != 0) continue;
                 if (HT == 0 && tap_dt(o) != 0) continue;
                 const int rx = gx - tap_dx(o), ry = gy - tap_dy(o), rt = gt - tap_dt(o);
-                if (rx < 0 || rx >= nx || ry < 0 || ry >= ny || rt >= nt) continue;
-                if (is_dirichlet(rx, ry, nx, ny)) continue;     // Dirichlet rows touch only themselves
+                if (!per && (rx < 0 || rx >= nx || ry < 0 || ry >= ny)) continue;
+                if (rt >= nt) continue;
+                if (!per && is_dirichlet(rx, ry, nx, ny)) continue;     // Dirichlet rows touch only themselves
                 const int cls = (nt > 1 && rt == 0) ? 1 : 0;
                 const double c = L.cf[cls][o];
                 if (c == 0.0) continue;
@@ -954,13 +1013,15 @@ __global__ void k_diag(const LevelView<T> L, double* __restrict__ diag) {
     const long long r = n / nx;
     const int y = (int)(r % ny), t = (int)(r / ny);
     double d = 0.0;
-    if (is_dirichlet(x, y, nx, ny)) {
+    const bool per = L.periodic != 0;       // torus: every row is an interior row
+    if (!per && is_dirichlet(x, y, nx, ny)) {
         d = (double)L.inv_eps2;
     } else {
         for (int o = 0; o < NTAP; ++o) {
             const int rx = x - tap_dx(o), ry = y - tap_dy(o), rt = t - tap_dt(o);
-            if (rx < 0 || rx >= nx || ry < 0 || ry >= ny || rt < 0 || rt >= nt) continue;
-            if (is_dirichlet(rx, ry, nx, ny)) continue;
+            if (rt < 0 || rt >= nt) continue;
+            if (!per && (rx < 0 || rx >= nx || ry < 0 || ry >= ny)) continue;
+            if (!per && is_dirichlet(rx, ry, nx, ny)) continue;
             const int cls = (nt > 1 && rt == 0) ? 1 : 0;
             const double c = (double)L.cf[cls][o];
             d += c * c;

@@ -81,6 +81,8 @@ template <typename T> void launch_restrict_xy(const T* in, T* out, int nx, int n
                                               const int32_t* const pj[2], const T* const pw[2], bool p1,
                                               const int span[2], int nblk, cudaStream_t s);
 template <typename T> void launch_prolong_add(T* xf, const T* xc, const Level& f, const Level& c, bool p1, int nblk, cudaStream_t s);
+// restriction between periodic (torus) levels, the transpose of launch_prolong_add
+template <typename T> void launch_restrict_torus(const T* in, T* out, const Level& f, const Level& c, bool p1, int nblk, cudaStream_t s);
 template <typename T> void launch_dense_solve(const T* Ainv, const T* b, T* x, int n, int nblk, cudaStream_t s);
 
 // PCG scalar and vector steps.  Per-RHS scalars live in `sc` (FP64):

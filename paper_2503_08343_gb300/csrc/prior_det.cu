@@ -13,6 +13,8 @@
 // interior determinants: the spatial block (or the t = 0 block) and the
 // transition block.
 //
+// A periodic prior has one circulant block on the torus and no Dirichlet
+// rows: its determinant and traces are sums over the 2D DFT symbol.
 // Interior operators are handled two ways:
 //  - symmetric and separable (no diagonal taps, equal opposite taps: the
 //    Matern blocks, and any block without advection): the operator is a
@@ -285,6 +287,36 @@ void band_lu_path(int mx, int my, const double a[NT7], const std::vector<Stencil
     for (long long n = 0; n < std::min<long long>(p, N); ++n) trace_row(n);
 }
 
+// Periodic (torus) blocks: B is circulant on the mx x my torus, diagonalised
+// by the 2D DFT, with symbol b(w) = sum_o a_o exp(i w.d_o) at the
+// frequencies w = 2 pi (j / mx, k / my), so log|det B| = sum_w log|b(w)| and
+// tr(B^-1 X) = sum_w x(w) / b(w) (real: the terms of w and -w are conjugate).
+void torus_form(int mx, int my, const double a[NT7], const std::vector<Stencil7>& X, InteriorDet& r) {
+    static const int DX[NT7] = {0, -1, 1, 0, 0, -1, 1}, DY[NT7] = {0, 0, 0, -1, 1, -1, 1};
+    r.logabsdet = 0.0;
+    r.sign = 1;
+    r.tr.assign(X.size(), 0.0);
+    for (int k = 0; k < my; ++k)
+        for (int j = 0; j < mx; ++j) {
+            const double wx = 2.0 * kPi * j / mx, wy = 2.0 * kPi * k / my;
+            double br = 0.0, bi = 0.0;
+            double xr[4] = {0, 0, 0, 0}, xi[4] = {0, 0, 0, 0};
+            for (int o = 0; o < NT7; ++o) {
+                const double ph = wx * DX[o] + wy * DY[o], c = std::cos(ph), sn = std::sin(ph);
+                br += a[o] * c;
+                bi += a[o] * sn;
+                for (size_t p = 0; p < X.size(); ++p) {
+                    xr[p] += X[p].c[o] * c;
+                    xi[p] += X[p].c[o] * sn;
+                }
+            }
+            const double m2 = br * br + bi * bi;
+            if (!(m2 > 0.0) || !std::isfinite(m2)) throw Error(GMRF_E_NOT_SPD, "prior block is singular");
+            r.logabsdet += 0.5 * std::log(m2);
+            for (size_t p = 0; p < X.size(); ++p) r.tr[p] += (xr[p] * br + xi[p] * bi) / m2;   // Re(x / b)
+        }
+}
+
 }  // namespace
 
 InteriorDet interior_logdet(int mx, int my, const double a[NT7], const std::vector<Stencil7>& X) {
@@ -301,6 +333,19 @@ InteriorDet interior_logdet(int mx, int my, const double a[NT7], const std::vect
 PriorDet prior_logdet(const gmrf_prior_desc& d, const Level& F) {
     PriorDet out;
     const DerivTaps D = derivative_taps(d, F);
+    if (F.periodic) {          // one circulant block on the torus, no Dirichlet rows
+        double a[NT7];
+        std::vector<Stencil7> X(4);
+        for (int o = 0; o < NT7; ++o) {
+            a[o] = F.cd[0][o];
+            for (int q = 0; q < 4; ++q) X[(size_t)q].c[o] = D.d[q][0][o];
+        }
+        InteriorDet b;
+        torus_form(F.nx, F.ny, a, X, b);
+        out.logdet = 2.0 * b.logabsdet;
+        for (int q = 0; q < 4; ++q) out.tr[q] = b.tr[(size_t)q];
+        return out;
+    }
     const bool st = d.kind == GMRF_ADVDIFF_ST_1D || d.kind == GMRF_ADVDIFF_ST_2D;
     const int mx = F.nx - 2, my = F.ny > 1 ? F.ny - 2 : 1;
     const long long ns = (long long)F.nx * F.ny;                 // spatial nodes

@@ -182,8 +182,12 @@ __global__ void __launch_bounds__(256) k_resid_df(const LevelView<double> L, con
                 const int e = tid + 256 * k;
                 if (KP * 256 > PN && e >= PN) break;
                 const int gx = tx0 + p_dx[k], gy = ty0 + p_dy[k], gt = tt0 + p_dt[k];
-                const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gt >= 0 && gt < nt;
-                const int node = in ? tbase + p_rel[k] : 0;
+                bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gt >= 0 && gt < nt;
+                int node = in ? tbase + p_rel[k] : 0;
+                if (L.periodic && !in && gt >= 0 && gt < nt && gx >= -2 && gx <= nx + 1 && gy >= -2 && gy <= ny + 1) {
+                    in = true;      // torus: the halo wraps
+                    node = (gt * ny + wrap_idx(gy, ny)) * nx + wrap_idx(gx, nx);
+                }
                 cp_v4<double>(reinterpret_cast<V4<double>*>(&S.p[st][e]), xb + (size_t)node * RW, in);
             }
             const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
@@ -230,12 +234,14 @@ __global__ void __launch_bounds__(256) k_resid_df(const LevelView<double> L, con
             const int e = tid + 256 * k;
             if (KS * 256 > SN && e >= SN) break;
             const int rx = tx0 + s_dx[k], ry = ty0 + s_dy[k], rt = tt0 + s_dt[k];
-            const bool inrow = rx >= 0 && rx < nx && ry >= 0 && ry < ny && rt < nt;
+            const bool per = L.periodic != 0;     // torus: rows one past each end wrap, no Dirichlet rows
+            const bool inrow = per ? (rx >= -1 && rx <= nx && ry >= -1 && ry <= ny && rt < nt)
+                                   : (rx >= 0 && rx < nx && ry >= 0 && ry < ny && rt < nt);
             V4d sv = v4d_zero();
-            if (inrow && !is_dirichlet(rx, ry, nx, ny)) {
+            if (inrow && (per || !is_dirichlet(rx, ry, nx, ny))) {
                 const bool first = HT > 0 && nt > 1 && rt == 0;
-                const bool xl = rx == 1, xr = rx == nx - 2;
-                const bool yl = HY > 0 && ry == 1, yr = HY > 0 && ry == ny - 2;
+                const bool xl = !per && rx == 1, xr = !per && rx == nx - 2;
+                const bool yl = !per && HY > 0 && ry == 1, yr = !per && HY > 0 && ry == ny - 2;
 #pragma unroll
                 for (int o = 0; o < NTAP; ++o) {
                     if (!tap_used(o)) continue;
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(256) k_resid_df(const LevelView<double> L, con
         const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
         if (gx < nx && gy < ny && gt < nt) {
             V4d q = v4d_zero();
-            if (is_dirichlet(gx, gy, nx, ny)) {
+            if (!L.periodic && is_dirichlet(gx, gy, nx, ny)) {
                 q = v4d_fma(eps2, sp[pbase], q);
             } else {
 #pragma unroll

@@ -94,8 +94,9 @@ int geometry_of(const gmrf_prior_desc& d) {
 }
 
 static void set_spacing(const gmrf_prior_desc& d, Level& L) {
-    L.hx = (d.hi[0] - d.lo[0]) / (L.nx - 1);
-    L.hy = L.ny > 1 ? (d.hi[1] - d.lo[1]) / (L.ny - 1) : 0.0;
+    // a torus of n nodes per axis has n intervals
+    L.hx = (d.hi[0] - d.lo[0]) / (L.periodic ? L.nx : L.nx - 1);
+    L.hy = L.ny > 1 ? (d.hi[1] - d.lo[1]) / (L.periodic ? L.ny : L.ny - 1) : 0.0;
     L.dt = L.nt > 1 ? (d.hi[2] - d.lo[2]) / (L.nt - 1) : 0.0;
     L.N = (long long)L.nx * L.ny * L.nt;
     L.tiles_x = (L.nx + geo_tx(L.geo) - 1) / geo_tx(L.geo);
@@ -107,14 +108,41 @@ static void set_spacing(const gmrf_prior_desc& d, Level& L) {
 // while a level has more than kCoarseMax nodes; an axis stops at 5 nodes.
 static const long long kCoarseMax = 600;
 
+// Periodic (x, y) torus: both axes halve together while both are even and at
+// least 8 (the transfers are then the P1 / bilinear interpolation of the
+// coarse torus and its transpose); the coarsest level may hold up to
+// kCoarseMaxPeriodic nodes.
+static const long long kCoarseMaxPeriodic = 1024;
+
 void build_hierarchy(const gmrf_prior_desc& d, std::vector<Level>& levels) {
     levels.clear();
     Level L;
     L.geo = geometry_of(d);
+    L.periodic = d.bc == GMRF_BC_PERIODIC ? 1 : 0;
     L.nx = d.nx; L.ny = d.ny; L.nt = d.nt;
+    if (L.periodic) { L.nx = d.nx - 1; L.ny = d.ny - 1; }   // the nodes on x = hi, y = hi are mirrors
     set_spacing(d, L);
     level_coefficients(d, L);
     levels.push_back(L);
+    if (L.periodic) {
+        while (levels.back().N > kCoarseMax) {
+            Level& f = levels.back();
+            if (f.nx % 2 != 0 || f.ny % 2 != 0 || f.nx < 8 || f.ny < 8) break;
+            Level c = f;
+            c.nx = f.nx / 2;
+            c.ny = f.ny / 2;
+            f.coarsen[0] = f.coarsen[1] = true;
+            f.coarsen[2] = false;
+            c.coarsen[0] = c.coarsen[1] = c.coarsen[2] = false;
+            set_spacing(d, c);
+            level_coefficients(d, c);
+            levels.push_back(c);
+        }
+        if (levels.back().N > kCoarseMaxPeriodic)
+            throw Error(GMRF_E_INVALID, "periodic grid: nx - 1 and ny - 1 must halve (even, >= 8) down to at most " +
+                                            std::to_string(kCoarseMaxPeriodic) + " coarsest nodes");
+        return;
+    }
     const bool ax[3] = {true, L.geo != GEO_XT, L.geo != GEO_XY};
     while (true) {
         Level& f = levels.back();
@@ -148,6 +176,15 @@ static void cell1d(double v, double lo, double hi, int n, int& i, double& w) {
     w = (v - (lo + i * h)) / h;
 }
 
+// the same on a torus of n nodes (n intervals): the cell's right node is
+// (i + 1) mod n
+static void cell1d_torus(double v, double lo, double hi, int n, int& i, double& w) {
+    const double h = (hi - lo) / n;
+    double f = std::floor((v - lo) / h);
+    i = (int)std::min(std::max(f, 0.0), (double)(n - 1));
+    w = (v - (lo + i * h)) / h;
+}
+
 // P1 barycentric weights in space (lower triangle (i,j),(i+1,j),(i+1,j+1)
 // when xi >= eta, upper (i,j),(i+1,j+1),(i,j+1) otherwise) times linear
 // weights in time.
@@ -172,8 +209,13 @@ static void point_row(const gmrf_prior_desc& d, const Level& L, const double* c,
     } else {
         int i, j, k = 0;
         double xi, eta, wt = 0.0;
-        cell1d(c[0], d.lo[0], d.hi[0], L.nx, i, xi);
-        cell1d(c[1], d.lo[1], d.hi[1], L.ny, j, eta);
+        if (L.periodic) {
+            cell1d_torus(c[0], d.lo[0], d.hi[0], L.nx, i, xi);
+            cell1d_torus(c[1], d.lo[1], d.hi[1], L.ny, j, eta);
+        } else {
+            cell1d(c[0], d.lo[0], d.hi[0], L.nx, i, xi);
+            cell1d(c[1], d.lo[1], d.hi[1], L.ny, j, eta);
+        }
         int vx[3], vy[3];
         double w[3];
         if (xi >= eta) {
@@ -185,6 +227,11 @@ static void point_row(const gmrf_prior_desc& d, const Level& L, const double* c,
             vx[1] = i + 1; vy[1] = j + 1; w[1] = xi;
             vx[2] = i; vy[2] = j + 1; w[2] = eta - xi;
         }
+        if (L.periodic)      // a node on x = hi or y = hi is its mirror (App. B, N_k = 1)
+            for (int a = 0; a < 3; ++a) {
+                if (vx[a] == L.nx) vx[a] = 0;
+                if (vy[a] == L.ny) vy[a] = 0;
+            }
         if (L.geo == GEO_XYT) cell1d(c[2], d.lo[2], d.hi[2], L.nt, k, wt);
         for (int b = 0; b < (L.geo == GEO_XYT ? 2 : 1); ++b) {
             const double ft = L.geo == GEO_XYT ? (b ? wt : 1 - wt) : 1.0;
@@ -292,7 +339,14 @@ void build_obs_stencil(Level& L) {
             std::vector<double>& c = C[o.node[a]];
             if (c.empty()) c.assign((size_t)OC, 0.0);
             for (int b = 0; b < o.nn; ++b) {
-                const int dx = o.ox[b] - o.ox[a], dy = o.oy[b] - o.oy[a], dt = o.ot[b] - o.ot[a];
+                int dx = o.ox[b] - o.ox[a], dy = o.oy[b] - o.oy[a];
+                const int dt = o.ot[b] - o.ot[a];
+                if (L.periodic) {      // neighbours across the seam of the torus
+                    if (dx > 1) dx -= L.nx;
+                    if (dx < -1) dx += L.nx;
+                    if (dy > 1) dy -= L.ny;
+                    if (dy < -1) dy += L.ny;
+                }
                 int idx;
                 if (L.geo == GEO_XY) idx = (dy + 1) * 3 + (dx + 1);
                 else if (L.geo == GEO_XT) idx = (dt + 1) * 3 + (dx + 1);
@@ -353,6 +407,29 @@ void build_obs_stencil(Level& L) {
 
 void build_transfer(Level& f, const Level& c) {
     const int nf[3] = {f.nx, f.ny, f.nt}, ncs[3] = {c.nx, c.ny, c.nt};
+    if (f.periodic) {
+        // torus n -> n / 2: fine i lies at coarse i / 2, between coarse
+        // j = i / 2 and (j + 1) mod m with weight w = (i mod 2) / 2 of the
+        // second (the kernels wrap j + 1); the restriction of periodic levels
+        // gathers its fine nodes directly, so it needs no range tables
+        for (int a = 0; a < 2; ++a) {
+            const int n = nf[a];
+            std::vector<int32_t> pj((size_t)n), zero((size_t)ncs[a], 0);
+            std::vector<float> pw((size_t)n);
+            std::vector<double> pwd((size_t)n);
+            for (int i = 0; i < n; ++i) {
+                pj[(size_t)i] = i / 2;
+                pwd[(size_t)i] = 0.5 * (i % 2);
+                pw[(size_t)i] = (float)pwd[(size_t)i];
+            }
+            dev_upload(&f.d_pj[a], pj);
+            dev_upload(&f.d_pw[a], pw);
+            dev_upload(&f.d_pwd[a], pwd);
+            dev_upload(&f.d_rs[a], zero);
+            dev_upload(&f.d_rc[a], zero);
+        }
+        return;
+    }
     for (int a = 0; a < 3; ++a) {
         if (!f.coarsen[a]) continue;
         const int n = nf[a], m = ncs[a];
@@ -418,7 +495,9 @@ static void coll_coef(const Colloc& c, const double* mu, int nx, int x, int t, d
 std::vector<double> dense_operator(const Level& L, const double* mu) {
     const long long n = L.N;
     std::vector<double> Q((size_t)(n * n), 0.0);
-    auto dir = [&](int x, int y) { return x == 0 || x == L.nx - 1 || (L.ny > 1 && (y == 0 || y == L.ny - 1)); };
+    auto dir = [&](int x, int y) {
+        return !L.periodic && (x == 0 || x == L.nx - 1 || (L.ny > 1 && (y == 0 || y == L.ny - 1)));
+    };
     std::vector<std::pair<long long, double>> row;
     for (long long r = 0; r < n; ++r) {
         const int x = (int)(r % L.nx);
@@ -432,7 +511,12 @@ std::vector<double> dense_operator(const Level& L, const double* mu) {
             for (int o = 0; o < NTAP; ++o) {
                 const double c = L.cd[cls][o];
                 if (c == 0.0) continue;
-                const int xx = x + tap_dx(o), yy = y + tap_dy(o), tt = t + tap_dt(o);
+                int xx = x + tap_dx(o), yy = y + tap_dy(o);
+                const int tt = t + tap_dt(o);
+                if (L.periodic) {
+                    xx = (xx + L.nx) % L.nx;
+                    yy = (yy + L.ny) % L.ny;
+                }
                 if (xx < 0 || xx >= L.nx || yy < 0 || yy >= L.ny || tt < 0 || tt >= L.nt) continue;
                 if (dir(xx, yy)) continue;
                 row.push_back({((long long)tt * L.ny + yy) * L.nx + xx, c});

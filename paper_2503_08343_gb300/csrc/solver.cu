@@ -307,7 +307,10 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
     const T* src = R;
     bool use_t1 = true;
     const bool plane = L.coarsen[0] && L.coarsen[1];
-    if (plane) {
+    if (L.periodic) {                // torus levels halve x and y together
+        launch_restrict_torus<T>(src, (T*)V.b[l + 1], L, C, P.transfer_p1, nblk, s);
+        last = -2;
+    } else if (plane) {
         T* dst = last == 1 ? (T*)V.b[l + 1] : (T*)V.t1[l];
         use_t1 = false;
         const int32_t* const rs[2] = {L.d_rs[0], L.d_rs[1]};
@@ -320,7 +323,7 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
         dims[1] = cdims[1];
         src = dst;
     }
-    for (int ax = plane ? 2 : 0; ax < 3; ++ax) {
+    for (int ax = plane ? 2 : 0; ax < 3 && last != -2; ++ax) {
         if (!L.coarsen[ax]) continue;
         T* dst = ax == last ? (T*)V.b[l + 1] : (use_t1 ? (T*)V.t1[l] : (T*)V.t2[l]);
         use_t1 = !use_t1;

@@ -130,7 +130,7 @@ constexpr int kMbarSpinCap = 1 << 22;
 // up without polling); a test hook
 __device__ int g_stencil_wait_cap = 0;
 
-template <int GEO, typename T, int MODE, int COL, int NS, int KB>
+template <int GEO, typename T, int MODE, int COL, int NS, int KB, int PER>
 __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nunits, const __grid_constant__ StencilMaps maps) {
     using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
     constexpr int TX = SM::TX, TY = SM::TY, TT = SM::TT, HY = SM::HY, HT = SM::HT;
@@ -152,6 +152,11 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     const LevelView<T>& L = A.L;
     const int nx = L.nx, ny = L.ny, nt = L.nt;
     const int N = (int)L.N;
+    // a periodic level has no Dirichlet rows (App. B, N_k = 1) and its rows
+    // extend one node past each end of the torus (rows of the wrapped halo)
+    constexpr bool per = PER != 0;
+    const int rlx = per ? -1 : 0, rhx = per ? nx + 1 : nx, rly = per ? -1 : 0, rhy = per ? ny + 1 : ny;
+    auto dirich = [&](int x, int y) { return !per && is_dirichlet(x, y, nx, ny); };
     const int nblk = A.nblk;
     const int ntiles = L.tiles_x * L.tiles_y * L.tiles_t;
     const int tid = threadIdx.x;
@@ -281,6 +286,31 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         if (abort_unit) break;
         issue(ahead, st == 0 ? NS - 1 : st - 1, done + NS - 1 < count);
         unit_next(ahead, tiles_x, tiles_y, tiles_t);
+        if (GEO == GEO_XY && PER) {
+            // torus: the tensor-map copy filled the halo past the grid with
+            // zeros; the halo nodes within two of the torus take their
+            // wrapped values (a tile at the seam only)
+            const int ex0 = cur.tx * TX, ey0 = cur.ty * TY;
+            if (ex0 < 2 || ex0 + TX + 2 > nx || ey0 < HY || ey0 + TY + HY > ny) {
+                const T* src = MODE == M_CHEB0 ? A.b : A.x;
+#pragma unroll
+                for (int k = 0; k < KP; ++k) {
+                    const int e = tid + 256 * k;
+                    if (KP * 256 > PN && e >= PN) break;
+                    const int gx = ex0 + p_dx[k], gy = ey0 + p_dy[k];
+                    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) continue;
+                    if (gx < -2 || gx > nx + 1 || gy < -2 || gy > ny + 1) continue;
+                    const int node = wrap_idx(gy, ny) * nx + wrap_idx(gx, nx);
+#pragma unroll
+                    for (int j = 0; j < KB; ++j) {
+                        const int blk = cur.grp * KB + j;
+                        if (blk < nblk) S.p[st][e][j] = v4load(src + ((size_t)blk * N + node) * RW);
+                    }
+                    if (MODE == M_CHEB0) S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? e : 0] = A.dinv[node];
+                }
+                if (MODE != M_CHEB0) __syncthreads();   // the in-place step below has its own barrier
+            }
+        }
         if (MODE == M_CHEB0) {      // staged b -> x1 = c0 D^-1 b in place
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
@@ -305,17 +335,17 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             const int e = tid + 256 * k;
             if (KS * 256 > SN && e >= SN) break;
             const int rx = tx0 + s_dx[k], ry = ty0 + s_dy[k], rt = tt0 + s_dt[k];
-            const bool inrow = rx >= 0 && rx < nx && ry >= 0 && ry < ny && rt < nt;
+            const bool inrow = rx >= rlx && rx < rhx && ry >= rly && ry < rhy && rt < nt;
             const int base = s_base[k];
             V4<T> sv[KB];
 #pragma unroll
             for (int j = 0; j < KB; ++j) sv[j] = v4zero<T>();
-            if (inrow && !is_dirichlet(rx, ry, nx, ny)) {
+            if (inrow && !dirich(rx, ry)) {
                 const bool first = HT > 0 && nt > 1 && rt == 0;
                 // a tap of a non-Dirichlet row reaches a Dirichlet column only
                 // from the second or second-last node of an axis
-                const bool xl = rx == 1, xr = rx == nx - 2;
-                const bool yl = HY > 0 && ry == 1, yr = HY > 0 && ry == ny - 2;
+                const bool xl = !per && rx == 1, xr = !per && rx == nx - 2;
+                const bool yl = !per && HY > 0 && ry == 1, yr = !per && HY > 0 && ry == ny - 2;
 #pragma unroll
                 for (int o = 0; o < NTAP; ++o) {
                     if (!tap_used(o)) continue;
@@ -393,7 +423,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
 #pragma unroll
         for (int j = 0; j < KB; ++j) { q[j] = v4zero<T>(); pown[j] = sp[pbase][j]; }
         if (own) {
-            if (is_dirichlet(gx, gy, nx, ny)) {
+            if (dirich(gx, gy)) {
 #pragma unroll
                 for (int j = 0; j < KB; ++j) q[j] = L.inv_eps2 * pown[j];
             } else {
@@ -568,19 +598,19 @@ constexpr int kMaxStencilGrid = 4096;
 static const char* mode_name(int m) {
     return m == M_APPLY ? "apply" : m == M_RESID ? "resid" : m == M_CHEB ? "cheb" : "cheb0";
 }
-template <int GEO, typename T, int MODE, int COL> static std::string stencil_name() {
-    return std::string("stencil<") + (GEO == GEO_XY ? "xy" : "xt") + (sizeof(T) == 8 ? ",f64," : ",f32,") + mode_name(MODE) +
-           ",col" + std::to_string(COL) + ">";
+template <int GEO, typename T, int MODE, int COL, int PER> static std::string stencil_name() {
+    return std::string("stencil<") + (GEO == GEO_XY ? (PER ? "torus" : "xy") : "xt") + (sizeof(T) == 8 ? ",f64," : ",f32,") +
+           mode_name(MODE) + ",col" + std::to_string(COL) + ">";
 }
 
 // dry: only the one-time set-up of this instantiation (function attributes,
 // occupancy query, which also loads the kernel's code), no launch
-template <int GEO, typename T, int MODE, int COL>
+template <int GEO, typename T, int MODE, int COL, int PER>
 static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false) {
     constexpr int NS = sizeof(T) == 8 ? 2 : GMRF_STENCIL_STAGES;
     constexpr int KB = sizeof(T) == 8 ? 1 : GMRF_STENCIL_KB;
     using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
-    auto kern = k_stencil<GEO, T, MODE, COL, NS, KB>;
+    auto kern = k_stencil<GEO, T, MODE, COL, NS, KB, PER>;
     static int attr_smem = 0;
     static int sms = 0, optin = 0;
     static std::map<size_t, int> per_sm;       // resident CTAs per SM by dynamic shared memory
@@ -638,7 +668,7 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false)
     int grid = grid_of(per);
     // launch shape: measured once per key when there is more than one unit per SM
     if (nunits > nsm && per > 1) {
-        const TuneKey key{stencil_name<GEO, T, MODE, COL>(), args.nblk, tune_units_bucket(nunits),
+        const TuneKey key{stencil_name<GEO, T, MODE, COL, PER>(), args.nblk, tune_units_bucket(nunits),
                           tune_obs_bucket(args.L.ostride, args.L.ocap > 0)};
         auto measure = [key, args, per, grid_of, run](cudaStream_t st) {
             TuneChoice c;
@@ -667,9 +697,10 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false)
 
 template <int GEO, typename T, int MODE>
 static int launch_geo_mode(const StencilArgs<T>& a, cudaStream_t s, bool dry) {
-    if (GEO == GEO_XT && a.L.col.kind == 1) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 1 : 0)>(a, s, dry);
-    if (GEO == GEO_XT && a.L.col.kind == 2) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0)>(a, s, dry);
-    return launch_one<GEO, T, MODE, 0>(a, s, dry);
+    if (GEO == GEO_XT && a.L.col.kind == 1) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 1 : 0), 0>(a, s, dry);
+    if (GEO == GEO_XT && a.L.col.kind == 2) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0), 0>(a, s, dry);
+    if (GEO == GEO_XY && a.L.periodic) return launch_one<GEO, T, MODE, 0, (GEO == GEO_XY ? 1 : 0)>(a, s, dry);
+    return launch_one<GEO, T, MODE, 0, 0>(a, s, dry);
 }
 
 template <typename T, int GEO>

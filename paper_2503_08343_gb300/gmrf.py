@@ -25,7 +25,8 @@ class PriorDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nt", C.c_int32),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("kappa", C.c_double), ("tau", C.c_double), ("nu", C.c_double),
-                ("cx", C.c_double), ("cy", C.c_double), ("kappa0", C.c_double), ("eps2", C.c_double)]
+                ("cx", C.c_double), ("cy", C.c_double), ("kappa0", C.c_double), ("eps2", C.c_double),
+                ("bc", C.c_int32)]
 
 
 class ObsDesc(C.Structure):
@@ -163,6 +164,7 @@ def prior_desc(prior: dict) -> PriorDesc:
         d.hi[i] = float(prior["hi"][i])
     for k in ("kappa", "tau", "nu", "cx", "cy", "kappa0", "eps2"):
         setattr(d, k, float(prior[k]))
+    d.bc = {"dirichlet": 0, "periodic": 1}[prior.get("bc", "dirichlet")]
     return d
 
 

@@ -42,6 +42,9 @@ CASES = {
                                   W.point_obs(W.prior_steady_advdiff2d(24, 8.0, nu=0.05, c=1.2), 80, 0.1,
                                               lambda z: np.sin(4 * z[:, 0]) * z[:, 1], seed=9)),
     "matern_24": lambda: W.c2_matern(n=24, m=60, seed=4, kappa=6.0),
+    "advdiff_torus_24": lambda: (W.periodic(W.prior_steady_advdiff2d(25, 7.0, nu=0.1, c=0.9)),
+                                 W.point_obs(W.periodic(W.prior_steady_advdiff2d(25, 7.0, nu=0.1, c=0.9)), 90, 0.1,
+                                             W.periodic_fourier(np.random.default_rng(3), 6, 3), seed=10)),
 }
 
 

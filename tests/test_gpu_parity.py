@@ -34,6 +34,12 @@ def _steady_case():
     return pr, ob
 
 
+def _torus_advdiff_case():
+    pr = W.periodic(W.prior_steady_advdiff2d(41, 8.0, nu=0.1, c=1.5))
+    ob = W.point_obs(pr, 250, 0.05, W.periodic_fourier(np.random.default_rng(8), 10, 4), seed=8)
+    return pr, ob
+
+
 CASES = {
     "matern64": lambda: W.c2_matern(n=64, m=400, seed=2),
     "matern45_ragged": lambda: W.c2_matern(n=45, m=150, seed=7, kappa=8.0),
@@ -41,6 +47,10 @@ CASES = {
     "st1d_37x21_ragged": lambda: W.c1_st1d(nx=37, nt=21, m=30, seed=5),
     "st2d_20x20x12": lambda: W.c5_st2d(n=20, nt=12, m=300, seed=5),
     "steady_advdiff40": _steady_case,
+    # periodic boundary (App. B, N_k = 1): 64^2 torus with two coarse levels,
+    # and a 40^2 torus with partial tiles at the seam
+    "matern_torus64": lambda: W.c2_matern_periodic(n=65, m=400, seed=3, kappa=10.0),
+    "advdiff_torus40": lambda: _torus_advdiff_case(),
 }
 
 

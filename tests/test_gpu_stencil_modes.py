@@ -23,7 +23,7 @@ gamma on the sum of absolute terms (each thread adds a few dozen FP32 terms
 before the FP64 reduction).
 
 Geometries: the tiled 2D and 1D space-time kernel, the marching 2D space-time
-kernel, ragged tiles, dense observations, linear and linearised Burgers
+kernel, ragged tiles, periodic tori (seam tiles), dense observations, linear and linearised Burgers
 collocation rows, the full-size 2D Matern workload (512^2, 10 000
 observations, 65 right-hand sides) and the first coarse multigrid level
 (rediscretised prior with the point data interpolated on the coarse mesh).
@@ -74,6 +74,11 @@ CASES = {
     "st1d_linear_collocation": (_linear_colloc, 3),
     "st2d_20x20x12_march": (lambda: W.c5_st2d(n=20, nt=12, m=300, seed=5), 3),
     "st2d_24x24x10_dense_obs": (lambda: W.c5_st2d(n=24, nt=10, m=5000, seed=3), 2),
+    # periodic boundary: tiles at the seam take their halo from the other side
+    "matern_torus40_ragged": (lambda: W.c2_matern_periodic(n=41, m=300, seed=9, kappa=8.0), 5),
+    "advdiff_torus32": (lambda: (W.periodic(W.prior_steady_advdiff2d(33, 6.0, nu=0.2, c=1.1)),
+                                 W.point_obs(W.periodic(W.prior_steady_advdiff2d(33, 6.0, nu=0.2, c=1.1)), 2000, 0.05,
+                                             W.periodic_fourier(np.random.default_rng(2), 6, 3), seed=4)), 3),
 }
 
 
@@ -142,6 +147,8 @@ def _check_modes(post_gpu, post_o, k, level, prec, seed, modes=(0, 1, 2, 3)):
 def _coarse_prior(pr, dims):
     pc = dict(pr)
     pc["n"] = tuple(int(v) for v in dims)
+    if pr.get("bc") == "periodic":      # level dims count torus nodes; the prior counts both ends
+        pc["n"] = (pc["n"][0] + 1, pc["n"][1] + 1, 1)
     return pc
 
 
@@ -155,7 +162,7 @@ def test_stencil_modes_match_the_oracle_operator(name, prec):
 
 
 @pytest.mark.parametrize("name", ["matern45_ragged", "steady_advdiff40", "st1d_37x21_ragged",
-                                  "st2d_20x20x12_march", "st2d_24x24x10_dense_obs"])
+                                  "st2d_20x20x12_march", "st2d_24x24x10_dense_obs", "matern_torus40_ragged"])
 def test_stencil_modes_on_the_first_coarse_level(name):
     # the coarse operator is the rediscretised prior with the same point data
     # interpolated on the coarse mesh

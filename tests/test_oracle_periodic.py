@@ -2,16 +2,8 @@
 forms that do not go through its element loops.
 
 On the torus every operator of the structured P1 mesh is circulant, so it is
-diagonalised by the 2D DFT.  With h the mesh width, the lumped mass is h^2,
-the P1 stiffness is the 5-point stencil (4; -1 at the four axis neighbours;
-the diagonal couplings vanish on right triangles), whose symbol is
-s(w) = 4 sin^2(w_x / 2) + 4 sin^2(w_y / 2), and the x-advection matrix
-int phi_i c d/dx phi_j collects, from the six triangles around a node, the
-antisymmetric stencil (c h / 6)[x+1: 2, x-1: -2, (+1,+1): 1, (-1,-1): -1,
-y+1: -1, y-1: 1], whose symbol is i (c h / 3)(2 sin w_x + sin(w_x + w_y)
-- sin w_y).  So B = tau h^-1 (kappa^2 h^2 + nu S + c Bx) has the symbol
-b(w) = (tau / h)(kappa^2 h^2 + nu s(w) + i (c h / 3)(...)), and
-Q = B^T B has |b(w)|^2.  Pins:
+diagonalised by the 2D DFT; tests/torus_symbol.py derives the symbols of the
+root B and of Q = B^T B by hand from the element integrals.  Pins:
 
 * B v and Q v equal their DFT forms (a row or column left out of the mirror
   condensation, a wrong mass or a wrong sign of the advection fails);
@@ -31,25 +23,11 @@ import pytest
 from oracle import fem, infer, linalg, observe
 from paper_2503_08343_gb300 import workloads as W
 
-
-def _symbol(pr):
-    m = pr["n"][0] - 1
-    h = (pr["hi"][0] - pr["lo"][0]) / m
-    w = 2.0 * np.pi * np.fft.fftfreq(m)           # frequencies along one axis
-    wy, wx = np.meshgrid(w, w, indexing="ij")     # field index j * m + i -> array [j, i]
-    s = 4.0 * np.sin(wx / 2) ** 2 + 4.0 * np.sin(wy / 2) ** 2
-    nu = 1.0 if pr["kind"] == "matern2d" else pr["nu"]
-    c = 0.0 if pr["kind"] == "matern2d" else pr["cx"]
-    adv = 1j * (c * h / 3.0) * (2.0 * np.sin(wx) + np.sin(wx + wy) - np.sin(wy))
-    return (pr["tau"] / h) * (pr["kappa"] ** 2 * h * h + nu * s + adv), m
+import torus_symbol as TS
 
 
-def _apply_symbol(sym, v, m):
-    """(C v) for the circulant C with (C v)_n = sum_d c_d v_(n+d), given its
-    symbol sum_d c_d exp(i w.d): in numpy's DFT convention a shift by +d
-    multiplies the transform by exp(+i w.d)."""
-    V = np.fft.fft2(v.reshape(m, m))
-    return np.real(np.fft.ifft2(sym * V)).ravel()
+_symbol = TS.symbol
+_apply_symbol = TS.apply_symbol
 
 
 PRIORS = {
@@ -106,12 +84,9 @@ def test_point_rows_wrap_to_the_mirror_nodes():
 
 def test_all_nodes_observed_posterior_mean_is_a_dft_solve():
     pr, ob = W.c2_matern_periodic(n=25, kappa=6.0, all_nodes=True, sigma=0.2, seed=4)
-    b, m = _symbol(pr)
     post = infer.condition(pr, ob)
     mu = infer.posterior_mean(post)
-    rinv = 1.0 / 0.2 ** 2
-    Y = np.fft.fft2((rinv * ob["y"]).reshape(m, m))
-    want = np.real(np.fft.ifft2(Y / (np.abs(b) ** 2 + rinv))).ravel()
+    want = TS.all_nodes_mean(pr, ob["y"], 0.2)
     assert np.max(np.abs(mu - want)) <= 1e-10 * np.max(np.abs(want))
 
 

@@ -5,7 +5,8 @@ log det Q by the oracle's banded Cholesky, 1/2 tr(Q^-1 dQ/dtheta) by its dense
 inverse and exact dQ/dtheta.  The library takes both from the diagonal blocks
 of the block lower-bidiagonal root (closed form for symmetric blocks, banded LU
 and the band of the inverse otherwise), so agreement at 1e-10 checks that
-reduction as well as the arithmetic.
+reduction as well as the arithmetic.  Periodic priors (a single circulant
+block on the torus) take the sums over the 2D DFT symbol.
 """
 import numpy as np
 import pytest
@@ -34,10 +35,13 @@ PRIORS = [
     W.prior_matern2d(11, 5.0),
     W.prior_steady_advdiff2d(10, 5.0, 0.05, 1.2),
     dict(W.prior_st2d(7, 4, 0.3, 0.0, 0.02, 6.0), hi=(1.0, 2.0, 0.5)),   # hx != hy
+    W.periodic(W.prior_matern2d(13, 5.0)),                  # torus: DFT symbol
+    W.periodic(W.prior_steady_advdiff2d(11, 5.0, 0.05, 1.2)),
+    dict(W.periodic(W.prior_steady_advdiff2d(9, 4.0, 0.1, 0.7)), hi=(1.0, 1.5, 0.0)),
 ]
 
 
-@pytest.mark.parametrize("prior", PRIORS, ids=lambda p: f"{p['kind']}_{p['n']}_{p['cx']}")
+@pytest.mark.parametrize("prior", PRIORS, ids=lambda p: f"{p['kind']}_{p['n']}_{p['cx']}_{p.get('bc', 'dir')}")
 def test_prior_logdet_and_traces_match_the_oracle(prior):
     ld, tr = gmrf.prior_logdet(prior)
     want = linalg.logdet(linalg.cholesky(fem.prior_precision(prior)))
