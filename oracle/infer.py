@@ -40,7 +40,9 @@ def condition(prior: dict, obs: dict, linearise_at: np.ndarray | None = None) ->
     Observation rows, in order: point data; initial-condition rows when
     obs["ic_sigma"] is set (values obs["ic_values"], default the Burgers
     initial condition -sin(pi x)); collocation rows when obs["colloc_sigma"]
-    is set.  Linear collocation (obs["colloc_c"] given) uses the constant
+    is set, in the form obs["colloc_form"]: "collocation" (default) or
+    "fem_cn" (Galerkin-tested Crank-Nicolson rows, observe.fem_cn_residual).
+    Linear collocation (obs["colloc_c"] given) uses the constant
     advection speed and right-hand side obs["colloc_f"]; Burgers collocation
     is linearised at `linearise_at` (Sec. 3.3: f(u) ~ f(u_k) + J (u - u_k),
     i.e. rows J with data J u_k - f(u_k)); without it the collocation rows
@@ -63,12 +65,12 @@ def condition(prior: dict, obs: dict, linearise_at: np.ndarray | None = None) ->
     if obs.get("colloc_sigma") is not None:
         nu = obs.get("burgers_nu", prior["nu"])
         if obs.get("colloc_c") is not None:
-            J = observe.burgers_jacobian(prior, np.zeros(Q.shape[0]), nu, advect=obs["colloc_c"])
+            J, _ = observe.pde_rows(prior, obs, np.zeros(Q.shape[0]), nu, advect=obs["colloc_c"])
             f = obs.get("colloc_f")
             yc = np.zeros(J.shape[0]) if f is None else np.asarray(f, dtype=np.float64)
         elif linearise_at is not None:
-            J = observe.burgers_jacobian(prior, linearise_at, nu)
-            yc = J @ linearise_at - observe.burgers_residual(prior, linearise_at, nu)
+            J, F = observe.pde_rows(prior, obs, linearise_at, nu)
+            yc = J @ linearise_at - F
         else:
             J = None
         if J is not None:
@@ -160,7 +162,7 @@ def neg_log_post(post_lin: Posterior, prior_Q: sp.csr_matrix, obs: dict, prior: 
         r = yic - u[:nx]
         val += 0.5 * float(np.sum(r * r)) / obs["ic_sigma"] ** 2
     if obs.get("colloc_sigma") is not None:
-        f = observe.burgers_residual(prior, u, obs.get("burgers_nu", prior["nu"]))
+        _, f = observe.pde_rows(prior, obs, u, obs.get("burgers_nu", prior["nu"]))
         val += 0.5 * float(np.sum(f * f)) / obs["colloc_sigma"] ** 2
     return val
 

@@ -15,12 +15,24 @@ Readings:
   (u_i^k - u_i^(k-1))/dt + a_i^k (u_(i+1)^k - u_(i-1)^k)/(2h)
   - nu (u_(i+1)^k - 2 u_i^k + u_(i-1)^k)/h^2, with a = c (linear proxy) or
   a = u (Burgers).
+* FEM observations (Sec. 3.1, A_ij = int <phi_i, D phi_j>, b_i = int <phi_i, f>)
+  with a Crank-Nicolson discretisation in time (Sec. 5, the Burgers comparison:
+  implicit-Euler prior, Crank-Nicolson FEM observations): at the same rows
+  (i, k) as the collocation rows, the spatial hat phi_i tests the P1
+  interpolant of each time level,
+  F_ik = int phi_i (u^k - u^(k-1))/dt + 1/2 [N_i(u^k) + N_i(u^(k-1))],
+  N_i(v) = int phi_i a v_x + nu int phi_i' v_x (the diffusion term integrated
+  by parts; phi_i vanishes at both ends of its support), with a = c or a = v
+  (Burgers).  The integrals are exact (consistent mass): three-point
+  Gauss-Legendre per element, exact for the cubic integrands here.
 * The observation rows are ordered: point data, then the initial-condition
   rows (every node at t = 0), then the collocation rows (t = 1..nt-1, then
   x = 1..nx-2).  Random draws for the observation part of a sample follow
   this order.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 import scipy.sparse as sp
@@ -161,3 +173,76 @@ def burgers_jacobian(prior: dict, u: np.ndarray, nu: float, advect=None) -> sp.c
     cols = np.concatenate([c for c, _ in entries])
     vals = np.concatenate([np.broadcast_to(v, (m,)) for _, v in entries])
     return sp.csr_matrix((vals, (rows, cols)), shape=(m, nx * nt))
+
+
+# ---------------------------------------------------------------------------
+# FEM (Galerkin-tested) Crank-Nicolson rows
+
+
+_GL_X = np.array([-math.sqrt(0.6), 0.0, math.sqrt(0.6)])
+_GL_W = np.array([5.0, 8.0, 5.0]) / 9.0
+
+
+def _fem_cn_row(xs, U, i, k, nu, dt, advect):
+    """Residual F_ik and its derivatives {(level, node): dF/du} for one row,
+    by Gauss-Legendre quadrature on the two elements of phi_i's support."""
+    F = 0.0
+    jac = {}
+    for (l, r) in ((i - 1, i), (i, i + 1)):
+        h = xs[r] - xs[l]
+        for xq, wq in zip(_GL_X, _GL_W):
+            x = xs[l] + 0.5 * h * (xq + 1.0)
+            w = 0.5 * h * wq
+            hat = {l: (xs[r] - x) / h, r: (x - xs[l]) / h}       # the two local hats
+            dhat = {l: -1.0 / h, r: 1.0 / h}
+            phi_i, dphi_i = hat[i], dhat[i]
+            vals, ders = {}, {}
+            for lev in (k, k - 1):
+                vals[lev] = hat[l] * U[lev, l] + hat[r] * U[lev, r]
+                ders[lev] = dhat[l] * U[lev, l] + dhat[r] * U[lev, r]
+            F += w * phi_i * (vals[k] - vals[k - 1]) / dt
+            for lev, sgn in ((k, 1.0), (k - 1, -1.0)):
+                a = vals[lev] if advect is None else advect
+                F += w * 0.5 * (phi_i * a * ders[lev] + nu * dphi_i * ders[lev])
+                for j in (l, r):
+                    da = hat[j] if advect is None else 0.0        # d a / d u_j (Burgers: a = v)
+                    d = sgn * phi_i * hat[j] / dt + 0.5 * (phi_i * (da * ders[lev] + a * dhat[j]) + nu * dphi_i * dhat[j])
+                    jac[(lev, j)] = jac.get((lev, j), 0.0) + w * d
+    return F, jac
+
+
+def fem_cn_residual(prior: dict, u: np.ndarray, nu: float, advect=None) -> np.ndarray:
+    """F_ik of the FEM Crank-Nicolson rows (see the module docstring) at the
+    collocation rows, for u_t + a u_x = nu u_xx with a = u (advect None) or
+    a = advect."""
+    nx, _, nt = prior["n"]
+    xs = fem.axis_nodes(prior["lo"][0], prior["hi"][0], nx)
+    _, _, dt = fem.grid_spacing(prior)
+    U = u.reshape(nt, nx)
+    i, k = colloc_rows(prior)
+    return np.array([_fem_cn_row(xs, U, int(a), int(b), nu, dt, advect)[0] for a, b in zip(i, k)])
+
+
+def fem_cn_jacobian(prior: dict, u: np.ndarray, nu: float, advect=None) -> sp.csr_matrix:
+    """dF/du of fem_cn_residual (Sec. 3.3, J^(k) of the FEM rows)."""
+    nx, _, nt = prior["n"]
+    xs = fem.axis_nodes(prior["lo"][0], prior["hi"][0], nx)
+    _, _, dt = fem.grid_spacing(prior)
+    U = u.reshape(nt, nx)
+    i, k = colloc_rows(prior)
+    rows, cols, vals = [], [], []
+    for r, (a, b) in enumerate(zip(i, k)):
+        _, jac = _fem_cn_row(xs, U, int(a), int(b), nu, dt, advect)
+        for (lev, j), v in jac.items():
+            rows.append(r)
+            cols.append(lev * nx + j)
+            vals.append(v)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(len(i), nx * nt))
+
+
+def pde_rows(prior: dict, obs: dict, u: np.ndarray, nu: float, advect=None):
+    """(J, f(u)) of the PDE observation rows in the form obs["colloc_form"]:
+    "collocation" (default; burgers_jacobian / burgers_residual) or "fem_cn"."""
+    if obs.get("colloc_form", "collocation") == "fem_cn":
+        return fem_cn_jacobian(prior, u, nu, advect), fem_cn_residual(prior, u, nu, advect)
+    return burgers_jacobian(prior, u, nu, advect), burgers_residual(prior, u, nu, advect)
