@@ -112,6 +112,13 @@ typedef struct gmrf_prior_desc {
  *    [nx * ny] (NULL: -sin(pi x)), noise ic_sigma.
  *  colloc: 1 = linear advection-diffusion residual with speed colloc_c and
  *    right-hand side colloc_f (NULL: 0) at interior nodes of levels k >= 1;
+ *    3, 4 = the same rows as 1, 2 in FEM form (Sec. 3.1, A_ij =
+ *    int phi_i D phi_j, exact integrals of the P1 interpolant, consistent
+ *    mass) with Crank-Nicolson in time (Sec. 5: FEM observations in
+ *    Crank-Nicolson form on an implicit-Euler prior): row (x, k) is
+ *    int phi_x (u^k - u^(k-1))/dt + 1/2 sum over levels k, k-1 of
+ *    (int phi_x a u_x + nu int phi_x' u_x), a = colloc_c (3) or a = u (4,
+ *    Burgers, linearised like 2); colloc_f gives int phi_x f per row (3).
  *    2 = Burgers residual (Sec. 3.3), linearised at the point given to
  *    gmrf_gauss_newton_step.  Diffusion colloc_nu, noise colloc_sigma.
  *    Defined for GMRF_ADVDIFF_ST_1D only. */

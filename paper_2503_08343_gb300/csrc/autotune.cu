@@ -159,7 +159,7 @@ TuneChoice tune_measure(const TuneKey& key, const std::vector<TuneChoice>& cands
     d << "{";
     for (size_t i = 0; i < cands.size(); ++i) {
         char t[32];
-        std::snprintf(t, sizeof(t), "%.5f", ms[i]);
+        std::snprintf(t, sizeof(t), "%.9g", ms[i]);
         d << (i ? ", " : "") << "\"" << cands[i].ctas_per_sm << "x" << cands[i].aux << "\": " << t;
     }
     d << "}";

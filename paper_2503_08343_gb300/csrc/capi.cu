@@ -220,6 +220,7 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
             L.d_obs = nullptr; L.d_tile_ptr = nullptr; L.d_tile_idx = nullptr;
             L.d_omap = nullptr; L.d_oent32 = nullptr; L.d_oent64 = nullptr;
             L.d_tsp32 = nullptr; L.d_tsp64 = nullptr;
+            L.d_tspc32 = nullptr; L.d_tspc64 = nullptr;
         }
         const int dimc = d.kind == GMRF_ADVDIFF_ST_2D ? 3 : 2;
         P.m = obs->m;
@@ -254,21 +255,44 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
         P.ncol = 0;
         if (obs->colloc) {
             require(d.kind == GMRF_ADVDIFF_ST_1D, "collocation rows need the 1D space-time prior");
-            require(obs->colloc == 1 || obs->colloc == 2, "colloc must be 0, 1 or 2");
+            require(obs->colloc >= 1 && obs->colloc <= 4, "colloc must be 0 .. 4");
             require(obs->colloc_sigma > 0, "colloc_sigma must be positive");
             P.ncol = (int64_t)(d.nx - 2) * (d.nt - 1);
             P.colloc_qeps = 1.0 / (obs->colloc_sigma * obs->colloc_sigma);
             P.colloc_nu = obs->colloc_nu;
             P.colloc_c = obs->colloc_c;
+            const bool fem_rows = obs->colloc >= 3;
+            const double hf = P.levels[0].hx;
             for (Level& L : P.levels) {
                 const double ncl = (double)(L.nx - 2) * (L.nt - 1);
-                L.col.kind = obs->colloc == 1 ? 1 : 0;    // Burgers rows enter once linearised
-                L.col.qeps = P.colloc_qeps * (double)P.ncol / ncl;
+                // Burgers rows (2, 4) enter once linearised
+                L.col.kind = (obs->colloc == 1 || obs->colloc == 3) ? obs->colloc : 0;
+                // coarse levels: the row-count ratio keeps J^T Q_eps J of the same size;
+                // FEM rows carry a factor h (int phi_i), which the ratio already covers
+                L.col.qeps = P.colloc_qeps * (double)P.ncol / ncl * (fem_rows ? (hf * hf) / (L.hx * L.hx) : 1.0);
                 L.col.inv_dt = 1.0 / L.dt;
                 L.col.inv_2h = 1.0 / (2.0 * L.hx);
                 L.col.nu_h2 = obs->colloc_nu / (L.hx * L.hx);
                 L.col.c = obs->colloc_c;
+                L.col.m6_dt = L.hx / (6.0 * L.dt);
+                L.col.nu_2h = obs->colloc_nu / (2.0 * L.hx);
                 L.col.row0 = (int32_t)(P.m + P.nic);
+            }
+            if (obs->colloc == 3) {
+                // b += J^T Q_eps f on the fine level (FEM rows: f = int phi_i f, given per row)
+                const Level& L = P.levels[0];
+                auto none = [](int, int) { return 0.0; };
+                for (int t = 1; t < L.nt; ++t)
+                    for (int x = 1; x < L.nx - 1; ++x) {
+                        const size_t r = (size_t)(t - 1) * (L.nx - 2) + (x - 1);
+                        const double v = L.col.qeps * (obs->colloc_f ? obs->colloc_f[r] : 0.0);
+                        double a[3], b[3];
+                        fem_cn_row(L.col, x, t, none, a, b);
+                        for (int e = 0; e < 3; ++e) {
+                            bstatic[(size_t)t * L.nx + x + e - 1] += a[e] * v;
+                            bstatic[(size_t)(t - 1) * L.nx + x + e - 1] += b[e] * v;
+                        }
+                    }
             }
             if (obs->colloc == 1) {
                 // b += J^T Q_eps f on the fine level
@@ -290,7 +314,7 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
         }
         P.nrows = P.m + P.nic + P.ncol;
         for (size_t l = 0; l < P.levels.size(); ++l) build_level_obs(d, P, coords, rinv, P.levels[l], l == 0);
-        if (obs->colloc == 2) {
+        if (obs->colloc == 2 || obs->colloc == 4) {
             for (Level& L : P.levels) {
                 L.d_mu32 = dev_alloc<float>((size_t)L.N);
                 L.d_mu64 = dev_alloc<double>((size_t)L.N);

@@ -1,4 +1,6 @@
-// Gauss-Newton for nonlinear collocation (Sec. 3.3): the Burgers residual
+// Gauss-Newton for nonlinear PDE observations (Sec. 3.3), collocation rows
+// (below) or FEM Crank-Nicolson rows (colloc = 4; see Colloc).  The Burgers
+// collocation residual
 //   f_r(u) = (u_r - u_{r-t})/dt + u_r (u_{r+x} - u_{r-x})/(2h) - nu (u_{r+x} - 2 u_r + u_{r-x})/h^2
 // at interior nodes of levels k >= 1 is linearised at u_k,
 //   f(u) ~ f(u_k) + J (u - u_k),  so the linearised data are J u_k - f(u_k) = u_r (u_{r+x} - u_{r-x})/(2h),
@@ -47,6 +49,33 @@ __global__ void k_gn_rhs(const LevelView<double> L, const double* __restrict__ u
     b[n] = bdata[n] + c.qeps * acc;
 }
 
+// FEM Crank-Nicolson Burgers rows: half the convection of row x on one
+// level, int phi_x v v_x / 2 = (v_(x+1) - v_(x-1))(v_(x+1) + v_x + v_(x-1)) / 12
+__device__ __forceinline__ double fem_half_conv(const double* lev, int x) {
+    return (lev[x + 1] - lev[x - 1]) * (lev[x + 1] + lev[x] + lev[x - 1]) * (1.0 / 12.0);
+}
+
+// b_J = J^T Q_eps (J u - f(u)) for the FEM Crank-Nicolson Burgers rows: the
+// convection is homogeneous of degree 2, so J u - f(u) of row (x, t) is the
+// sum of its two half convections
+__global__ void k_gn_rhs_fem(const LevelView<double> L, const double* __restrict__ u, const double* __restrict__ bdata,
+                             double* __restrict__ b) {
+    const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (n >= L.N) return;
+    const int nx = L.nx, nt = L.nt;
+    const int x = (int)(n % nx), t = (int)(n / nx);
+    auto mu_at = [&](int xx, int tt) { return u[(long long)tt * nx + xx]; };
+    int rxs[6], rts[6];
+    double cfs[6];
+    const int nr = fem_cn_column(L.col, nx, nt, x, t, mu_at, rxs, rts, cfs);
+    double acc = 0.0;
+    for (int k = 0; k < nr; ++k) {
+        const double* lk = u + (long long)rts[k] * nx;
+        acc += cfs[k] * (fem_half_conv(lk, rxs[k]) + fem_half_conv(lk - nx, rxs[k]));
+    }
+    b[n] = bdata[n] + L.col.qeps * acc;
+}
+
 // sum over collocation rows of f(v)^2 (FP64), per-CTA partials
 __global__ void k_colloc_misfit(const LevelView<double> L, double nu, const double* __restrict__ v, double* __restrict__ part) {
     const int nx = L.nx, nt = L.nt;
@@ -57,8 +86,18 @@ __global__ void k_colloc_misfit(const LevelView<double> L, double nu, const doub
         const int x = 1 + (int)(r % (nx - 2)), t = 1 + (int)(r / (nx - 2));
         const long long i = (long long)t * nx + x;
         const double h = 0.5 / L.col.inv_2h;
-        const double f = (v[i] - v[i - nx]) * L.col.inv_dt + v[i] * (v[i + 1] - v[i - 1]) * L.col.inv_2h -
-                         nu * (v[i + 1] - 2.0 * v[i] + v[i - 1]) / (h * h);
+        double f;
+        if (L.col.kind == 4) {
+            // int phi_x (v^t - v^(t-1))/dt + 1/2 sum over both levels of (convection + nu stiffness)
+            const double* a = v + (long long)t * nx;
+            const double* p = a - nx;
+            const double m = L.col.m6_dt, k = L.col.nu_2h;
+            f = m * ((a[x - 1] - p[x - 1]) + 4.0 * (a[x] - p[x]) + (a[x + 1] - p[x + 1])) + fem_half_conv(a, x) +
+                fem_half_conv(p, x) + k * (2.0 * a[x] - a[x - 1] - a[x + 1]) + k * (2.0 * p[x] - p[x - 1] - p[x + 1]);
+        } else {
+            f = (v[i] - v[i - nx]) * L.col.inv_dt + v[i] * (v[i + 1] - v[i - 1]) * L.col.inv_2h -
+                nu * (v[i + 1] - 2.0 * v[i] + v[i - 1]) / (h * h);
+        }
         s = f * f;
     }
     double sv[4] = {s, 0.0, 0.0, 0.0};
@@ -159,7 +198,7 @@ void linearise(Posterior& P, const double* u, cudaStream_t s) {
         GCK(cudaMemcpyAsync(L.d_mu64, ul.data(), sizeof(double) * ul.size(), cudaMemcpyHostToDevice, s));
         GCK(cudaMemcpyAsync(L.d_mu32, u32.data(), sizeof(float) * u32.size(), cudaMemcpyHostToDevice, s));
         GCK(cudaStreamSynchronize(s));
-        L.col.kind = 2;
+        L.col.kind = P.colloc_kind;     // 2: collocation, 4: FEM Crank-Nicolson rows
     }
     for (auto& kv : P.ws) {       // captured graphs hold the old coefficients by value
         for (Workspace::Vecs* V : {&kv.second->v32, &kv.second->v64}) {
@@ -179,7 +218,8 @@ void linearise(Posterior& P, const double* u, cudaStream_t s) {
     // at a Gauss-Newton fixed point H^-1 b_lin = u, so the mean slot of later
     // sampling calls is the Laplace mean
     if (!P.d_blin) P.d_blin = dev_alloc<double>((size_t)F.N);
-    k_gn_rhs<<<blocks_of(F.N), 256, 0, s>>>(F.view<double>(), u, P.d_bdata, P.d_blin);
+    if (P.colloc_kind == 4) k_gn_rhs_fem<<<blocks_of(F.N), 256, 0, s>>>(F.view<double>(), u, P.d_bdata, P.d_blin);
+    else k_gn_rhs<<<blocks_of(F.N), 256, 0, s>>>(F.view<double>(), u, P.d_bdata, P.d_blin);
     note_launch();
     P.linearised = true;
 }
@@ -226,7 +266,8 @@ static double dot1(Workspace& W, const double* a, const double* b, long long N, 
 
 GnResult gauss_newton_step(Posterior& P, double* u_io, double* d_io, bool u_dev, bool d_dev, const gmrf_solve_opts& o,
                            cudaStream_t s) {
-    if (P.colloc_kind != 2) throw Error(GMRF_E_INVALID, "gauss_newton_step needs Burgers collocation (colloc = 2)");
+    if (P.colloc_kind != 2 && P.colloc_kind != 4)
+        throw Error(GMRF_E_INVALID, "gauss_newton_step needs Burgers rows (colloc = 2 or 4)");
     Level& F = P.levels[0];
     const long long N = F.N;
     Workspace& W = workspace(P, 1);

@@ -34,12 +34,86 @@ struct ObsRow {
 //   centre 1/dt + da + 2 nu/h^2, x-1: -a/(2h) - nu/h^2, x+1: a/(2h) - nu/h^2,
 //   t-1: -1/dt, with a = c (linear) or a = u_k(x) and da = (u_k(x+1) - u_k(x-1))/(2h)
 //   (Burgers, linearised at u_k).
+//
+// FEM rows with Crank-Nicolson in time (kinds 3 and 4; Sec. 3.1 FEM
+// observations, A_ij = int phi_i D phi_j, exact integrals of the P1
+// interpolant): row (x, k) has taps x-1, x, x+1 on level k (a) and on level
+// k-1 (b),
+//   a_e =  (h/6dt) [1 4 1]_e + (nu/2h) [-1 2 -1]_e + d_e(level k),
+//   b_e = -(h/6dt) [1 4 1]_e + (nu/2h) [-1 2 -1]_e + d_e(level k-1),
+// half the convection derivative d: linear c/4 [-1 0 1]; Burgers, from
+// int phi_i v v_x = (v_(x+1) - v_(x-1))(v_(x+1) + v_x + v_(x-1))/6 linearised
+// at u_k: [-(2u_(x-1) + u_x), u_(x+1) - u_(x-1), 2u_(x+1) + u_x] / 12.
 struct Colloc {
-    int kind;          // 0 none, 1 linear, 2 Burgers
+    int kind;          // 0 none, 1 linear, 2 Burgers, 3 linear FEM Crank-Nicolson, 4 Burgers FEM Crank-Nicolson
     double qeps;       // 1 / sigma^2, scaled on coarse levels by the row-count ratio
     double inv_dt, inv_2h, nu_h2, c;
+    double m6_dt;      // h / (6 dt)   (FEM rows)
+    double nu_2h;      // nu / (2 h)   (FEM rows)
     int32_t row0;      // global observation row of the first collocation row
 };
+
+// half convection derivative d_e of an FEM Crank-Nicolson row centred at x,
+// from the linearisation point at x-1, x, x+1 on one level
+template <typename T>
+__host__ __device__ __forceinline__ void fem_cn_half_conv(const Colloc& c, T ul, T u0, T ur, T d[3]) {
+    if (c.kind == 3) {
+        const T q = (T)(0.25 * c.c);
+        d[0] = -q; d[1] = T(0); d[2] = q;
+    } else {
+        const T k = T(1) / T(12);
+        d[0] = -(T(2) * ul + u0) * k;
+        d[1] = (ur - ul) * k;
+        d[2] = (T(2) * ur + u0) * k;
+    }
+}
+
+// the FEM Crank-Nicolson rows touching node (x, t) and the coefficient of
+// the node in each: rows (x+d, t) by their tap -d on their own level, rows
+// (x+d, t+1) by their tap -d on the level before; mu(x, t) reads the
+// linearisation point (kind 4).  Returns the number of rows (<= 6).
+template <typename MU>
+__host__ __device__ inline int fem_cn_column(const Colloc& c, int nx, int nt, int x, int t, MU mu, int rx[6], int rt[6],
+                                             double cf[6]);
+
+// the fixed part of tap e: sign * (h/6dt) [1 4 1]_e + (nu/2h) [-1 2 -1]_e
+// (sign +1 on the row's own level, -1 on the level before)
+template <typename T>
+__host__ __device__ __forceinline__ T fem_cn_fixed(const Colloc& c, int e, T sign) {
+    const T m = (T)c.m6_dt * (e == 1 ? T(4) : T(1));
+    const T k = (T)c.nu_2h * (e == 1 ? T(2) : T(-1));
+    return sign * m + k;
+}
+
+template <typename MU>
+__host__ __device__ inline int fem_cn_column(const Colloc& c, int nx, int nt, int x, int t, MU mu, int rx[6], int rt[6],
+                                             double cf[6]) {
+    int n = 0;
+    for (int d = -1; d <= 1; ++d) {
+        const int r = x + d;
+        if (r < 1 || r > nx - 2) continue;
+        double hd[3];
+        fem_cn_half_conv<double>(c, c.kind == 4 ? mu(r - 1, t) : 0.0, c.kind == 4 ? mu(r, t) : 0.0,
+                                 c.kind == 4 ? mu(r + 1, t) : 0.0, hd);
+        if (t >= 1) { rx[n] = r; rt[n] = t; cf[n] = fem_cn_fixed<double>(c, 1 - d, 1.0) + hd[1 - d]; ++n; }
+        if (t + 1 <= nt - 1) { rx[n] = r; rt[n] = t + 1; cf[n] = fem_cn_fixed<double>(c, 1 - d, -1.0) + hd[1 - d]; ++n; }
+    }
+    return n;
+}
+
+// the six taps of FEM Crank-Nicolson row (x, t): a on level t at x-1, x, x+1,
+// b on level t-1
+template <typename MU>
+__host__ __device__ inline void fem_cn_row(const Colloc& c, int x, int t, MU mu, double a[3], double b[3]) {
+    double dk[3], dp[3];
+    const bool bu = c.kind == 4;
+    fem_cn_half_conv<double>(c, bu ? mu(x - 1, t) : 0.0, bu ? mu(x, t) : 0.0, bu ? mu(x + 1, t) : 0.0, dk);
+    fem_cn_half_conv<double>(c, bu ? mu(x - 1, t - 1) : 0.0, bu ? mu(x, t - 1) : 0.0, bu ? mu(x + 1, t - 1) : 0.0, dp);
+    for (int e = 0; e < 3; ++e) {
+        a[e] = fem_cn_fixed<double>(c, e, 1.0) + dk[e];
+        b[e] = fem_cn_fixed<double>(c, e, -1.0) + dp[e];
+    }
+}
 
 // Everything a stencil kernel needs about one level, passed by value.
 template <typename T>
@@ -111,6 +185,8 @@ struct Level {
     // time-stepping preconditioner factors (collocation levels), device
     float* d_tsp32 = nullptr;
     double* d_tsp64 = nullptr;
+    float* d_tspc32 = nullptr;     // FEM Crank-Nicolson rows: coupling coefficients
+    double* d_tspc64 = nullptr;
     // coarsest level: dense inverse of Q_u|y (device, row-major)
     float* d_dense32 = nullptr;
     double* d_dense64 = nullptr;

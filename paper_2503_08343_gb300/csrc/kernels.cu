@@ -808,7 +808,23 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
                 q = fma4(c, sz[lt - tap_dt(o)][ly + HYS - tap_dy(o)][lx + 1 - tap_dx(o)], q);
             }
         }
-        if (L.col.kind != 0) {
+        if (L.col.kind >= 3) {
+            // FEM Crank-Nicolson rows: J^T Q_eps^1/2 z3 over the (up to six) rows
+            // touching the node, draws as for the collocation rows below
+            const double sq_eps = sqrt(L.col.qeps);
+            auto mu_at = [&](int x, int t) -> double { return L.mu ? L.mu[(long long)t * nx + x] : 0.0; };
+            int rxs[6], rts[6];
+            double cfs[6];
+            const int nr = fem_cn_column(L.col, nx, nt, gx, gt, mu_at, rxs, rts, cfs);
+            for (int k = 0; k < nr; ++k) {
+                const uint64_t orow = (uint64_t)L.col.row0 + (uint64_t)(rts[k] - 1) * (nx - 2) + (rxs[k] - 1);
+                double v[4];
+                const double* zr = z2 + ((size_t)blk * rows + orow) * RW;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) v[cc] = (sid[cc] >= 0 && z2 != nullptr) ? zr[cc] : 0.0;
+                q = fma4(cfs[k] * sq_eps, V4<double>{v[0], v[1], v[2], v[3]}, q);
+            }
+        } else if (L.col.kind != 0) {
             // J^T Q_eps^1/2 z3: rows (x, t), (x-1, t), (x+1, t), (x, t+1) with draws on
             // stream 1 at row index row0 + (t - 1)(nx - 2) + (x - 1)
             const double sq_eps = sqrt(L.col.qeps);
@@ -1027,7 +1043,15 @@ __global__ void k_diag(const LevelView<T> L, double* __restrict__ diag) {
             d += c * c;
         }
     }
-    if (L.col.kind != 0) {
+    if (L.col.kind >= 3) {
+        auto mu_at = [&](int xx, int tt) -> double { return L.mu ? (double)L.mu[(long long)tt * nx + xx] : 0.0; };
+        int rxs[6], rts[6];
+        double cfs[6];
+        const int nr = fem_cn_column(L.col, nx, nt, x, t, mu_at, rxs, rts, cfs);
+        double acc = 0.0;
+        for (int k = 0; k < nr; ++k) acc += cfs[k] * cfs[k];
+        d += L.col.qeps * acc;
+    } else if (L.col.kind != 0) {
         auto mu_at = [&](int xx, int tt) -> double { return L.mu ? (double)L.mu[(long long)tt * nx + xx] : 0.0; };
         auto coef = [&](int rx, int rt, int which) -> double {
             double a, da;

@@ -528,7 +528,24 @@ std::vector<double> dense_operator(const Level& L, const double* mu) {
     for (const ObsRow& o : L.h_obs)
         for (int a = 0; a < o.nn; ++a)
             for (int b = 0; b < o.nn; ++b) Q[(size_t)o.node[a] * n + o.node[b]] += o.rinv * o.wd[a] * o.wd[b];
-    if (L.col.kind != 0) {
+    if (L.col.kind >= 3) {         // FEM Crank-Nicolson rows: six taps each
+        auto mu_at = [&](int xx, int tt) { return mu ? mu[(size_t)tt * L.nx + xx] : 0.0; };
+        for (int t = 1; t < L.nt; ++t)
+            for (int x = 1; x < L.nx - 1; ++x) {
+                double a[3], b[3];
+                fem_cn_row(L.col, x, t, mu_at, a, b);
+                long long nd[6];
+                double cv[6];
+                for (int e = 0; e < 3; ++e) {
+                    nd[e] = (long long)t * L.nx + x + e - 1;
+                    cv[e] = a[e];
+                    nd[3 + e] = (long long)(t - 1) * L.nx + x + e - 1;
+                    cv[3 + e] = b[e];
+                }
+                for (int i = 0; i < 6; ++i)
+                    for (int j = 0; j < 6; ++j) Q[(size_t)(nd[i] * n + nd[j])] += L.col.qeps * cv[i] * cv[j];
+            }
+    } else if (L.col.kind != 0) {
         for (int t = 1; t < L.nt; ++t)
             for (int x = 1; x < L.nx - 1; ++x) {
                 double cC, cL, cR;

@@ -58,6 +58,7 @@ void level_free(Level& L) {
     }
     dev_free(L.d_dense32); dev_free(L.d_dense64);
     dev_free(L.d_tsp32); dev_free(L.d_tsp64);
+    dev_free(L.d_tspc32); dev_free(L.d_tspc64);
     L = Level();
 }
 
@@ -139,7 +140,7 @@ static void setup_diag(Level& L, cudaStream_t s, double* share = nullptr) {
 
 static void setup_dense(Level& L, cudaStream_t s) {
     std::vector<double> mu;
-    if (L.col.kind == 2 && L.d_mu64) {
+    if ((L.col.kind == 2 || L.col.kind == 4) && L.d_mu64) {
         mu.resize((size_t)L.N);
         GCK(cudaMemcpyAsync(mu.data(), L.d_mu64, mu.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         GCK(cudaStreamSynchronize(s));
@@ -263,7 +264,7 @@ static int vcycle(Posterior& P, Workspace& W, Workspace::Vecs& V, int l, const T
     const int nl = (int)P.levels.size();
     Level& L = P.levels[l];
     const int nblk = W.nblk;
-    if (l == 0 && P.use_tsp) {
+    if (l == 0 && P.use_tsp && tsp_fits<T>(L)) {
         launch_tsp<T>(L, P.ic_rinv, L.inv_eps2, b, (T*)V.t1[0], x, nblk, s);
         if (rz_partial) {
             launch_dot<T>(b, x, L.N, nblk, rz_partial, elem_parts(L.N), s);

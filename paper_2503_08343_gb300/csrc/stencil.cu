@@ -74,7 +74,7 @@ template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct alignas
     V4<T> sj[COL ? SN : 1][KB];
     V4<T> qobs[TN][KB];        // A^T R^-1 A p at the tile's observed nodes
     T dinvh[NH][PH];           // CHEB0: D^-1 on the staged nodes
-    T mu[COL == 2 ? NS : 1][COL == 2 ? PN : 1];
+    T mu[(COL == 2 || COL == 4) ? NS : 1][(COL == 2 || COL == 4) ? PN : 1];
     static_assert((PN * sizeof(V4<T>)) % 128 == 0 && (TN * sizeof(V4<T>)) % 128 == 0,
                   "stage buffers of the TMA boxes keep 128-byte alignment");
 };
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 cp_scalar<T>(&S.dinv[MODE == M_CHEB ? st : 0][tid], A.dinv + (own ? (gt * ny + gy) * nx + gx : 0), own);
             }
             const int tbase = (tt0 * ny + ty0) * nx + tx0;
-            if (COL == 2 || MODE == M_CHEB0) {      // per-node scalars of the tile and halo
+            if (COL == 2 || COL == 4 || MODE == M_CHEB0) {      // per-node scalars of the tile and halo
 #pragma unroll
                 for (int k = 0; k < KP; ++k) {
                     const int e = tid + 256 * k;
@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                     const int gx = tx0 + p_dx[k], gy = ty0 + p_dy[k], gt = tt0 + p_dt[k];
                     const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gt >= 0 && gt < nt;
                     const int node = in ? tbase + p_rel[k] : 0;
-                    if (COL == 2) cp_scalar<T>(&S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0], L.mu + node, in);
+                    if (COL == 2 || COL == 4)
+                        cp_scalar<T>(&S.mu[(COL == 2 || COL == 4) ? st : 0][(COL == 2 || COL == 4) ? e : 0], L.mu + node, in);
                     if (MODE == M_CHEB0) cp_scalar<T>(&S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? e : 0], A.dinv + node, in);
                 }
             }
@@ -325,7 +326,9 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         const int grp = cur.grp;
         const int tx0 = cur.tx * TX, ty0 = cur.ty * TY, tt0 = cur.tt * TT;
         const V4<T>(*sp)[KB] = S.p[st];
-        auto smu = [&](int e) -> T { return COL == 2 ? S.mu[COL == 2 ? st : 0][COL == 2 ? e : 0] : T(0); };
+        auto smu = [&](int e) -> T {
+            return (COL == 2 || COL == 4) ? S.mu[(COL == 2 || COL == 4) ? st : 0][(COL == 2 || COL == 4) ? e : 0] : T(0);
+        };
 
         // s = B p on the rows of the tile plus a one-node ring.  Dirichlet rows
         // are zero; rows next to the boundary skip the Dirichlet columns
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             }
 #pragma unroll
             for (int j = 0; j < KB; ++j) S.s[e][j] = sv[j];
-            if (COL) {
+            if (COL == 1 || COL == 2) {
 #pragma unroll
                 for (int j = 0; j < KB; ++j) {
                     V4<T> sjv = v4zero<T>();
@@ -371,6 +374,24 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                         sjv = fma4(cL, sp[base - 1][j], sjv);
                         sjv = fma4(cR, sp[base + 1][j], sjv);
                         sjv = fma4((T)(-L.col.inv_dt), sp[base - PY * PX][j], sjv);
+                    }
+                    S.sj[COL ? e : 0][j] = sjv;
+                }
+            } else if (COL >= 3) {
+                // FEM Crank-Nicolson row: taps x-1, x, x+1 on this level and the one before
+                constexpr int TP = PY * PX;           // one time level back in the staged tile
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    V4<T> sjv = v4zero<T>();
+                    if (inrow && rx >= 1 && rx <= nx - 2 && rt >= 1) {
+                        T dk[3], dp[3];
+                        fem_cn_half_conv<T>(L.col, smu(base - 1), smu(base), smu(base + 1), dk);
+                        fem_cn_half_conv<T>(L.col, smu(base - TP - 1), smu(base - TP), smu(base - TP + 1), dp);
+#pragma unroll
+                        for (int e3 = 0; e3 < 3; ++e3) {
+                            sjv = fma4(fem_cn_fixed<T>(L.col, e3, T(1)) + dk[e3], sp[base + e3 - 1][j], sjv);
+                            sjv = fma4(fem_cn_fixed<T>(L.col, e3, T(-1)) + dp[e3], sp[base - TP + e3 - 1][j], sjv);
+                        }
                     }
                     S.sj[COL ? e : 0][j] = sjv;
                 }
@@ -437,7 +458,28 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                     for (int j = 0; j < KB; ++j) q[j] = fma4(c, S.s[sbase + soff<SX, SY>(o)][j], q[j]);
                 }
             }
-            if (COL) {
+            if (COL >= 3) {
+                // FEM Crank-Nicolson rows touching this column: (x+d, t) by their
+                // tap -d on their own level, (x+d, t+1) by their tap -d on the
+                // level before; both carry the half convection derivative of
+                // row x+d at level t
+                const int sb = lt * SX + (lx + 1);
+                T dd[3][3];
+#pragma unroll
+                for (int d = -1; d <= 1; ++d)
+                    fem_cn_half_conv<T>(L.col, smu(pbase + d - 1), smu(pbase + d), smu(pbase + d + 1), dd[d + 1]);
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    V4<T> acc = v4zero<T>();
+#pragma unroll
+                    for (int d = -1; d <= 1; ++d) {
+                        const T hd = dd[d + 1][1 - d];
+                        acc = fma4(fem_cn_fixed<T>(L.col, 1 - d, T(1)) + hd, S.sj[COL ? sb + d : 0][j], acc);
+                        acc = fma4(fem_cn_fixed<T>(L.col, 1 - d, T(-1)) + hd, S.sj[COL ? sb + SX + d : 0][j], acc);
+                    }
+                    q[j] = fma4((T)L.col.qeps, acc, q[j]);
+                }
+            } else if (COL) {
                 // rows touching this column: itself (centre), x-1 row (its x+1 tap),
                 // x+1 row (its x-1 tap), t+1 row (its t-1 tap)
                 const int sb = lt * SX + (lx + 1);
@@ -699,6 +741,8 @@ template <int GEO, typename T, int MODE>
 static int launch_geo_mode(const StencilArgs<T>& a, cudaStream_t s, bool dry) {
     if (GEO == GEO_XT && a.L.col.kind == 1) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 1 : 0), 0>(a, s, dry);
     if (GEO == GEO_XT && a.L.col.kind == 2) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0), 0>(a, s, dry);
+    if (GEO == GEO_XT && a.L.col.kind == 3) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 3 : 0), 0>(a, s, dry);
+    if (GEO == GEO_XT && a.L.col.kind == 4) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 4 : 0), 0>(a, s, dry);
     if (GEO == GEO_XY && a.L.periodic) return launch_one<GEO, T, MODE, 0, (GEO == GEO_XY ? 1 : 0)>(a, s, dry);
     return launch_one<GEO, T, MODE, 0, 0>(a, s, dry);
 }

@@ -6,7 +6,8 @@
 // collocation rows at interior nodes of levels k >= 1, with W their
 // precisions.  Jt is square and block lower-bidiagonal in time (implicit
 // Euler): level k reads level k (a tridiagonal stencil in x) and level k-1
-// (-1/dt at the same x).  Its inverse is one forward time sweep and Jt^-T one
+// (-1/dt at the same x; FEM Crank-Nicolson rows: a tridiagonal stencil,
+// whose coefficients k_tsp_couple stores).  Its inverse is one forward time sweep and Jt^-T one
 // backward sweep, each level a tridiagonal solve, so
 //     z = M r = Jt^-1 W^-1 Jt^-T r
 // costs two sweeps and leaves the prior's interior part and the point data,
@@ -51,6 +52,10 @@ constexpr int kRows = 8;                                        // interior rows
 constexpr int kTspMaxNx = kLanes * (kRows + 1);
 constexpr int kRowF = 5, kLaneF = 3 + 2 * kSteps;
 constexpr int kFactorBlock = kRowF * kRows * kLanes + kLaneF * kLanes;
+// FEM Crank-Nicolson rows couple three nodes of the neighbouring level: per
+// (direction, level) the coupling coefficients of every row, [3][kRows][kLanes]
+// for the chunk rows and [3][kLanes] for the separators (x-1, x, x+1)
+constexpr int kCplBlock = 3 * kRows * kLanes + 3 * kLanes;
 static_assert((1 << kSteps) == kLanes, "cyclic reduction covers the lanes");
 
 // Level row coefficients of J (lower x-1, diagonal, upper x+1) at node x of
@@ -60,6 +65,14 @@ __device__ __forceinline__ void j_row(const LevelView<T>& L, const T* mu, int x,
     const int nx = L.nx;
     if (k == 0 || x <= 0 || x >= nx - 1) { lo = T(0); di = T(1); up = T(0); return; }
     const Colloc& c = L.col;
+    if (c.kind >= 3) {         // FEM Crank-Nicolson row: its taps on its own level
+        T d[3];
+        fem_cn_half_conv<T>(c, mu ? mu[x - 1] : T(0), mu ? mu[x] : T(0), mu ? mu[x + 1] : T(0), d);
+        lo = fem_cn_fixed<T>(c, 0, T(1)) + d[0];
+        di = fem_cn_fixed<T>(c, 1, T(1)) + d[1];
+        up = fem_cn_fixed<T>(c, 2, T(1)) + d[2];
+        return;
+    }
     T a, da;
     if (c.kind == 1) { a = (T)c.c; da = T(0); }
     else {
@@ -96,7 +109,7 @@ __global__ void __launch_bounds__(kLanes) k_tsp_factor(const LevelView<T> L, T* 
     const int dir = blockIdx.x / nt, k = blockIdx.x % nt;
     const int lane = threadIdx.x;
     const int m = (nx + kLanes - 1) / kLanes, s = lane * m, mi = max(0, min(m, nx - s)), mint = mi - 1;
-    const T* mu = L.col.kind == 2 ? L.mu + (size_t)k * nx : nullptr;
+    const T* mu = (L.col.kind == 2 || L.col.kind == 4) ? L.mu + (size_t)k * nx : nullptr;
     T* blk = f + (size_t)blockIdx.x * kFactorBlock;
     T* rowf = blk;                                   // [field][j][lane]
     T* lanef = blk + kRowF * kRows * kLanes;         // [field][lane]
@@ -187,22 +200,70 @@ __global__ void __launch_bounds__(kLanes) k_tsp_factor(const LevelView<T> L, T* 
     lanef[2 * kLanes + lane] = T(1) / rb;
 }
 
+// Coupling coefficients of FEM Crank-Nicolson rows, one CTA of kLanes
+// threads per (direction, level) like k_tsp_factor: the forward sweep at
+// level k adds sum_e -b_e(x, k) z_(k-1)(x + e - 1) to row x's right-hand side
+// (b: row (x, k)'s taps on level k-1); the backward sweep at level k adds
+// sum_d -b_(1-d)(x + d, k + 1) y_(k+1)(x + d) (the transposed coupling, which
+// also reaches the boundary nodes).  Stored as (x-1, x, x+1) coefficients.
+template <typename T>
+__global__ void __launch_bounds__(kLanes) k_tsp_couple(const LevelView<T> L, T* __restrict__ f) {
+    const int nx = L.nx, nt = L.nt;
+    const int dir = blockIdx.x / nt, k = blockIdx.x % nt;
+    const int lane = threadIdx.x;
+    const int m = (nx + kLanes - 1) / kLanes, s = lane * m, mi = max(0, min(m, nx - s)), mint = mi - 1;
+    T* blk = f + (size_t)blockIdx.x * kCplBlock;
+    const Colloc& c = L.col;
+    // b taps of row (x, kr) (zero unless x is interior and kr >= 1)
+    auto btaps = [&](int x, int kr, T b[3]) {
+        b[0] = b[1] = b[2] = T(0);
+        if (x < 1 || x > nx - 2 || kr < 1 || kr >= nt) return;
+        const T* mp = L.mu ? L.mu + (size_t)(kr - 1) * nx : nullptr;
+        T d[3];
+        fem_cn_half_conv<T>(c, mp ? mp[x - 1] : T(0), mp ? mp[x] : T(0), mp ? mp[x + 1] : T(0), d);
+        for (int e = 0; e < 3; ++e) b[e] = fem_cn_fixed<T>(c, e, T(-1)) + d[e];
+    };
+    auto coeffs = [&](int x, T out[3]) {
+        if (dir == 0) {
+            T b[3];
+            btaps(x, k, b);
+            for (int e = 0; e < 3; ++e) out[e] = -b[e];
+        } else {
+            for (int d = -1; d <= 1; ++d) {
+                T b[3];
+                btaps(x + d, k + 1, b);
+                out[d + 1] = -b[1 - d];
+            }
+        }
+    };
+    for (int j = 0; j < kRows; ++j) {
+        T o[3] = {T(0), T(0), T(0)};
+        if (j < mint) coeffs(s + j, o);
+        for (int e = 0; e < 3; ++e) blk[(e * kRows + j) * kLanes + lane] = o[e];
+    }
+    T o[3] = {T(0), T(0), T(0)};
+    if (mi > 0) coeffs(s + mi - 1, o);
+    for (int e = 0; e < 3; ++e) blk[3 * kRows * kLanes + e * kLanes + lane] = o[e];
+}
+
 // One CTA (kLanes threads) per block of four right-hand sides.  y is scratch
 // of the blocked layout; r and z are blocked.  Shared memory: factors
 // [2][kFactorBlock], inputs [2][nx + kLanes] four-wide chunks laid out with one
 // gap after each lane's chunk (x -> x + x / m: a lane reads its rows at
 // base + j, and neighbouring lanes fall in distinct bank groups), the lane
 // exchange buffers.
-template <typename T>
-__global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* __restrict__ fac, T iw_ic, T iw_bnd,
-                                               T iw_q, const T* __restrict__ r, T* __restrict__ y, T* __restrict__ z) {
+template <typename T, bool FEM>
+__global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* __restrict__ fac, const T* __restrict__ cpl,
+                                               T iw_ic, T iw_bnd, T iw_q, const T* __restrict__ r, T* __restrict__ y,
+                                               T* __restrict__ z) {
     extern __shared__ __align__(16) unsigned char tsp_smem[];
     __shared__ V4<T> xch[2][kLanes];
     const int nx = L.nx, nt = L.nt;
     const long long N = L.N;
     const int NXC = nx + kLanes;                         // chunks per input row, gaps included
     T* sfac = reinterpret_cast<T*>(tsp_smem);            // [2][kFactorBlock]
-    V4<T>* sin = reinterpret_cast<V4<T>*>(sfac + 2 * kFactorBlock);   // [2][NXC]
+    T* scpl = sfac + 2 * kFactorBlock;                   // FEM: [2][kCplBlock]
+    V4<T>* sin = reinterpret_cast<V4<T>*>(scpl + (FEM ? 2 * kCplBlock : 0));   // [2][NXC]
     const int lane = threadIdx.x, wl = lane & 31;
     const int blk = blockIdx.x;
     const int m = (nx + kLanes - 1) / kLanes;
@@ -225,6 +286,11 @@ __global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* _
         const char* gf = reinterpret_cast<const char*>(fac + ((size_t)dir * nt + k) * kFactorBlock);
         char* df = reinterpret_cast<char*>(sfac + (size_t)slot * kFactorBlock);
         for (int c = lane; c < (int)(kFactorBlock * sizeof(T) / 16); c += kLanes) cp_async16(df + c * 16, gf + c * 16, true);
+        if (FEM) {
+            const char* gc = reinterpret_cast<const char*>(cpl + ((size_t)dir * nt + k) * kCplBlock);
+            char* dc = reinterpret_cast<char*>(scpl + (size_t)slot * kCplBlock);
+            for (int c = lane; c < (int)(kCplBlock * sizeof(T) / 16); c += kLanes) cp_async16(dc + c * 16, gc + c * 16, true);
+        }
     };
     // four-wide exchange with the lane d below / above (shuffles within a warp,
     // shared memory across warps; every thread calls it)
@@ -284,13 +350,29 @@ __global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* _
             auto F = [&](int field, int j) { return rowf[(field * kRows + j) * kLanes + lane]; };
             const bool couple = bwd ? k + 1 < nt : k > 0;     // the level reached by the time step
             const int jlo = s0 > 0 ? 0 : 1;                  // x = 0 (lane 0, row 0) is a boundary node
+            // FEM rows: the coupled level's values at x - 1 and x + 1 across
+            // chunk ends (the previous lane's separator, the next lane's first row)
+            V4<T> prevsep = v4zero<T>(), nextfirst = v4zero<T>();
+            const T* cplf = scpl + (size_t)slot * kCplBlock;
+            auto CP = [&](int e, int j) { return cplf[(e * kRows + j) * kLanes + lane]; };
+            if (FEM) {
+                V4<T> dummy;
+                exch(csep, 1, prevsep, dummy);
+                exch(mint > 0 ? car[0] : csep, 1, dummy, nextfirst);
+            }
             // right-hand sides of the interior rows, then p'_j = d_j / den_j - (A_j / den_j) p'_{j-1}
             V4<T> pprev = v4zero<T>();
 #pragma unroll
             for (int j = 0; j < kRows; ++j) {
                 if (j < mint) {
                     V4<T> v = in[j];
-                    if (couple && j >= jlo) v = fma4(inv_dt, car[j], v);
+                    if (FEM) {
+                        const V4<T> cl = j > 0 ? car[j > 0 ? j - 1 : 0] : prevsep;
+                        const V4<T> cr = j < mint - 1 ? car[j + 1 < kRows ? j + 1 : j] : csep;
+                        v = fma4(CP(0, j), cl, fma4(CP(1, j), car[j], fma4(CP(2, j), cr, v)));
+                    } else if (couple && j >= jlo) {
+                        v = fma4(inv_dt, car[j], v);
+                    }
                     pprev = fma4(-F(0, j), pprev, F(1, j) * v);
                     xv[j] = pprev;
                 }
@@ -309,7 +391,16 @@ __global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* _
             V4<T> dsep = v4zero<T>();
             if (mi > 0) {
                 dsep = in[mi - 1];
-                if (couple && xs_int) dsep = fma4(inv_dt, csep, dsep);
+                if (FEM) {
+                    V4<T> cl = prevsep;
+#pragma unroll
+                    for (int j = 0; j < kRows; ++j)
+                        if (j == mint - 1) cl = car[j];
+                    const T* sc = cplf + 3 * kRows * kLanes;
+                    dsep = fma4(sc[0 * kLanes + lane], cl, fma4(sc[1 * kLanes + lane], csep, fma4(sc[2 * kLanes + lane], nextfirst, dsep)));
+                } else if (couple && xs_int) {
+                    dsep = fma4(inv_dt, csep, dsep);
+                }
             }
             const V4<T> pf = mint > 0 ? xv[0] : v4zero<T>();
             V4<T> pup, pnx;
@@ -352,6 +443,23 @@ bool tsp_applicable(const Level& L, int nic) {
     return L.geo == GEO_XT && L.col.kind != 0 && nic > 0 && L.nx <= kTspMaxNx;
 }
 
+static size_t tsp_smem(const Level& L, size_t elem) {
+    const bool fem = L.col.kind >= 3;
+    return elem * (size_t)2 * (kFactorBlock + (fem ? kCplBlock : 0)) + 4 * elem * (size_t)2 * (L.nx + kLanes);
+}
+
+template <typename T> bool tsp_fits(const Level& L) {
+    static const int optin = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return 0;
+        return v;
+    }();
+    return tsp_smem(L, sizeof(T)) + 2 * sizeof(V4<T>) * kLanes <= (size_t)optin;
+}
+template bool tsp_fits<float>(const Level&);
+template bool tsp_fits<double>(const Level&);
+
 // Factors of every level and both sweep directions, in both precisions
 // (the FP32 inner solve and the plain FP64 path); rerun whenever the
 // linearisation point changes.
@@ -363,23 +471,39 @@ void tsp_prepare(Level& L, cudaStream_t s) {
     note_launch();
     k_tsp_factor<double><<<2 * L.nt, kLanes, 0, s>>>(L.view<double>(), L.d_tsp64);
     note_launch();
+    if (L.col.kind >= 3) {
+        const size_t nc = (size_t)2 * L.nt * kCplBlock;
+        if (!L.d_tspc32) L.d_tspc32 = dev_alloc<float>(nc);
+        if (!L.d_tspc64) L.d_tspc64 = dev_alloc<double>(nc);
+        k_tsp_couple<float><<<2 * L.nt, kLanes, 0, s>>>(L.view<float>(), L.d_tspc32);
+        note_launch();
+        k_tsp_couple<double><<<2 * L.nt, kLanes, 0, s>>>(L.view<double>(), L.d_tspc64);
+        note_launch();
+    }
     GCK(cudaGetLastError());
 }
 
-template <typename T>
-void launch_tsp(const Level& L, double w_ic, double w_bnd, const T* r, T* y, T* z, int nblk, cudaStream_t s) {
-    const size_t smem = sizeof(T) * (size_t)2 * kFactorBlock + sizeof(V4<T>) * (size_t)2 * (L.nx + kLanes);
+template <typename T, bool FEM>
+static void launch_tsp_kind(const Level& L, double w_ic, double w_bnd, const T* r, T* y, T* z, int nblk, cudaStream_t s) {
+    const size_t smem = tsp_smem(L, sizeof(T));
     const T* fac = sizeof(T) == 4 ? reinterpret_cast<const T*>(L.d_tsp32) : reinterpret_cast<const T*>(L.d_tsp64);
-    if (!fac) throw Error(GMRF_E_INVALID, "time-stepping preconditioner: factors not prepared");
+    const T* cpl = sizeof(T) == 4 ? reinterpret_cast<const T*>(L.d_tspc32) : reinterpret_cast<const T*>(L.d_tspc64);
+    if (!fac || (FEM && !cpl)) throw Error(GMRF_E_INVALID, "time-stepping preconditioner: factors not prepared");
     static size_t attr = 0;
     if (smem > attr) {
-        if (cudaFuncSetAttribute(k_tsp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_tsp<T, FEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             throw Error(GMRF_E_CUDA, "time-stepping preconditioner: shared memory attribute");
         attr = smem;
     }
     const double iq = L.col.qeps > 0 ? 1.0 / L.col.qeps : 0.0;
-    k_tsp<T><<<nblk, kLanes, smem, s>>>(L.view<T>(), fac, (T)(1.0 / w_ic), (T)(1.0 / w_bnd), (T)iq, r, y, z);
+    k_tsp<T, FEM><<<nblk, kLanes, smem, s>>>(L.view<T>(), fac, cpl, (T)(1.0 / w_ic), (T)(1.0 / w_bnd), (T)iq, r, y, z);
     note_launch();
+}
+
+template <typename T>
+void launch_tsp(const Level& L, double w_ic, double w_bnd, const T* r, T* y, T* z, int nblk, cudaStream_t s) {
+    if (L.col.kind >= 3) launch_tsp_kind<T, true>(L, w_ic, w_bnd, r, y, z, nblk, s);
+    else launch_tsp_kind<T, false>(L, w_ic, w_bnd, r, y, z, nblk, s);
 }
 template void launch_tsp<float>(const Level&, double, double, const float*, float*, float*, int, cudaStream_t);
 template void launch_tsp<double>(const Level&, double, double, const double*, double*, double*, int, cudaStream_t);

@@ -223,6 +223,8 @@ class Posterior:
                 o.ic_values = _dptr(icv)
         if obs.get("colloc_sigma") is not None:
             o.colloc = 1 if obs.get("colloc_c") is not None else 2
+            if obs.get("colloc_form", "collocation") == "fem_cn":
+                o.colloc += 2          # FEM Crank-Nicolson rows: 3 linear, 4 Burgers
             o.colloc_sigma = float(obs["colloc_sigma"])
             o.colloc_c = float(obs.get("colloc_c") or 0.0)
             o.colloc_nu = float(obs.get("burgers_nu", prior.spec["nu"]))

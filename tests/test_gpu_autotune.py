@@ -68,8 +68,8 @@ def _check_choices(log):
     for ent in log:
         ms = ent["ms"]
         assert ms, ent
-        best = min(ms, key=ms.get)
-        assert best == f"{ent['ctas_per_sm']}x{ent['aux']}", ent
+        chosen = f"{ent['ctas_per_sm']}x{ent['aux']}"
+        assert chosen in ms and ms[chosen] == min(ms.values()), ent
         assert all(v > 0 for v in ms.values()), ent
         for lab in ms:
             k, aux = (int(v) for v in lab.split("x"))

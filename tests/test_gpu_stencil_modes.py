@@ -24,7 +24,7 @@ before the FP64 reduction).
 
 Geometries: the tiled 2D and 1D space-time kernel, the marching 2D space-time
 kernel, ragged tiles, periodic tori (seam tiles), dense observations, linear and linearised Burgers
-collocation rows, the full-size 2D Matern workload (512^2, 10 000
+collocation rows and their FEM Crank-Nicolson form, the full-size 2D Matern workload (512^2, 10 000
 observations, 65 right-hand sides) and the first coarse multigrid level
 (rediscretised prior with the point data interpolated on the coarse mesh).
 """
@@ -59,10 +59,10 @@ def lib():
     return gmrf.load()
 
 
-def _linear_colloc():
+def _linear_colloc(form="collocation"):
     pr, ob = W.c1_st1d(nx=37, nt=21, m=30, seed=5)
     f = np.random.default_rng(3).normal(size=(37 - 2) * (21 - 1))
-    return pr, dict(ob, colloc_sigma=0.05, colloc_c=0.5, burgers_nu=0.01, colloc_f=f)
+    return pr, dict(ob, colloc_sigma=0.05, colloc_c=0.5, burgers_nu=0.01, colloc_f=f, colloc_form=form)
 
 
 CASES = {
@@ -72,6 +72,7 @@ CASES = {
                                              W.fourier_modes(np.random.default_rng(1), 8, 2, 4), seed=3)), 4),
     "st1d_37x21_ragged": (lambda: W.c1_st1d(nx=37, nt=21, m=30, seed=5), 6),
     "st1d_linear_collocation": (_linear_colloc, 3),
+    "st1d_linear_fem_cn": (lambda: _linear_colloc("fem_cn"), 3),
     "st2d_20x20x12_march": (lambda: W.c5_st2d(n=20, nt=12, m=300, seed=5), 3),
     "st2d_24x24x10_dense_obs": (lambda: W.c5_st2d(n=24, nt=10, m=5000, seed=3), 2),
     # periodic boundary: tiles at the seam take their halo from the other side
@@ -175,10 +176,14 @@ def test_stencil_modes_on_the_first_coarse_level(name):
     _check_modes(post, orc, k, 1, 0, seed=11)
 
 
-def test_stencil_modes_burgers_linearised():
-    # collocation rows of the Burgers residual linearised at the Gauss-Newton
-    # iterate the library holds after one step (Sec. 3.3)
+@pytest.mark.parametrize("form", ["collocation", "fem_cn"])
+def test_stencil_modes_burgers_linearised(form):
+    # collocation (or FEM Crank-Nicolson) rows of the Burgers residual
+    # linearised at the Gauss-Newton iterate the library holds after one step
+    # (Sec. 3.3)
     pr, ob = W.c3_burgers(nx=65, nt=33, m=40)
+    # FEM rows are preconditioned by the multigrid alone: a gentler row noise
+    ob = dict(ob, colloc_form=form) if form == "collocation" else dict(ob, colloc_form=form, colloc_sigma=1e-4)
     post = gmrf.Posterior(gmrf.Prior(pr), ob)
     u, _ = post.solve_mean()
     d = np.zeros_like(u)
