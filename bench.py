@@ -260,9 +260,10 @@ def run_ours(args, rank, world):
     # step), timed with CUDA events on its stream over 50 launches, beside the
     # apply and residual forms of the same fused stencil
     peak, peak_kind = measured_peak_hbm()
-    per_unit = {0: 8.0, 1: 12.0, 2: 21.0}      # algorithmic bytes per RHS x unknown (FP32)
+    # pcg: the PCG iteration's apply with its vector work (reads p, z, x; writes q, p', x)
+    per_unit = {0: 8.0, 1: 12.0, 2: 21.0, 3: 24.0}      # algorithmic bytes per RHS x unknown (FP32)
     kern = {}
-    for kid, name in ((0, "apply"), (1, "residual"), (2, "chebyshev")):
+    for kid, name in ((0, "apply"), (1, "residual"), (2, "chebyshev"), (3, "pcg")):
         ms_k = post.time_stencil(kid, NS + 1, iters=50)
         gbs = per_unit[kid] * units / (ms_k * 1e-3) / 1e9
         kern[name] = {"ms": ms_k, "GB/s": gbs, "frac": gbs / peak, "bytes_per_rhs_unknown": per_unit[kid]}
@@ -298,7 +299,7 @@ def run_ours(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
-STENCIL_BYTES = {0: 8.0, 1: 12.0, 2: 21.0}      # algorithmic bytes per RHS x unknown (FP32): apply, residual, Chebyshev
+STENCIL_BYTES = {0: 8.0, 1: 12.0, 2: 21.0, 3: 24.0}   # algorithmic bytes per RHS x unknown (FP32): apply, residual, Chebyshev, PCG
 
 
 def run_stencil_timing(which: str, iters: int) -> None:
@@ -308,25 +309,25 @@ def run_stencil_timing(which: str, iters: int) -> None:
     range "stencil_<mode>" for a profiler filter.  Shapes: c2 = 2D Matern
     512^2 with 65 right-hand sides; c3 = Burgers 1024 x 1024 with 33,
     linearised by one Gauss-Newton step so that the collocation rows are
-    active (apply and residual only: its preconditioner is the
+    active (apply, residual and the fused PCG mode: its preconditioner is the
     time-stepping one, not Chebyshev smoothing; 1 B per RHS x unknown more for
     the linearisation point); c5 = 2D space-time 128^2 x 64 with 33 (the
-    marching kernel)."""
+    marching kernel, which has no fused PCG mode)."""
     import torch
     from paper_2503_08343_gb300 import gmrf, workloads as W
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
         peak = float(json.load(f)["hbm_gbs"])
     extra = 0.0
-    modes = ((0, "apply"), (1, "residual"), (2, "chebyshev"))
+    modes = ((0, "apply"), (1, "residual"), (2, "chebyshev"), (3, "pcg"))
     if which == "c2":
         pr, ob = W.c2_matern(n=N_SIDE, m=M_OBS)
         k = NS + 1
     elif which == "c3":
         pr, ob = W.c3_burgers(nx=1024, nt=1024)
-        k, extra, modes = 33, 1.0, modes[:2]
+        k, extra, modes = 33, 1.0, (modes[0], modes[1], modes[3])
     else:
         pr, ob = W.c5_st2d(n=128, nt=64, m=20000, seed=5)
-        k = 33
+        k, modes = 33, modes[:3]            # the marching kernel has no fused PCG mode
     post = gmrf.Posterior(gmrf.Prior(pr), ob)
     if which == "c3":
         import numpy as np

@@ -329,7 +329,8 @@ gmrf_status gmrf_normals(uint64_t seed, int32_t stream, int32_t sample0, int32_t
  * (CUDA events around the launches), for a batch of k right-hand sides of
  * random data.  kernel: 0 = apply (y = Q_u|y x), 1 = residual
  * (r = b - Q_u|y x), 2 = Chebyshev smoothing step
- * (d' = c1 d + c2 D^-1 (b - Q_u|y x), x' = x + d'). */
+ * (d' = c1 d + c2 D^-1 (b - Q_u|y x), x' = x + d'), 3 = the conjugate-gradient
+ * iteration's fused apply (p' = z + beta p, q = Q_u|y p', x += alpha p). */
 gmrf_status gmrf_time_stencil(gmrf_posterior* post, int32_t kernel, int32_t k, int32_t iters, double* ms);
 
 /* One launch of the fused stencil kernel on multigrid level `level`
@@ -344,6 +345,11 @@ gmrf_status gmrf_time_stencil(gmrf_posterior* post, int32_t kernel, int32_t k, i
  *  mode 2 Chebyshev:  out2 = c1 d + c2 D^-1 (b - Q_l x),  out = x + out2,
  *                     dots = b^T out (d may be NULL: taken as 0)
  *  mode 3 Chebyshev from zero: x1 = c0 D^-1 b, then mode 2 with x = d = x1.
+ *  mode 4 PCG (one conjugate-gradient iteration's vector work around the
+ *                     apply): p' = d + c2 x (x the previous direction, d the
+ *                     preconditioned residual, c2 = beta), out = Q_l p',
+ *                     dots = p'^T out; out2 holds [2][k][N_l]: p', then the
+ *                     iterate update b + c1 x (b the iterate, c1 = alpha).
  * dots: [k] host.  Allocates its own scratch. */
 gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t precision, int32_t mode, int32_t k,
                               const double* x, const double* b, const double* d, double c0, double c1, double c2,

@@ -782,7 +782,7 @@ gmrf_status gmrf_normals(uint64_t seed, int32_t stream, int32_t sample0, int32_t
 
 gmrf_status gmrf_time_stencil(gmrf_posterior* post, int32_t kernel, int32_t k, int32_t iters, double* ms) {
     return guard([&] {
-        require(post && k >= 1 && iters >= 1 && ms && kernel >= 0 && kernel <= 2, "bad argument");
+        require(post && k >= 1 && iters >= 1 && ms && kernel >= 0 && kernel <= 3, "bad argument");
         enter(post->prior);
         *ms = time_stencil(post->impl, kernel, (k + 3) / 4, iters, post->prior->impl.stream);
     });
@@ -795,16 +795,17 @@ gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t preci
         require(post && k >= 1 && out && dots, "bad argument");
         require(level >= 0 && level < (int32_t)post->impl.levels.size(), "level out of range");
         require(precision == 0 || precision == 1, "precision must be 0 or 1");
-        require(mode >= 0 && mode <= 3, "mode must be 0..3");
+        require(mode >= 0 && mode <= 4, "mode must be 0..4");
         require(mode == 3 || x, "x is required");
         require(mode == 0 || b, "b is required");
-        require(mode < 2 || out2, "out2 is required for the Chebyshev modes");
+        require(mode < 2 || out2, "out2 is required for the Chebyshev and PCG modes");
+        require(mode != 4 || d, "d is required for the PCG mode");
         enter(post->prior);
         Posterior& P = post->impl;
         const cudaStream_t s = P.prior->stream;
         const long long N = P.levels[(size_t)level].N;
         const size_t n = (size_t)N * k;
-        double* buf = dev_alloc<double>(5 * n);
+        double* buf = dev_alloc<double>(6 * n);
         const double* src[3] = {x, b, d};
         const double* din[3] = {nullptr, nullptr, nullptr};
         for (int i = 0; i < 3; ++i)
@@ -813,10 +814,12 @@ gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t preci
                 din[i] = buf + i * n;
             }
         try {
-            stencil_step(P, level, precision, mode, k, din[0], mode == 0 ? nullptr : din[1], mode == 2 ? din[2] : nullptr,
-                         c0, c1, c2, buf + 3 * n, mode >= 2 ? buf + 4 * n : nullptr, dots, s);
+            stencil_step(P, level, precision, mode, k, din[0], mode == 0 ? nullptr : din[1],
+                         (mode == 2 || mode == 4) ? din[2] : nullptr, c0, c1, c2, buf + 3 * n, mode >= 2 ? buf + 4 * n : nullptr,
+                         mode == 4 ? buf + 5 * n : nullptr, dots, s);
             copy_out(out, buf + 3 * n, n, s);
             if (mode >= 2) copy_out(out2, buf + 4 * n, n, s);
+            if (mode == 4) copy_out(out2 + n, buf + 5 * n, n, s);
             GCK(cudaStreamSynchronize(s));
         } catch (...) {
             cudaStreamSynchronize(s);

@@ -86,7 +86,7 @@ double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s)
 // d (mode 2, may be null) and outputs out, out2 (modes 2-3); dots[k] (host)
 // receives the kernel's per-RHS dot products.
 void stencil_step(Posterior& P, int level, int prec, int mode, int k, const double* x, const double* b, const double* d,
-                  double c0, double c1, double c2, double* out, double* out2, double* dots, cudaStream_t s);
+                  double c0, double c1, double c2, double* out, double* out2, double* out3, double* dots, cudaStream_t s);
 
 // noalloc.cu: loads what gmrf_apply_posterior_noalloc uses for this posterior
 void noalloc_prepare(const Posterior& P);
@@ -178,7 +178,7 @@ struct Workspace {
     // per-level vectors for each precision
     struct Vecs {
         bool ready = false;
-        void* pcg[5] = {};             // x, r, p, q, z (fine level)
+        void* pcg[6] = {};             // x, r, p, q, z, p' (fine level; p and p' alternate in the fused iteration)
         std::vector<void*> xa, xb, d, res, b, t1, t2;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;

@@ -302,6 +302,31 @@ __global__ void __launch_bounds__(256) k_update_xp(T* __restrict__ x, T* __restr
     }
 }
 
+// x += alpha p: the iterate's last update after the fused iterations
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_x(T* __restrict__ x, const T* __restrict__ p, const double* __restrict__ sc,
+                                                  long long N) {
+    const int blk = blockIdx.y;
+    const double* alpha = sc + 2 * (gridDim.y * RW) + blk * RW;
+    const T a0 = (T)alpha[0], a1 = (T)alpha[1], a2 = (T)alpha[2], a3 = (T)alpha[3];
+    for (int k = 0; k < EPT; ++k) {
+        const long long n = (long long)blockIdx.x * ECHUNK + k * 256 + threadIdx.x;
+        if (n >= N) break;
+        const size_t off = ((size_t)blk * N + n) * RW;
+        const V4<T> pv = v4load(p + off);
+        V4<T> xv = v4load(x + off);
+        xv.a = fma(a0, pv.a, xv.a); xv.b = fma(a1, pv.b, xv.b); xv.c = fma(a2, pv.c, xv.c); xv.d = fma(a3, pv.d, xv.d);
+        v4store(x + off, xv);
+    }
+}
+
+template <typename T>
+void launch_pcg_update_x(T* x, const T* p, const double* sc, long long N, int nblk, cudaStream_t s) {
+    { k_update_x<T><<<dim3(elem_parts(N), nblk), 256, 0, s>>>(x, p, sc, N); note_launch(); }
+}
+template void launch_pcg_update_x<float>(float*, const float*, const double*, long long, int, cudaStream_t);
+template void launch_pcg_update_x<double>(double*, const double*, const double*, long long, int, cudaStream_t);
+
 template <typename T>
 void launch_pcg_update_xp(T* x, T* p, const T* z, const double* sc, long long N, int nblk, cudaStream_t s) {
     { k_update_xp<T><<<dim3(elem_parts(N), nblk), 256, 0, s>>>(x, p, z, sc, N); note_launch(); }

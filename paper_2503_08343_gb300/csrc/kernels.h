@@ -16,7 +16,7 @@ unsigned long long launch_count();
 
 // CHEB0: the first two Chebyshev steps from x = 0 in one pass; x1 = c0 D^-1 b
 // is formed in shared memory from the staged b, then one CHEB step with d = x1
-enum StencilMode { M_APPLY = 0, M_RESID = 1, M_CHEB = 2, M_CHEB0 = 3 };
+enum StencilMode { M_APPLY = 0, M_RESID = 1, M_CHEB = 2, M_CHEB0 = 3, M_PCG = 4 };
 
 template <typename T>
 struct StencilArgs {
@@ -32,6 +32,14 @@ struct StencilArgs {
     double* partial;   // per-CTA dot partials [nblk][grid][4] or null
     int nblk;
     const T* rweight;  // RESID: if set, the dot is sum r^2 * rweight[node] (D^-1-weighted norm)
+    // PCG (one conjugate-gradient iteration's vector work around the apply):
+    // x = previous direction p (staged with halo), d = preconditioned
+    // residual z (staged with halo), b = iterate (own nodes); per right-hand
+    // side alpha, beta ([nblk][4]);  p' = z + beta p, out = Q p', out2 = p',
+    // out3 = b + alpha p (the iterate's update of the previous iteration)
+    T* out3;
+    const double* alpha;
+    const double* beta;
 };
 
 // Dot partials written to `partial` as [nblk][grid][4] (APPLY x.Qx, RESID
@@ -93,6 +101,8 @@ template <typename T> void launch_dense_solve(const T* Ainv, const T* b, T* x, i
 template <typename T> void launch_pcg_update_r(T* r, const T* q, const double* sc, long long N, int nblk, cudaStream_t s);
 template <typename T> void launch_pcg_update_xp(T* x, T* p, const T* z, const double* sc, long long N, int nblk,
                                                 cudaStream_t s);
+// x += alpha p (the last iterate update after fused iterations)
+template <typename T> void launch_pcg_update_x(T* x, const T* p, const double* sc, long long N, int nblk, cudaStream_t s);
 void launch_pcg_scalar(int kind, const double* red, double* sc, int nblk, double tol2, cudaStream_t s);
 // launch_reduce into `red` followed by launch_pcg_scalar on it, as one kernel
 void launch_reduce_scalar(int kind, const double* partial, int nparts, int nblk, double* red, double* sc, double tol2,

@@ -184,7 +184,7 @@ template <typename T> static void alloc_vecs(Posterior& P, Workspace& W, Workspa
     if (V.ready) return;
     const int nblk = W.nblk;
     const long long N0 = P.levels[0].N;
-    for (int i = 0; i < 5; ++i) V.pcg[i] = dev_alloc<T>((size_t)nblk * N0 * 4);
+    for (int i = 0; i < 6; ++i) V.pcg[i] = dev_alloc<T>((size_t)nblk * N0 * 4);
     const size_t nl = P.levels.size();
     V.xa.assign(nl, nullptr); V.xb.assign(nl, nullptr); V.d.assign(nl, nullptr); V.res.assign(nl, nullptr);
     V.b.assign(nl, nullptr); V.t1.assign(nl, nullptr); V.t2.assign(nl, nullptr);
@@ -354,25 +354,64 @@ template <typename T> static double* scal(Workspace& W);
 template <> double* scal<float>(Workspace& W) { return W.sc32; }
 template <> double* scal<double>(Workspace& W) { return W.sc64; }
 
-// one PCG iteration: q = Q p, alpha, r -= alpha q, z = M r, beta, then x += alpha p and
-// p = z + beta p in one pass
+// The tiled stencil kernels carry the vector work of one iteration in their
+// PCG mode (the marching space-time kernel does not); GMRF_PCG_FUSED=0 selects
+// the separate passes.
+static bool pcg_fused(const Level& L) {
+    static const bool on = [] {
+        const char* v = std::getenv("GMRF_PCG_FUSED");
+        return !(v && v[0] == '0');
+    }();
+    return on && L.geo != GEO_XYT;
+}
+
+// One PCG iteration.  Separate passes: q = Q p, alpha, r -= alpha q, z = M r,
+// beta, then x += alpha p and p = z + beta p in one pass.  Fused: the last
+// pass moves into the next iteration's apply, which stages the previous
+// direction and z with their halos and forms x += alpha p, p' = z + beta p
+// and q = Q p' in one kernel; p and p' alternate between two buffers (a
+// neighbouring CTA still reads the old direction's halo), so iteration
+// `parity` reads V.pcg[parity ? 5 : 2] and writes the other one, and after
+// the last iteration pcg_finish adds the pending alpha p to x.
 template <typename T>
-static void pcg_iteration(Posterior& P, Workspace& W, Workspace::Vecs& V, double tol2, cudaStream_t s) {
+static void pcg_iteration(Posterior& P, Workspace& W, Workspace::Vecs& V, double tol2, cudaStream_t s, int parity) {
     Level& L = P.levels[0];
     const int nblk = W.nblk;
     T *x = (T*)V.pcg[0], *r = (T*)V.pcg[1], *p = (T*)V.pcg[2], *q = (T*)V.pcg[3], *z = (T*)V.pcg[4];
     double* sc = scal<T>(W);
-    const int nt = (int)L.ntiles(), ne = elem_parts(L.N);
+    const int P4 = nblk * 4;
     StencilArgs<T> a{};
     a.L = L.view<T>();
     a.nblk = nblk;
-    a.x = p; a.out = q; a.partial = W.partial;
-    const int ng = launch_stencil<T>(L.geo, M_APPLY, a, s);
-    launch_reduce_scalar(0, W.partial, ng, nblk, W.red, sc, tol2, s);
+    a.partial = W.partial;
+    const bool fused = pcg_fused(L);
+    if (fused) {
+        T* pc = (T*)V.pcg[parity ? 5 : 2];
+        T* pn = (T*)V.pcg[parity ? 2 : 5];
+        a.x = pc; a.d = z; a.b = x;
+        a.out = q; a.out2 = pn; a.out3 = x;
+        a.alpha = sc + 2 * P4; a.beta = sc + 3 * P4;
+        const int ng = launch_stencil<T>(L.geo, M_PCG, a, s);
+        launch_reduce_scalar(0, W.partial, ng, nblk, W.red, sc, tol2, s);
+    } else {
+        a.x = p; a.out = q;
+        const int ng = launch_stencil<T>(L.geo, M_APPLY, a, s);
+        launch_reduce_scalar(0, W.partial, ng, nblk, W.red, sc, tol2, s);
+    }
     launch_pcg_update_r<T>(r, q, sc, L.N, nblk, s);
     const int nz = vcycle<T>(P, W, V, 0, r, z, W.partial, s);
     launch_reduce_scalar(2, W.partial, nz, nblk, W.red, sc, tol2, s);
-    launch_pcg_update_xp<T>(x, p, z, sc, L.N, nblk, s);     // x += alpha p with this iteration's p
+    if (!fused) launch_pcg_update_xp<T>(x, p, z, sc, L.N, nblk, s);     // x += alpha p with this iteration's p
+}
+
+// After `iters` iterations: the fused form still owes x += alpha p with the
+// direction of the last iteration (written to V.pcg[2] after an even count).
+template <typename T>
+static void pcg_finish(Posterior& P, Workspace& W, Workspace::Vecs& V, int iters, cudaStream_t s) {
+    Level& L = P.levels[0];
+    if (!pcg_fused(L) || iters <= 0) return;
+    const T* pl = (const T*)V.pcg[(iters % 2 == 0) ? 2 : 5];
+    launch_pcg_update_x<T>((T*)V.pcg[0], pl, scal<T>(W), L.N, W.nblk, s);
 }
 
 static const int kItersPerGraph = 2;
@@ -425,7 +464,7 @@ static int pcg(Posterior& P, Workspace& W, double tol, int maxit, cudaStream_t s
         for (int pass = 0; pass < 2; ++pass) {
             GCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
             capture_begin();
-            for (int k = 0; k < kItersPerGraph; ++k) pcg_iteration<T>(P, W, V, tol2, s);
+            for (int k = 0; k < kItersPerGraph; ++k) pcg_iteration<T>(P, W, V, tol2, s, k & 1);
             V.graph_kernels = capture_end();
             cudaMemcpyAsync(W.h_active, sc + 6 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s);
             cudaMemcpyAsync(W.h_red, sc + 7 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s);
@@ -444,7 +483,7 @@ static int pcg(Posterior& P, Workspace& W, double tol, int maxit, cudaStream_t s
             note_graph_launch(V.graph_kernels);
             it += kItersPerGraph;
         } else {
-            pcg_iteration<T>(P, W, V, tol2, s);
+            pcg_iteration<T>(P, W, V, tol2, s, it & 1);
             GCK(cudaMemcpyAsync(W.h_active, sc + 6 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
             GCK(cudaMemcpyAsync(W.h_red, sc + 7 * P4, sizeof(double) * P4, cudaMemcpyDeviceToHost, s));
             it += 1;
@@ -458,6 +497,7 @@ static int pcg(Posterior& P, Workspace& W, double tol, int maxit, cudaStream_t s
         if (!any) break;
         if (deadline && std::chrono::steady_clock::now() > *deadline) throw Error(GMRF_E_TIMEOUT, "solve exceeded timeout_s");
     }
+    pcg_finish<T>(P, W, V, it, s);
     return it;
 }
 
@@ -721,6 +761,7 @@ static void build_solve_graph(Posterior& P, Workspace& W, SolveGraph& G, const d
     G.k_pre = capture_end();
     cudaGraph_t pbody = add_while(G.cap2, h_pcg);
     capture_begin();
+    pcg_finish<float>(P, W, V, kItersPerGraph, G.cap2);     // the body runs whole pairs of iterations
     const int ne = elem_parts(L.N);
     launch_axpy_mixed(x64, W.norms, (const float*)V.pcg[0], L.N, nblk, W.partial, G.cap2);
     launch_reduce(W.partial, ne, nblk, W.red, G.cap2);
@@ -735,7 +776,7 @@ static void build_solve_graph(Posterior& P, Workspace& W, SolveGraph& G, const d
     // PCG body: kItersPerGraph iterations, then the loop test
     GCK(cudaStreamBeginCaptureToGraph(G.cap3, pbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     capture_begin();
-    for (int k = 0; k < kItersPerGraph; ++k) pcg_iteration<float>(P, W, V, tol2, G.cap3);
+    for (int k = 0; k < kItersPerGraph; ++k) pcg_iteration<float>(P, W, V, tol2, G.cap3, k & 1);
     k_pcg_cond<<<1, 256, 0, G.cap3>>>(W.sc32, P4, G.is, o.max_inner, kItersPerGraph, h_pcg);
     note_launch();
     G.k_pcg = capture_end();
@@ -938,6 +979,12 @@ double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s)
     a.x = x; a.out = y; a.partial = W.partial;
     if (mode != M_APPLY) a.b = b;
     if (mode == M_CHEB) { a.d = d; a.dinv = L.d_dinv32; a.out2 = y2; a.c1 = 0.5f; a.c2 = 0.25f; }
+    double* ab = nullptr;
+    if (mode == M_PCG) {        // the fused iteration: direction, z and iterate in, q, p' and iterate out
+        ab = dev_alloc<double>((size_t)nblk * 8);
+        GCK(cudaMemsetAsync(ab, 0, sizeof(double) * nblk * 8, s));
+        a.d = d; a.out2 = (float*)W.v32.pcg[5]; a.out3 = b; a.alpha = ab; a.beta = ab + nblk * 4;
+    }
     launch_stencil<float>(L.geo, mode, a, s);
     cudaEvent_t e0, e1;
     GCK(cudaEventCreate(&e0));
@@ -950,13 +997,15 @@ double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s)
     GCK(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    dev_free(ab);
     return ms / iters;
 }
 
 
 template <typename T>
 static void stencil_step_t(Posterior& P, int level, int mode, int k, const double* x, const double* b, const double* d,
-                           double c0, double c1, double c2, double* out, double* out2, double* dots, cudaStream_t s) {
+                           double c0, double c1, double c2, double* out, double* out2, double* out3, double* dots,
+                           cudaStream_t s) {
     Level& L = P.levels[(size_t)level];
     const long long N = L.N;
     const int nblk = (k + 3) / 4;
@@ -965,8 +1014,15 @@ static void stencil_step_t(Posterior& P, int level, int mode, int k, const doubl
     for (int i = 0; i < k; ++i) rows[(size_t)i] = i;
     int32_t* drows = dev_alloc<int32_t>(rows.size());
     double* b64 = dev_alloc<double>(nv);
-    T* v[5];
-    for (int i = 0; i < 5; ++i) v[i] = dev_alloc<T>(nv);   // x, b, d, out, out2 (blocked)
+    T* v[6];
+    for (int i = 0; i < 6; ++i) v[i] = dev_alloc<T>(nv);   // x, b, d, out, out2, out3 (blocked)
+    double* ab = dev_alloc<double>((size_t)nblk * 8);      // PCG: alpha, beta per right-hand side
+    {
+        std::vector<double> h((size_t)nblk * 8);
+        for (int i = 0; i < nblk * 4; ++i) { h[(size_t)i] = c1; h[(size_t)(nblk * 4 + i)] = c2; }
+        GCK(cudaMemcpyAsync(ab, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s));
+        GCK(cudaStreamSynchronize(s));
+    }
     const int parts = std::max(stencil_max_grid(), march_max_grid());
     double* part = dev_alloc<double>((size_t)nblk * parts * 4);
     double* red = dev_alloc<double>((size_t)nblk * 4);
@@ -987,7 +1043,12 @@ static void stencil_step_t(Posterior& P, int level, int mode, int k, const doubl
     a.nblk = nblk;
     a.x = v[0];
     if (mode != M_APPLY) a.b = v[1];
-    if (mode == M_CHEB && d) a.d = v[2];
+    if ((mode == M_CHEB || mode == M_PCG) && d) a.d = v[2];
+    if (mode == M_PCG) {
+        a.out3 = v[5];
+        a.alpha = ab;
+        a.beta = ab + nblk * 4;
+    }
     a.dinv = sizeof(T) == 8 ? reinterpret_cast<const T*>(L.d_dinv64) : reinterpret_cast<const T*>(L.d_dinv32);
     a.out = v[3];
     a.out2 = v[4];
@@ -997,8 +1058,8 @@ static void stencil_step_t(Posterior& P, int level, int mode, int k, const doubl
     a.partial = part;
     const int nparts = launch_stencil<T>(L.geo, mode, a, s);
     launch_reduce(part, nparts, nblk, red, s);
-    double* dst[2] = {out, out2};
-    for (int i = 0; i < 2; ++i) {
+    double* dst[3] = {out, out2, out3};
+    for (int i = 0; i < 3; ++i) {
         if (!dst[i]) continue;
         launch_widen<T>(v[3 + i], b64, (long long)nv, s);
         launch_unpack(b64, dst[i], drows, N, nblk, s);
@@ -1010,16 +1071,17 @@ static void stencil_step_t(Posterior& P, int level, int mode, int k, const doubl
     for (int i = 0; i < k; ++i) dots[i] = h[(size_t)i];
     dev_free(drows);
     dev_free(b64);
-    for (int i = 0; i < 5; ++i) dev_free(v[i]);
+    for (int i = 0; i < 6; ++i) dev_free(v[i]);
+    dev_free(ab);
     dev_free(part);
     dev_free(red);
     if (aborted) throw Error(GMRF_E_CUDA, "stencil kernel: staged input tile did not arrive (bounded wait)");
 }
 
 void stencil_step(Posterior& P, int level, int prec, int mode, int k, const double* x, const double* b, const double* d,
-                  double c0, double c1, double c2, double* out, double* out2, double* dots, cudaStream_t s) {
-    if (prec == 1) stencil_step_t<double>(P, level, mode, k, x, b, d, c0, c1, c2, out, out2, dots, s);
-    else stencil_step_t<float>(P, level, mode, k, x, b, d, c0, c1, c2, out, out2, dots, s);
+                  double c0, double c1, double c2, double* out, double* out2, double* out3, double* dots, cudaStream_t s) {
+    if (prec == 1) stencil_step_t<double>(P, level, mode, k, x, b, d, c0, c1, c2, out, out2, out3, dots, s);
+    else stencil_step_t<float>(P, level, mode, k, x, b, d, c0, c1, c2, out, out2, out3, dots, s);
 }
 
 }  // namespace gmrf

@@ -64,11 +64,13 @@ template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct alignas
     static constexpr int NB = MODE == M_APPLY ? 1 : NS;
     static constexpr int ND = MODE == M_CHEB ? NS : 1;
     static constexpr int NH = MODE == M_CHEB0 ? NS : 1, PH = MODE == M_CHEB0 ? PN : 1;
+    static constexpr int NZ = MODE == M_PCG ? NS : 1, PZ = MODE == M_PCG ? PN : 1;
     // TMA destinations (p, b, d) first: every stage buffer starts on a
     // 128-byte boundary
     V4<T> p[NS][PN][KB];
     V4<T> b[NB][TN][KB];
     V4<T> d[ND][TN][KB];
+    V4<T> z[NZ][PZ][KB];       // PCG: the preconditioned residual with halo
     T dinv[ND][TN];
     V4<T> s[SN][KB];
     V4<T> sj[COL ? SN : 1][KB];
@@ -219,12 +221,14 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 const int row0 = HY > 0 ? ty0 : tt0, hrow = HY > 0 ? HY : HT;
                 const bool with_d = MODE == M_CHEB && A.d != nullptr;
                 const unsigned bytes = (unsigned)(PN * sizeof(V4<T>)) + (MODE != M_APPLY ? (unsigned)(TN * sizeof(V4<T>)) : 0u) +
-                                       (with_d ? (unsigned)(TN * sizeof(V4<T>)) : 0u);
+                                       (with_d ? (unsigned)(TN * sizeof(V4<T>)) : 0u) +
+                                       (MODE == M_PCG ? (unsigned)(PN * sizeof(V4<T>)) : 0u);
                 mbar_expect_tx(&bars[st], bytes);
                 pend |= 1u << st;
                 tma_load_3d(&S.p[st][0][0], &maps.p, 4 * (tx0 - 2), row0 - hrow, grp, &bars[st]);
                 if (MODE != M_APPLY) tma_load_3d(&S.b[MODE != M_APPLY ? st : 0][0][0], &maps.b, 4 * tx0, row0, grp, &bars[st]);
                 if (with_d) tma_load_3d(&S.d[MODE == M_CHEB ? st : 0][0][0], &maps.d, 4 * tx0, row0, grp, &bars[st]);
+                if (MODE == M_PCG) tma_load_3d(&S.z[MODE == M_PCG ? st : 0][0][0], &maps.d, 4 * (tx0 - 2), row0 - hrow, grp, &bars[st]);
             }
             // D^-1 is one value per node: its rows (4 nx bytes) need not be 16-byte
             // multiples, which a tensor map requires, so it is copied per thread
@@ -308,9 +312,41 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                         if (blk < nblk) S.p[st][e][j] = v4load(src + ((size_t)blk * N + node) * RW);
                     }
                     if (MODE == M_CHEB0) S.dinvh[MODE == M_CHEB0 ? st : 0][MODE == M_CHEB0 ? e : 0] = A.dinv[node];
+                    if (MODE == M_PCG) {
+#pragma unroll
+                        for (int j = 0; j < KB; ++j) {
+                            const int blk = cur.grp * KB + j;
+                            if (blk < nblk) S.z[MODE == M_PCG ? st : 0][MODE == M_PCG ? e : 0][j] = v4load(A.d + ((size_t)blk * N + node) * RW);
+                        }
+                    }
                 }
                 if (MODE != M_CHEB0) __syncthreads();   // the in-place step below has its own barrier
             }
+        }
+        V4<T> pold[KB];             // PCG: the previous direction at the own node
+        if (MODE == M_PCG) {        // staged p, z -> p' = z + beta p in place
+#pragma unroll
+            for (int j = 0; j < KB; ++j) pold[j] = S.p[st][pbase][j];
+            V4<T> bt[KB];
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                const int blk = min(cur.grp * KB + j, nblk - 1);
+                const double* bp = A.beta + (size_t)blk * RW;
+                bt[j] = V4<T>{(T)bp[0], (T)bp[1], (T)bp[2], (T)bp[3]};
+            }
+            __syncthreads();        // every own-node read of the old direction is done
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const int e = tid + 256 * k;
+                if (KP * 256 > PN && e >= PN) break;
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    const V4<T> pv = S.p[st][e][j], zv = S.z[MODE == M_PCG ? st : 0][MODE == M_PCG ? e : 0][j];
+                    S.p[st][e][j] = V4<T>{fma(bt[j].a, pv.a, zv.a), fma(bt[j].b, pv.b, zv.b), fma(bt[j].c, pv.c, zv.c),
+                                          fma(bt[j].d, pv.d, zv.d)};
+                }
+            }
+            __syncthreads();
         }
         if (MODE == M_CHEB0) {      // staged b -> x1 = c0 D^-1 b in place
 #pragma unroll
@@ -512,10 +548,17 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             const int blk = grp * KB + j;
             if (!own || blk >= nblk) continue;
             const size_t off = ((size_t)blk * N + node) * RW;
-            if (MODE == M_APPLY) {
+            if (MODE == M_APPLY || MODE == M_PCG) {
                 v4store(A.out + off, q[j]);
                 dacc[j][0] += pown[j].a * q[j].a; dacc[j][1] += pown[j].b * q[j].b;
                 dacc[j][2] += pown[j].c * q[j].c; dacc[j][3] += pown[j].d * q[j].d;
+                if (MODE == M_PCG) {
+                    const double* ap = A.alpha + (size_t)blk * RW;
+                    const V4<T> xo = S.b[MODE != M_APPLY ? st : 0][tid][j];
+                    v4store(A.out2 + off, pown[j]);
+                    v4store(A.out3 + off, V4<T>{fma((T)ap[0], pold[j].a, xo.a), fma((T)ap[1], pold[j].b, xo.b),
+                                                fma((T)ap[2], pold[j].c, xo.c), fma((T)ap[3], pold[j].d, xo.d)});
+                }
             } else if (MODE == M_RESID) {
                 const V4<T> r = S.b[MODE != M_APPLY ? st : 0][tid][j] - q[j];
                 v4store(A.out + off, r);
@@ -638,7 +681,7 @@ constexpr int kMaxStencilGrid = 4096;
 #endif
 
 static const char* mode_name(int m) {
-    return m == M_APPLY ? "apply" : m == M_RESID ? "resid" : m == M_CHEB ? "cheb" : "cheb0";
+    return m == M_APPLY ? "apply" : m == M_RESID ? "resid" : m == M_CHEB ? "cheb" : m == M_CHEB0 ? "cheb0" : "pcg";
 }
 template <int GEO, typename T, int MODE, int COL, int PER> static std::string stencil_name() {
     return std::string("stencil<") + (GEO == GEO_XY ? (PER ? "torus" : "xy") : "xt") + (sizeof(T) == 8 ? ",f64," : ",f32,") +
@@ -704,6 +747,7 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false)
         maps.p = tile_map<GEO, T>(MODE == M_CHEB0 ? aa.b : aa.x, aa.L, aa.nblk, true);
         if (MODE != M_APPLY) maps.b = tile_map<GEO, T>(aa.b, aa.L, aa.nblk, false);
         if (MODE == M_CHEB && aa.d != nullptr) maps.d = tile_map<GEO, T>(aa.d, aa.L, aa.nblk, false);
+        if (MODE == M_PCG) maps.d = tile_map<GEO, T>(aa.d, aa.L, aa.nblk, true);
         kern<<<(unsigned)grid, 256, smem, st>>>(aa, (int)nunits, maps);
         if (count) note_launch();
     };
@@ -723,6 +767,9 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false)
             if (args.d) t.d = (const T*)sc.zeros(vb, st);
             t.out = (T*)sc.zeros(vb, st);
             if (args.out2) t.out2 = (T*)sc.zeros(vb, st);
+            if (args.out3) t.out3 = (T*)sc.zeros(vb, st);
+            if (args.alpha) t.alpha = (const double*)sc.zeros(sizeof(double) * 4 * args.nblk, st);
+            if (args.beta) t.beta = (const double*)sc.zeros(sizeof(double) * 4 * args.nblk, st);
             if (args.partial) t.partial = (double*)sc.zeros(sizeof(double) * 4 * args.nblk * kMaxStencilGrid, st);
             std::vector<TuneChoice> cands;
             for (int k = per; k >= 1; --k) cands.push_back(TuneChoice{k, 0});
@@ -752,6 +799,7 @@ static int launch_geo(int mode, const StencilArgs<T>& a, cudaStream_t s, bool dr
     if (mode == M_APPLY) return launch_geo_mode<GEO, T, M_APPLY>(a, s, dry);
     if (mode == M_RESID) return launch_geo_mode<GEO, T, M_RESID>(a, s, dry);
     if (mode == M_CHEB0) return launch_geo_mode<GEO, T, M_CHEB0>(a, s, dry);
+    if (mode == M_PCG) return launch_geo_mode<GEO, T, M_PCG>(a, s, dry);
     return launch_geo_mode<GEO, T, M_CHEB>(a, s, dry);
 }
 

@@ -520,6 +520,7 @@ int launch_march_mode(const StencilArgs<T>& a, cudaStream_t s, bool dry = false)
 }  // namespace
 
 template <typename T> int launch_march(int mode, const StencilArgs<T>& a, cudaStream_t s) {
+    if (mode == M_PCG) throw std::runtime_error("space-time stencil: no fused conjugate-gradient mode");
     if (mode == M_APPLY) return launch_march_mode<T, M_APPLY>(a, s);
     if (mode == M_RESID) return launch_march_mode<T, M_RESID>(a, s);
     if (mode == M_CHEB0) return launch_march_mode<T, M_CHEB0>(a, s);
@@ -529,6 +530,7 @@ template int launch_march<float>(int, const StencilArgs<float>&, cudaStream_t);
 template int launch_march<double>(int, const StencilArgs<double>&, cudaStream_t);
 
 template <typename T> void march_prepare(int mode, const StencilArgs<T>& a) {
+    if (mode == M_PCG) throw std::runtime_error("space-time stencil: no fused conjugate-gradient mode");
     if (mode == M_APPLY) launch_march_mode<T, M_APPLY>(a, 0, true);
     else if (mode == M_RESID) launch_march_mode<T, M_RESID>(a, 0, true);
     else if (mode == M_CHEB0) launch_march_mode<T, M_CHEB0>(a, 0, true);

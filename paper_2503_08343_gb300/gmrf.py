@@ -305,17 +305,21 @@ class Posterior:
 
     def stencil_step(self, mode, x=None, b=None, d=None, level=0, precision=0, c0=0.0, c1=0.0, c2=0.0):
         """One launch of the fused stencil kernel (gmrf_stencil_step): mode 0
-        apply, 1 residual, 2 Chebyshev step, 3 Chebyshev from zero; inputs
-        [k][N_level].  Returns (out, out2 or None, dots)."""
+        apply, 1 residual, 2 Chebyshev step, 3 Chebyshev from zero, 4 PCG
+        iteration (x previous direction, b iterate, d preconditioned residual,
+        c1 alpha, c2 beta); inputs [k][N_level].  Returns (out, out2 or None,
+        dots), and for mode 4 (q, p', dots, updated iterate)."""
         ref = next(v for v in (x, b) if v is not None)
         k, n = np.atleast_2d(ref).shape
         prep = lambda v: None if v is None else np.ascontiguousarray(np.atleast_2d(v), dtype=np.float64)
         x, b, d = prep(x), prep(b), prep(d)
         out = np.empty((k, n))
-        out2 = np.empty((k, n)) if mode >= 2 else None
+        out2 = np.empty((2 * k if mode == 4 else k, n)) if mode >= 2 else None
         dots = np.empty(k)
         _check(load().gmrf_stencil_step(self.h, level, precision, mode, k, _ptr(x), _ptr(b), _ptr(d),
                                         c0, c1, c2, _ptr(out), _ptr(out2), _dptr(dots)))
+        if mode == 4:
+            return out, out2[:k], dots, out2[k:]
         return out, out2, dots
 
     def level_info(self):

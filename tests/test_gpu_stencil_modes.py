@@ -9,6 +9,8 @@ means, just after more iterations.  So each mode is checked here directly:
   residual          out = b - Q x
   Chebyshev         out2 = c1 d + c2 D^-1 (b - Q x),  out = x + out2
   Chebyshev-from-0  x1 = c0 D^-1 b, then the Chebyshev step with x = d = x1
+  PCG               p' = d + beta x, out = Q p', iterate b + alpha x (the
+                    conjugate-gradient iteration's vector work around the apply)
 
 with Q the level's posterior precision (Sec. 3.1: Q + A^T Q_eps A, collocation
 rows included) and D its diagonal.  The reference is computed in FP64 from the
@@ -91,7 +93,7 @@ def _bound_matrix(post):
     return (aB.T @ aB + aA.T @ sp.diags(post.rinv) @ aA).tocsr()
 
 
-def _check_modes(post_gpu, post_o, k, level, prec, seed, modes=(0, 1, 2, 3)):
+def _check_modes(post_gpu, post_o, k, level, prec, seed, modes=(0, 1, 2, 3, 4)):
     rng = np.random.default_rng(seed)
     N = post_o.Q.shape[0]
     rnd = lambda: rng.normal(size=(k, N))
@@ -132,6 +134,19 @@ def _check_modes(post_gpu, post_o, k, level, prec, seed, modes=(0, 1, 2, 3)):
         close(out, x + dn, np.abs(x) + 2 * bdn, "chebyshev x")
         assert np.all(np.abs(dots - np.sum(b * (x + dn), axis=1))
                       <= gd * np.sum(np.abs(b) * (np.abs(x) + 2 * bdn), axis=1))
+    if 4 in modes and post_o.prior["kind"] != "advdiff_st2d":     # the marching kernel has no PCG mode
+        # p' = d + beta x, q = Q p', iterate b + alpha x (x the previous
+        # direction, d the preconditioned residual)
+        al, be = (c1, c2) if prec == 1 else (float(np.float32(0.31)), float(np.float32(0.57)))
+        q, pn, dots, xn = post_gpu.stencil_step(4, x=x, b=b, d=d, level=level, precision=prec, c1=al, c2=be)
+        pref = d + be * x
+        apn = np.abs(d) + abs(be) * np.abs(x)
+        close(pn, pref, apn, "pcg direction")
+        Qp = (Q @ pref.T).T
+        Mp = (M @ apn.T).T
+        close(q, Qp, 2 * Mp, "pcg apply")
+        close(xn, b + al * x, np.abs(b) + abs(al) * np.abs(x), "pcg iterate")
+        assert np.all(np.abs(dots - np.sum(pref * Qp, axis=1)) <= gd * np.sum(2 * apn * Mp, axis=1))
     if 3 in modes:
         out, out2, dots = post_gpu.stencil_step(3, b=b, level=level, precision=prec, c0=c0, c1=c1, c2=c2)
         x1 = c0 * dinv * b
@@ -190,7 +205,7 @@ def test_stencil_modes_burgers_linearised(form):
     post.gauss_newton_step(u, d)
     orc = infer.condition(pr, ob, linearise_at=u)
     for prec in (0, 1):
-        _check_modes(post, orc, 5, 0, prec, seed=21 + prec, modes=(0, 1))
+        _check_modes(post, orc, 5, 0, prec, seed=21 + prec, modes=(0, 1, 4))
 
 
 def test_stencil_modes_full_size_matern_65_rhs():
