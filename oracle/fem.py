@@ -22,7 +22,18 @@ Readings of the paper used here (where it is silent or ambiguous):
   field at k equals the field at mirror(k), and the unknowns are the
   (n - 1)^2 nodes of the torus.  In matrix form K_t = T^T K T and
   ml_t = T^T ml with T the n^2 x (n - 1)^2 mirror map.
-* Space-time noise is white in space and lumped, w ~ N(0, tau^2 dt Ml)
+* Matern transition noise (App. A: "we choose W_s as spatial Matern noise"),
+  when prior["noise_kappa"] > 0: the spatial noise W_s is the unit-variance
+  alpha = 2 Matern field with inverse range kappa_s, Dirichlet on the same
+  boundary, so the FEM-tested noise w = int phi W_s of the interior has
+  covariance tau^2 dt Ml Sigma_s Ml with Sigma_s^-1 = tau_s^2 K_s Ml^-1 K_s
+  (K_s = kappa_s^2 Ml + S on the interior, tau_s = matern_tau_unit(kappa_s)).
+  The root of its precision is (tau_s / (tau sqrt dt)) Ml^-1/2 K_s Ml^-1, so
+  the interior rows of the level blocks are T_K times the white-noise rows,
+  T_K = tau_s Ml^-1/2 K_s Ml^-1/2 (symmetric; identity on the boundary rows
+  and on the initial level).  prior["decay"] (default 0) scales the previous
+  level by rho = 1 - decay: G u^k = rho Ml u^(k-1) + w (an AR(1) in time).
+* Space-time noise is otherwise white in space and lumped, w ~ N(0, tau^2 dt Ml)
   (App. A with Sigma = M^-1), so the whole prior scales as tau^-2.  The
   initial block is a Matern alpha = 2 precision with kappa0, normalised to
   unit marginal variance (tau0).
@@ -244,14 +255,16 @@ def prior_root(prior: dict) -> sp.csr_matrix:
     tau0 = matern_tau_unit(prior["kappa0"], dim)
     K0c = constrain(prior["kappa0"] ** 2 * sp.diags(ml) + S, sbnd)
     Gc = constrain(sp.diags(ml) + dt * (prior["nu"] * S + Badv), sbnd)
+    rho = 1.0 - prior.get("decay", 0.0)
     Mlc = sp.diags(np.where(sbnd, 0.0, ml))
     d0 = np.where(sbnd, inv_eps, (tau0 / tau) / np.sqrt(ml))
     dk = np.where(sbnd, inv_eps, 1.0 / (tau * math.sqrt(dt) * np.sqrt(ml)))
+    TK = noise_transform(prior)
     blocks = [[None] * nt for _ in range(nt)]
     blocks[0][0] = sp.diags(d0) @ K0c
     for k in range(1, nt):
-        blocks[k][k] = sp.diags(dk) @ Gc
-        blocks[k][k - 1] = -(sp.diags(dk) @ Mlc)
+        blocks[k][k] = TK @ sp.diags(dk) @ Gc
+        blocks[k][k - 1] = -rho * (TK @ sp.diags(dk) @ Mlc)
     for k in range(nt):
         for l in range(nt):
             if blocks[k][l] is None and abs(k - l) > 1:
@@ -260,6 +273,21 @@ def prior_root(prior: dict) -> sp.csr_matrix:
                 blocks[k][l] = sp.csr_matrix((Ns, Ns))
     B = sp.bmat(blocks, format="csr")
     return B
+
+
+def noise_transform(prior: dict) -> sp.csr_matrix:
+    """T_K of the Matern transition noise (see the module docstring) on one
+    time level: tau_s Ml^-1/2 K_s Ml^-1/2 on the interior nodes, identity on
+    the boundary; the identity for white noise."""
+    S, ml, _, dim = spatial_mesh(prior)
+    ks = prior.get("noise_kappa", 0.0)
+    if not ks > 0.0:
+        return sp.identity(len(ml), format="csr")
+    sbnd = spatial_boundary(prior)
+    keep = sp.diags((~sbnd).astype(float))
+    Ks = keep @ (ks ** 2 * sp.diags(ml) + S) @ keep            # K_s on the interior block
+    r = 1.0 / np.sqrt(ml)
+    return (matern_tau_unit(ks, dim) * sp.diags(r) @ Ks @ sp.diags(r) + sp.diags(sbnd.astype(float))).tocsr()
 
 
 def _zero_boundary(X: sp.spmatrix, bnd: np.ndarray) -> sp.csr_matrix:
@@ -344,6 +372,13 @@ def prior_root_derivative(prior: dict, name: str) -> sp.csr_matrix:
         dG = dt * (Bx if name == "c" else S)
         for k in range(1, nt):
             blocks[k][k] = sp.diags(dk) @ _zero_boundary(dG, sbnd)
+    TK = noise_transform(prior)
+    rho = 1.0 - prior.get("decay", 0.0)
+    for k in range(1, nt):          # the transition rows carry T_K (and the decay on the previous level)
+        if blocks[k][k] is not None:
+            blocks[k][k] = TK @ blocks[k][k]
+        if blocks[k][k - 1] is not None:
+            blocks[k][k - 1] = rho * (TK @ blocks[k][k - 1])
     for k in range(nt):
         for l in range(nt):
             if blocks[k][l] is None and (k == l or k == l + 1):
