@@ -45,6 +45,9 @@ struct StencilArgs {
 // Dot partials written to `partial` as [nblk][grid][4] (APPLY x.Qx, RESID
 // |r|^2, CHEB b.x_new); returns the grid size, i.e. the partial count per block.
 template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s);
+// the pointers a mode reads and writes are all set (host check before every
+// launch; throws std::runtime_error naming the missing one)
+template <typename T> void stencil_check_args(int mode, int col, const StencilArgs<T>& a);
 // 2D space x time: the 2.5D-blocked kernel of stencil_march.cu (called by launch_stencil)
 template <typename T> int launch_march(int mode, const StencilArgs<T>& a, cudaStream_t s);
 int stencil_max_grid();

@@ -959,7 +959,11 @@ SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64,
     return st;
 }
 
-double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s) {
+double time_stencil(Posterior& P, int kernel, int nblk, int iters, cudaStream_t s) {
+    // kernel ids of gmrf_time_stencil: 0 apply, 1 residual, 2 Chebyshev, 3 PCG
+    const int mode = kernel == 3 ? (int)M_PCG : kernel;
+    if (mode != M_APPLY && mode != M_RESID && mode != M_CHEB && mode != M_PCG)
+        throw Error(GMRF_E_INVALID, "time_stencil: unknown kernel");
     Workspace& W = workspace(P, nblk);
     alloc_vecs<float>(P, W, W.v32);
     Level& L = P.levels[0];

@@ -803,7 +803,29 @@ static int launch_geo(int mode, const StencilArgs<T>& a, cudaStream_t s, bool dr
     return launch_geo_mode<GEO, T, M_CHEB>(a, s, dry);
 }
 
+template <typename T> void stencil_check_args(int mode, int col, const StencilArgs<T>& a) {
+    auto need = [&](const void* p, const char* what) {
+        if (p == nullptr) throw std::runtime_error(std::string("stencil launch: ") + what + " is required for mode " + mode_name(mode));
+    };
+    if (mode != M_APPLY && mode != M_RESID && mode != M_CHEB && mode != M_CHEB0 && mode != M_PCG)
+        throw std::runtime_error("stencil launch: unknown mode");
+    if (a.nblk <= 0 || a.L.N <= 0) throw std::runtime_error("stencil launch: empty batch or level");
+    need(a.out, "out");
+    if (mode != M_CHEB0) need(a.x, "x");
+    if (mode != M_APPLY) need(a.b, "b");
+    if (mode == M_CHEB || mode == M_CHEB0) { need(a.dinv, "dinv"); need(a.out2, "out2"); }
+    if (mode == M_PCG) {
+        need(a.d, "d (z)"); need(a.out2, "out2 (p')"); need(a.out3, "out3 (iterate)");
+        need(a.alpha, "alpha"); need(a.beta, "beta");
+    }
+    if (col == 2 || col == 4) need(a.L.mu, "the linearisation point");
+    if (a.L.ocap > 0) { need(a.L.omap, "observation map"); need(a.L.oent, "observation entries"); }
+}
+template void stencil_check_args<float>(int, int, const StencilArgs<float>&);
+template void stencil_check_args<double>(int, int, const StencilArgs<double>&);
+
 template <typename T> int launch_stencil(int geo, int mode, const StencilArgs<T>& a, cudaStream_t s) {
+    stencil_check_args<T>(mode, a.L.col.kind, a);
     if (geo == GEO_XY) return launch_geo<T, GEO_XY>(mode, a, s);
     if (geo == GEO_XT) return launch_geo<T, GEO_XT>(mode, a, s);
     return launch_march<T>(mode, a, s);
