@@ -101,6 +101,16 @@ typedef struct gmrf_prior_desc {
     double kappa0;             /* space-time: Matern kappa of the initial level */
     double eps2;               /* Dirichlet boundary variance (App. B "M_kk = eps^2") */
     int32_t bc;                /* gmrf_boundary (0: Dirichlet) */
+    /* Space-time priors (App. A): transition G u^k = (1 - decay) Ml u^(k-1) + w.
+     * noise_kappa > 0 (GMRF_ADVDIFF_ST_1D only): the spatial noise W_s is the
+     * unit-variance alpha = 2 Matern field of inverse range noise_kappa
+     * (Dirichlet on the same boundary), so w ~ N(0, tau^2 dt Ml Sigma_s Ml),
+     * Sigma_s^-1 = tau_s^2 K_s Ml^-1 K_s, K_s = noise_kappa^2 Ml + S; B's
+     * transition rows become T_K B_w, T_K = tau_s Ml^-1/2 K_s Ml^-1/2 on the
+     * interior.  noise_kappa = 0: white spatial noise, w ~ N(0, tau^2 dt Ml).
+     * decay in [0, 1) (both space-time kinds): an AR(1) in time (0: none). */
+    double noise_kappa;
+    double decay;
 } gmrf_prior_desc;
 
 /* Observations (Sec. 3.1).  All pointers are host memory, read during the call.

@@ -145,6 +145,9 @@ gmrf_status gmrf_build_prior(const gmrf_prior_desc* desc, void* stream, gmrf_pri
         require((long long)d.nx * d.ny * d.nt < (1LL << 31), "grid too large for 32-bit node indices");
         require(d.nx < 32768 && d.ny < 32768 && d.nt < 32768, "axes are limited to 32767 nodes");
         require(d.bc == GMRF_BC_DIRICHLET || d.bc == GMRF_BC_PERIODIC, "unknown boundary");
+        require(d.noise_kappa >= 0.0 && (d.noise_kappa == 0.0 || d.kind == GMRF_ADVDIFF_ST_1D),
+                "Matern transition noise: the 1D space-time prior");
+        require(d.decay >= 0.0 && d.decay < 1.0 && (d.decay == 0.0 || st), "decay: in [0, 1), space-time priors");
         if (d.bc == GMRF_BC_PERIODIC)
             require(!st && d.nx >= 5 && d.ny >= 5, "periodic boundary: spatial priors with at least 5 nodes per axis");
         gmrf_prior* p = new gmrf_prior();
@@ -899,6 +902,7 @@ gmrf_status gmrf_loglik_grad_ex(gmrf_posterior* post, int32_t nprobes, uint64_t 
         require(post && grad && nprobes >= 1, "bad argument");
         Posterior& P = post->impl;
         require(P.nic == 0 && P.colloc_kind == 0, "gmrf_loglik_grad is defined for point data only");
+        require(!P.levels[0].noise, "gmrf_loglik_grad: white transition noise only");
         enter(post->prior);
         const gmrf_solve_opts o = resolve_opts(opts);
         const auto t0 = std::chrono::steady_clock::now();

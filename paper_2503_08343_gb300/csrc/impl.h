@@ -138,11 +138,15 @@ struct LevelView {
     int ostride;       // bytes per tile of oent (multiple of 16)
     int obs_direct;    // 1: read the tables from global memory instead of staging them (set per launch)
     int periodic;      // 1: the (x, y) torus of a periodic prior (no Dirichlet nodes, neighbours wrap)
+    int noise;         // 1: Matern transition noise, B = T_K B_w (1D space-time)
+    T tk_c, tk_o;      // T_K between interior rows of levels >= 1: diagonal, x neighbours
 };
 
 struct Level {
     int geo = 0;
     int periodic = 0;  // (x, y) torus: nx, ny count the torus nodes, h = (hi - lo) / nx
+    int noise = 0;     // Matern transition noise (1D space-time): B = T_K B_w
+    double tk_c = 1.0, tk_o = 0.0;
     int nx = 1, ny = 1, nt = 1;
     long long N = 0;
     double hx = 0, hy = 0, dt = 0;

@@ -159,6 +159,9 @@ template <typename T> LevelView<T> Level::view() const {
     v.ocap = d_omap ? ocap : 0;
     v.obs_direct = 0;
     v.periodic = periodic;
+    v.noise = noise;
+    v.tk_c = (T)tk_c;
+    v.tk_o = (T)tk_o;
     return v;
 }
 
@@ -782,6 +785,10 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
     constexpr int SX = TX + 2, SY = TY + HY, ST = TT + HT;
     __shared__ V4<double> sz[ST][SY][SX];       // z1 on the rows touching the tile
     __shared__ V4<double> sq[TT][TY][TX];
+    // Matern transition noise: B^T z1 = B_w^T (T_K z1), z1 staged on rows two
+    // past the tile first
+    constexpr int SXN = GEO == GEO_XT ? SX + 2 : 1;
+    __shared__ V4<double> zw[GEO == GEO_XT ? ST : 1][SXN];
     const int nx = L.nx, ny = L.ny, nt = L.nt;
     const long long N = L.N;
     const int tile = blockIdx.x, blk = blockIdx.y, tid = threadIdx.x;
@@ -793,6 +800,30 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
 #pragma unroll
     for (int c = 0; c < 4; ++c) sid[c] = slot_sample[blk * RW + c];
 
+    if (GEO == GEO_XT && L.noise) {
+        for (int e = tid; e < SXN * ST; e += 256) {
+            const int sx = e % SXN, st = e / SXN;
+            const int rx = tx0 - 2 + sx, rt = tt0 + st;
+            V4<double> z = v4zero<double>();
+            if (z1 != nullptr && rx >= 0 && rx < nx && rt < nt) z = v4load(z1 + ((size_t)blk * N + (long long)rt * nx + rx) * RW);
+            zw[GEO == GEO_XT ? st : 0][GEO == GEO_XT ? sx : 0] = z;
+        }
+        __syncthreads();
+        const double tc = L.tk_c, to = L.tk_o;
+        for (int e = tid; e < SX * ST; e += 256) {
+            const int sx = e % SX, st = e / SX;
+            const int rx = tx0 - 1 + sx, rt = tt0 + st;
+            const V4<double>* row = &zw[GEO == GEO_XT ? st : 0][0];
+            V4<double> v = row[sx + 1];
+            if (rt >= 1 && rt < nt && rx >= 1 && rx <= nx - 2) {       // interior rows of levels >= 1
+                V4<double> w = tc * v;
+                if (rx - 1 >= 1) w = fma4(to, row[sx], w);
+                if (rx + 1 <= nx - 2) w = fma4(to, row[sx + 2], w);
+                v = w;
+            }
+            sz[st][0][sx] = v;
+        }
+    } else
     for (int e = tid; e < SX * SY * ST; e += 256) {
         const int sx = e % SX, sy = (e / SX) % SY, st = e / (SX * SY);
         int rx = tx0 - 1 + sx, ry = ty0 - HYS + sy;
@@ -1057,6 +1088,30 @@ __global__ void k_diag(const LevelView<T> L, double* __restrict__ diag) {
     const bool per = L.periodic != 0;       // torus: every row is an interior row
     if (!per && is_dirichlet(x, y, nx, ny)) {
         d = (double)L.inv_eps2;
+    } else if (L.noise) {
+        // B = T_K B_w (1D space-time): column n of B_w has rows (x-1..x+1, t)
+        // and (x, t+1); T_K mixes interior rows of levels >= 1 with their x
+        // neighbours, so the column of B lives on rows x-2..x+2 of level t and
+        // x-1..x+1 of level t+1
+        auto bw = [&](int rx, int rt) -> double {      // B_w[(rx, rt), (x, t)]
+            if (rx < 1 || rx > nx - 2 || rt < 0 || rt >= nt) return 0.0;
+            const int cls = (nt > 1 && rt == 0) ? 1 : 0;
+            for (int o = 0; o < NTAP; ++o)
+                if (rx + tap_dx(o) == x && tap_dy(o) == 0 && rt + tap_dt(o) == t && x >= 1 && x <= nx - 2)
+                    return (double)L.cf[cls][o];
+            return 0.0;
+        };
+        for (int rt = t; rt <= t + 1 && rt < nt; ++rt)
+            for (int rx = x - 2; rx <= x + 2; ++rx) {
+                if (rx < 0 || rx >= nx) continue;
+                double v = bw(rx, rt);
+                if (rt >= 1 && rx >= 1 && rx <= nx - 2) {
+                    v = L.tk_c * v;
+                    if (rx - 1 >= 1) v += L.tk_o * bw(rx - 1, rt);
+                    if (rx + 1 <= nx - 2) v += L.tk_o * bw(rx + 1, rt);
+                }
+                d += v * v;
+            }
     } else {
         for (int o = 0; o < NTAP; ++o) {
             const int rx = x - tap_dx(o), ry = y - tap_dy(o), rt = t - tap_dt(o);

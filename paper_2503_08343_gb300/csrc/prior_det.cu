@@ -372,6 +372,18 @@ PriorDet prior_logdet(const gmrf_prior_desc& d, const Level& F) {
         const double nk = (double)(F.nt - 1);
         logdetB += b0.logabsdet + nk * b1.logabsdet;
         for (int q = 0; q < 4; ++q) tr[q] = b0.tr[(size_t)q] + nk * b1.tr[(size_t)q];
+        if (F.noise) {
+            // B = T_K B_w on the transition levels: + log|det T_K| per level
+            // (interior tridiagonal Toeplitz, DST eigenvalues); T_K does not
+            // depend on the parameters, so the traces are those of B_w
+            double lt = 0.0;
+            for (int j = 1; j <= mx; ++j) {
+                const double lam = F.tk_c + 2.0 * F.tk_o * std::cos(kPi * j / (mx + 1));
+                if (!(lam != 0.0)) throw Error(GMRF_E_NOT_SPD, "noise transform is singular");
+                lt += std::log(std::fabs(lam));
+            }
+            logdetB += nk * lt;
+        }
     }
     out.logdet = 2.0 * logdetB;
     for (int q = 0; q < 4; ++q) out.tr[q] = tr[q];

@@ -399,7 +399,7 @@ __global__ void k_scale_cast_df(const double* __restrict__ r, const double* __re
 
 }  // namespace
 
-bool resid_df_applicable(const Level& L) { return (L.geo == GEO_XY || L.geo == GEO_XT) && L.col.kind == 0; }
+bool resid_df_applicable(const Level& L) { return (L.geo == GEO_XY || L.geo == GEO_XT) && L.col.kind == 0 && !L.noise; }
 
 int launch_resid_df(const Level& Lv, const double* x, const double* b, double* out, const double* rweight,
                     double* partial, int nblk, cudaStream_t s) {

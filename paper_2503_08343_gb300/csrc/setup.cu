@@ -75,7 +75,16 @@ void level_coefficients(const gmrf_prior_desc& d, Level& L) {
         const double dt = L.dt;
         const double dk = 1.0 / (d.tau * std::sqrt(dt) * std::sqrt(o.M));
         for (int t = 0; t < NTAP; ++t) L.cd[0][t] = dk * (dt * (d.nu * o.S[t] + o.A[t]) + (t == 0 ? o.M : 0.0));
-        L.cd[0][7] = -dk * o.M;
+        L.cd[0][7] = -(1.0 - d.decay) * dk * o.M;        // AR(1) decay of the previous level
+        // Matern transition noise (1D): T_K = tau_s Ml^-1/2 K_s Ml^-1/2 with
+        // K_s = kappa_s^2 Ml + S, lumped Ml = h: tau_s (kappa_s^2 + 2/h^2) on the
+        // diagonal, -tau_s / h^2 to each x neighbour
+        L.noise = d.noise_kappa > 0.0 ? 1 : 0;
+        if (L.noise) {
+            const double ts = matern_tau_unit(d.noise_kappa, dim);
+            L.tk_c = ts * (d.noise_kappa * d.noise_kappa + 2.0 / (L.hx * L.hx));
+            L.tk_o = -ts / (L.hx * L.hx);
+        }
         const double d0 = (matern_tau_unit(d.kappa0, dim) / d.tau) / std::sqrt(o.M);
         for (int t = 0; t < NTAP; ++t) L.cd[1][t] = d0 * (o.S[t] + (t == 0 ? d.kappa0 * d.kappa0 * o.M : 0.0));
         L.cd[1][7] = 0.0;
@@ -498,12 +507,12 @@ std::vector<double> dense_operator(const Level& L, const double* mu) {
     auto dir = [&](int x, int y) {
         return !L.periodic && (x == 0 || x == L.nx - 1 || (L.ny > 1 && (y == 0 || y == L.ny - 1)));
     };
-    std::vector<std::pair<long long, double>> row;
+    std::vector<std::vector<std::pair<long long, double>>> rows((size_t)n);
     for (long long r = 0; r < n; ++r) {
         const int x = (int)(r % L.nx);
         const long long q = r / L.nx;
         const int y = (int)(q % L.ny), t = (int)(q / L.ny);
-        row.clear();
+        std::vector<std::pair<long long, double>>& row = rows[(size_t)r];
         if (dir(x, y)) {
             row.push_back({r, L.inv_eps});
         } else {
@@ -522,9 +531,23 @@ std::vector<double> dense_operator(const Level& L, const double* mu) {
                 row.push_back({((long long)tt * L.ny + yy) * L.nx + xx, c});
             }
         }
+    }
+    if (L.noise) {          // B = T_K B_w: interior rows of levels >= 1 mix with their x neighbours
+        std::vector<std::vector<std::pair<long long, double>>> out = rows;
+        for (long long r = 0; r < n; ++r) {
+            const int x = (int)(r % L.nx), t = (int)(r / ((long long)L.nx * L.ny));
+            if (t < 1 || x < 1 || x > L.nx - 2) continue;
+            std::map<long long, double> acc;
+            for (auto& e : rows[(size_t)r]) acc[e.first] += L.tk_c * e.second;
+            if (x - 1 >= 1) for (auto& e : rows[(size_t)(r - 1)]) acc[e.first] += L.tk_o * e.second;
+            if (x + 1 <= L.nx - 2) for (auto& e : rows[(size_t)(r + 1)]) acc[e.first] += L.tk_o * e.second;
+            out[(size_t)r].assign(acc.begin(), acc.end());
+        }
+        rows.swap(out);
+    }
+    for (auto& row : rows)
         for (auto& a : row)
             for (auto& b : row) Q[(size_t)(a.first * n + b.first)] += a.second * b.second;
-    }
     for (const ObsRow& o : L.h_obs)
         for (int a = 0; a < o.nn; ++a)
             for (int b = 0; b < o.nn; ++b) Q[(size_t)o.node[a] * n + o.node[b]] += o.rinv * o.wd[a] * o.wd[b];

@@ -55,12 +55,18 @@ __device__ __forceinline__ void jcoef(const Colloc& c, T mu_c, T mu_l, T mu_r, T
 // (TMA destinations first, on 128-byte boundaries), the s tile and the
 // per-node scalars.
 
-template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct alignas(128) StencilSmem {
+// NOISE (1D space-time with Matern transition noise): B = T_K B_w with T_K a
+// three-point operator per level, so the input halo is 4 in x, B_w p is formed
+// on rows three past the tile (ring 3), T_K twice brings it back to ring 1.
+template <int GEO, typename T, int MODE, int COL, int NS, int KB, int NOISE = 0> struct alignas(128) StencilSmem {
     using G = Geo<GEO>;
     static constexpr int TX = G::TX, TY = G::TY, TT = G::TT, HY = G::HY, HT = G::HT;
-    static constexpr int PX = TX + 4, PY = TY + 2 * HY, PT = TT + 2 * HT;
+    static constexpr int HX = NOISE ? 4 : 2, SR = NOISE ? 3 : 1;
+    static constexpr int PX = TX + 2 * HX, PY = TY + 2 * HY, PT = TT + 2 * HT;
     static constexpr int SX = TX + 2, SY = TY + HY, ST = TT + HT;
+    static constexpr int SXW = TX + 2 * SR, SX2 = TX + 4;
     static constexpr int TN = TX * TY * TT, PN = PX * PY * PT, SN = SX * SY * ST;
+    static constexpr int SNW = SXW * SY * ST, SN2 = SX2 * SY * ST;
     static constexpr int NB = MODE == M_APPLY ? 1 : NS;
     static constexpr int ND = MODE == M_CHEB ? NS : 1;
     static constexpr int NH = MODE == M_CHEB0 ? NS : 1, PH = MODE == M_CHEB0 ? PN : 1;
@@ -73,6 +79,8 @@ template <int GEO, typename T, int MODE, int COL, int NS, int KB> struct alignas
     V4<T> z[NZ][PZ][KB];       // PCG: the preconditioned residual with halo
     T dinv[ND][TN];
     V4<T> s[SN][KB];
+    V4<T> sw[NOISE ? SNW : 1][KB];     // NOISE: B_w p on ring 3
+    V4<T> s2[NOISE ? SN2 : 1][KB];     // NOISE: T_K B_w p on ring 2
     V4<T> sj[COL ? SN : 1][KB];
     V4<T> qobs[TN][KB];        // A^T R^-1 A p at the tile's observed nodes
     T dinvh[NH][PH];           // CHEB0: D^-1 on the staged nodes
@@ -132,15 +140,17 @@ constexpr int kMbarSpinCap = 1 << 22;
 // up without polling); a test hook
 __device__ int g_stencil_wait_cap = 0;
 
-template <int GEO, typename T, int MODE, int COL, int NS, int KB, int PER>
+template <int GEO, typename T, int MODE, int COL, int NS, int KB, int PER, int NOISE>
 __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nunits, const __grid_constant__ StencilMaps maps) {
-    using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
+    using SM = StencilSmem<GEO, T, MODE, COL, NS, KB, NOISE>;
     constexpr int TX = SM::TX, TY = SM::TY, TT = SM::TT, HY = SM::HY, HT = SM::HT;
     constexpr int PX = SM::PX, PY = SM::PY, PN = SM::PN, TN = SM::TN;
     constexpr int SX = SM::SX, SY = SM::SY, SN = SM::SN;
+    constexpr int HX = SM::HX, SR = SM::SR, SXW = SM::SXW, SNW = SM::SNW, SX2 = SM::SX2, SN2 = SM::SN2;
     constexpr int HYS = HY / 2;
     constexpr int OC = ObsStencil<GEO>::OC;
-    constexpr int KP = (PN + 255) / 256, KS = (SN + 255) / 256;
+    constexpr int KP = (PN + 255) / 256, KS = (SNW + 255) / 256;
+    static_assert(!NOISE || (GEO == GEO_XT && HY == 0 && SY == 1), "Matern transition noise: 1D space-time tiles");
     static_assert(SN >= TN, "s tile covers the node tile");
     static_assert(NS >= 2, "the copy pipeline needs two stages");
     static_assert(KB == 1, "the input tile is one TMA box of one block");
@@ -188,18 +198,22 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     for (int k = 0; k < KP; ++k) {
         const int e = tid + 256 * k;
         const int px = e % PX, py = (e / PX) % PY, pt = e / (PX * PY);
-        p_dx[k] = px - 2; p_dy[k] = py - HY; p_dt[k] = pt - HT;
+        p_dx[k] = px - HX; p_dy[k] = py - HY; p_dt[k] = pt - HT;
         p_rel[k] = (p_dt[k] * ny + p_dy[k]) * nx + p_dx[k];
     }
-    int s_dx[KS], s_dy[KS], s_dt[KS], s_base[KS];
+    // s items: rows of B_w p on ring SR around the tile (s_e1: the item's
+    // index in the ring-1 layout, -1 outside it)
+    int s_dx[KS], s_dy[KS], s_dt[KS], s_base[KS], s_e1[KS];
 #pragma unroll
     for (int k = 0; k < KS; ++k) {
         const int e = tid + 256 * k;
-        const int sx = e % SX, sy = (e / SX) % SY, stt = e / (SX * SY);
-        s_dx[k] = sx - 1; s_dy[k] = sy - HYS; s_dt[k] = stt;
-        s_base[k] = ((stt + HT) * PY + (sy + HY - HYS)) * PX + (sx + 1);
+        const int sx = e % SXW, sy = (e / SXW) % SY, stt = e / (SXW * SY);
+        s_dx[k] = sx - SR; s_dy[k] = sy - HYS; s_dt[k] = stt;
+        s_base[k] = ((stt + HT) * PY + (sy + HY - HYS)) * PX + (sx - SR + HX);
+        const int x1 = sx - (SR - 1);
+        s_e1[k] = (x1 >= 0 && x1 < SX) ? (stt * SY + sy) * SX + x1 : -1;
     }
-    const int pbase = ((lt + HT) * PY + (ly + HY)) * PX + (lx + 2);
+    const int pbase = ((lt + HT) * PY + (ly + HY)) * PX + (lx + HX);
     const int sbase = (lt * SY + (ly + HYS)) * SX + (lx + 1);
 
     if (A.partial != nullptr)
@@ -225,10 +239,10 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                                        (MODE == M_PCG ? (unsigned)(PN * sizeof(V4<T>)) : 0u);
                 mbar_expect_tx(&bars[st], bytes);
                 pend |= 1u << st;
-                tma_load_3d(&S.p[st][0][0], &maps.p, 4 * (tx0 - 2), row0 - hrow, grp, &bars[st]);
+                tma_load_3d(&S.p[st][0][0], &maps.p, 4 * (tx0 - HX), row0 - hrow, grp, &bars[st]);
                 if (MODE != M_APPLY) tma_load_3d(&S.b[MODE != M_APPLY ? st : 0][0][0], &maps.b, 4 * tx0, row0, grp, &bars[st]);
                 if (with_d) tma_load_3d(&S.d[MODE == M_CHEB ? st : 0][0][0], &maps.d, 4 * tx0, row0, grp, &bars[st]);
-                if (MODE == M_PCG) tma_load_3d(&S.z[MODE == M_PCG ? st : 0][0][0], &maps.d, 4 * (tx0 - 2), row0 - hrow, grp, &bars[st]);
+                if (MODE == M_PCG) tma_load_3d(&S.z[MODE == M_PCG ? st : 0][0][0], &maps.d, 4 * (tx0 - HX), row0 - hrow, grp, &bars[st]);
             }
             // D^-1 is one value per node: its rows (4 nx bytes) need not be 16-byte
             // multiples, which a tensor map requires, so it is copied per thread
@@ -366,13 +380,14 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             return (COL == 2 || COL == 4) ? S.mu[(COL == 2 || COL == 4) ? st : 0][(COL == 2 || COL == 4) ? e : 0] : T(0);
         };
 
-        // s = B p on the rows of the tile plus a one-node ring.  Dirichlet rows
-        // are zero; rows next to the boundary skip the Dirichlet columns
-        // (App. B column elimination), all other rows take every tap.
+        // s = B p on the rows of the tile plus a one-node ring (NOISE: B_w p on
+        // ring 3).  Dirichlet rows are zero; rows next to the boundary skip the
+        // Dirichlet columns (App. B column elimination), all other rows take
+        // every tap.
 #pragma unroll
         for (int k = 0; k < KS; ++k) {
             const int e = tid + 256 * k;
-            if (KS * 256 > SN && e >= SN) break;
+            if (KS * 256 > SNW && e >= SNW) break;
             const int rx = tx0 + s_dx[k], ry = ty0 + s_dy[k], rt = tt0 + s_dt[k];
             const bool inrow = rx >= rlx && rx < rhx && ry >= rly && ry < rhy && rt < nt;
             const int base = s_base[k];
@@ -398,7 +413,12 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 }
             }
 #pragma unroll
-            for (int j = 0; j < KB; ++j) S.s[e][j] = sv[j];
+            for (int j = 0; j < KB; ++j) {
+                if (NOISE) S.sw[NOISE ? e : 0][j] = sv[j];
+                else S.s[e][j] = sv[j];
+            }
+            const int e1 = s_e1[k];        // collocation rows on ring 1 only
+            if (COL && e1 < 0) continue;
             if (COL == 1 || COL == 2) {
 #pragma unroll
                 for (int j = 0; j < KB; ++j) {
@@ -411,7 +431,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                         sjv = fma4(cR, sp[base + 1][j], sjv);
                         sjv = fma4((T)(-L.col.inv_dt), sp[base - PY * PX][j], sjv);
                     }
-                    S.sj[COL ? e : 0][j] = sjv;
+                    S.sj[COL ? e1 : 0][j] = sjv;
                 }
             } else if (COL >= 3) {
                 // FEM Crank-Nicolson row: taps x-1, x, x+1 on this level and the one before
@@ -429,7 +449,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                             sjv = fma4(fem_cn_fixed<T>(L.col, e3, T(-1)) + dp[e3], sp[base - TP + e3 - 1][j], sjv);
                         }
                     }
-                    S.sj[COL ? e : 0][j] = sjv;
+                    S.sj[COL ? e1 : 0][j] = sjv;
                 }
             }
         }
@@ -455,7 +475,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             const int nd = reinterpret_cast<const int16_t*>(oent_t + (size_t)L.ocap * OC * sizeof(T))[oe];
             if (nd >= 0) {
                 const int ex = nd % TX, ey = (nd / TX) % TY, et = nd / (TX * TY);
-                const int pb = ((et + HT) * PY + (ey + HY)) * PX + (ex + 2);
+                const int pb = ((et + HT) * PY + (ey + HY)) * PX + (ex + HX);
                 const T* c = reinterpret_cast<const T*>(oent_t) + oe * OC;
                 V4<T> v[KB];
 #pragma unroll
@@ -471,6 +491,34 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
             }
         }
         __syncthreads();
+        if (NOISE) {
+            // s <- T_K T_K s: T_K = tk_c on the diagonal and tk_o to the two
+            // x neighbours, between interior rows of levels t >= 1 (identity
+            // on the boundary rows and the initial level)
+            const T tc = (T)L.tk_c, to = (T)L.tk_o;
+            auto tk = [&](const V4<T>* src, int i, int rx, int rt) -> V4<T> {
+                V4<T> v = src[i];
+                if (rt >= 1 && rt < nt && rx >= 1 && rx <= nx - 2) {
+                    V4<T> w = tc * v;
+                    if (rx - 1 >= 1) w = fma4(to, src[i - 1], w);
+                    if (rx + 1 <= nx - 2) w = fma4(to, src[i + 1], w);
+                    v = w;
+                }
+                return v;
+            };
+            for (int e = tid; e < (NOISE ? SN2 : 1); e += 256) {       // ring 3 -> ring 2
+                const int sx = e % SX2, stt = e / SX2;
+                const int rx = tx0 - 2 + sx, rt = tt0 + stt;
+                S.s2[NOISE ? e : 0][0] = tk(reinterpret_cast<const V4<T>*>(S.sw), stt * SXW + sx + 1, rx, rt);
+            }
+            __syncthreads();
+            for (int e = tid; e < SN; e += 256) {                       // ring 2 -> ring 1
+                const int sx = e % SX, stt = e / SX;
+                const int rx = tx0 - 1 + sx, rt = tt0 + stt;
+                S.s[e][0] = tk(reinterpret_cast<const V4<T>*>(S.s2), stt * SX2 + sx + 1, rx, rt);
+            }
+            __syncthreads();
+        }
 
         // q = B^T s (+ J^T Q_eps sj + A^T R^-1 A p) at the thread's own node
         const int gx = tx0 + lx, gy = ty0 + ly, gt = tt0 + lt;
@@ -632,11 +680,11 @@ void encode_tensor_map(CUtensorMap* m, bool f64, int rank, const void* base, con
     if (r != CUDA_SUCCESS) throw std::runtime_error("tensor map of a stencil operand: error " + std::to_string((int)r));
 }
 
-template <int GEO, typename T>
+template <int GEO, typename T, int NOISE = 0>
 static CUtensorMap tile_map(const T* v, const LevelView<T>& L, int nblk, bool halo) {
     using G = Geo<GEO>;
     static_assert(G::HY == 0 || G::TT == 1, "2D tiles have one time level");
-    constexpr int PX = G::TX + 4, PR = G::HY > 0 ? G::TY + 2 * G::HY : G::TT + 2 * G::HT;
+    constexpr int PX = G::TX + (NOISE ? 8 : 4), PR = G::HY > 0 ? G::TY + 2 * G::HY : G::TT + 2 * G::HT;
     constexpr int TR = G::HY > 0 ? G::TY : G::TT;
     const cuuint64_t rows = G::HY > 0 ? (cuuint64_t)L.ny : (cuuint64_t)L.nt;
     const cuuint64_t dims[3] = {(cuuint64_t)4 * L.nx, rows, (cuuint64_t)nblk};
@@ -690,12 +738,12 @@ template <int GEO, typename T, int MODE, int COL, int PER> static std::string st
 
 // dry: only the one-time set-up of this instantiation (function attributes,
 // occupancy query, which also loads the kernel's code), no launch
-template <int GEO, typename T, int MODE, int COL, int PER>
+template <int GEO, typename T, int MODE, int COL, int PER, int NOISE = 0>
 static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false) {
     constexpr int NS = sizeof(T) == 8 ? 2 : GMRF_STENCIL_STAGES;
     constexpr int KB = sizeof(T) == 8 ? 1 : GMRF_STENCIL_KB;
-    using SM = StencilSmem<GEO, T, MODE, COL, NS, KB>;
-    auto kern = k_stencil<GEO, T, MODE, COL, NS, KB, PER>;
+    using SM = StencilSmem<GEO, T, MODE, COL, NS, KB, NOISE>;
+    auto kern = k_stencil<GEO, T, MODE, COL, NS, KB, PER, NOISE>;
     static int attr_smem = 0;
     static int sms = 0, optin = 0;
     static std::map<size_t, int> per_sm;       // resident CTAs per SM by dynamic shared memory
@@ -744,17 +792,17 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false)
     auto run = [kern, smem, nunits](const StencilArgs<T>& aa, int grid, cudaStream_t st, bool count) {
         StencilMaps maps;
         std::memset(&maps, 0, sizeof(maps));
-        maps.p = tile_map<GEO, T>(MODE == M_CHEB0 ? aa.b : aa.x, aa.L, aa.nblk, true);
-        if (MODE != M_APPLY) maps.b = tile_map<GEO, T>(aa.b, aa.L, aa.nblk, false);
-        if (MODE == M_CHEB && aa.d != nullptr) maps.d = tile_map<GEO, T>(aa.d, aa.L, aa.nblk, false);
-        if (MODE == M_PCG) maps.d = tile_map<GEO, T>(aa.d, aa.L, aa.nblk, true);
+        maps.p = tile_map<GEO, T, NOISE>(MODE == M_CHEB0 ? aa.b : aa.x, aa.L, aa.nblk, true);
+        if (MODE != M_APPLY) maps.b = tile_map<GEO, T, NOISE>(aa.b, aa.L, aa.nblk, false);
+        if (MODE == M_CHEB && aa.d != nullptr) maps.d = tile_map<GEO, T, NOISE>(aa.d, aa.L, aa.nblk, false);
+        if (MODE == M_PCG) maps.d = tile_map<GEO, T, NOISE>(aa.d, aa.L, aa.nblk, true);
         kern<<<(unsigned)grid, 256, smem, st>>>(aa, (int)nunits, maps);
         if (count) note_launch();
     };
     int grid = grid_of(per);
     // launch shape: measured once per key when there is more than one unit per SM
     if (nunits > nsm && per > 1) {
-        const TuneKey key{stencil_name<GEO, T, MODE, COL, PER>(), args.nblk, tune_units_bucket(nunits),
+        const TuneKey key{stencil_name<GEO, T, MODE, COL, PER>() + (NOISE ? "+noise" : ""), args.nblk, tune_units_bucket(nunits),
                           tune_obs_bucket(args.L.ostride, args.L.ocap > 0)};
         auto measure = [key, args, per, grid_of, run](cudaStream_t st) {
             TuneChoice c;
@@ -786,6 +834,13 @@ static int launch_one(const StencilArgs<T>& a, cudaStream_t s, bool dry = false)
 
 template <int GEO, typename T, int MODE>
 static int launch_geo_mode(const StencilArgs<T>& a, cudaStream_t s, bool dry) {
+    if (GEO == GEO_XT && a.L.noise) {       // Matern transition noise: point data or Burgers rows
+        constexpr int NZ = GEO == GEO_XT ? 1 : 0;
+        if (a.L.col.kind == 0) return launch_one<GEO, T, MODE, 0, 0, NZ>(a, s, dry);
+        if (a.L.col.kind == 2) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0), 0, NZ>(a, s, dry);
+        if (a.L.col.kind == 4) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 4 : 0), 0, NZ>(a, s, dry);
+        throw std::runtime_error("Matern transition noise: point data or Burgers rows only");
+    }
     if (GEO == GEO_XT && a.L.col.kind == 1) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 1 : 0), 0>(a, s, dry);
     if (GEO == GEO_XT && a.L.col.kind == 2) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 2 : 0), 0>(a, s, dry);
     if (GEO == GEO_XT && a.L.col.kind == 3) return launch_one<GEO, T, MODE, (GEO == GEO_XT ? 3 : 0), 0>(a, s, dry);

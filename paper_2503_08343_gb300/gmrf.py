@@ -26,7 +26,7 @@ class PriorDesc(C.Structure):
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("kappa", C.c_double), ("tau", C.c_double), ("nu", C.c_double),
                 ("cx", C.c_double), ("cy", C.c_double), ("kappa0", C.c_double), ("eps2", C.c_double),
-                ("bc", C.c_int32)]
+                ("bc", C.c_int32), ("noise_kappa", C.c_double), ("decay", C.c_double)]
 
 
 class ObsDesc(C.Structure):
@@ -165,6 +165,8 @@ def prior_desc(prior: dict) -> PriorDesc:
     for k in ("kappa", "tau", "nu", "cx", "cy", "kappa0", "eps2"):
         setattr(d, k, float(prior[k]))
     d.bc = {"dirichlet": 0, "periodic": 1}[prior.get("bc", "dirichlet")]
+    d.noise_kappa = float(prior.get("noise_kappa", 0.0))
+    d.decay = float(prior.get("decay", 0.0))
     return d
 
 

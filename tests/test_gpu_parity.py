@@ -34,6 +34,11 @@ def _steady_case():
     return pr, ob
 
 
+def _noise_case():
+    pr, ob = W.c1_st1d(nx=37, nt=21, m=40, seed=9)
+    return dict(pr, noise_kappa=10.0, decay=0.1), ob
+
+
 def _torus_advdiff_case():
     pr = W.periodic(W.prior_steady_advdiff2d(41, 8.0, nu=0.1, c=1.5))
     ob = W.point_obs(pr, 250, 0.05, W.periodic_fourier(np.random.default_rng(8), 10, 4), seed=8)
@@ -51,6 +56,8 @@ CASES = {
     # and a 40^2 torus with partial tiles at the seam
     "matern_torus64": lambda: W.c2_matern_periodic(n=65, m=400, seed=3, kappa=10.0),
     "advdiff_torus40": lambda: _torus_advdiff_case(),
+    # Matern transition noise and AR(1) decay in the 1D space-time prior (App. A)
+    "st1d_noise_37x21": lambda: _noise_case(),
 }
 
 

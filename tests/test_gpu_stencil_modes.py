@@ -26,7 +26,7 @@ before the FP64 reduction).
 
 Geometries: the tiled 2D and 1D space-time kernel, the marching 2D space-time
 kernel, ragged tiles, periodic tori (seam tiles), dense observations, linear and linearised Burgers
-collocation rows and their FEM Crank-Nicolson form, the full-size 2D Matern workload (512^2, 10 000
+collocation rows and their FEM Crank-Nicolson form, Matern transition noise, the full-size 2D Matern workload (512^2, 10 000
 observations, 65 right-hand sides) and the first coarse multigrid level
 (rediscretised prior with the point data interpolated on the coarse mesh).
 """
@@ -75,6 +75,8 @@ CASES = {
     "st1d_37x21_ragged": (lambda: W.c1_st1d(nx=37, nt=21, m=30, seed=5), 6),
     "st1d_linear_collocation": (_linear_colloc, 3),
     "st1d_linear_fem_cn": (lambda: _linear_colloc("fem_cn"), 3),
+    "st1d_noise_ragged": (lambda: (dict(W.c1_st1d(nx=37, nt=21, m=30, seed=5)[0], noise_kappa=8.0, decay=0.15),
+                                   W.c1_st1d(nx=37, nt=21, m=30, seed=5)[1]), 5),
     "st2d_20x20x12_march": (lambda: W.c5_st2d(n=20, nt=12, m=300, seed=5), 3),
     "st2d_24x24x10_dense_obs": (lambda: W.c5_st2d(n=24, nt=10, m=5000, seed=3), 2),
     # periodic boundary: tiles at the seam take their halo from the other side
@@ -177,7 +179,7 @@ def test_stencil_modes_match_the_oracle_operator(name, prec):
     _check_modes(post, infer.condition(pr, ob), k, 0, prec, seed=zlib.crc32(name.encode()) % 1000)
 
 
-@pytest.mark.parametrize("name", ["matern45_ragged", "steady_advdiff40", "st1d_37x21_ragged",
+@pytest.mark.parametrize("name", ["matern45_ragged", "steady_advdiff40", "st1d_37x21_ragged", "st1d_noise_ragged",
                                   "st2d_20x20x12_march", "st2d_24x24x10_dense_obs", "matern_torus40_ragged"])
 def test_stencil_modes_on_the_first_coarse_level(name):
     # the coarse operator is the rediscretised prior with the same point data
@@ -191,14 +193,16 @@ def test_stencil_modes_on_the_first_coarse_level(name):
     _check_modes(post, orc, k, 1, 0, seed=11)
 
 
-@pytest.mark.parametrize("form", ["collocation", "fem_cn"])
+@pytest.mark.parametrize("form", ["collocation", "fem_cn", "noise"])
 def test_stencil_modes_burgers_linearised(form):
     # collocation (or FEM Crank-Nicolson) rows of the Burgers residual
     # linearised at the Gauss-Newton iterate the library holds after one step
     # (Sec. 3.3)
     pr, ob = W.c3_burgers(nx=65, nt=33, m=40)
-    # FEM rows are preconditioned by the multigrid alone: a gentler row noise
-    ob = dict(ob, colloc_form=form) if form == "collocation" else dict(ob, colloc_form=form, colloc_sigma=1e-4)
+    if form == "noise":         # Matern transition noise in the prior, collocation rows
+        pr = dict(pr, noise_kappa=12.0)
+    else:
+        ob = dict(ob, colloc_form=form)
     post = gmrf.Posterior(gmrf.Prior(pr), ob)
     u, _ = post.solve_mean()
     d = np.zeros_like(u)

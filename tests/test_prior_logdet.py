@@ -35,13 +35,16 @@ PRIORS = [
     W.prior_matern2d(11, 5.0),
     W.prior_steady_advdiff2d(10, 5.0, 0.05, 1.2),
     dict(W.prior_st2d(7, 4, 0.3, 0.0, 0.02, 6.0), hi=(1.0, 2.0, 0.5)),   # hx != hy
+    dict(W.prior_st1d(14, 6, 0.5, 0.05), noise_kappa=9.0, decay=0.2),   # Matern transition noise, AR decay
+    dict(W.prior_st1d(11, 5, 0.0, 0.05), noise_kappa=5.0),
+    dict(W.prior_st2d(8, 5, 0.3, 0.0, 0.02, 6.0), decay=0.4),
     W.periodic(W.prior_matern2d(13, 5.0)),                  # torus: DFT symbol
     W.periodic(W.prior_steady_advdiff2d(11, 5.0, 0.05, 1.2)),
     dict(W.periodic(W.prior_steady_advdiff2d(9, 4.0, 0.1, 0.7)), hi=(1.0, 1.5, 0.0)),
 ]
 
 
-@pytest.mark.parametrize("prior", PRIORS, ids=lambda p: f"{p['kind']}_{p['n']}_{p['cx']}_{p.get('bc', 'dir')}")
+@pytest.mark.parametrize("prior", PRIORS, ids=lambda p: f"{p['kind']}_{p['n']}_{p['cx']}_{p.get('bc', 'dir')}_{p.get('noise_kappa', 0)}_{p.get('decay', 0)}")
 def test_prior_logdet_and_traces_match_the_oracle(prior):
     ld, tr = gmrf.prior_logdet(prior)
     want = linalg.logdet(linalg.cholesky(fem.prior_precision(prior)))
