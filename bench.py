@@ -10,6 +10,7 @@ Metric: RHS x unknowns solved per second (whole job, all GPUs).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --stencil-timing c2|c3|c5   # per-kernel stencil timings
   python bench.py --config c1|c3|c4|c5        # the other workloads, one JSON line each
+  python bench.py --study priors              # prior comparison on Burgers (error vs collocation points)
 
 N > 1 runs under torchrun, one process per GPU: each rank solves its own
 replica (the workload is one posterior; it has no data-parallel split), so
@@ -546,6 +547,44 @@ def run_config(which: str, cpu: bool = True) -> None:
     print(json.dumps(out), flush=True)
 
 
+STUDY_STRIDES = (None, (32, 25), (32, 10), (16, 10), (8, 10), (8, 5), (4, 5), (2, 2), (1, 1))
+
+
+def run_prior_study(gn_steps: int = 8) -> None:
+    """Physics-informed vs generic prior on Burgers (the Sec. 5 prior
+    comparison on synthetic data): relative L2 error of the posterior mode
+    against the Cole-Hopf solution as collocation points are added, for the
+    advection-diffusion prior and a product Matern prior (both with Matern
+    transition noise), on a 257 x 101 space-time grid with the initial
+    condition as data.  One JSON line per prior and point count."""
+    import numpy as np
+    from paper_2503_08343_gb300 import gmrf, workloads as W
+    opts = gmrf.default_opts(max_inner=200, max_refine=30)
+    for kind in W.STUDY_PRIORS:
+        for stride in STUDY_STRIDES:
+            pr, ob = W.burgers_prior_study(kind, stride)
+            nx, _, nt = pr["n"]
+            xs = np.linspace(pr["lo"][0], pr["hi"][0], nx)
+            ts = np.linspace(pr["lo"][2], pr["hi"][2], nt)
+            truth = W.cole_hopf_burgers(xs[None, :], ts[:, None], ob["burgers_nu"]).ravel()
+            post = gmrf.Posterior(gmrf.Prior(pr), ob)
+            t0 = time.perf_counter()
+            u, info = post.solve_mean(opts=opts)
+            points, steps, dec = 0, 0, None
+            if stride is not None:
+                points = len(range(stride[0], nx - 1, stride[0])) * len(range(stride[1], nt, stride[1]))
+                d = np.zeros_like(u)
+                for steps in range(1, gn_steps + 1):
+                    dec, _, info = post.gauss_newton_step(u, d, opts=opts)
+                    if dec < 1e-10:
+                        break
+            dt = time.perf_counter() - t0
+            err = float(np.linalg.norm(u - truth) / np.linalg.norm(truth))
+            print(json.dumps({"study": "burgers_prior_comparison", "prior": kind, "collocation_points": points,
+                              "stride": stride, "rel_l2_error": err, "gauss_newton_steps": steps,
+                              "last_decrement": dec, "s": round(dt, 3), "grid": [nx, nt]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -558,7 +597,12 @@ def main():
     ap.add_argument("--config", choices=["c1", "c3", "c4", "c5", "c5plain"], default=None,
                     help="time one of the other workloads through the library API (one JSON line)")
     ap.add_argument("--grid", type=int, default=256, help="--config c5 / c5plain: grid side (nodes per axis)")
+    ap.add_argument("--study", choices=["priors"], default=None,
+                    help="priors: physics-informed vs product Matern prior on Burgers, error vs collocation points")
     args = ap.parse_args()
+    if args.study:
+        run_prior_study()
+        return
     if args.config:
         run_config.grid = args.grid
         run_config(args.config, cpu=not args.no_cpu_baseline)

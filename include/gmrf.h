@@ -146,6 +146,11 @@ typedef struct gmrf_obs_desc {
     double colloc_c;
     double colloc_nu;
     const double* colloc_f;
+    /* collocation points: only the rows with x % colloc_stride_x == 0 and
+     * k % colloc_stride_t == 0 observe the PDE (0 or 1: every row); the
+     * others keep their row index (random draws) with zero weight */
+    int32_t colloc_stride_x;
+    int32_t colloc_stride_t;
 } gmrf_obs_desc;
 
 typedef struct gmrf_solve_opts {

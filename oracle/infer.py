@@ -42,6 +42,8 @@ def condition(prior: dict, obs: dict, linearise_at: np.ndarray | None = None) ->
     initial condition -sin(pi x)); collocation rows when obs["colloc_sigma"]
     is set, in the form obs["colloc_form"]: "collocation" (default) or
     "fem_cn" (Galerkin-tested Crank-Nicolson rows, observe.fem_cn_residual).
+    obs["colloc_stride"] = (sx, st) keeps the rows with i % sx == 0 and
+    k % st == 0 (observe.colloc_active; the others get zero weight).
     Linear collocation (obs["colloc_c"] given) uses the constant
     advection speed and right-hand side obs["colloc_f"]; Burgers collocation
     is linearised at `linearise_at` (Sec. 3.3: f(u) ~ f(u_k) + J (u - u_k),
@@ -75,7 +77,7 @@ def condition(prior: dict, obs: dict, linearise_at: np.ndarray | None = None) ->
             J = None
         if J is not None:
             rows.append(J)
-            rinvs.append(np.full(J.shape[0], 1.0 / obs["colloc_sigma"] ** 2))
+            rinvs.append(observe.colloc_active(prior, obs) / obs["colloc_sigma"] ** 2)
             ys.append(yc)
     Aall = sp.vstack(rows).tocsr()
     rinv_all = np.concatenate(rinvs)
@@ -163,7 +165,7 @@ def neg_log_post(post_lin: Posterior, prior_Q: sp.csr_matrix, obs: dict, prior: 
         val += 0.5 * float(np.sum(r * r)) / obs["ic_sigma"] ** 2
     if obs.get("colloc_sigma") is not None:
         _, f = observe.pde_rows(prior, obs, u, obs.get("burgers_nu", prior["nu"]))
-        val += 0.5 * float(np.sum(f * f)) / obs["colloc_sigma"] ** 2
+        val += 0.5 * float(np.sum(observe.colloc_active(prior, obs) * f * f)) / obs["colloc_sigma"] ** 2
     return val
 
 

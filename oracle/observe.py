@@ -127,6 +127,17 @@ def ic_matrix(prior: dict) -> sp.csr_matrix:
     return sp.csr_matrix((np.ones(ns), (np.arange(ns), np.arange(ns))), shape=(ns, ns * nt))
 
 
+def colloc_active(prior: dict, obs: dict) -> np.ndarray:
+    """Which collocation rows observe the PDE: with obs["colloc_stride"] =
+    (sx, st) only the rows with i % sx == 0 and k % st == 0 (a grid of
+    collocation points, coarser than the mesh); all rows by default.  The
+    other rows stay in the row numbering with zero weight (no observation),
+    so random draws keep their row indices."""
+    sx, st = obs.get("colloc_stride", (1, 1))
+    i, k = colloc_rows(prior)
+    return (i % int(sx) == 0) & (k % int(st) == 0)
+
+
 def colloc_rows(prior: dict):
     """(i, k) pairs of the collocation rows: interior x, time levels >= 1."""
     nx, ny, nt = prior["n"]

@@ -266,13 +266,25 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
             P.colloc_c = obs->colloc_c;
             const bool fem_rows = obs->colloc >= 3;
             const double hf = P.levels[0].hx;
-            for (Level& L : P.levels) {
-                const double ncl = (double)(L.nx - 2) * (L.nt - 1);
+            // rows observing the PDE: x % sx == 0 and t % st == 0 (strides halve on coarser levels)
+            const int sx0 = std::max(1, (int)obs->colloc_stride_x), st0 = std::max(1, (int)obs->colloc_stride_t);
+            auto active = [](int nx, int nt, int sx, int st) {
+                long long cx = 0, ct = 0;
+                for (int x = 1; x <= nx - 2; ++x) cx += x % sx == 0;
+                for (int t = 1; t <= nt - 1; ++t) ct += t % st == 0;
+                return (double)(cx * ct);
+            };
+            const double nfine = active(P.levels[0].nx, P.levels[0].nt, sx0, st0);
+            for (size_t l = 0; l < P.levels.size(); ++l) {
+                Level& L = P.levels[l];
+                L.col.sx = std::max(1, sx0 >> (int)l);
+                L.col.st = std::max(1, st0 >> (int)l);
+                const double ncl = active(L.nx, L.nt, L.col.sx, L.col.st);
                 // Burgers rows (2, 4) enter once linearised
                 L.col.kind = (obs->colloc == 1 || obs->colloc == 3) ? obs->colloc : 0;
                 // coarse levels: the row-count ratio keeps J^T Q_eps J of the same size;
                 // FEM rows carry a factor h (int phi_i), which the ratio already covers
-                L.col.qeps = P.colloc_qeps * (double)P.ncol / ncl * (fem_rows ? (hf * hf) / (L.hx * L.hx) : 1.0);
+                L.col.qeps = ncl > 0 ? P.colloc_qeps * nfine / ncl * (fem_rows ? (hf * hf) / (L.hx * L.hx) : 1.0) : 0.0;
                 L.col.inv_dt = 1.0 / L.dt;
                 L.col.inv_2h = 1.0 / (2.0 * L.hx);
                 L.col.nu_h2 = obs->colloc_nu / (L.hx * L.hx);
@@ -287,6 +299,7 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
                 auto none = [](int, int) { return 0.0; };
                 for (int t = 1; t < L.nt; ++t)
                     for (int x = 1; x < L.nx - 1; ++x) {
+                        if (!colloc_on(L.col, x, t)) continue;
                         const size_t r = (size_t)(t - 1) * (L.nx - 2) + (x - 1);
                         const double v = L.col.qeps * (obs->colloc_f ? obs->colloc_f[r] : 0.0);
                         double a[3], b[3];
@@ -302,6 +315,7 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
                 const Level& L = P.levels[0];
                 for (int t = 1; t < L.nt; ++t)
                     for (int x = 1; x < L.nx - 1; ++x) {
+                        if (!colloc_on(L.col, x, t)) continue;
                         const size_t r = (size_t)(t - 1) * (L.nx - 2) + (x - 1);
                         const double f = obs->colloc_f ? obs->colloc_f[r] : 0.0;
                         const double a = L.col.c;

@@ -42,7 +42,7 @@ __global__ void k_gn_rhs(const LevelView<double> L, const double* __restrict__ u
     const int rts[4] = {t, t, t, t + 1};
     for (int k = 0; k < 4; ++k) {
         const int rx = rxs[k], rt = rts[k];
-        if (rx < 1 || rx > nx - 2 || rt < 1 || rt >= nt) continue;
+        if (rx < 1 || rx > nx - 2 || rt < 1 || rt >= nt || !colloc_on(c, rx, rt)) continue;
         const double cf = k == 0 ? coef(rx, rt, 0) : (k == 1 ? coef(rx, rt, 2) : (k == 2 ? coef(rx, rt, 1) : -c.inv_dt));
         acc += cf * yJ(rx, rt);
     }
@@ -82,7 +82,7 @@ __global__ void k_colloc_misfit(const LevelView<double> L, double nu, const doub
     const long long nrow = (long long)(nx - 2) * (nt - 1);
     const long long r = (long long)blockIdx.x * 256 + threadIdx.x;
     double s = 0.0;
-    if (r < nrow) {
+    if (r < nrow && colloc_on(L.col, 1 + (int)(r % (nx - 2)), 1 + (int)(r / (nx - 2)))) {
         const int x = 1 + (int)(r % (nx - 2)), t = 1 + (int)(r / (nx - 2));
         const long long i = (long long)t * nx + x;
         const double h = 0.5 / L.col.inv_2h;

@@ -51,7 +51,14 @@ struct Colloc {
     double m6_dt;      // h / (6 dt)   (FEM rows)
     double nu_2h;      // nu / (2 h)   (FEM rows)
     int32_t row0;      // global observation row of the first collocation row
+    int32_t sx, st;    // rows observe the PDE where x % sx == 0 and t % st == 0 (1, 1: every row)
 };
+
+// row (x, t) of the collocation rows observes the PDE (the others have zero
+// weight; they keep their place in the row numbering)
+__host__ __device__ __forceinline__ bool colloc_on(const Colloc& c, int x, int t) {
+    return (c.sx <= 1 || x % c.sx == 0) && (c.st <= 1 || t % c.st == 0);
+}
 
 // half convection derivative d_e of an FEM Crank-Nicolson row centred at x,
 // from the linearisation point at x-1, x, x+1 on one level
@@ -92,11 +99,13 @@ __host__ __device__ inline int fem_cn_column(const Colloc& c, int nx, int nt, in
     for (int d = -1; d <= 1; ++d) {
         const int r = x + d;
         if (r < 1 || r > nx - 2) continue;
+        const bool on_t = t >= 1 && colloc_on(c, r, t), on_t1 = t + 1 <= nt - 1 && colloc_on(c, r, t + 1);
+        if (!on_t && !on_t1) continue;
         double hd[3];
         fem_cn_half_conv<double>(c, c.kind == 4 ? mu(r - 1, t) : 0.0, c.kind == 4 ? mu(r, t) : 0.0,
                                  c.kind == 4 ? mu(r + 1, t) : 0.0, hd);
-        if (t >= 1) { rx[n] = r; rt[n] = t; cf[n] = fem_cn_fixed<double>(c, 1 - d, 1.0) + hd[1 - d]; ++n; }
-        if (t + 1 <= nt - 1) { rx[n] = r; rt[n] = t + 1; cf[n] = fem_cn_fixed<double>(c, 1 - d, -1.0) + hd[1 - d]; ++n; }
+        if (on_t) { rx[n] = r; rt[n] = t; cf[n] = fem_cn_fixed<double>(c, 1 - d, 1.0) + hd[1 - d]; ++n; }
+        if (on_t1) { rx[n] = r; rt[n] = t + 1; cf[n] = fem_cn_fixed<double>(c, 1 - d, -1.0) + hd[1 - d]; ++n; }
     }
     return n;
 }

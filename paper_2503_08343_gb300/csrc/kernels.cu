@@ -898,7 +898,7 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
             const int rts[4] = {gt, gt, gt, gt + 1};
             for (int k = 0; k < 4; ++k) {
                 const int rx = rxs[k], rt = rts[k];
-                if (rx < 1 || rx > nx - 2 || rt < 1 || rt >= nt) continue;
+                if (rx < 1 || rx > nx - 2 || rt < 1 || rt >= nt || !colloc_on(L.col, rx, rt)) continue;
                 const double c = k == 0 ? coef(rx, rt, 0) : (k == 1 ? coef(rx, rt, 2) : (k == 2 ? coef(rx, rt, 1) : -L.col.inv_dt));
                 const uint64_t orow = (uint64_t)L.col.row0 + (uint64_t)(rt - 1) * (nx - 2) + (rx - 1);
                 double v[4];
@@ -1146,7 +1146,7 @@ __global__ void k_diag(const LevelView<T> L, double* __restrict__ diag) {
         double acc = 0.0;
         for (int k = 0; k < 4; ++k) {
             const int rx = rxs[k], rt = rts[k];
-            if (rx < 1 || rx > nx - 2 || rt < 1 || rt >= nt) continue;
+            if (rx < 1 || rx > nx - 2 || rt < 1 || rt >= nt || !colloc_on(L.col, rx, rt)) continue;
             const double c = k == 0 ? coef(rx, rt, 0) : (k == 1 ? coef(rx, rt, 2) : (k == 2 ? coef(rx, rt, 1) : -L.col.inv_dt));
             acc += c * c;
         }

@@ -555,6 +555,7 @@ std::vector<double> dense_operator(const Level& L, const double* mu) {
         auto mu_at = [&](int xx, int tt) { return mu ? mu[(size_t)tt * L.nx + xx] : 0.0; };
         for (int t = 1; t < L.nt; ++t)
             for (int x = 1; x < L.nx - 1; ++x) {
+                if (!colloc_on(L.col, x, t)) continue;
                 double a[3], b[3];
                 fem_cn_row(L.col, x, t, mu_at, a, b);
                 long long nd[6];
@@ -571,6 +572,7 @@ std::vector<double> dense_operator(const Level& L, const double* mu) {
     } else if (L.col.kind != 0) {
         for (int t = 1; t < L.nt; ++t)
             for (int x = 1; x < L.nx - 1; ++x) {
+                if (!colloc_on(L.col, x, t)) continue;
                 double cC, cL, cR;
                 coll_coef(L.col, mu, L.nx, x, t, cC, cL, cR);
                 const long long nd[4] = {(long long)t * L.nx + x, (long long)t * L.nx + x - 1, (long long)t * L.nx + x + 1,

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
 #pragma unroll
                 for (int j = 0; j < KB; ++j) {
                     V4<T> sjv = v4zero<T>();
-                    if (inrow && rx >= 1 && rx <= nx - 2 && rt >= 1) {
+                    if (inrow && rx >= 1 && rx <= nx - 2 && rt >= 1 && colloc_on(L.col, rx, rt)) {
                         T cC, cL, cR;
                         jcoef<T, COL>(L.col, smu(base), smu(base - 1), smu(base + 1), cC, cL, cR);
                         sjv = cC * sp[base][j];
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
 #pragma unroll
                 for (int j = 0; j < KB; ++j) {
                     V4<T> sjv = v4zero<T>();
-                    if (inrow && rx >= 1 && rx <= nx - 2 && rt >= 1) {
+                    if (inrow && rx >= 1 && rx <= nx - 2 && rt >= 1 && colloc_on(L.col, rx, rt)) {
                         T dk[3], dp[3];
                         fem_cn_half_conv<T>(L.col, smu(base - 1), smu(base), smu(base + 1), dk);
                         fem_cn_half_conv<T>(L.col, smu(base - TP - 1), smu(base - TP), smu(base - TP + 1), dp);

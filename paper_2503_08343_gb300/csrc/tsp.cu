@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* _
 }  // namespace
 
 bool tsp_applicable(const Level& L, int nic) {
-    return L.geo == GEO_XT && L.col.kind != 0 && nic > 0 && L.nx <= kTspMaxNx;
+    // every collocation row present (the time-stepping factorisation needs the square J_t)
+    return L.geo == GEO_XT && L.col.kind != 0 && L.col.sx <= 1 && L.col.st <= 1 && nic > 0 && L.nx <= kTspMaxNx;
 }
 
 static size_t tsp_smem(const Level& L, size_t elem) {

@@ -34,7 +34,8 @@ class ObsDesc(C.Structure):
                 ("sigma", C.POINTER(C.c_double)), ("sigma_all", C.c_double),
                 ("ic", C.c_int32), ("ic_sigma", C.c_double), ("ic_values", C.POINTER(C.c_double)),
                 ("colloc", C.c_int32), ("colloc_sigma", C.c_double), ("colloc_c", C.c_double),
-                ("colloc_nu", C.c_double), ("colloc_f", C.POINTER(C.c_double))]
+                ("colloc_nu", C.c_double), ("colloc_f", C.POINTER(C.c_double)),
+                ("colloc_stride_x", C.c_int32), ("colloc_stride_t", C.c_int32)]
 
 
 class SolveOpts(C.Structure):
@@ -227,6 +228,7 @@ class Posterior:
             o.colloc = 1 if obs.get("colloc_c") is not None else 2
             if obs.get("colloc_form", "collocation") == "fem_cn":
                 o.colloc += 2          # FEM Crank-Nicolson rows: 3 linear, 4 Burgers
+            o.colloc_stride_x, o.colloc_stride_t = (int(v) for v in obs.get("colloc_stride", (1, 1)))
             o.colloc_sigma = float(obs["colloc_sigma"])
             o.colloc_c = float(obs.get("colloc_c") or 0.0)
             o.colloc_nu = float(obs.get("burgers_nu", prior.spec["nu"]))

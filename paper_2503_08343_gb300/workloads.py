@@ -279,3 +279,38 @@ def c5_st2d(n: int = 256, nt: int = 256, m: int = 50000, seed: int = 5):
 
 #: random-draw seeds for the Philox streams (samples, probes), per workload
 DRAW_SEED = {"c1": 1001, "c2": 1002, "c3": 1003, "c4": 1004, "c5": 1005}
+
+
+# ---------------------------------------------------------------------------
+# physics-informed vs generic prior on Burgers (the Sec. 5 prior comparison,
+# on synthetic data): the initial condition as data, nonlinear collocation
+# at a grid of points coarser than the mesh
+
+
+STUDY_PRIORS = ("advdiff", "product_matern")
+
+
+def burgers_prior_study(prior: str, stride, nx: int = 257, nt: int = 101, nu: float = 0.01,
+                        noise_kappa: float = 35.0, colloc_sigma: float = 1e-3, ic_sigma: float = 1e-3):
+    """Burgers on (-1, 1) x (0, 1) with u(x, 0) = -sin(pi x) observed at every
+    t = 0 node (noise ic_sigma) and the collocation rows on the points
+    x % sx == 0, k % st == 0 (stride (sx, st); None: no collocation).
+    prior "advdiff": the advection-diffusion proxy (c = 1, the diffusion of the
+    equation) with Matern transition noise of inverse range noise_kappa;
+    "product_matern": no dynamics (c = nu = 0), the same Matern noise and an
+    AR(1) decay with temporal range 3 (a separable Matern prior with
+    nu_t = 1/2 in time).  Returns (prior, obs)."""
+    if prior == "advdiff":
+        pr = prior_st1d(nx, nt, c=1.0, nu=nu, tau=1.0, kappa0=10.0, x0=-1.0, x1=1.0, t1=1.0)
+        pr = dict(pr, noise_kappa=float(noise_kappa))
+    else:
+        dt = 1.0 / (nt - 1)
+        decay = 1.0 - math.exp(-dt / 3.0)
+        # stationary variance tau^2 dt / (1 - rho^2) of about one
+        tau = math.sqrt((1.0 - (1.0 - decay) ** 2) / dt)
+        pr = prior_st1d(nx, nt, c=0.0, nu=0.0, tau=tau, kappa0=float(noise_kappa), x0=-1.0, x1=1.0, t1=1.0)
+        pr = dict(pr, noise_kappa=float(noise_kappa), decay=decay)
+    ob = dict(coords=np.zeros((0, 2)), y=np.zeros(0), sigma=np.zeros(0), ic_sigma=float(ic_sigma), burgers_nu=nu)
+    if stride is not None:
+        ob = dict(ob, colloc_sigma=float(colloc_sigma), colloc_stride=(int(stride[0]), int(stride[1])))
+    return pr, ob

@@ -26,11 +26,14 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-@pytest.mark.parametrize("n,nt,nu,noise", [(65, 33, 0.05, 0.0), (97, 65, 0.01, 0.0), (65, 33, 0.05, 15.0)])
-def test_gauss_newton_iterates_match_the_oracle(n, nt, nu, noise):
+@pytest.mark.parametrize("n,nt,nu,noise,stride", [(65, 33, 0.05, 0.0, 1), (97, 65, 0.01, 0.0, 1), (65, 33, 0.05, 15.0, 1),
+                                                   (65, 33, 0.05, 0.0, 4), (65, 33, 0.05, 15.0, 8)])
+def test_gauss_newton_iterates_match_the_oracle(n, nt, nu, noise, stride):
     pr, ob = W.c3_burgers(nx=n, nt=nt, m=60, seed=3, nu=nu)
     if noise:                   # Matern transition noise in the prior (App. A)
         pr = dict(pr, noise_kappa=noise)
+    if stride > 1:              # collocation points on a coarser grid than the mesh
+        ob = dict(ob, colloc_stride=(stride, stride))
     post = gmrf.Posterior(gmrf.Prior(pr), ob)
     u_gpu, info = post.solve_mean()
     u_or = infer.posterior_mean(infer.condition(pr, ob))

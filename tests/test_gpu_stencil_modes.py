@@ -75,6 +75,7 @@ CASES = {
     "st1d_37x21_ragged": (lambda: W.c1_st1d(nx=37, nt=21, m=30, seed=5), 6),
     "st1d_linear_collocation": (_linear_colloc, 3),
     "st1d_linear_fem_cn": (lambda: _linear_colloc("fem_cn"), 3),
+    "st1d_linear_colloc_strided": (lambda: (_linear_colloc()[0], dict(_linear_colloc()[1], colloc_stride=(3, 2))), 3),
     "st1d_noise_ragged": (lambda: (dict(W.c1_st1d(nx=37, nt=21, m=30, seed=5)[0], noise_kappa=8.0, decay=0.15),
                                    W.c1_st1d(nx=37, nt=21, m=30, seed=5)[1]), 5),
     "st2d_20x20x12_march": (lambda: W.c5_st2d(n=20, nt=12, m=300, seed=5), 3),

@@ -337,3 +337,23 @@ def test_gauss_newton_reaches_a_stationary_point_near_the_cole_hopf_truth():
     X = np.tile(xs, n)
     truth = W.cole_hopf_burgers(X, T, 0.05)
     assert np.abs(u - truth).max() < 0.05
+
+
+def test_collocation_stride_is_conditioning_on_the_active_rows_only():
+    # zero-weight rows observe nothing: the posterior equals conditioning on
+    # the active rows alone (rows x % sx == 0, k % st == 0)
+    import scipy.sparse as sp
+    pr, ob = W.c3_burgers(nx=17, nt=9, m=10)
+    u = np.random.default_rng(4).normal(size=17 * 9) * 0.1
+    obs = dict(ob, colloc_stride=(3, 2))
+    post = infer.condition(pr, obs, linearise_at=u)
+    act = observe.colloc_active(pr, obs)
+    i, k = observe.colloc_rows(pr)
+    assert np.array_equal(act, (i % 3 == 0) & (k % 2 == 0)) and act.sum() == 5 * 4
+    J, F = observe.pde_rows(pr, obs, u, obs["burgers_nu"])
+    Ja = J[np.flatnonzero(act)]
+    full = infer.condition(pr, dict(ob, colloc_sigma=None))
+    Qa = full.Qpost + (Ja.T @ Ja) / obs["colloc_sigma"] ** 2
+    ba = full.b + Ja.T @ ((Ja @ u - F[act]) / obs["colloc_sigma"] ** 2)
+    assert abs(post.Qpost - Qa).max() <= 1e-9 * abs(Qa).max()
+    assert np.max(np.abs(post.b - ba)) <= 1e-9 * np.max(np.abs(ba))
