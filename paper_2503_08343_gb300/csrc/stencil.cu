@@ -339,8 +339,16 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         }
         V4<T> pold[KB];             // PCG: the previous direction at the own node
         if (MODE == M_PCG) {        // staged p, z -> p' = z + beta p in place
+            // the own node's old direction from global memory (L2: the tile was
+            // just copied), so the in-place update needs no barrier before it
+            const int ox = cur.tx * TX + lx, oy = cur.ty * TY + ly, ot = cur.tt * TT + lt;
+            const bool oown = ox < nx && oy < ny && ot < nt;
+            const size_t onode = oown ? ((size_t)ot * ny + oy) * nx + ox : 0;
 #pragma unroll
-            for (int j = 0; j < KB; ++j) pold[j] = S.p[st][pbase][j];
+            for (int j = 0; j < KB; ++j) {
+                const int blk = min(cur.grp * KB + j, nblk - 1);
+                pold[j] = v4load(A.x + ((size_t)blk * N + onode) * RW);
+            }
             V4<T> bt[KB];
 #pragma unroll
             for (int j = 0; j < KB; ++j) {
@@ -348,7 +356,6 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 const double* bp = A.beta + (size_t)blk * RW;
                 bt[j] = V4<T>{(T)bp[0], (T)bp[1], (T)bp[2], (T)bp[3]};
             }
-            __syncthreads();        // every own-node read of the old direction is done
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
                 const int e = tid + 256 * k;
