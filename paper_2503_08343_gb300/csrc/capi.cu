@@ -342,7 +342,7 @@ gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_pos
         posterior_setup_levels(P, s);
         if (obs->ic) P.ic_rinv = 1.0 / (obs->ic_sigma * obs->ic_sigma);
         P.use_tsp = tsp_applicable(P.levels[0], (int)P.nic);
-        if (P.use_tsp) tsp_prepare(P.levels[0], s);
+        if (P.use_tsp) tsp_prepare(P.levels[0], (int)P.nic, s);
         dev_upload(&P.d_bstatic, bstatic);
         if (P.nic) dev_upload(&P.d_icvals, P.ic_values);
         P.d_bdata = dev_alloc<double>((size_t)F.N);

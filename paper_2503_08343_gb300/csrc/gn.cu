@@ -213,7 +213,7 @@ void linearise(Posterior& P, const double* u, cudaStream_t s) {
     }
     posterior_refresh_operator(P, s);
     P.use_tsp = tsp_applicable(F, (int)P.nic);
-    if (P.use_tsp) tsp_prepare(F, s);
+    if (P.use_tsp) tsp_prepare(F, (int)P.nic, s);
     // data right-hand side of the linearised problem, b_lin = A^T R^-1 y + J^T Q_eps (J u - f(u));
     // at a Gauss-Newton fixed point H^-1 b_lin = u, so the mean slot of later
     // sampling calls is the Laplace mean

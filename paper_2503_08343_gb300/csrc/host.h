@@ -95,7 +95,7 @@ void noalloc_prepare(const Posterior& P);
 bool tsp_applicable(const Level& L, int nic);
 // the application kernel's shared memory fits for precision T
 template <typename T> bool tsp_fits(const Level& L);
-void tsp_prepare(Level& L, cudaStream_t s);
+void tsp_prepare(Level& L, int nic, cudaStream_t s);
 template <typename T>
 void launch_tsp(const Level& L, double w_ic, double w_bnd, const T* r, T* y, T* z, int nblk, cudaStream_t s);
 

@@ -198,7 +198,8 @@ struct Level {
     // time-stepping preconditioner factors (collocation levels), device
     float* d_tsp32 = nullptr;
     double* d_tsp64 = nullptr;
-    float* d_tspc32 = nullptr;     // FEM Crank-Nicolson rows: coupling coefficients
+    int tsp_ic = 0;                // the initial condition is observed (level 0 of J_t: its rows)
+    float* d_tspc32 = nullptr;     // per-row coupling coefficients (FEM rows, mixed PDE / prior rows)
     double* d_tspc64 = nullptr;
     // coarsest level: dense inverse of Q_u|y (device, row-major)
     float* d_dense32 = nullptr;

@@ -58,12 +58,37 @@ constexpr int kFactorBlock = kRowF * kRows * kLanes + kLaneF * kLanes;
 constexpr int kCplBlock = 3 * kRows * kLanes + 3 * kLanes;
 static_assert((1 << kSteps) == kLanes, "cyclic reduction covers the lanes");
 
-// Level row coefficients of J (lower x-1, diagonal, upper x+1) at node x of
-// level k, with mu the linearisation point of the level (Burgers).
+// The rows of J_t: boundary rows (the prior's Dirichlet rows), the initial
+// level's data rows (the initial condition observed at every node) or, without
+// them, the prior's initial-level rows, and on levels k >= 1 the PDE rows
+// where the PDE is observed and the prior's transition rows elsewhere (rows
+// between the collocation points, or every row without collocation).
+enum TspRow { TR_BND = 0, TR_IC, TR_PRIOR0, TR_COL, TR_PRIOR };
 template <typename T>
-__device__ __forceinline__ void j_row(const LevelView<T>& L, const T* mu, int x, int k, T& lo, T& di, T& up) {
+__device__ __forceinline__ int tsp_row_kind(const LevelView<T>& L, int x, int k, int has_ic) {
+    if (x <= 0 || x >= L.nx - 1) return TR_BND;
+    if (k == 0) return has_ic ? TR_IC : TR_PRIOR0;
+    if (L.col.kind != 0 && colloc_on(L.col, x, k)) return TR_COL;
+    return TR_PRIOR;
+}
+
+// Level row coefficients of J_t (lower x-1, diagonal, upper x+1) at node x of
+// level k, with mu the linearisation point of the level (Burgers).  Prior rows
+// are the white-noise root's rows (with Matern transition noise the weight of
+// a level's prior rows is T_K^2 instead of one; see k_tsp_tscale).
+template <typename T>
+__device__ __forceinline__ void j_row(const LevelView<T>& L, const T* mu, int x, int k, int has_ic, T& lo, T& di,
+                                      T& up) {
     const int nx = L.nx;
-    if (k == 0 || x <= 0 || x >= nx - 1) { lo = T(0); di = T(1); up = T(0); return; }
+    const int kind = tsp_row_kind<T>(L, x, k, has_ic);
+    if (kind == TR_BND || kind == TR_IC) { lo = T(0); di = T(1); up = T(0); return; }
+    if (kind == TR_PRIOR0 || kind == TR_PRIOR) {    // the root's taps; Dirichlet columns eliminated
+        const int cls = kind == TR_PRIOR0 ? 1 : 0;
+        lo = x - 1 >= 1 ? L.cf[cls][1] : T(0);
+        di = L.cf[cls][0];
+        up = x + 1 <= nx - 2 ? L.cf[cls][2] : T(0);
+        return;
+    }
     const Colloc& c = L.col;
     if (c.kind >= 3) {         // FEM Crank-Nicolson row: its taps on its own level
         T d[3];
@@ -87,23 +112,23 @@ __device__ __forceinline__ void j_row(const LevelView<T>& L, const T* mu, int x,
 // Row x of the level system: J's level block D_k (TR = false) or its
 // transpose (TR = true: sub-diagonal up(x-1), super-diagonal lo(x+1)).
 template <typename T, bool TR>
-__device__ __forceinline__ void level_row(const LevelView<T>& L, const T* mu, int x, int k, T& A, T& B, T& C) {
+__device__ __forceinline__ void level_row(const LevelView<T>& L, const T* mu, int x, int k, int has_ic, T& A, T& B, T& C) {
     T lo, di, up;
-    j_row<T>(L, mu, x, k, lo, di, up);
+    j_row<T>(L, mu, x, k, has_ic, lo, di, up);
     B = di;
     if (!TR) { A = lo; C = up; return; }
     T l2, d2, u2;
     A = T(0);
     C = T(0);
-    if (x > 0) { j_row<T>(L, mu, x - 1, k, l2, d2, u2); A = u2; }
-    if (x < L.nx - 1) { j_row<T>(L, mu, x + 1, k, l2, d2, u2); C = l2; }
+    if (x > 0) { j_row<T>(L, mu, x - 1, k, has_ic, l2, d2, u2); A = u2; }
+    if (x < L.nx - 1) { j_row<T>(L, mu, x + 1, k, has_ic, l2, d2, u2); C = l2; }
 }
 
 // One CTA of kLanes threads per (direction, level): the matrix-only part of
 // the partition solve.  blockIdx.x = dir * nt + k, dir 0 = D_k (forward
 // sweep), 1 = D_k^T.
 template <typename T>
-__global__ void __launch_bounds__(kLanes) k_tsp_factor(const LevelView<T> L, T* __restrict__ f) {
+__global__ void __launch_bounds__(kLanes) k_tsp_factor(const LevelView<T> L, int has_ic, T* __restrict__ f) {
     __shared__ T xa[kLanes], xb[kLanes], xc[kLanes];
     const int nx = L.nx, nt = L.nt;
     const int dir = blockIdx.x / nt, k = blockIdx.x % nt;
@@ -114,8 +139,8 @@ __global__ void __launch_bounds__(kLanes) k_tsp_factor(const LevelView<T> L, T* 
     T* rowf = blk;                                   // [field][j][lane]
     T* lanef = blk + kRowF * kRows * kLanes;         // [field][lane]
     auto row = [&](int x, T& A, T& B, T& C) {
-        if (dir == 0) level_row<T, false>(L, mu, x, k, A, B, C);
-        else level_row<T, true>(L, mu, x, k, A, B, C);
+        if (dir == 0) level_row<T, false>(L, mu, x, k, has_ic, A, B, C);
+        else level_row<T, true>(L, mu, x, k, has_ic, A, B, C);
     };
     T qv[kRows], rv[kRows], cv[kRows];
     T cprev = T(0), qprev = T(0);
@@ -200,24 +225,28 @@ __global__ void __launch_bounds__(kLanes) k_tsp_factor(const LevelView<T> L, T* 
     lanef[2 * kLanes + lane] = T(1) / rb;
 }
 
-// Coupling coefficients of FEM Crank-Nicolson rows, one CTA of kLanes
-// threads per (direction, level) like k_tsp_factor: the forward sweep at
-// level k adds sum_e -b_e(x, k) z_(k-1)(x + e - 1) to row x's right-hand side
-// (b: row (x, k)'s taps on level k-1); the backward sweep at level k adds
+// Coupling coefficients of every row of J_t to the neighbouring level (FEM
+// Crank-Nicolson rows, mixed PDE and prior rows), one CTA of kLanes threads
+// per (direction, level) like k_tsp_factor: the forward sweep at level k adds
+// sum_e -b_e(x, k) z_(k-1)(x + e - 1) to row x's right-hand side (b: row
+// (x, k)'s taps on level k-1); the backward sweep at level k adds
 // sum_d -b_(1-d)(x + d, k + 1) y_(k+1)(x + d) (the transposed coupling, which
 // also reaches the boundary nodes).  Stored as (x-1, x, x+1) coefficients.
 template <typename T>
-__global__ void __launch_bounds__(kLanes) k_tsp_couple(const LevelView<T> L, T* __restrict__ f) {
+__global__ void __launch_bounds__(kLanes) k_tsp_couple(const LevelView<T> L, int has_ic, T* __restrict__ f) {
     const int nx = L.nx, nt = L.nt;
     const int dir = blockIdx.x / nt, k = blockIdx.x % nt;
     const int lane = threadIdx.x;
     const int m = (nx + kLanes - 1) / kLanes, s = lane * m, mi = max(0, min(m, nx - s)), mint = mi - 1;
     T* blk = f + (size_t)blockIdx.x * kCplBlock;
     const Colloc& c = L.col;
-    // b taps of row (x, kr) (zero unless x is interior and kr >= 1)
+    // taps of row (x, kr) on level kr - 1 (zero unless x is interior and kr >= 1)
     auto btaps = [&](int x, int kr, T b[3]) {
         b[0] = b[1] = b[2] = T(0);
         if (x < 1 || x > nx - 2 || kr < 1 || kr >= nt) return;
+        const int kind = tsp_row_kind<T>(L, x, kr, has_ic);
+        if (kind == TR_PRIOR) { b[1] = L.cf[0][7]; return; }       // the root's t-1 tap
+        if (c.kind == 1 || c.kind == 2) { b[1] = -(T)c.inv_dt; return; }   // implicit-Euler collocation row
         const T* mp = L.mu ? L.mu + (size_t)(kr - 1) * nx : nullptr;
         T d[3];
         fem_cn_half_conv<T>(c, mp ? mp[x - 1] : T(0), mp ? mp[x] : T(0), mp ? mp[x + 1] : T(0), d);
@@ -254,8 +283,8 @@ __global__ void __launch_bounds__(kLanes) k_tsp_couple(const LevelView<T> L, T* 
 // exchange buffers.
 template <typename T, bool FEM>
 __global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* __restrict__ fac, const T* __restrict__ cpl,
-                                               T iw_ic, T iw_bnd, T iw_q, const T* __restrict__ r, T* __restrict__ y,
-                                               T* __restrict__ z) {
+                                               T iw_ic, T iw_bnd, T iw_q, int has_ic, int sweep_lo, int sweep_hi,
+                                               const T* __restrict__ r, T* __restrict__ y, T* __restrict__ z) {
     extern __shared__ __align__(16) unsigned char tsp_smem[];
     __shared__ V4<T> xch[2][kLanes];
     const int nx = L.nx, nt = L.nt;
@@ -322,7 +351,13 @@ __global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* _
     for (int j = 0; j < kRows; ++j) car[j] = v4zero<T>();
     const int xs = s0 + mi - 1;
     const bool xs_int = xs > 0 && xs < nx - 1;
-    for (int sweep = 0; sweep < 2; ++sweep) {
+    // W^-1 of a row: the inverse precision of its observation (initial
+    // condition, PDE), of the Dirichlet rows, or one for the prior's rows
+    auto wrow = [&](int x, int k) -> T {
+        const int kind = tsp_row_kind<T>(L, x, k, has_ic);
+        return kind == TR_BND ? iw_bnd : kind == TR_IC ? iw_ic : kind == TR_COL ? iw_q : T(1);
+    };
+    for (int sweep = sweep_lo; sweep < sweep_hi; ++sweep) {
         // sweep 0, backward: J^T y = r from the last level down, then y / W;
         // sweep 1, forward: J z = W^-1 y from the first level up
         const bool bwd = sweep == 0;
@@ -417,35 +452,82 @@ __global__ void __launch_bounds__(kLanes) k_tsp(const LevelView<T> L, const T* _
             const V4<T> X = lanef[2 * kLanes + lane] * rd;
             V4<T> Xl, Xr;
             exch(X, 1, Xl, Xr);
-            const T iwi = k == 0 ? iw_ic : iw_q;               // interior x; boundary x gets iw_bnd
             T* ob = dst + ((size_t)blk * N + (size_t)k * nx + s0) * RW;
 #pragma unroll
             for (int j = 0; j < kRows; ++j) {
                 if (j < mint) {
                     const V4<T> xj = fma4(F(4, j), X, fma4(F(3, j), Xl, xv[j]));
                     car[j] = xj;
-                    const T wsc = (s0 + j == 0) ? iw_bnd : iwi;
-                    v4store(ob + (size_t)j * RW, bwd ? wsc * xj : xj);
+                    v4store(ob + (size_t)j * RW, bwd ? wrow(s0 + j, k) * xj : xj);
                 }
             }
             if (mi > 0) {
                 csep = X;
-                const T wsc = (xs == 0 || xs == nx - 1) ? iw_bnd : iwi;
-                v4store(ob + (size_t)(xs - s0) * RW, bwd ? wsc * X : X);
+                v4store(ob + (size_t)(xs - s0) * RW, bwd ? wrow(xs, k) * X : X);
             }
         }
     }
 }
 
+// Matern transition noise: the prior rows of a level k >= 1 carry the weight
+// T_K^2 (B = T_K B_w), so between the sweeps y_k <- T_P^-2 y_k, with T_P the
+// level's T_K between its prior rows (identity on the other rows, which are
+// decoupled from them).  One CTA per (level, block): thread 0 forms the
+// Thomas multipliers of T_P in shared memory, threads 0..3 solve the four
+// right-hand sides twice.
+template <typename T>
+__global__ void __launch_bounds__(32) k_tsp_tscale(const LevelView<T> L, int has_ic, T* __restrict__ y) {
+    extern __shared__ __align__(16) unsigned char ts_smem[];
+    T* cp = reinterpret_cast<T*>(ts_smem);           // [nx]: modified super-diagonal
+    T* den = cp + L.nx;                              // [nx]: 1 / pivot
+    const int nx = L.nx, k = blockIdx.x + 1, blk = blockIdx.y;
+    const T tc = (T)L.tk_c, to = (T)L.tk_o;
+    auto prior = [&](int x) { return x >= 0 && x < nx && tsp_row_kind<T>(L, x, k, has_ic) == TR_PRIOR; };
+    if (threadIdx.x == 0) {
+        T cprev = T(0);
+        for (int x = 0; x < nx; ++x) {
+            const bool px = prior(x);
+            const T a = px && prior(x - 1) ? to : T(0);
+            const T b = px ? tc : T(1);
+            const T c = px && prior(x + 1) ? to : T(0);
+            const T inv = T(1) / (b - a * cprev);
+            den[x] = inv;
+            cprev = c * inv;
+            cp[x] = cprev;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x >= 4) return;
+    T* v = y + ((size_t)blk * L.N + (size_t)k * nx) * RW + threadIdx.x;
+    for (int rep = 0; rep < 2; ++rep) {
+        T dprev = T(0);
+        for (int x = 0; x < nx; ++x) {
+            const T a = prior(x) && prior(x - 1) ? to : T(0);
+            dprev = (v[(size_t)x * RW] - a * dprev) * den[x];
+            v[(size_t)x * RW] = dprev;
+        }
+        for (int x = nx - 2; x >= 0; --x) v[(size_t)x * RW] -= cp[x] * v[(size_t)(x + 1) * RW];
+    }
+}
+
 }  // namespace
 
+// rows of J_t that need the per-row coupling arrays (anything but the
+// implicit-Euler collocation rows at every node with the initial condition observed)
+static bool tsp_mixed(const Level& L) {
+    return L.col.kind >= 3 || L.col.kind == 0 || L.col.sx > 1 || L.col.st > 1 || !L.tsp_ic;
+}
+
 bool tsp_applicable(const Level& L, int nic) {
-    // every collocation row present (the time-stepping factorisation needs the square J_t)
-    return L.geo == GEO_XT && L.col.kind != 0 && L.col.sx <= 1 && L.col.st <= 1 && nic > 0 && L.nx <= kTspMaxNx;
+    // PDE rows (collocation or FEM) or a prior with Matern transition noise
+    // (whose multigrid is slow: B has a wider stencil); every level block of
+    // J_t is tridiagonal either way
+    (void)nic;
+    return L.geo == GEO_XT && (L.col.kind != 0 || L.noise) && L.nx <= kTspMaxNx;
 }
 
 static size_t tsp_smem(const Level& L, size_t elem) {
-    const bool fem = L.col.kind >= 3;
+    const bool fem = tsp_mixed(L);
     return elem * (size_t)2 * (kFactorBlock + (fem ? kCplBlock : 0)) + 4 * elem * (size_t)2 * (L.nx + kLanes);
 }
 
@@ -464,21 +546,22 @@ template bool tsp_fits<double>(const Level&);
 // Factors of every level and both sweep directions, in both precisions
 // (the FP32 inner solve and the plain FP64 path); rerun whenever the
 // linearisation point changes.
-void tsp_prepare(Level& L, cudaStream_t s) {
+void tsp_prepare(Level& L, int nic, cudaStream_t s) {
+    L.tsp_ic = nic > 0 ? 1 : 0;
     const size_t n = (size_t)2 * L.nt * kFactorBlock;
     if (!L.d_tsp32) L.d_tsp32 = dev_alloc<float>(n);
     if (!L.d_tsp64) L.d_tsp64 = dev_alloc<double>(n);
-    k_tsp_factor<float><<<2 * L.nt, kLanes, 0, s>>>(L.view<float>(), L.d_tsp32);
+    k_tsp_factor<float><<<2 * L.nt, kLanes, 0, s>>>(L.view<float>(), L.tsp_ic, L.d_tsp32);
     note_launch();
-    k_tsp_factor<double><<<2 * L.nt, kLanes, 0, s>>>(L.view<double>(), L.d_tsp64);
+    k_tsp_factor<double><<<2 * L.nt, kLanes, 0, s>>>(L.view<double>(), L.tsp_ic, L.d_tsp64);
     note_launch();
-    if (L.col.kind >= 3) {
+    if (tsp_mixed(L)) {
         const size_t nc = (size_t)2 * L.nt * kCplBlock;
         if (!L.d_tspc32) L.d_tspc32 = dev_alloc<float>(nc);
         if (!L.d_tspc64) L.d_tspc64 = dev_alloc<double>(nc);
-        k_tsp_couple<float><<<2 * L.nt, kLanes, 0, s>>>(L.view<float>(), L.d_tspc32);
+        k_tsp_couple<float><<<2 * L.nt, kLanes, 0, s>>>(L.view<float>(), L.tsp_ic, L.d_tspc32);
         note_launch();
-        k_tsp_couple<double><<<2 * L.nt, kLanes, 0, s>>>(L.view<double>(), L.d_tspc64);
+        k_tsp_couple<double><<<2 * L.nt, kLanes, 0, s>>>(L.view<double>(), L.tsp_ic, L.d_tspc64);
         note_launch();
     }
     GCK(cudaGetLastError());
@@ -497,13 +580,27 @@ static void launch_tsp_kind(const Level& L, double w_ic, double w_bnd, const T* 
         attr = smem;
     }
     const double iq = L.col.qeps > 0 ? 1.0 / L.col.qeps : 0.0;
-    k_tsp<T, FEM><<<nblk, kLanes, smem, s>>>(L.view<T>(), fac, cpl, (T)(1.0 / w_ic), (T)(1.0 / w_bnd), (T)iq, r, y, z);
+    const T a = (T)(1.0 / w_ic), b = (T)(1.0 / w_bnd), q = (T)iq;
+    // with Matern transition noise the prior rows' weight T_K^2 is applied
+    // between the backward and the forward sweep
+    const bool tscale = L.noise && (L.col.kind == 0 || L.col.sx > 1 || L.col.st > 1) && L.nt > 1;
+    if (!tscale) {
+        k_tsp<T, FEM><<<nblk, kLanes, smem, s>>>(L.view<T>(), fac, cpl, a, b, q, L.tsp_ic, 0, 2, r, y, z);
+        note_launch();
+        return;
+    }
+    k_tsp<T, FEM><<<nblk, kLanes, smem, s>>>(L.view<T>(), fac, cpl, a, b, q, L.tsp_ic, 0, 1, r, y, z);
+    note_launch();
+    const size_t tsm = 2 * sizeof(T) * (size_t)L.nx;
+    k_tsp_tscale<T><<<dim3((unsigned)(L.nt - 1), (unsigned)nblk), 32, tsm, s>>>(L.view<T>(), L.tsp_ic, y);
+    note_launch();
+    k_tsp<T, FEM><<<nblk, kLanes, smem, s>>>(L.view<T>(), fac, cpl, a, b, q, L.tsp_ic, 1, 2, r, y, z);
     note_launch();
 }
 
 template <typename T>
 void launch_tsp(const Level& L, double w_ic, double w_bnd, const T* r, T* y, T* z, int nblk, cudaStream_t s) {
-    if (L.col.kind >= 3) launch_tsp_kind<T, true>(L, w_ic, w_bnd, r, y, z, nblk, s);
+    if (tsp_mixed(L)) launch_tsp_kind<T, true>(L, w_ic, w_bnd, r, y, z, nblk, s);
     else launch_tsp_kind<T, false>(L, w_ic, w_bnd, r, y, z, nblk, s);
 }
 template void launch_tsp<float>(const Level&, double, double, const float*, float*, float*, int, cudaStream_t);
