@@ -559,7 +559,13 @@ def run_prior_study(gn_steps: int = 8) -> None:
     condition as data.  One JSON line per prior and point count."""
     import numpy as np
     from paper_2503_08343_gb300 import gmrf, workloads as W
-    opts = gmrf.default_opts(max_inner=200, max_refine=30)
+    # Collocation points on a coarse grid: the time-stepping preconditioner
+    # leaves one outlying eigenvalue per point (the prior row it replaces), so
+    # the FP64 inner iteration may need thousands of steps, and the weights of
+    # the PDE rows against the prior rows between them (1e4 : 1 here) bound
+    # the attainable residual near 1e-8.  Gauss-Newton needs no more: its
+    # directions are solved to rtol 1e-8.
+    opts = gmrf.default_opts(rtol=1e-8, max_inner=3000, max_refine=20)
     for kind in W.STUDY_PRIORS:
         for stride in STUDY_STRIDES:
             pr, ob = W.burgers_prior_study(kind, stride)
@@ -571,17 +577,24 @@ def run_prior_study(gn_steps: int = 8) -> None:
             t0 = time.perf_counter()
             u, info = post.solve_mean(opts=opts)
             points, steps, dec = 0, 0, None
+            solved = bool(info["converged"])
             if stride is not None:
                 points = len(range(stride[0], nx - 1, stride[0])) * len(range(stride[1], nt, stride[1]))
                 d = np.zeros_like(u)
                 for steps in range(1, gn_steps + 1):
-                    dec, _, info = post.gauss_newton_step(u, d, opts=opts)
+                    try:
+                        dec, _, info = post.gauss_newton_step(u, d, opts=opts)
+                    except gmrf.GmrfError:      # caps reached: the step still moved u
+                        solved = False
+                        continue
+                    solved &= bool(info["converged"])
                     if dec < 1e-10:
                         break
             dt = time.perf_counter() - t0
             err = float(np.linalg.norm(u - truth) / np.linalg.norm(truth))
             print(json.dumps({"study": "burgers_prior_comparison", "prior": kind, "collocation_points": points,
                               "stride": stride, "rel_l2_error": err, "gauss_newton_steps": steps,
+                              "solves_converged": solved,
                               "last_decrement": dec, "s": round(dt, 3), "grid": [nx, nt]}), flush=True)
 
 

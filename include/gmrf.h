@@ -157,9 +157,13 @@ typedef struct gmrf_solve_opts {
     double rtol;               /* per-RHS FP64 residual target ||b - Q_u|y x||_D / ||b - Q_u|y x0||_D,
                                   ||v||_D^2 = sum_i v_i^2 / (Q_u|y)_ii (default 1e-10) */
     int32_t max_refine;        /* FP64 refinement steps (default 12) */
-    int32_t max_inner;         /* inner PCG iterations per refinement step (default 40) */
+    int32_t max_inner;         /* inner PCG iterations per refinement step (default 200) */
     double inner_rtol;         /* inner reduction of the preconditioned residual norm (default 1e-5) */
-    int32_t precision;         /* 0: FP32 inner + FP64 refinement; 1: plain FP64 PCG */
+    int32_t precision;         /* 0: FP32 inner + FP64 refinement; 1: plain FP64 PCG.  1D space-time
+                                  posteriors whose time-stepping preconditioner mixes PDE rows with the
+                                  prior's rows (collocation points on a coarser grid than the mesh, or
+                                  no observed initial condition) always take 1: FP32 cannot resolve
+                                  their weights (1 / colloc_sigma^2 against one) */
     int32_t batched;           /* 1: all right-hand sides in one batch; 0: one at a time */
     double timeout_s;          /* wall-clock limit, 0 = none */
 } gmrf_solve_opts;
@@ -251,7 +255,8 @@ gmrf_status gmrf_marginal_var_batch(gmrf_posterior* const* posts, int32_t count,
 
 /* One Gauss-Newton step on -log pi(u) (Sec. 3.3, eq. nonlinear-mode) for
  * Burgers collocation: H = Q + J^T Q_eps J + A^T R^-1 A at mu_k, solve
- * H d = -grad, warm-started from delta_prev, then Armijo backtracking
+ * H d = -grad, warm-started from delta_prev when that gives a smaller
+ * starting residual than zero (the solve's rtol is relative to it), then Armijo backtracking
  * (halving from 1, c1 = 1e-4, at most 20 halvings).  mu_k [N] (in/out, host
  * or device), delta_prev [N] (in/out, may be all zero).  newton_decrement
  * (host) receives d^T H d, alpha (host, may be NULL) the step length. */
@@ -365,6 +370,10 @@ gmrf_status gmrf_time_stencil(gmrf_posterior* post, int32_t kernel, int32_t k, i
  *                     preconditioned residual, c2 = beta), out = Q_l p',
  *                     dots = p'^T out; out2 holds [2][k][N_l]: p', then the
  *                     iterate update b + c1 x (b the iterate, c1 = alpha).
+ *  mode 5 preconditioner (level 0 only): out = M b with M the preconditioner
+ *                     of the posterior's solves (a multigrid V-cycle, or the
+ *                     time-stepping preconditioner J~^-1 W^-1 J~^-T where it
+ *                     applies), dots = b^T out; x, d and out2 are unused.
  * dots: [k] host.  Allocates its own scratch. */
 gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t precision, int32_t mode, int32_t k,
                               const double* x, const double* b, const double* d, double c0, double c1, double c2,

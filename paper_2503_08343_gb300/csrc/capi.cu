@@ -105,7 +105,7 @@ void gmrf_default_opts(gmrf_solve_opts* o) {
     if (!o) return;
     o->rtol = 1e-10;
     o->max_refine = 12;
-    o->max_inner = 60;
+    o->max_inner = 200;
     o->inner_rtol = 1e-5;
     o->precision = 0;
     o->batched = 1;
@@ -709,7 +709,10 @@ gmrf_status gmrf_marginal_var_batch(gmrf_posterior* const* posts, int32_t count,
     }
     {
         const gmrf_solve_opts o = resolve_opts(opts);
-        if (nthreads <= 1 && device_loop_usable(o)) return marginal_var_batch_async(posts, count, ns, seed, means, vars, o, infos);
+        bool fp32_inner = true;
+        for (int i = 0; i < count; ++i) fp32_inner &= !inner_needs_fp64(posts[i]->impl);
+        if (nthreads <= 1 && fp32_inner && device_loop_usable(o))
+            return marginal_var_batch_async(posts, count, ns, seed, means, vars, o, infos);
     }
     // Posteriors of one prior share its stream (and a posterior listed twice
     // shares its workspace), so each group of instances with the same prior
@@ -812,10 +815,11 @@ gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t preci
         require(post && k >= 1 && out && dots, "bad argument");
         require(level >= 0 && level < (int32_t)post->impl.levels.size(), "level out of range");
         require(precision == 0 || precision == 1, "precision must be 0 or 1");
-        require(mode >= 0 && mode <= 4, "mode must be 0..4");
-        require(mode == 3 || x, "x is required");
+        require(mode >= 0 && mode <= 5, "mode must be 0..5");
+        require(mode != 5 || level == 0, "mode 5 (preconditioner) is for level 0");
+        require(mode == 3 || mode == 5 || x, "x is required");
         require(mode == 0 || b, "b is required");
-        require(mode < 2 || out2, "out2 is required for the Chebyshev and PCG modes");
+        require(mode < 2 || mode == 5 || out2, "out2 is required for the Chebyshev and PCG modes");
         require(mode != 4 || d, "d is required for the PCG mode");
         enter(post->prior);
         Posterior& P = post->impl;
@@ -832,10 +836,11 @@ gmrf_status gmrf_stencil_step(gmrf_posterior* post, int32_t level, int32_t preci
             }
         try {
             stencil_step(P, level, precision, mode, k, din[0], mode == 0 ? nullptr : din[1],
-                         (mode == 2 || mode == 4) ? din[2] : nullptr, c0, c1, c2, buf + 3 * n, mode >= 2 ? buf + 4 * n : nullptr,
+                         (mode == 2 || mode == 4) ? din[2] : nullptr, c0, c1, c2, buf + 3 * n,
+                         (mode >= 2 && mode <= 4) ? buf + 4 * n : nullptr,
                          mode == 4 ? buf + 5 * n : nullptr, dots, s);
             copy_out(out, buf + 3 * n, n, s);
-            if (mode >= 2) copy_out(out2, buf + 4 * n, n, s);
+            if (mode >= 2 && mode <= 4) copy_out(out2, buf + 4 * n, n, s);
             if (mode == 4) copy_out(out2 + n, buf + 5 * n, n, s);
             GCK(cudaStreamSynchronize(s));
         } catch (...) {

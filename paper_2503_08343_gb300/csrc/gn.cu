@@ -293,6 +293,26 @@ GnResult gauss_newton_step(Posterior& P, double* u_io, double* d_io, bool u_dev,
     note_launch();
     k_to_slot0<<<blocks_of(N), 256, 0, s>>>(d, W.x64, N);
     note_launch();
+    // The solve stops on its residual relative to the starting one.  Near the
+    // mode the direction shrinks by orders of magnitude from step to step, so
+    // b - H d_prev can be far larger than b and a stop relative to it far too
+    // early: start from zero unless the previous direction reduces the
+    // residual (both in the D^-1-weighted norm of the stopping test).
+    {
+        StencilArgs<double> a{};
+        a.L = F.view<double>();
+        a.nblk = 1;
+        a.x = W.x64;
+        a.b = W.b64;
+        a.out = W.r64;
+        a.partial = W.partial;
+        a.rweight = F.d_dinv64;
+        const int ng = launch_stencil<double>(F.geo, M_RESID, a, s);
+        const double r0 = reduce_host(W, W.partial, ng, s);
+        launch_norm2w(W.b64, F.d_dinv64, N, 1, W.partial, elem_parts(N), s);
+        const double b0 = reduce_host(W, W.partial, elem_parts(N), s);
+        if (!(r0 < b0)) GCK(cudaMemsetAsync(W.x64, 0, sizeof(double) * (size_t)N * 4, s));
+    }
     GnResult res;
     res.stats = solve_blocked(P, 1, W.b64, W.x64, o, s);
     k_from_slot0<<<blocks_of(N), 256, 0, s>>>(W.x64, d, N);

@@ -85,6 +85,8 @@ double time_stencil(Posterior& P, int mode, int nblk, int iters, cudaStream_t s)
 // device FP64 [k][N_level] inputs x (unused by mode 3), b (modes 1-3),
 // d (mode 2, may be null) and outputs out, out2 (modes 2-3); dots[k] (host)
 // receives the kernel's per-RHS dot products.
+// stencil_step mode that applies the solve's preconditioner (level 0)
+constexpr int kStepPrecond = 5;
 void stencil_step(Posterior& P, int level, int prec, int mode, int k, const double* x, const double* b, const double* d,
                   double c0, double c1, double c2, double* out, double* out2, double* out3, double* dots, cudaStream_t s);
 
@@ -93,6 +95,9 @@ void noalloc_prepare(const Posterior& P);
 
 // tsp.cu
 bool tsp_applicable(const Level& L, int nic);
+bool tsp_mixed_weights(const Level& L);
+// the inner PCG of this posterior's solves must run in FP64 (see tsp_mixed_weights)
+bool inner_needs_fp64(const Posterior& P);
 // the application kernel's shared memory fits for precision T
 template <typename T> bool tsp_fits(const Level& L);
 void tsp_prepare(Level& L, int nic, cudaStream_t s);

@@ -842,8 +842,12 @@ static SolveStats solve_blocked_graph(Posterior& P, int nblk, const double* b64,
     return solve_graph_collect(P, nblk, s);
 }
 
-SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o,
+bool inner_needs_fp64(const Posterior& P) { return P.use_tsp && tsp_mixed_weights(P.levels[0]); }
+
+SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o_in,
                          cudaStream_t s, bool x_zero) {
+    gmrf_solve_opts o = o_in;
+    if (inner_needs_fp64(P)) o.precision = 1;
     if (device_loop_usable(o)) return solve_blocked_graph(P, nblk, b64, x64, o, s);
     (void)x_zero;
     Workspace& W = workspace(P, nblk);
@@ -1027,7 +1031,7 @@ static void stencil_step_t(Posterior& P, int level, int mode, int k, const doubl
         GCK(cudaMemcpyAsync(ab, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s));
         GCK(cudaStreamSynchronize(s));
     }
-    const int parts = std::max(stencil_max_grid(), march_max_grid());
+    const int parts = std::max(std::max(stencil_max_grid(), march_max_grid()), elem_parts(N));
     double* part = dev_alloc<double>((size_t)nblk * parts * 4);
     double* red = dev_alloc<double>((size_t)nblk * 4);
     GCK(cudaMemcpyAsync(drows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s));
@@ -1060,7 +1064,16 @@ static void stencil_step_t(Posterior& P, int level, int mode, int k, const doubl
     a.c1 = (T)c1;
     a.c2 = (T)c2;
     a.partial = part;
-    const int nparts = launch_stencil<T>(L.geo, mode, a, s);
+    int nparts = 0;
+    if (mode == kStepPrecond) {
+        // the solve's preconditioner on the finest level: z = M b
+        if (level != 0) throw Error(GMRF_E_INVALID, "stencil_step: the preconditioner mode is for level 0");
+        Workspace& W = workspace(P, nblk);
+        alloc_vecs<T>(P, W, vecs<T>(W));
+        nparts = vcycle<T>(P, W, vecs<T>(W), 0, v[1], v[3], part, s);
+    } else {
+        nparts = launch_stencil<T>(L.geo, mode, a, s);
+    }
     launch_reduce(part, nparts, nblk, red, s);
     double* dst[3] = {out, out2, out3};
     for (int i = 0; i < 3; ++i) {

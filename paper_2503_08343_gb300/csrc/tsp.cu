@@ -518,6 +518,16 @@ static bool tsp_mixed(const Level& L) {
     return L.col.kind >= 3 || L.col.kind == 0 || L.col.sx > 1 || L.col.st > 1 || !L.tsp_ic;
 }
 
+// PDE rows (weight Q_eps) next to prior rows (weight one) in J_t: for a
+// right-hand side in the span of the PDE rows (what the refinement residual
+// mostly is once the PDE is nearly met) the exact M r is of order 1 / Q_eps,
+// but the rounding errors of the backward sweep land on the prior rows with
+// weight one, about eps * Q_eps |J| / |B| relative to it: beyond one in FP32
+// for any useful Q_eps, so such solves run their inner iteration in FP64
+bool tsp_mixed_weights(const Level& L) {
+    return L.col.kind != 0 && L.col.qeps > 0 && (L.col.sx > 1 || L.col.st > 1 || !L.tsp_ic);
+}
+
 bool tsp_applicable(const Level& L, int nic) {
     // PDE rows (collocation or FEM) or a prior with Matern transition noise
     // (whose multigrid is slow: B has a wider stencil); every level block of

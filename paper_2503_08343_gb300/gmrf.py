@@ -311,14 +311,15 @@ class Posterior:
         """One launch of the fused stencil kernel (gmrf_stencil_step): mode 0
         apply, 1 residual, 2 Chebyshev step, 3 Chebyshev from zero, 4 PCG
         iteration (x previous direction, b iterate, d preconditioned residual,
-        c1 alpha, c2 beta); inputs [k][N_level].  Returns (out, out2 or None,
-        dots), and for mode 4 (q, p', dots, updated iterate)."""
+        c1 alpha, c2 beta), 5 the solve's preconditioner z = M b (level 0);
+        inputs [k][N_level].  Returns (out, out2 or None, dots), and for mode 4
+        (q, p', dots, updated iterate)."""
         ref = next(v for v in (x, b) if v is not None)
         k, n = np.atleast_2d(ref).shape
         prep = lambda v: None if v is None else np.ascontiguousarray(np.atleast_2d(v), dtype=np.float64)
         x, b, d = prep(x), prep(b), prep(d)
         out = np.empty((k, n))
-        out2 = np.empty((2 * k if mode == 4 else k, n)) if mode >= 2 else None
+        out2 = np.empty((2 * k if mode == 4 else k, n)) if 2 <= mode <= 4 else None
         dots = np.empty(k)
         _check(load().gmrf_stencil_step(self.h, level, precision, mode, k, _ptr(x), _ptr(b), _ptr(d),
                                         c0, c1, c2, _ptr(out), _ptr(out2), _dptr(dots)))

@@ -291,17 +291,20 @@ STUDY_PRIORS = ("advdiff", "product_matern")
 
 
 def burgers_prior_study(prior: str, stride, nx: int = 257, nt: int = 101, nu: float = 0.01,
-                        noise_kappa: float = 35.0, colloc_sigma: float = 1e-3, ic_sigma: float = 1e-3):
+                        noise_kappa: float = 35.0, colloc_sigma: float = 1e-2, ic_sigma: float = 1e-3):
     """Burgers on (-1, 1) x (0, 1) with u(x, 0) = -sin(pi x) observed at every
     t = 0 node (noise ic_sigma) and the collocation rows on the points
     x % sx == 0, k % st == 0 (stride (sx, st); None: no collocation).
-    prior "advdiff": the advection-diffusion proxy (c = 1, the diffusion of the
-    equation) with Matern transition noise of inverse range noise_kappa;
+    prior "advdiff": the advection-diffusion proxy with the bulk advection of
+    the initial condition (its mean, zero for -sin(pi x)) and the diffusion of
+    the equation, with Matern transition noise of inverse range noise_kappa;
     "product_matern": no dynamics (c = nu = 0), the same Matern noise and an
     AR(1) decay with temporal range 3 (a separable Matern prior with
     nu_t = 1/2 in time).  Returns (prior, obs)."""
     if prior == "advdiff":
-        pr = prior_st1d(nx, nt, c=1.0, nu=nu, tau=1.0, kappa0=10.0, x0=-1.0, x1=1.0, t1=1.0)
+        xs = np.linspace(-1.0, 1.0, nx)
+        c = float(np.round(np.mean(-np.sin(np.pi * xs)), 12)) + 0.0   # bulk advection of the initial condition
+        pr = prior_st1d(nx, nt, c=c, nu=nu, tau=1.0, kappa0=10.0, x0=-1.0, x1=1.0, t1=1.0)
         pr = dict(pr, noise_kappa=float(noise_kappa))
     else:
         dt = 1.0 / (nt - 1)

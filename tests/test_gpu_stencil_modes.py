@@ -36,7 +36,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from oracle import infer
+from oracle import infer, observe
 from paper_2503_08343_gb300 import gmrf
 from paper_2503_08343_gb300 import workloads as W
 
@@ -88,15 +88,40 @@ CASES = {
 }
 
 
-def _bound_matrix(post):
+def _bound_matrix(post, jabs=None):
     """|B|^T |B| + |A|^T Q_eps |A|: the absolute-value form of how the
-    kernel evaluates Q (the stacked root twice, then the observation rows)."""
+    kernel evaluates Q (the stacked root twice, then the observation rows).
+    jabs replaces |A| on the collocation rows (the last rows of A)."""
     aB = abs(post.B)
     aA = abs(post.A)
+    if jabs is not None:
+        aA = sp.vstack([aA[:aA.shape[0] - jabs.shape[0]], jabs]).tocsr()
     return (aB.T @ aB + aA.T @ sp.diags(post.rinv) @ aA).tocsr()
 
 
-def _check_modes(post_gpu, post_o, k, level, prec, seed, modes=(0, 1, 2, 3, 4)):
+def _colloc_abs(pr, ob, u):
+    """|J| as the kernel forms the linearised Burgers rows: each coefficient
+    is a fixed part (time and diffusion terms) plus terms linear in the
+    linearisation point, and it rounds on the size of those terms, not of
+    their sum (an advection tap can cancel the diffusion tap).  The convective
+    part J(v) - J(0) is linear in v and each of its coefficients reads u at
+    one or two nodes of a level, at x distance 0, 1 or 2; the absolute-value
+    form of such a coefficient is the largest |J(v) - J(0)| over v = s |u|
+    with the sign patterns s = 1, (-1)^x and (+1 for x mod 4 in {0, 1}, -1
+    otherwise), which give every such pair of nodes both equal and opposite
+    signs."""
+    nx = pr["n"][0]
+    nu = ob["burgers_nu"]
+    J0 = observe.pde_rows(pr, ob, np.zeros_like(u), nu)[0].tocsr()
+    x = np.arange(u.size) % nx
+    conv = None
+    for sgn in (np.ones(u.size), (-1.0) ** x, np.where(x % 4 < 2, 1.0, -1.0)):
+        c = abs(observe.pde_rows(pr, ob, sgn * np.abs(u), nu)[0].tocsr() - J0)
+        conv = c if conv is None else conv.maximum(c)
+    return (abs(J0) + conv).tocsr()
+
+
+def _check_modes(post_gpu, post_o, k, level, prec, seed, modes=(0, 1, 2, 3, 4), jabs=None):
     rng = np.random.default_rng(seed)
     N = post_o.Q.shape[0]
     rnd = lambda: rng.normal(size=(k, N))
@@ -108,7 +133,7 @@ def _check_modes(post_gpu, post_o, k, level, prec, seed, modes=(0, 1, 2, 3, 4)):
     else:
         c0, c1, c2 = C0, C1, C2
     Q = post_o.Qpost
-    M = _bound_matrix(post_o)
+    M = _bound_matrix(post_o, jabs)
     dinv = 1.0 / Q.diagonal()
     g, gd = GAMMA[prec], 2 * GAMMA[prec]
     Qx = (Q @ x.T).T
@@ -194,23 +219,30 @@ def test_stencil_modes_on_the_first_coarse_level(name):
     _check_modes(post, orc, k, 1, 0, seed=11)
 
 
-@pytest.mark.parametrize("form", ["collocation", "fem_cn", "noise"])
+@pytest.mark.parametrize("form", ["collocation", "fem_cn", "noise", "strided", "fem_cn_strided"])
 def test_stencil_modes_burgers_linearised(form):
     # collocation (or FEM Crank-Nicolson) rows of the Burgers residual
     # linearised at the Gauss-Newton iterate the library holds after one step
-    # (Sec. 3.3)
+    # (Sec. 3.3); "strided": collocation points on every fourth node in x and
+    # t (sigma 1e-3, as in the Gauss-Newton test)
     pr, ob = W.c3_burgers(nx=65, nt=33, m=40)
     if form == "noise":         # Matern transition noise in the prior, collocation rows
         pr = dict(pr, noise_kappa=12.0)
     else:
-        ob = dict(ob, colloc_form=form)
+        ob = dict(ob, colloc_form=form.replace("_strided", "").replace("strided", "collocation"))
+    if form.endswith("strided"):
+        ob = dict(ob, colloc_stride=(4, 4), colloc_sigma=1e-3)
     post = gmrf.Posterior(gmrf.Prior(pr), ob)
     u, _ = post.solve_mean()
     d = np.zeros_like(u)
-    post.gauss_newton_step(u, d)
+    try:
+        post.gauss_newton_step(u, d, opts=gmrf.default_opts(max_refine=3))
+    except gmrf.GmrfError:
+        pass            # a step stopped at its caps still leaves the rows linearised at the returned u
     orc = infer.condition(pr, ob, linearise_at=u)
+    jabs = _colloc_abs(pr, ob, u)
     for prec in (0, 1):
-        _check_modes(post, orc, 5, 0, prec, seed=21 + prec, modes=(0, 1, 4))
+        _check_modes(post, orc, 5, 0, prec, seed=21 + prec, modes=(0, 1, 4), jabs=jabs)
 
 
 def test_stencil_modes_full_size_matern_65_rhs():
