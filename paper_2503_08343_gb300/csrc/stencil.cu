@@ -194,12 +194,14 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
 
     // per-thread geometry of the staged items and the s items (same every unit)
     int p_dx[KP], p_dy[KP], p_dt[KP], p_rel[KP];
+    unsigned p_own = 0;     // bit k: staged item k is a node of the tile itself
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
         const int e = tid + 256 * k;
         const int px = e % PX, py = (e / PX) % PY, pt = e / (PX * PY);
         p_dx[k] = px - HX; p_dy[k] = py - HY; p_dt[k] = pt - HT;
         p_rel[k] = (p_dt[k] * ny + p_dy[k]) * nx + p_dx[k];
+        if (p_dx[k] >= 0 && p_dx[k] < TX && p_dy[k] >= 0 && p_dy[k] < TY && p_dt[k] >= 0 && p_dt[k] < TT) p_own |= 1u << k;
     }
     // s items: rows of B_w p on ring SR around the tile (s_e1: the item's
     // index in the ring-1 layout, -1 outside it)
@@ -287,6 +289,10 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
     T dacc[KB][4];
 #pragma unroll
     for (int j = 0; j < KB; ++j) dacc[j][0] = dacc[j][1] = dacc[j][2] = dacc[j][3] = T(0);
+    // PCG: alpha and beta of the unit's right-hand sides, reloaded when the
+    // block group changes (a CTA's units are consecutive, so rarely)
+    V4<T> pcg_a[KB], pcg_b[KB];
+    int pcg_grp = -1;
     int st = 0;
 #pragma unroll 1
     // Two barriers per unit: the first (after this unit's copies landed) also
@@ -339,33 +345,37 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
         }
         V4<T> pold[KB];             // PCG: the previous direction at the own node
         if (MODE == M_PCG) {        // staged p, z -> p' = z + beta p in place
-            // the own node's old direction from global memory (L2: the tile was
-            // just copied), so the in-place update needs no barrier before it
-            const int ox = cur.tx * TX + lx, oy = cur.ty * TY + ly, ot = cur.tt * TT + lt;
-            const bool oown = ox < nx && oy < ny && ot < nt;
-            const size_t onode = oown ? ((size_t)ot * ny + oy) * nx + ox : 0;
+            if (cur.grp != pcg_grp) {
+                pcg_grp = cur.grp;
 #pragma unroll
-            for (int j = 0; j < KB; ++j) {
-                const int blk = min(cur.grp * KB + j, nblk - 1);
-                pold[j] = v4load(A.x + ((size_t)blk * N + onode) * RW);
+                for (int j = 0; j < KB; ++j) {
+                    const int blk = min(cur.grp * KB + j, nblk - 1);
+                    const double* ap = A.alpha + (size_t)blk * RW;
+                    const double* bp = A.beta + (size_t)blk * RW;
+                    pcg_a[j] = V4<T>{(T)ap[0], (T)ap[1], (T)ap[2], (T)ap[3]};
+                    pcg_b[j] = V4<T>{(T)bp[0], (T)bp[1], (T)bp[2], (T)bp[3]};
+                }
             }
-            V4<T> bt[KB];
+            auto upd = [&](int e, int j) {
+                const V4<T> pv = S.p[st][e][j], zv = S.z[MODE == M_PCG ? st : 0][MODE == M_PCG ? e : 0][j];
+                S.p[st][e][j] = V4<T>{fma(pcg_b[j].a, pv.a, zv.a), fma(pcg_b[j].b, pv.b, zv.b), fma(pcg_b[j].c, pv.c, zv.c),
+                                      fma(pcg_b[j].d, pv.d, zv.d)};
+            };
+            // the own node is updated by its own thread, which reads the old
+            // direction there first; every halo item by the thread that stages
+            // it (the two sets are disjoint, so no barrier before the update)
 #pragma unroll
             for (int j = 0; j < KB; ++j) {
-                const int blk = min(cur.grp * KB + j, nblk - 1);
-                const double* bp = A.beta + (size_t)blk * RW;
-                bt[j] = V4<T>{(T)bp[0], (T)bp[1], (T)bp[2], (T)bp[3]};
+                pold[j] = S.p[st][pbase][j];
+                upd(pbase, j);
             }
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
                 const int e = tid + 256 * k;
                 if (KP * 256 > PN && e >= PN) break;
+                if ((p_own >> k) & 1u) continue;
 #pragma unroll
-                for (int j = 0; j < KB; ++j) {
-                    const V4<T> pv = S.p[st][e][j], zv = S.z[MODE == M_PCG ? st : 0][MODE == M_PCG ? e : 0][j];
-                    S.p[st][e][j] = V4<T>{fma(bt[j].a, pv.a, zv.a), fma(bt[j].b, pv.b, zv.b), fma(bt[j].c, pv.c, zv.c),
-                                          fma(bt[j].d, pv.d, zv.d)};
-                }
+                for (int j = 0; j < KB; ++j) upd(e, j);
             }
             __syncthreads();
         }
@@ -608,11 +618,10 @@ __global__ void __launch_bounds__(256) k_stencil(const StencilArgs<T> A, int nun
                 dacc[j][0] += pown[j].a * q[j].a; dacc[j][1] += pown[j].b * q[j].b;
                 dacc[j][2] += pown[j].c * q[j].c; dacc[j][3] += pown[j].d * q[j].d;
                 if (MODE == M_PCG) {
-                    const double* ap = A.alpha + (size_t)blk * RW;
                     const V4<T> xo = S.b[MODE != M_APPLY ? st : 0][tid][j];
                     v4store(A.out2 + off, pown[j]);
-                    v4store(A.out3 + off, V4<T>{fma((T)ap[0], pold[j].a, xo.a), fma((T)ap[1], pold[j].b, xo.b),
-                                                fma((T)ap[2], pold[j].c, xo.c), fma((T)ap[3], pold[j].d, xo.d)});
+                    v4store(A.out3 + off, V4<T>{fma(pcg_a[j].a, pold[j].a, xo.a), fma(pcg_a[j].b, pold[j].b, xo.b),
+                                                fma(pcg_a[j].c, pold[j].c, xo.c), fma(pcg_a[j].d, pold[j].d, xo.d)});
                 }
             } else if (MODE == M_RESID) {
                 const V4<T> r = S.b[MODE != M_APPLY ? st : 0][tid][j] - q[j];
