@@ -157,7 +157,8 @@ typedef struct gmrf_solve_opts {
     double rtol;               /* per-RHS FP64 residual target ||b - Q_u|y x||_D / ||b - Q_u|y x0||_D,
                                   ||v||_D^2 = sum_i v_i^2 / (Q_u|y)_ii (default 1e-10) */
     int32_t max_refine;        /* FP64 refinement steps (default 12) */
-    int32_t max_inner;         /* inner PCG iterations per refinement step (default 200) */
+    int32_t max_inner;         /* inner PCG iterations per refinement step; 0 (default): 60 with the
+                                  multigrid preconditioner, 200 with the time-stepping one */
     double inner_rtol;         /* inner reduction of the preconditioned residual norm (default 1e-5) */
     int32_t precision;         /* 0: FP32 inner + FP64 refinement; 1: plain FP64 PCG.  1D space-time
                                   posteriors whose time-stepping preconditioner mixes PDE rows with the

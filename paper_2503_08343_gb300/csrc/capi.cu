@@ -76,7 +76,7 @@ static gmrf_solve_opts resolve_opts(const gmrf_solve_opts* o) {
     gmrf_solve_opts r = *o;
     if (!(r.rtol > 0)) r.rtol = d.rtol;
     if (r.max_refine <= 0) r.max_refine = d.max_refine;
-    if (r.max_inner <= 0) r.max_inner = d.max_inner;
+    if (r.max_inner < 0) r.max_inner = 0;      // automatic, resolved per posterior
     if (!(r.inner_rtol > 0)) r.inner_rtol = d.inner_rtol;
     return r;
 }
@@ -105,7 +105,7 @@ void gmrf_default_opts(gmrf_solve_opts* o) {
     if (!o) return;
     o->rtol = 1e-10;
     o->max_refine = 12;
-    o->max_inner = 200;
+    o->max_inner = 0;
     o->inner_rtol = 1e-5;
     o->precision = 0;
     o->batched = 1;

@@ -98,6 +98,10 @@ bool tsp_applicable(const Level& L, int nic);
 bool tsp_mixed_weights(const Level& L);
 // the inner PCG of this posterior's solves must run in FP64 (see tsp_mixed_weights)
 bool inner_needs_fp64(const Posterior& P);
+// o with its automatic fields resolved for P (max_inner <= 0: 60 with the
+// multigrid preconditioner, 200 with the time-stepping one; FP64 inner solve
+// where inner_needs_fp64)
+gmrf_solve_opts solve_opts_for(const Posterior& P, const gmrf_solve_opts& o);
 // the application kernel's shared memory fits for precision T
 template <typename T> bool tsp_fits(const Level& L);
 void tsp_prepare(Level& L, int nic, cudaStream_t s);

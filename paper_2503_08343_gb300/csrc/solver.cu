@@ -791,13 +791,28 @@ static void build_solve_graph(Posterior& P, Workspace& W, SolveGraph& G, const d
     G.max_inner = o.max_inner;
 }
 
+bool inner_needs_fp64(const Posterior& P) { return P.use_tsp && tsp_mixed_weights(P.levels[0]); }
+
+gmrf_solve_opts solve_opts_for(const Posterior& P, const gmrf_solve_opts& o_in) {
+    gmrf_solve_opts o = o_in;
+    // automatic inner cap: the multigrid inner solve is restarted from the
+    // FP64 residual after 60 iterations (measured faster than longer FP32
+    // runs on the space-time priors); the time-stepping preconditioner
+    // leaves one outlying eigenvalue per data point or collocation point and
+    // needs the longer Krylov run
+    if (o.max_inner <= 0) o.max_inner = P.use_tsp ? 200 : 60;
+    if (inner_needs_fp64(P)) o.precision = 1;
+    return o;
+}
+
 bool device_loop_usable(const gmrf_solve_opts& o) {
     return o.precision != 1 && o.batched != 0 && !(o.timeout_s > 0) && device_loop_enabled();
 }
 
 // Enqueues the device-driven solve on s (builds its graph on first use) and
 // the copy of the controller state to pinned host memory; nothing waits.
-void solve_graph_launch(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o, cudaStream_t s) {
+void solve_graph_launch(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o_in, cudaStream_t s) {
+    const gmrf_solve_opts o = solve_opts_for(P, o_in);
     Workspace& W = workspace(P, nblk);
     alloc_vecs<float>(P, W, W.v32);
     const double inner_tol = o.inner_rtol;
@@ -842,12 +857,9 @@ static SolveStats solve_blocked_graph(Posterior& P, int nblk, const double* b64,
     return solve_graph_collect(P, nblk, s);
 }
 
-bool inner_needs_fp64(const Posterior& P) { return P.use_tsp && tsp_mixed_weights(P.levels[0]); }
-
 SolveStats solve_blocked(Posterior& P, int nblk, const double* b64, double* x64, const gmrf_solve_opts& o_in,
                          cudaStream_t s, bool x_zero) {
-    gmrf_solve_opts o = o_in;
-    if (inner_needs_fp64(P)) o.precision = 1;
+    const gmrf_solve_opts o = solve_opts_for(P, o_in);
     if (device_loop_usable(o)) return solve_blocked_graph(P, nblk, b64, x64, o, s);
     (void)x_zero;
     Workspace& W = workspace(P, nblk);
