@@ -773,6 +773,8 @@ __global__ void __launch_bounds__(256) k_sample_normals(uint64_t seed, const int
     if (n0 + 1 < M) v4store(p + RW, V4<double>{b[0], b[1], b[2], b[3]});
 }
 
+constexpr int kObsChunk = 64;      // observation rows staged at a time by k_sample_rhs
+
 template <int GEO>
 __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, uint64_t seed,
                                                     const int32_t* __restrict__ slot_sample,
@@ -784,7 +786,9 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
     constexpr int HYS = HY / 2;
     constexpr int SX = TX + 2, SY = TY + HY, ST = TT + HT;
     __shared__ V4<double> sz[ST][SY][SX];       // z1 on the rows touching the tile
-    __shared__ V4<double> sq[TT][TY][TX];
+    __shared__ int32_t s_onode[kObsChunk][8];   // a chunk of the tile's observation rows
+    __shared__ double s_ow[kObsChunk][8];
+    __shared__ int32_t s_orow[kObsChunk];
     // Matern transition noise: B^T z1 = B_w^T (T_K z1), z1 staged on rows two
     // past the tile first
     constexpr int SXN = GEO == GEO_XT ? SX + 2 : 1;
@@ -910,38 +914,42 @@ __global__ void __launch_bounds__(256) k_sample_rhs(const LevelView<double> L, u
             }
         }
     }
-    sq[lt][ly][lx] = q;
-    __syncthreads();
     if (L.obs != nullptr) {
+        // A^T R^-1/2 z2 at the own node: the tile's observation rows are
+        // staged in chunks (nodes, weights w sqrt(rinv), rows), then each
+        // node adds its terms in list order (ascending row index) and node
+        // order within a row, so the sum is the same on every run
+        const int32_t me = own ? (int32_t)(((long long)gt * ny + gy) * nx + gx) : -1;
         const int k0 = L.tile_ptr[tile], k1 = L.tile_ptr[tile + 1];
-        for (int k = k0 + tid; k < k1; k += 256) {
-            const ObsRow& o = L.obs[L.tile_idx[k]];
-            double v[4];
+        for (int c0 = k0; c0 < k1; c0 += kObsChunk) {        // the same trip count in every thread
+            const int cn = min(kObsChunk, k1 - c0);
+            __syncthreads();                                  // the previous chunk has been read
+            for (int e = tid; e < cn * 8; e += 256) {
+                const int j = e >> 3, n = e & 7;
+                const ObsRow& o = L.obs[L.tile_idx[c0 + j]];
+                s_onode[j][n] = n < o.nn ? o.node[n] : -1;
+                s_ow[j][n] = n < o.nn ? o.wd[n] * sqrt(o.rinv) : 0.0;
+                if (n == 0) s_orow[j] = o.row;
+            }
+            __syncthreads();
+            if (own) {
+                for (int j = 0; j < cn; ++j) {
 #pragma unroll
-            const double* zr = z2 + ((size_t)blk * rows + o.row) * RW;
+                    for (int n = 0; n < 8; ++n) {
+                        if (s_onode[j][n] != me) continue;
+                        double v[4];
+                        const double* zr = z2 + ((size_t)blk * rows + s_orow[j]) * RW;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = (sid[c] >= 0 && z2 != nullptr) ? zr[c] : 0.0;
-            const double sr = sqrt(o.rinv);
-            for (int n = 0; n < o.nn; ++n) {
-                const long long nd = o.node[n];
-                const int ox = (int)(nd % nx);
-                const long long r2 = nd / nx;
-                const int oy = (int)(r2 % ny), ot = (int)(r2 / ny);
-                const int ux = ox - tx0, uy = oy - ty0, ut = ot - tt0;
-                if (ux < 0 || ux >= TX || uy < 0 || uy >= TY || ut < 0 || ut >= TT) continue;
-                double* dst = reinterpret_cast<double*>(&sq[ut][uy][ux]);
-                const double w = o.wd[n] * sr;
-                atomicAdd(dst + 0, w * v[0]);
-                atomicAdd(dst + 1, w * v[1]);
-                atomicAdd(dst + 2, w * v[2]);
-                atomicAdd(dst + 3, w * v[3]);
+                        for (int c = 0; c < 4; ++c) v[c] = (sid[c] >= 0 && z2 != nullptr) ? zr[c] : 0.0;
+                        q = fma4(s_ow[j][n], V4<double>{v[0], v[1], v[2], v[3]}, q);
+                    }
+                }
             }
         }
-        __syncthreads();
     }
     if (own) {
         const long long node = ((long long)gt * ny + gy) * nx + gx;
-        V4<double> out = sq[lt][ly][lx];
+        V4<double> out = q;
         double* po = reinterpret_cast<double*>(&out);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -985,16 +993,53 @@ void launch_rademacher_fill(uint64_t seed, const int32_t* slot_sample, double* b
     { k_rademacher_fill<<<dim3((unsigned)((N + 255) / 256), nblk), 256, 0, s>>>(seed, slot_sample, b64, N); note_launch(); }
 }
 
-// data right-hand side A^T R^-1 y of the point observations
-__global__ void k_obs_scatter(const ObsRow* __restrict__ obs, int nobs, const double* __restrict__ y, double* __restrict__ b) {
-    const int k = blockIdx.x * 256 + threadIdx.x;
-    if (k >= nobs) return;
-    const ObsRow& o = obs[k];
-    const double v = o.rinv * y[o.row];
-    for (int n = 0; n < o.nn; ++n) atomicAdd(b + o.node[n], o.wd[n] * v);
+// Observation sums at the nodes, gathered per tile: each node of the tile
+// adds the terms of the tile's observation rows that touch it, in list order
+// (ascending row index) and node order within a row, so the result is the
+// same on every run (no atomics).  kind 0: the data right-hand side
+// A^T R^-1 y over the point rows (row index < nrows_y); kind 1: the
+// observation part sum_k rinv_k w_kn^2 of the diagonal over every row.
+template <int GEO>
+__global__ void __launch_bounds__(256) k_obs_gather(const LevelView<double> L, int kind, int nrows_y,
+                                                    const double* __restrict__ y, double* __restrict__ out) {
+    using G = Geo<GEO>;
+    constexpr int TX = G::TX, TY = G::TY;
+    const int nx = L.nx, ny = L.ny, nt = L.nt;
+    const int tile = blockIdx.x, tid = threadIdx.x;
+    const int tx0 = (tile % L.tiles_x) * TX;
+    const int rest = tile / L.tiles_x;
+    const int ty0 = (rest % L.tiles_y) * TY;
+    const int tt0 = (rest / L.tiles_y) * G::TT;
+    const int gx = tx0 + tid % TX, gy = ty0 + (tid / TX) % TY, gt = tt0 + tid / (TX * TY);
+    if (gx >= nx || gy >= ny || gt >= nt) return;
+    const int32_t me = (int32_t)(((long long)gt * ny + gy) * nx + gx);
+    const int k0 = L.tile_ptr[tile], k1 = L.tile_ptr[tile + 1];
+    double acc = out[me];
+    bool hit = false;
+    for (int k = k0; k < k1; ++k) {
+        const ObsRow& o = L.obs[L.tile_idx[k]];
+        if (kind == 0 && o.row >= nrows_y) continue;
+        for (int n = 0; n < o.nn; ++n) {
+            if (o.node[n] != me) continue;
+            acc += kind == 0 ? o.wd[n] * (o.rinv * y[o.row]) : o.wd[n] * o.wd[n] * o.rinv;
+            hit = true;
+        }
+    }
+    if (hit) out[me] = acc;
 }
-void launch_obs_scatter(const ObsRow* obs, int nobs, const double* y, double* b, cudaStream_t s) {
-    if (nobs > 0) { k_obs_scatter<<<(nobs + 255) / 256, 256, 0, s>>>(obs, nobs, y, b); note_launch(); }
+
+static void launch_obs_gather(const Level& Lv, int kind, int nrows_y, const double* y, double* out, cudaStream_t s) {
+    if (Lv.nobs <= 0) return;
+    const LevelView<double> L = Lv.view<double>();
+    const unsigned grid = (unsigned)((long long)L.tiles_x * L.tiles_y * L.tiles_t);
+    if (Lv.geo == GEO_XY) k_obs_gather<GEO_XY><<<grid, 256, 0, s>>>(L, kind, nrows_y, y, out);
+    else if (Lv.geo == GEO_XT) k_obs_gather<GEO_XT><<<grid, 256, 0, s>>>(L, kind, nrows_y, y, out);
+    else k_obs_gather<GEO_XYT><<<grid, 256, 0, s>>>(L, kind, nrows_y, y, out);
+    note_launch();
+}
+
+void launch_obs_scatter(const Level& L, int nrows_y, const double* y, double* b, cudaStream_t s) {
+    if (nrows_y > 0) launch_obs_gather(L, 0, nrows_y, y, b, s);
 }
 
 // layout conversion between blocked batches and [count][N] row-major arrays;
@@ -1161,15 +1206,7 @@ template <typename T> void launch_diag(int geo, const LevelView<T>& L, double* d
 template void launch_diag<float>(int, const LevelView<float>&, double*, cudaStream_t);
 template void launch_diag<double>(int, const LevelView<double>&, double*, cudaStream_t);
 
-__global__ void k_obs_diag(const ObsRow* __restrict__ obs, int nobs, double* __restrict__ diag) {
-    const int k = blockIdx.x * 256 + threadIdx.x;
-    if (k >= nobs) return;
-    const ObsRow& o = obs[k];
-    for (int n = 0; n < o.nn; ++n) atomicAdd(diag + o.node[n], o.wd[n] * o.wd[n] * o.rinv);
-}
-void launch_obs_diag(const ObsRow* obs, int nobs, double* diag, cudaStream_t s) {
-    if (nobs > 0) { k_obs_diag<<<(nobs + 255) / 256, 256, 0, s>>>(obs, nobs, diag); note_launch(); }
-}
+void launch_obs_diag(const Level& L, double* diag, cudaStream_t s) { launch_obs_gather(L, 1, 0, nullptr, diag, s); }
 
 // max_n (total_n - prior_n) / total_n: the largest share of a node's diagonal
 // contributed by the observation rows.  Non-negative doubles order like their

@@ -139,14 +139,17 @@ void launch_scale64(const double* r64, const double* norms, double* out, long lo
 void launch_sample_rhs(int geo, const LevelView<double>& L, uint64_t seed, const int32_t* slot_sample,
                        const double* bdata, double* b64, double* z1, double* z2, long long rows, int nblk,
                        cudaStream_t s);
-void launch_obs_scatter(const ObsRow* obs, int nobs, const double* y, double* b, cudaStream_t s);
+// data right-hand side A^T R^-1 y of the point rows (row index < nrows_y),
+// added into b; deterministic per-tile gather
+void launch_obs_scatter(const Level& L, int nrows_y, const double* y, double* b, cudaStream_t s);
 void launch_pack(const double* src, double* dst, const int32_t* slot_src, long long N, int nblk, cudaStream_t s);
 void launch_unpack(const double* src, double* dst, const int32_t* slot_dst, long long N, int nblk, cudaStream_t s);
 template <typename QT>
 void launch_rbmc(const QT* Qx, const double* x, const double* diag, const int32_t* slot_sample, long long N,
                  int nblk, int ns, double* var, double* se, cudaStream_t s);
 template <typename T> void launch_diag(int geo, const LevelView<T>& L, double* diag64, cudaStream_t s);
-void launch_obs_diag(const ObsRow* obs, int nobs, double* diag, cudaStream_t s);
+// observation part of the diagonal, added into diag; deterministic per-tile gather
+void launch_obs_diag(const Level& L, double* diag, cudaStream_t s);
 void launch_max_share(const double* prior, const double* total, long long N, unsigned long long* out, cudaStream_t s);
 void launch_finish_diag(const double* diag, float* dinv32, double* dinv64, long long N, cudaStream_t s);
 void launch_normals(uint64_t seed, int stream, int sample0, int count, long long n, double* out, cudaStream_t s);

@@ -126,7 +126,7 @@ static void setup_diag(Level& L, cudaStream_t s, double* share = nullptr) {
         GCK(cudaMemsetAsync(d_share, 0, sizeof(unsigned long long), s));
         GCK(cudaMemcpyAsync(L.d_dinv64, L.d_diag64, (size_t)L.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-    launch_obs_diag(L.d_obs, L.nobs, L.d_diag64, s);
+    launch_obs_diag(L, L.d_diag64, s);
     if (share) {
         launch_max_share(L.d_dinv64, L.d_diag64, L.N, d_share, s);
         unsigned long long bits = 0;
