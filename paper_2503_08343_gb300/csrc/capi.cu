@@ -200,7 +200,7 @@ void gmrf_prior_destroy(gmrf_prior* p) {
 static void rebuild_bdata(Posterior& P, cudaStream_t s) {
     const Level& L = P.levels[0];
     GCK(cudaMemcpyAsync(P.d_bdata, P.d_bstatic, sizeof(double) * L.N, cudaMemcpyDeviceToDevice, s));
-    launch_obs_scatter(L, (int)P.m, P.d_ypoint, P.d_bdata, s);
+    launch_obs_data_rhs(L, (int)P.m, P.d_ypoint, P.d_bdata, s);
 }
 
 gmrf_status gmrf_condition(gmrf_prior* prior, const gmrf_obs_desc* obs, gmrf_posterior** out) {

@@ -1038,7 +1038,7 @@ static void launch_obs_gather(const Level& Lv, int kind, int nrows_y, const doub
     note_launch();
 }
 
-void launch_obs_scatter(const Level& L, int nrows_y, const double* y, double* b, cudaStream_t s) {
+void launch_obs_data_rhs(const Level& L, int nrows_y, const double* y, double* b, cudaStream_t s) {
     if (nrows_y > 0) launch_obs_gather(L, 0, nrows_y, y, b, s);
 }
 

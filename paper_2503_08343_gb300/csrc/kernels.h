@@ -141,7 +141,7 @@ void launch_sample_rhs(int geo, const LevelView<double>& L, uint64_t seed, const
                        cudaStream_t s);
 // data right-hand side A^T R^-1 y of the point rows (row index < nrows_y),
 // added into b; deterministic per-tile gather
-void launch_obs_scatter(const Level& L, int nrows_y, const double* y, double* b, cudaStream_t s);
+void launch_obs_data_rhs(const Level& L, int nrows_y, const double* y, double* b, cudaStream_t s);
 void launch_pack(const double* src, double* dst, const int32_t* slot_src, long long N, int nblk, cudaStream_t s);
 void launch_unpack(const double* src, double* dst, const int32_t* slot_dst, long long N, int nblk, cudaStream_t s);
 template <typename QT>
