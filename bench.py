@@ -313,7 +313,9 @@ def run_stencil_timing(which: str, iters: int) -> None:
     active (apply, residual and the fused PCG mode: its preconditioner is the
     time-stepping one, not Chebyshev smoothing; 1 B per RHS x unknown more for
     the linearisation point); c5 = 2D space-time 128^2 x 64 with 33 (the
-    marching kernel, which has no fused PCG mode)."""
+    marching kernel, which has no fused PCG mode).  c3 also runs one
+    application of the time-stepping preconditioner in the NVTX range
+    "tsp_apply"."""
     import torch
     from paper_2503_08343_gb300 import gmrf, workloads as W
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -343,6 +345,18 @@ def run_stencil_timing(which: str, iters: int) -> None:
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push(f"stencil_{name}")
         post.time_stencil(mode, k, 1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if which == "c3":
+        # one application of the direction solve's preconditioner (the
+        # time-stepping sweeps, one block of four right-hand sides) inside the
+        # NVTX range "tsp_apply", for a profiler filter
+        import numpy as np
+        rhs = np.random.default_rng(0).normal(size=(4, post.N))
+        post.stencil_step(5, b=rhs)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("tsp_apply")
+        post.stencil_step(5, b=rhs)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
 
