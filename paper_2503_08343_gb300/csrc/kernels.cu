@@ -1120,7 +1120,7 @@ template void launch_rbmc<float>(const float*, const double*, const double*, con
 template void launch_rbmc<double>(const double*, const double*, const double*, const int32_t*, long long, int, int,
                                   double*, double*, cudaStream_t);
 
-// diagonal of B^T B + J^T Q_eps J at every node (observation part added by k_obs_diag)
+// diagonal of B^T B + J^T Q_eps J at every node (observation part added by k_obs_gather)
 template <typename T>
 __global__ void k_diag(const LevelView<T> L, double* __restrict__ diag) {
     const long long n = (long long)blockIdx.x * 256 + threadIdx.x;
