@@ -357,3 +357,28 @@ def test_collocation_stride_is_conditioning_on_the_active_rows_only():
     ba = full.b + Ja.T @ ((Ja @ u - F[act]) / obs["colloc_sigma"] ** 2)
     assert abs(post.Qpost - Qa).max() <= 1e-9 * abs(Qa).max()
     assert np.max(np.abs(post.b - ba)) <= 1e-9 * np.max(np.abs(ba))
+
+
+def test_single_interior_node_reduces_to_scalar_conditioning():
+    # 3 x 3 Matern grid (Sec. 2.2, App. B): the eight boundary nodes are
+    # Dirichlet rows with precision 1/eps2 and no coupling, the centre row of
+    # B is kappa^2 h^2 + 4 (lumped mass h^2, the 5-point stiffness diagonal 4),
+    # so Q_cc = tau^2 (kappa^2 h^2 + 4)^2 / h^2.  One observation at the centre
+    # (barycentric weight 1) makes the posterior a scalar Gaussian update.
+    kappa, tau, eps2, y, sigma = 4.0, 0.3, 1e-8, 0.7, 0.1
+    pr = dict(W.c2_matern(n=3, m=1, seed=1, kappa=kappa)[0], tau=tau, eps2=eps2)
+    ob = {"coords": np.array([[0.5, 0.5]]), "y": np.array([y]), "sigma": np.array([sigma])}
+    post = infer.condition(pr, ob)
+    h = 0.5
+    q_c = tau ** 2 * (kappa ** 2 * h ** 2 + 4.0) ** 2 / h ** 2
+    Q = post.Q.toarray()
+    want = np.diag(np.full(9, 1.0 / eps2))
+    want[4, 4] = q_c
+    assert np.allclose(Q, want, rtol=1e-13, atol=0.0)
+    prec = q_c + 1.0 / sigma ** 2
+    mu = infer.posterior_mean(post)
+    var = infer.marginal_variance(post)
+    assert mu[4] == pytest.approx((y / sigma ** 2) / prec, rel=1e-13)
+    assert np.all(np.delete(mu, 4) == 0.0)
+    assert var[4] == pytest.approx(1.0 / prec, rel=1e-12)
+    assert np.allclose(np.delete(var, 4), eps2, rtol=1e-12)
